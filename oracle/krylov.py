@@ -1,0 +1,150 @@
+"""Krylov solvers (oracle, test infrastructure).
+
+* fgmres: right-preconditioned flexible GMRES(m) -- the textbook method of Saad & Schultz
+  (1986) with the flexible variant of Saad (1993), modified Gram-Schmidt Arnoldi and complex
+  Givens rotations for the Hessenberg least-squares problem.  With a fixed linear
+  preconditioner it is ordinary right-preconditioned GMRES.  The iterate is accepted only
+  when the true residual ||b - A x|| / ||b|| <= tol (the relative stopping rule of Sec. VI);
+  the Givens estimate only decides when to leave an Arnoldi cycle early.
+* bicgstab: the paper's preconditioned Bi-CGSTAB, Alg. 3, with the relative stopping rule.
+
+Iterations are counted as preconditioner applications (Arnoldi steps for GMRES).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, List
+
+import numpy as np
+
+
+@dataclass
+class SolveInfo:
+    converged: bool = False
+    iterations: int = 0
+    restarts: int = 0
+    rel_residual: float = float("inf")
+    history: List[float] = field(default_factory=list)   # Givens / true residual estimates
+
+
+def _dot(a: np.ndarray, b: np.ndarray) -> complex:
+    """<a, b> = a^H b."""
+    return complex(np.vdot(a.ravel(), b.ravel()))
+
+
+def _norm(a: np.ndarray) -> float:
+    return float(np.sqrt(np.vdot(a.ravel(), a.ravel()).real))
+
+
+def givens(a: complex, b: complex):
+    """Rotation [[c, s], [-conj(s), c]] (c real) mapping (a, b) to (r, 0)."""
+    if b == 0:
+        return 1.0, 0.0 + 0.0j
+    if a == 0:
+        return 0.0, 1.0 + 0.0j
+    rho = np.sqrt(abs(a) ** 2 + abs(b) ** 2)
+    c = abs(a) / rho
+    s = (a / abs(a)) * np.conj(b) / rho
+    return c, s
+
+
+def fgmres(apply_A: Callable, apply_M: Callable, b: np.ndarray, tol: float, restart: int,
+           maxit: int, x0: np.ndarray = None):
+    """Solve A x = b with right-preconditioned FGMRES(restart); returns (x, SolveInfo)."""
+    info = SolveInfo()
+    x = np.zeros_like(b) if x0 is None else x0.astype(np.complex128).copy()
+    bnorm = _norm(b)
+    if bnorm == 0.0:
+        info.converged, info.rel_residual = True, 0.0
+        return np.zeros_like(b), info
+    m = restart
+    while True:
+        r = b - apply_A(x)
+        beta = _norm(r)
+        info.rel_residual = beta / bnorm
+        info.history.append(info.rel_residual)
+        if info.rel_residual <= tol:
+            info.converged = True
+            return x, info
+        if info.iterations >= maxit:
+            return x, info
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta
+        j_end = 0
+        for j in range(m):
+            Z.append(apply_M(V[j]))                  # z_j = M^{-1} v_j
+            w = apply_A(Z[j])
+            for i in range(j + 1):                   # modified Gram-Schmidt
+                H[i, j] = _dot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = _norm(w)
+            info.iterations += 1
+            for i in range(j):                       # previous rotations on column j
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            cs[j], sn[j] = givens(H[j, j], H[j + 1, j])
+            H[j, j] = cs[j] * H[j, j] + sn[j] * H[j + 1, j]
+            H[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(sn[j]) * g[j]
+            g[j] = cs[j] * g[j]
+            j_end = j + 1
+            est = abs(g[j + 1]) / bnorm
+            info.history.append(est)
+            breakdown = H[j, j] == 0 or _norm(w) == 0.0
+            if est <= tol or info.iterations >= maxit or breakdown:
+                break
+            V.append(w / _norm(w))
+        # back substitution for the upper-triangular j_end x j_end system
+        y = np.zeros(j_end, dtype=np.complex128)
+        for i in range(j_end - 1, -1, -1):
+            y[i] = (g[i] - np.dot(H[i, i + 1:j_end], y[i + 1:j_end])) / H[i, i]
+        for i in range(j_end):
+            x = x + y[i] * Z[i]
+        info.restarts += 1
+
+
+def bicgstab(apply_A: Callable, apply_M: Callable, b: np.ndarray, tol: float, maxit: int,
+             x0: np.ndarray = None):
+    """Preconditioned Bi-CGSTAB of Alg. 3 (MG cycles at steps 9 and 14), relative stopping rule."""
+    info = SolveInfo()
+    x = np.zeros_like(b) if x0 is None else x0.astype(np.complex128).copy()
+    bnorm = _norm(b)
+    if bnorm == 0.0:
+        info.converged, info.rel_residual = True, 0.0
+        return np.zeros_like(b), info
+    r = b - apply_A(x)
+    r_hat = r.copy()
+    rho_prev, alpha, sigma = 1.0 + 0j, 1.0 + 0j, 1.0 + 0j
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    while info.iterations < maxit:
+        rho = _dot(r_hat, r)
+        beta = (rho / rho_prev) * (alpha / sigma)
+        p = r + beta * (p - sigma * v)
+        y = apply_M(p)
+        v = apply_A(y)
+        alpha = rho / _dot(r_hat, v)
+        hvec = x + alpha * y
+        s = r - alpha * v
+        z = apply_M(s)
+        t = apply_A(z)
+        sigma = _dot(t, s) / _dot(t, t)
+        x = hvec + sigma * z
+        r = s - sigma * t
+        rho_prev = rho
+        info.iterations += 2
+        info.rel_residual = _norm(r) / bnorm
+        info.history.append(info.rel_residual)
+        if info.rel_residual <= tol:
+            true_rel = _norm(b - apply_A(x)) / bnorm
+            info.rel_residual = true_rel
+            if true_rel <= tol:
+                info.converged = True
+                break
+    return x, info

@@ -1,0 +1,413 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: the local Fourier symbols
+of Sec. IV-B, exact discrete identities of the transfer operators (Sec. IV-C), a library LU
+solve, a manufactured solution, the textbook multigrid iteration-matrix identity, finite
+differences of the data term (Prop. 1), and the free-space Green's function.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import scipy.special as ssp
+
+import oracle as O
+import workloads as W
+
+
+def plane_wave_grid(ny, nx, t1, t2):
+    m = np.arange(nx)[None, :]
+    n = np.arange(ny)[:, None]
+    return np.exp(1j * (t1 * m + t2 * n))
+
+
+def interior_mask(p, margin=1):
+    """Points of Omega at least `margin` cells from the grid edge (alpha = 1 there)."""
+    mask = np.zeros((p.ny, p.nx), dtype=bool)
+    a = max(p.abl, margin)
+    mask[a:p.ny - a, a:p.nx - a] = True
+    return mask
+
+
+THETAS = [(0.0, 0.0), (0.3, -1.1), (math.pi / 2, 0.7), (2.5, 3.0), (-math.pi, 1.3)]
+
+
+@pytest.mark.parametrize("t1,t2", THETAS)
+def test_stencil_matches_lfa_symbol(t1, t2):
+    """Interior rows of A act on e^{j(t1 m + t2 n)} as a^h(theta) = (4 - 2cos t1 - 2cos t2 - k^2h^2)/h^2 (Sec. IV-B)."""
+    p = O.Problem(20, 14, 5, h=0.37, k=2 * math.pi / 7.0, beta=0.3)
+    c = O.fine_coefficient(p, np.zeros((p.ny_int, p.nx_int)))
+    D = O.operator_diagonal(c, O.absorbing_factor(p), p.h, p.k)
+    v = plane_wave_grid(p.ny, p.nx, t1, t2)
+    Av = O.apply_operator(D, v, p.h)
+    a_h = (4 - 2 * math.cos(t1) - 2 * math.cos(t2) - p.k ** 2 * p.h ** 2) / p.h ** 2
+    mask = interior_mask(p)
+    np.testing.assert_allclose(Av[mask], a_h * v[mask], rtol=0, atol=1e-12 * (8 / p.h ** 2))
+
+
+@pytest.mark.parametrize("t1,t2", THETAS)
+def test_shifted_operator_symbol(t1, t2):
+    """K_kappa = -lap - kappa k^2 has symbol (4 - 2cos t1 - 2cos t2)/h^2 - kappa k^2 on Omega (Sec. IV-B)."""
+    p = O.Problem(18, 18, 4, h=1.0, k=2 * math.pi / 10.0)
+    c = O.fine_coefficient(p, np.zeros((p.ny_int, p.nx_int)))
+    kappa = 1 + 0.5j
+    hier = O.build_hierarchy(p, c, 1, kappa)
+    v = plane_wave_grid(p.ny, p.nx, t1, t2)
+    Kv = O.apply_operator(hier[0].D, v, p.h)
+    sym = (4 - 2 * math.cos(t1) - 2 * math.cos(t2)) / p.h ** 2 - kappa * p.k ** 2
+    mask = interior_mask(p)
+    np.testing.assert_allclose(Kv[mask], sym * v[mask], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("t1,t2", THETAS)
+def test_jacobi_symbol(t1, t2):
+    """One damped Jacobi step on the error e^{j theta.x} multiplies it by
+    s^h(theta) = 1 - w + 2w (cos t1 + cos t2)/(4 - k^2 h^2) (Sec. IV-B, unshifted, constant k)."""
+    p = O.Problem(16, 16, 4, h=1.0, k=2 * math.pi / 10.0)
+    c = O.fine_coefficient(p, np.zeros((p.ny_int, p.nx_int)))
+    lv = O.build_hierarchy(p, c, 1, 1.0)[0]
+    w = 0.8
+    e = plane_wave_grid(p.ny, p.nx, t1, t2)
+    e1 = O.jacobi(lv, np.zeros_like(e), e, w)
+    s = 1 - w + 2 * w * (math.cos(t1) + math.cos(t2)) / (4 - (p.k * p.h) ** 2)
+    mask = interior_mask(p)
+    np.testing.assert_allclose(e1[mask], s * e[mask], rtol=0, atol=1e-13)
+
+
+def test_jacobi_divergence_bound():
+    """max_theta |s^h| = 1 - w + 4w/(4 - k^2h^2) > 1 (Sec. IV-B), reached by the smooth mode."""
+    p = O.Problem(16, 16, 4, h=1.0, k=2 * math.pi / 10.0)
+    c = O.fine_coefficient(p, np.zeros((p.ny_int, p.nx_int)))
+    lv = O.build_hierarchy(p, c, 1, 1.0)[0]
+    w = 0.8
+    mask = interior_mask(p)
+    best = 0.0
+    for t1 in np.linspace(-math.pi, math.pi, 13):
+        for t2 in np.linspace(-math.pi, math.pi, 13):
+            e = plane_wave_grid(p.ny, p.nx, t1, t2)
+            e1 = O.jacobi(lv, np.zeros_like(e), e, w)
+            best = max(best, float(np.max(np.abs(e1[mask] / e[mask]))))
+    bound = 1 - w + 4 * w / (4 - (p.k * p.h) ** 2)
+    assert bound > 1.0
+    assert abs(best - bound) < 1e-12
+
+
+@pytest.mark.parametrize("ny,nx", [(7, 9), (8, 8), (10, 13), (12, 6), (3, 3), (2, 5)])
+def test_restriction_prolongation_adjoint_exact(ny, nx):
+    """P is the adjoint of R with the 1/16 weights: 4 <R x, y> = <x, P y>, bit-exact on integers (Sec. IV-C)."""
+    rng = np.random.default_rng(ny * 100 + nx)
+    x = rng.integers(-50, 50, size=(ny, nx)).astype(np.float64)
+    y = rng.integers(-50, 50, size=(O.coarse_size(ny), O.coarse_size(nx))).astype(np.float64)
+    lhs = 4.0 * np.sum(O.restrict(x) * y)
+    rhs = np.sum(x * O.prolong(y, ny, nx))
+    assert lhs == rhs
+
+
+def _restrict_brute(r):
+    ny, nx = r.shape
+    nyc, nxc = O.coarse_size(ny), O.coarse_size(nx)
+    out = np.zeros((nyc, nxc), dtype=r.dtype)
+
+    def at(n, m):
+        return r[n, m] if (0 <= n < ny and 0 <= m < nx) else 0.0
+
+    for j in range(nyc):
+        for i in range(nxc):
+            m, n = 2 * i, 2 * j
+            out[j, i] = (4 * at(n, m)
+                         + 2 * (at(n, m - 1) + at(n, m + 1) + at(n - 1, m) + at(n + 1, m))
+                         + at(n - 1, m - 1) + at(n + 1, m - 1) + at(n - 1, m + 1) + at(n + 1, m + 1)) / 16.0
+    return out
+
+
+def _prolong_brute(ec, ny, nx):
+    nyc, nxc = ec.shape
+
+    def at(j, i):
+        return ec[j, i] if (0 <= j < nyc and 0 <= i < nxc) else 0.0
+
+    e = np.zeros((ny, nx), dtype=ec.dtype)
+    for n in range(ny):
+        for m in range(nx):
+            if m % 2 == 0 and n % 2 == 0:
+                e[n, m] = at(n // 2, m // 2)
+            elif m % 2 == 1 and n % 2 == 0:
+                e[n, m] = 0.5 * (at(n // 2, (m - 1) // 2) + at(n // 2, (m + 1) // 2))
+            elif m % 2 == 0 and n % 2 == 1:
+                e[n, m] = 0.5 * (at((n - 1) // 2, m // 2) + at((n + 1) // 2, m // 2))
+            else:
+                e[n, m] = 0.25 * (at((n - 1) // 2, (m - 1) // 2) + at((n + 1) // 2, (m - 1) // 2)
+                                  + at((n - 1) // 2, (m + 1) // 2) + at((n + 1) // 2, (m + 1) // 2))
+    return e
+
+
+@pytest.mark.parametrize("ny,nx", [(7, 9), (8, 8), (11, 6), (1, 4)])
+def test_transfer_operators_brute_force(ny, nx):
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+    np.testing.assert_allclose(O.restrict(r), _restrict_brute(r), rtol=0, atol=1e-15)
+    ec = rng.standard_normal((O.coarse_size(ny), O.coarse_size(nx)))
+    np.testing.assert_allclose(O.prolong(ec, ny, nx), _prolong_brute(ec, ny, nx), rtol=0, atol=1e-15)
+
+
+def test_restriction_keeps_constants_and_prolongation_keeps_bilinear():
+    ny, nx = 13, 16
+    rc = O.restrict(np.ones((ny, nx)))
+    assert np.all(rc[1:-1, 1:-1] == 1.0)
+    nyc, nxc = O.coarse_size(ny), O.coarse_size(nx)
+    I, J = np.meshgrid(np.arange(nxc), np.arange(nyc))
+    ec = 3.0 + 2.0 * (2 * I) - 5.0 * (2 * J) + 0.25 * (2 * I) * (2 * J)   # bilinear in fine coords
+    e = O.prolong(ec, ny, nx)
+    M, N = np.meshgrid(np.arange(nx), np.arange(ny))
+    ref = 3.0 + 2.0 * M - 5.0 * N + 0.25 * M * N
+    inside = (M <= 2 * (nxc - 1)) & (N <= 2 * (nyc - 1))
+    np.testing.assert_array_equal(e[inside], ref[inside])
+
+
+def test_prolongation_is_four_times_restriction_transpose():
+    ny, nx = 9, 8
+    nyc, nxc = O.coarse_size(ny), O.coarse_size(nx)
+    R = np.zeros((nyc * nxc, ny * nx))
+    for q in range(ny * nx):
+        u = np.zeros(ny * nx)
+        u[q] = 1.0
+        R[:, q] = O.restrict(u.reshape(ny, nx)).ravel()
+    P = np.zeros((ny * nx, nyc * nxc))
+    for q in range(nyc * nxc):
+        u = np.zeros(nyc * nxc)
+        u[q] = 1.0
+        P[:, q] = O.prolong(u.reshape(nyc, nxc), ny, nx).ravel()
+    np.testing.assert_array_equal(P, 4.0 * R.T)
+
+
+def _small(nint=16, abl=4, seed=5, beta=0.15, ppw=8.0):
+    p = O.Problem(nint, nint + 2, abl, h=1.0, k=2 * math.pi / ppw, beta=beta)
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0.0, 0.4, size=(p.ny_int, p.nx_int))
+    return p, f
+
+
+def test_operator_complex_symmetric_and_absorbing():
+    """A^T = A exactly, Im diag(A) <= 0 (absorbing reading), matrix-free apply = sparse matvec."""
+    p, f = _small()
+    c = O.fine_coefficient(p, f)
+    D = O.operator_diagonal(c, O.absorbing_factor(p), p.h, p.k)
+    A = O.assemble_operator(D, p.h)
+    assert (A - A.T).count_nonzero() == 0
+    assert np.all(D.imag <= 0.0)
+    assert np.all(D.imag[0, :] < 0.0) and np.all(D.imag[:, -1] < 0.0)
+    x = W.random_field((p.ny, p.nx), 1)
+    np.testing.assert_allclose(O.apply_operator(D, x, p.h).ravel(), A @ x.ravel(), rtol=1e-14, atol=1e-14)
+    y = W.random_field((p.ny, p.nx), 2)
+    lhs = np.vdot(y.ravel(), (A @ x.ravel()))
+    rhs_ = np.vdot((A.conj().T @ y.ravel()), x.ravel())
+    assert abs(lhs - rhs_) <= 1e-13 * abs(lhs)
+
+
+def test_layout_x_is_fast_axis():
+    """u_{m,n} is entry n*nx + m with x = m h (Sec. IV-A): a plane wave along +x varies along columns."""
+    p = O.Problem(6, 4, 2, h=0.5, k=1.3)
+    u = O.incident_field(p, 0.0)
+    assert u.shape == (p.ny, p.nx)
+    np.testing.assert_allclose(u[0, :], np.exp(1j * p.k * p.h * np.arange(p.nx)))
+    np.testing.assert_array_equal(u, np.repeat(u[:1, :], p.ny, axis=0))
+
+
+def test_layer_factor_geometry():
+    """alpha = 1 on Omega, 1 + j beta at the outer edge of the layer along an axis, corners further."""
+    p = O.Problem(10, 8, 3, h=1.0, k=1.0, beta=0.2)
+    a = O.absorbing_factor(p)
+    assert np.all(a[3:11, 3:13] == 1.0)
+    assert a[5, 0] == pytest.approx(1 + 0.2j, abs=1e-15) and a[0, 7] == pytest.approx(1 + 0.2j, abs=1e-15)
+    assert a[0, 0] == pytest.approx(1 + 0.4j, abs=1e-15)
+    assert a[5, 1] == pytest.approx(1 + 0.2j * 4 / 9, abs=1e-15)
+
+
+def test_level_counts():
+    sizes = {160: [160, 80, 40, 20], 576: [576, 288, 144, 72, 36, 18], 1120: [1120, 560, 280, 140, 70, 35]}
+    for n, ref in sizes.items():
+        out = [n]
+        while len(out) < len(ref):
+            out.append(O.coarse_size(out[-1]))
+        assert out == ref
+
+
+def test_gmres_matches_direct_solve():
+    """FGMRES to rel. residual 1e-13 agrees with a sparse LU solve (SuperLU) within 1e-10."""
+    p, f = _small()
+    s = O.MGHSolver(p, f, levels=3, nu1=1, nu2=1, restart=20, tol=1e-13)
+    b = O.rhs(p, f, 0.4)
+    u, info = s.solve(b)
+    assert info.converged
+    ref = O.direct_solve(p, s.D, b)
+    assert np.linalg.norm(u - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_bicgstab_matches_direct_solve():
+    p, f = _small(seed=9)
+    s = O.MGHSolver(p, f, levels=2, nu1=1, nu2=1, tol=1e-12, krylov="bicgstab", shift=1.0)
+    b = O.rhs(p, f, -0.7)
+    u, info = s.solve(b)
+    assert info.converged
+    ref = O.direct_solve(p, s.D, b)
+    assert np.linalg.norm(u - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_manufactured_solution():
+    p, f = _small(seed=11)
+    s = O.MGHSolver(p, f, levels=3, nu1=2, nu2=2, tol=1e-13)
+    X, Y = np.meshgrid(np.arange(p.nx), np.arange(p.ny))
+    u_star = np.sin(0.3 * X) * np.cos(0.2 * Y) * np.exp(-((X - 12) ** 2 + (Y - 13) ** 2) / 60.0) * (1 + 0.5j)
+    A = O.assemble_operator(s.D, p.h)
+    b = (A @ u_star.ravel()).reshape(u_star.shape)
+    u, info = s.solve(b)
+    assert info.converged
+    assert np.linalg.norm(u - u_star) <= 1e-10 * np.linalg.norm(u_star)
+
+
+def test_zero_contrast_gives_zero_field():
+    p = O.Problem(12, 12, 3, h=1.0, k=0.7)
+    f = np.zeros((12, 12))
+    s = O.MGHSolver(p, f, levels=2, nu1=1, nu2=1)
+    u, infos = s.forward([0.0, 1.0])
+    assert np.all(u == 0.0)
+    assert all(i.iterations == 0 and i.converged for i in infos)
+
+
+def _dense(op, n):
+    M = np.zeros((n, n), dtype=np.complex128)
+    for q in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[q] = 1.0
+        M[:, q] = op(e)
+    return M
+
+
+def _vcycle_matrix_closed_form(hier, l, nu1, nu2, omega):
+    """Textbook MG identity (zero initial guess): M_l^{-1} = (I - E_l) K_l^{-1},
+    E_l = S^nu2 (I - P M_{l+1}^{-1} R K_l) S^nu1, S = I - omega D^{-1} K_l; coarsest M^{-1} = K^{-1}."""
+    lv = hier[l]
+    n = lv.nx * lv.ny
+    K = O.assemble_operator(lv.D, lv.h).toarray()
+    Kinv = np.linalg.inv(K)
+    if l == len(hier) - 1:
+        return Kinv
+    c = hier[l + 1]
+    nc = c.nx * c.ny
+    R = _dense(lambda e: O.restrict(e.reshape(lv.ny, lv.nx)).ravel(), n)[:nc, :] if False else \
+        np.stack([O.restrict(np.eye(n)[q].reshape(lv.ny, lv.nx)).ravel() for q in range(n)], axis=1)
+    P = np.stack([O.prolong(np.eye(nc)[q].reshape(c.ny, c.nx), lv.ny, lv.nx).ravel() for q in range(nc)], axis=1)
+    S = np.eye(n) - omega * np.diag(1.0 / lv.D.ravel()) @ K
+    Mc = _vcycle_matrix_closed_form(hier, l + 1, nu1, nu2, omega)
+    E = np.linalg.matrix_power(S, nu2) @ (np.eye(n) - P @ Mc @ R @ K) @ np.linalg.matrix_power(S, nu1)
+    return (np.eye(n) - E) @ Kinv
+
+
+@pytest.mark.parametrize("nu", [0, 1, 2])
+def test_vcycle_equals_iteration_matrix_identity(nu):
+    p = O.Problem(8, 6, 2, h=1.0, k=2 * math.pi / 6.0, beta=0.3)
+    rng = np.random.default_rng(4)
+    f = rng.uniform(0, 0.3, size=(p.ny_int, p.nx_int))
+    c = O.fine_coefficient(p, f)
+    pre = O.Preconditioner(p, c, levels=3, nu1=nu, nu2=nu, omega=0.8, shift=1 + 0.5j)
+    n = p.nx * p.ny
+    M_proc = _dense(lambda e: pre(e.reshape(p.ny, p.nx)).ravel(), n)
+    M_ref = _vcycle_matrix_closed_form(pre.hier, 0, nu, nu, 0.8)
+    assert np.max(np.abs(M_proc - M_ref)) <= 1e-11 * np.max(np.abs(M_ref))
+
+
+def test_two_grid_without_smoothing_is_p_kinv_r():
+    """Alg. 1 with nu1 = nu2 = 0 and an exact coarse solve is P K_c^{-1} R."""
+    p = O.Problem(10, 10, 2, h=1.0, k=0.9)
+    c = O.fine_coefficient(p, np.full((10, 10), 0.2))
+    pre = O.Preconditioner(p, c, levels=2, nu1=0, nu2=0, omega=0.8, shift=1 + 0.5j)
+    b = W.random_field((p.ny, p.nx), 3)
+    cl = pre.hier[1]
+    Kc = O.assemble_operator(cl.D, cl.h).toarray()
+    ref = O.prolong(np.linalg.solve(Kc, O.restrict(b).ravel()).reshape(cl.ny, cl.nx), p.ny, p.nx)
+    np.testing.assert_allclose(pre(b), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_coarse_coefficient_ring_is_background():
+    p = O.Problem(20, 20, 4, h=1.0, k=0.8)
+    f = np.full((20, 20), 0.5)
+    c = O.fine_coefficient(p, f)
+    hier = O.build_hierarchy(p, c, 3, 1.0)
+    for lv in hier[1:]:
+        assert np.all(lv.c[0, :] == p.k ** 2) and np.all(lv.c[:, -1] == p.k ** 2)
+    # interior coarse points average the fine coefficient (full weighting of a constant)
+    assert hier[1].c[8, 8] == pytest.approx(p.k ** 2 * 1.5)
+
+
+def _fd_problem():
+    p = O.Problem(10, 10, 3, h=1.0, k=2 * math.pi / 6.0, beta=0.3)
+    rng = np.random.default_rng(21)
+    f = rng.uniform(0.0, 0.3, size=(10, 10))
+    thetas = [0.0, 0.6]
+    rec = np.array([(p.abl + n) * p.nx + p.abl + 8 for n in range(p.ny_int)], dtype=np.int64)
+    y = W.random_field((2, rec.size), 22) * 0.1
+    return p, f, thetas, rec, y
+
+
+def _loss_direct(p, f, thetas, rec, y):
+    c = O.fine_coefficient(p, f)
+    D = O.operator_diagonal(c, O.absorbing_factor(p), p.h, p.k)
+    us = np.stack([O.direct_solve(p, D, O.rhs(p, f, t)) for t in thetas])
+    return O.misfit(O.sample(us, rec), y)[1]
+
+
+def test_gradient_matches_finite_differences():
+    """dL/df_d from one adjoint solve per angle (Prop. 1) vs central differences of L."""
+    p, f, thetas, rec, y = _fd_problem()
+    s = O.MGHSolver(p, f, levels=2, nu1=1, nu2=1, tol=1e-13)
+    loss, g, _ = s.gradient(thetas, rec, y)
+    assert loss == pytest.approx(_loss_direct(p, f, thetas, rec, y), rel=1e-10)
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        d = rng.standard_normal(f.shape)
+        eps = 1e-5
+        fd = (_loss_direct(p, f + eps * d, thetas, rec, y) - _loss_direct(p, f - eps * d, thetas, rec, y)) / (2 * eps)
+        assert np.sum(g * d) == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+
+def test_prop1_linearisation():
+    """d u_sc = A^{-1} diag(u) k^2 df_d (Prop. 1) vs central differences of the solution."""
+    p, f, thetas, _, _ = _fd_problem()
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal(f.shape)
+    c = O.fine_coefficient(p, f)
+    D = O.operator_diagonal(c, O.absorbing_factor(p), p.h, p.k)
+    u_sc = O.direct_solve(p, D, O.rhs(p, f, 0.3))
+    u = u_sc + O.incident_field(p, 0.3)
+    jv = O.direct_solve(p, D, p.k ** 2 * O.embed(p, v) * u)
+    eps = 1e-6
+
+    def usc(ff):
+        cc = O.fine_coefficient(p, ff)
+        DD = O.operator_diagonal(cc, O.absorbing_factor(p), p.h, p.k)
+        return O.direct_solve(p, DD, O.rhs(p, ff, 0.3))
+
+    fd = (usc(f + eps * v) - usc(f - eps * v)) / (2 * eps)
+    assert np.linalg.norm(jv - fd) <= 1e-7 * np.linalg.norm(jv)
+
+
+def test_point_source_is_outgoing():
+    """With the damping sign reading, a point source radiates like (j/4) H0^(1)(k r), the outgoing
+    free-space Green's function of -lap - k^2 under the e^{-j w t} convention (Sec. II-A)."""
+    p = O.Problem(60, 60, 30, h=1.0, k=2 * math.pi / 12.0, beta=1.0)
+    c = O.fine_coefficient(p, np.zeros((60, 60)))
+    D = O.operator_diagonal(c, O.absorbing_factor(p), p.h, p.k)
+    b = np.zeros((p.ny, p.nx), dtype=np.complex128)
+    cy = cx = p.abl + 30
+    b[cy, cx] = 1.0 / p.h ** 2
+    u = O.direct_solve(p, D, b)
+    X, Y = np.meshgrid(np.arange(p.nx), np.arange(p.ny))
+    r = np.hypot(X - cx, Y - cy) * p.h
+    ring = (r > 8) & (r < 25)
+    g_out = 0.25j * ssp.hankel1(0, p.k * r[ring])
+    g_in = -0.25j * ssp.hankel2(0, p.k * r[ring])
+    err_out = np.linalg.norm(u[ring] - g_out) / np.linalg.norm(g_out)
+    err_in = np.linalg.norm(u[ring] - g_in) / np.linalg.norm(g_in)
+    assert err_out < 0.1
+    assert err_in > 1.0
