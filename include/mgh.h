@@ -1,0 +1,188 @@
+/*
+ * mgh.h -- C ABI of the GB300 multigrid-preconditioned Helmholtz solver.
+ *
+ * The library solves, for a batch of incident plane waves that share one contrast, the
+ * discretised scattered-field Helmholtz equation of the paper (Sec. II-A, Sec. IV-A)
+ *
+ *     A u_sc = b,   A = -lap_h - alpha * k^2 (1 + f_d),   b = k^2 f_d u_in,
+ *
+ * on the extended grid Omega_e = Omega + absorbing layer, with the five-point Laplacian and a
+ * first-order Sommerfeld closure on the outer edge.  The solver is right-preconditioned
+ * flexible GMRES(m) whose preconditioner is one multigrid cycle (Alg. 2) on the shifted
+ * Laplacian K_kappa = -lap_h - kappa * alpha * k^2 (1 + f_d) (Sec. IV-B/C): damped Jacobi
+ * smoothing (eq. dampedJ), full-weighting restriction, bilinear prolongation, re-discretised
+ * coarse levels and an exact coarsest solve.  The gradient of the quadratic data term of
+ * Sec. V in the contrast is obtained through one adjoint solve per illumination (Prop. 1).
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are interleaved (re, im) pairs of double (mgh_cdouble).
+ *   - Every field is stored row-major [B][ny][nx] on the extended grid (nx = nx_int + 2*abl,
+ *     ny = ny_int + 2*abl), x fastest: the unknown u_{m,n} is element n*nx + m (Sec. IV-A);
+ *     interior-only arrays are [ny_int][nx_int] (or [B][ny_int][nx_int]).
+ *   - Unless stated otherwise every data pointer is DEVICE memory owned by the caller; the
+ *     library never frees it and never keeps it after the call returns.
+ *   - Calls are asynchronous on the handle's CUDA stream (given at mgh_create), except that
+ *     an entry point that returns host values (mgh_solve_info, a loss) synchronises that
+ *     stream before returning.
+ *   - Errors are reported by the return code only; nothing is thrown across the ABI.  On
+ *     MGH_INVALID_ARG nothing was launched.  On MGH_CUDA_ERROR the handle should be destroyed.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef MGH_H
+#define MGH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } mgh_cdouble;
+
+typedef enum {
+  MGH_OK = 0,
+  MGH_INVALID_ARG = 1,      /* bad size, null pointer, batch above batch_max, call order */
+  MGH_NOT_CONVERGED = 2,    /* maxit reached for at least one right-hand side; best iterate kept */
+  MGH_CUDA_ERROR = 3,       /* a CUDA call failed; the message is in mgh_last_error() */
+  MGH_OUT_OF_MEMORY = 4,    /* device allocation failed at create */
+  MGH_TIMEOUT = 5,          /* reserved: a device-side wait gave up */
+  MGH_NOT_SUPPORTED = 6     /* option not built into this library */
+} mgh_status;
+
+typedef enum {
+  MGH_PREC_FP64 = 0,        /* everything in complex FP64 (the plain form) */
+  MGH_PREC_MIXED32 = 1      /* multigrid cycle in complex FP32, FP64 outer Krylov and residuals */
+} mgh_precision;
+
+/* Solver parameters.  Lengths are in the same unit as h (grid cells when h = 1). */
+typedef struct {
+  int nx_int, ny_int;       /* interior Omega size in grid points */
+  int abl;                  /* absorbing-layer width L in cells, per side (Sec. IV-A) */
+  double h;                 /* grid spacing */
+  double k;                 /* background wavenumber k = k0 * eta_b */
+  double beta;              /* layer strength: alpha = 1 + j*beta*(d/L)^2, d = distance to Omega in cells */
+  double shift_re, shift_im;/* kappa of K_kappa (Sec. IV-B); (1, 0) is the unshifted operator */
+  int levels;               /* multigrid levels including the finest, >= 1 (Alg. 2) */
+  int nu1, nu2;             /* pre- and post-relaxation sweeps, 0..4 (Alg. 2) */
+  double omega;             /* damped-Jacobi weight omega_S in (0, 1] (eq. dampedJ) */
+  int restart;              /* GMRES restart length m, 1..32 */
+  int maxit;                /* maximum Arnoldi steps per right-hand side */
+  double tol;               /* stop when ||b - A x||_2 <= tol * ||b||_2 (true FP64 residual) */
+  int precision;            /* mgh_precision */
+  int batch_max;            /* largest batch B any later call may use; sizes the workspace */
+} mgh_params;
+
+typedef struct {
+  int iterations;           /* Arnoldi steps (preconditioner applications) */
+  int restarts;             /* completed GMRES cycles */
+  int converged;            /* 1 if the true relative residual reached tol */
+  double rel_residual;      /* final true ||b - A x|| / ||b|| (0 when b = 0) */
+} mgh_solve_info;
+
+typedef struct mgh_handle mgh_handle;
+
+/* Fill *p with the defaults (disk workload of 128^2 + 16, FP64, GMRES(20), 4 levels, 2+2 sweeps). */
+void mgh_default_params(mgh_params* p);
+
+/* Bytes of device memory mgh_create would allocate for these parameters. */
+mgh_status mgh_workspace_bytes(const mgh_params* p, size_t* bytes);
+
+/* Create a solver: validates p, allocates the hierarchy and Krylov workspace for p->batch_max
+ * right-hand sides, and binds the handle to `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream).  The contrast starts at f_d = 0. */
+mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void mgh_destroy(mgh_handle* h);
+
+/* Set the contrast f_d = (n/n_b)^2 - 1 on Omega ([ny_int][nx_int] doubles, device) and rebuild
+ * the operator and the multigrid hierarchy on the device (Sec. IV-A, Sec. IV-C): the fine
+ * coefficient k^2 (1 + f_d) (k^2 in the layer), the coarse coefficients by full weighting with
+ * the outer ring reset to k^2, the diagonals of A and of every K_kappa level, and the inverse
+ * of the coarsest K_kappa (LU with partial pivoting). */
+mgh_status mgh_set_contrast(mgh_handle* h, const double* f_d);
+
+/* Incident plane waves u_in = exp(j k (x cos(theta) + y sin(theta))), x = m h, y = n h
+ * (Sec. II-A); theta: B angles in radians (device); u_in: [B][ny][nx] (device). */
+mgh_status mgh_incident_field(mgh_handle* h, const double* theta, int B, mgh_cdouble* u_in);
+
+/* Right-hand sides b = k^2 f_d u_in for B angles (Sec. II-A, eq. HelmScatterRightIncident):
+ * b: [B][ny][nx] (device), zero in the layer. */
+mgh_status mgh_rhs(mgh_handle* h, const double* theta, int B, mgh_cdouble* b);
+
+/* y = A x for B fields (Sec. IV-A five-point row with the Sommerfeld closure), FP64.
+ * x, y: [B][ny][nx] (device), must not overlap. */
+mgh_status mgh_apply(mgh_handle* h, const mgh_cdouble* x, int B, mgh_cdouble* y);
+
+/* z = K_MG^{-1} b: one multigrid cycle with zero initial guess on K_kappa (Alg. 2, V-cycle),
+ * computed in the handle's precision; b, z: [B][ny][nx] (device), FP64 in and out. */
+mgh_status mgh_precondition(mgh_handle* h, const mgh_cdouble* b, int B, mgh_cdouble* z);
+
+/* Exact solve with the coarsest-level operator (the last level of Alg. 2):
+ * b, x: [B][ny_c][nx_c] (device), FP64; nx_c, ny_c from mgh_level_shape(levels-1). */
+mgh_status mgh_coarse_solve(mgh_handle* h, const mgh_cdouble* b, int B, mgh_cdouble* x);
+
+/* Shape and spacing of multigrid level `level` (0 = finest).  Host outputs; any may be NULL. */
+mgh_status mgh_level_shape(const mgh_handle* h, int level, int* nx, int* ny, double* h_level);
+
+/* Copy level `level`'s real coefficient k0^2 eta^2 ([ny_l][nx_l] doubles) to `c` (device). */
+mgh_status mgh_level_coefficient(mgh_handle* h, int level, double* c);
+
+/* Solve A x = b for B right-hand sides with FGMRES(m) + one multigrid cycle per step.
+ * b: [B][ny][nx] (device); x: [B][ny][nx] (device), read as the initial guess and overwritten
+ * with the solution; info: B host records or NULL.  Every right-hand side stops on its own
+ * true FP64 residual.  A zero right-hand side gives x = 0 with 0 iterations.
+ * Returns MGH_NOT_CONVERGED if any right-hand side hit maxit (x holds its last iterate). */
+mgh_status mgh_solve(mgh_handle* h, const mgh_cdouble* b, int B, mgh_cdouble* x,
+                     mgh_solve_info* info);
+
+/* Forward model for B angles: u_sc = A^{-1} (k^2 f_d u_in(theta)) on Omega_e (Sec. II-A,
+ * Sec. IV-A).  theta: B angles (device); u_sc: [B][ny][nx] (device, overwritten; the initial
+ * guess is 0); info: B host records or NULL. */
+mgh_status mgh_forward(mgh_handle* h, const double* theta, int B, mgh_cdouble* u_sc,
+                       mgh_solve_info* info);
+
+/* Truncate B fields from Omega_e to Omega (Sec. IV-A): u [B][ny][nx] -> u_int [B][ny_int][nx_int]. */
+mgh_status mgh_crop(mgh_handle* h, const mgh_cdouble* u, int B, mgh_cdouble* u_int);
+
+/* Receiver sampling S u: out[q][r] = u[q][rec[r]] for M receivers given as flat extended-grid
+ * indices n*nx + m (device int64, each in [0, nx*ny)); out: [B][M] (device). */
+mgh_status mgh_sample(mgh_handle* h, const mgh_cdouble* u, int B, const int64_t* rec, int M,
+                      mgh_cdouble* out);
+
+/* Adjoint of mgh_sample: G = S^T vals, i.e. G[q] = 0 except G[q][rec[r]] = vals[q][r]
+ * (receivers must be distinct); vals: [B][M] (device), G: [B][ny][nx] (device, overwritten). */
+mgh_status mgh_scatter(mgh_handle* h, const mgh_cdouble* vals, int B, const int64_t* rec, int M,
+                       mgh_cdouble* G);
+
+/* Data-term residual and adjoint source for L = 1/2 sum_q ||S u_q - y_q||^2 (Sec. V):
+ * r = S u - y ([B][M], device), G = S^T r scattered on Omega_e ([B][ny][nx], device, zero
+ * elsewhere; receivers must be distinct), and the loss L written to *loss_host (host, may be
+ * NULL; when non-NULL the call synchronises the stream).  G is the gradient of L with respect
+ * to u in PyTorch's complex convention (2 dL/d conj(u)). */
+mgh_status mgh_misfit(mgh_handle* h, const mgh_cdouble* u, const mgh_cdouble* y, int B,
+                      const int64_t* rec, int M, mgh_cdouble* r, mgh_cdouble* G, double* loss_host);
+
+/* Gradient of a real loss L(u_sc) in the contrast f_d (Prop. 1): given G = 2 dL/d conj(u_sc)
+ * on Omega_e ([B][ny][nx], device) for the B angles theta (device) and their scattered fields
+ * u_sc ([B][ny][nx], device), solves A z_q = conj(G_q) with the same FGMRES engine (A is
+ * complex symmetric) and writes grad[n][m] = k^2 sum_q Re(z_q u_q) on Omega, u_q = u_in,q +
+ * u_sc,q ([ny_int][nx_int] doubles, device, overwritten).  info: B host records or NULL. */
+mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u_sc,
+                        const mgh_cdouble* G, int B, double* grad, mgh_solve_info* info);
+
+/* Kernel launches issued by this handle since creation (or since the last reset). */
+uint64_t mgh_launch_count(const mgh_handle* h, int reset);
+
+/* Static description of a status code. */
+const char* mgh_status_string(mgh_status s);
+
+/* Message of the last failing CUDA call in this process ("" if none). */
+const char* mgh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGH_H */

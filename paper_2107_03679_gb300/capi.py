@@ -1,0 +1,231 @@
+"""ctypes binding of the C ABI in include/mgh.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and forwards device pointers
+taken from torch tensors; all arithmetic happens in the CUDA library.  Importing this module
+loads libmgh.so and raises if it is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgh.so")
+
+MGH_OK, MGH_INVALID_ARG, MGH_NOT_CONVERGED, MGH_CUDA_ERROR, MGH_OUT_OF_MEMORY, MGH_TIMEOUT, MGH_NOT_SUPPORTED = range(7)
+MGH_PREC_FP64, MGH_PREC_MIXED32 = 0, 1
+PRECISIONS = {"fp64": MGH_PREC_FP64, "mixed32": MGH_PREC_MIXED32}
+
+
+class mgh_params(ctypes.Structure):
+    _fields_ = [
+        ("nx_int", ctypes.c_int), ("ny_int", ctypes.c_int), ("abl", ctypes.c_int),
+        ("h", ctypes.c_double), ("k", ctypes.c_double), ("beta", ctypes.c_double),
+        ("shift_re", ctypes.c_double), ("shift_im", ctypes.c_double),
+        ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+        ("omega", ctypes.c_double),
+        ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
+        ("precision", ctypes.c_int), ("batch_max", ctypes.c_int),
+    ]
+
+
+class mgh_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_residual", ctypes.c_double)]
+
+
+class MGHError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        msg = _lib.mgh_status_string(status).decode()
+        extra = _lib.mgh_last_error().decode()
+        super().__init__(f"{fn}: {msg}" + (f" [{extra}]" if extra and status == MGH_CUDA_ERROR else ""))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()'). There is no CPU fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int
+    pp = ctypes.POINTER(mgh_params)
+    info_p = ctypes.POINTER(mgh_solve_info)
+    sig = {
+        "mgh_default_params": (None, [pp]),
+        "mgh_workspace_bytes": (S, [pp, ctypes.POINTER(ctypes.c_size_t)]),
+        "mgh_create": (S, [pp, P, ctypes.POINTER(P)]),
+        "mgh_destroy": (None, [P]),
+        "mgh_set_contrast": (S, [P, P]),
+        "mgh_incident_field": (S, [P, P, I, P]),
+        "mgh_rhs": (S, [P, P, I, P]),
+        "mgh_apply": (S, [P, P, I, P]),
+        "mgh_precondition": (S, [P, P, I, P]),
+        "mgh_coarse_solve": (S, [P, P, I, P]),
+        "mgh_level_shape": (S, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "mgh_level_coefficient": (S, [P, I, P]),
+        "mgh_solve": (S, [P, P, I, P, info_p]),
+        "mgh_forward": (S, [P, P, I, P, info_p]),
+        "mgh_crop": (S, [P, P, I, P]),
+        "mgh_sample": (S, [P, P, I, P, I, P]),
+        "mgh_scatter": (S, [P, P, I, P, I, P]),
+        "mgh_misfit": (S, [P, P, P, I, P, I, P, P, ctypes.POINTER(D)]),
+        "mgh_gradient": (S, [P, P, P, P, I, P, info_p]),
+        "mgh_launch_count": (ctypes.c_uint64, [P, I]),
+        "mgh_status_string": (ctypes.c_char_p, [S]),
+        "mgh_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+# names of the C entry points declared in include/mgh.h
+EXPORTED = [
+    "mgh_default_params", "mgh_workspace_bytes", "mgh_create", "mgh_destroy", "mgh_set_contrast",
+    "mgh_incident_field", "mgh_rhs", "mgh_apply", "mgh_precondition", "mgh_coarse_solve",
+    "mgh_level_shape", "mgh_level_coefficient", "mgh_solve", "mgh_forward", "mgh_crop", "mgh_sample",
+    "mgh_scatter", "mgh_misfit", "mgh_gradient", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
+]
+
+
+def _check(fn: str, status: int, allow=(MGH_OK,)):
+    if status not in allow:
+        raise MGHError(fn, status)
+    return status
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (checked dtype and size)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (device memory)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, {numel} needed")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mgh_default_params() -> mgh_params:
+    p = mgh_params()
+    _lib.mgh_default_params(ctypes.byref(p))
+    return p
+
+
+def mgh_workspace_bytes(p: mgh_params) -> int:
+    n = ctypes.c_size_t(0)
+    _check("mgh_workspace_bytes", _lib.mgh_workspace_bytes(ctypes.byref(p), ctypes.byref(n)))
+    return int(n.value)
+
+
+def mgh_create(p: mgh_params, stream) -> ctypes.c_void_p:
+    h = ctypes.c_void_p(0)
+    _check("mgh_create", _lib.mgh_create(ctypes.byref(p), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def mgh_destroy(h) -> None:
+    _lib.mgh_destroy(h)
+
+
+def _infos(B):
+    return (mgh_solve_info * B)()
+
+
+def _infos_to_list(arr):
+    return [dict(iterations=a.iterations, restarts=a.restarts, converged=bool(a.converged),
+                 rel_residual=a.rel_residual) for a in arr]
+
+
+def mgh_set_contrast(h, f_d):
+    _check("mgh_set_contrast", _lib.mgh_set_contrast(h, f_d))
+
+
+def mgh_incident_field(h, theta, B, u_in):
+    _check("mgh_incident_field", _lib.mgh_incident_field(h, theta, B, u_in))
+
+
+def mgh_rhs(h, theta, B, b):
+    _check("mgh_rhs", _lib.mgh_rhs(h, theta, B, b))
+
+
+def mgh_apply(h, x, B, y):
+    _check("mgh_apply", _lib.mgh_apply(h, x, B, y))
+
+
+def mgh_precondition(h, b, B, z):
+    _check("mgh_precondition", _lib.mgh_precondition(h, b, B, z))
+
+
+def mgh_coarse_solve(h, b, B, x):
+    _check("mgh_coarse_solve", _lib.mgh_coarse_solve(h, b, B, x))
+
+
+def mgh_level_shape(h, level):
+    nx, ny, hl = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+    _check("mgh_level_shape", _lib.mgh_level_shape(h, level, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(hl)))
+    return nx.value, ny.value, hl.value
+
+
+def mgh_level_coefficient(h, level, c):
+    _check("mgh_level_coefficient", _lib.mgh_level_coefficient(h, level, c))
+
+
+def mgh_solve(h, b, B, x, allow_not_converged=True):
+    info = _infos(B)
+    st = _lib.mgh_solve(h, b, B, x, info)
+    _check("mgh_solve", st, (MGH_OK, MGH_NOT_CONVERGED) if allow_not_converged else (MGH_OK,))
+    return _infos_to_list(info)
+
+
+def mgh_forward(h, theta, B, u_sc, allow_not_converged=True):
+    info = _infos(B)
+    st = _lib.mgh_forward(h, theta, B, u_sc, info)
+    _check("mgh_forward", st, (MGH_OK, MGH_NOT_CONVERGED) if allow_not_converged else (MGH_OK,))
+    return _infos_to_list(info)
+
+
+def mgh_crop(h, u, B, u_int):
+    _check("mgh_crop", _lib.mgh_crop(h, u, B, u_int))
+
+
+def mgh_sample(h, u, B, rec, M, out):
+    _check("mgh_sample", _lib.mgh_sample(h, u, B, rec, M, out))
+
+
+def mgh_scatter(h, vals, B, rec, M, G):
+    _check("mgh_scatter", _lib.mgh_scatter(h, vals, B, rec, M, G))
+
+
+def mgh_misfit(h, u, y, B, rec, M, r, G, want_loss=True):
+    loss = ctypes.c_double(0.0)
+    _check("mgh_misfit", _lib.mgh_misfit(h, u, y, B, rec, M, r, G, ctypes.byref(loss) if want_loss else None))
+    return loss.value
+
+
+def mgh_gradient(h, theta, u_sc, G, B, grad, allow_not_converged=True):
+    info = _infos(B)
+    st = _lib.mgh_gradient(h, theta, u_sc, G, B, grad, info)
+    _check("mgh_gradient", st, (MGH_OK, MGH_NOT_CONVERGED) if allow_not_converged else (MGH_OK,))
+    return _infos_to_list(info)
+
+
+def mgh_launch_count(h, reset=False) -> int:
+    return int(_lib.mgh_launch_count(h, 1 if reset else 0))
+
+
+def mgh_status_string(s: int) -> str:
+    return _lib.mgh_status_string(s).decode()
+
+
+def mgh_last_error() -> str:
+    return _lib.mgh_last_error().decode()

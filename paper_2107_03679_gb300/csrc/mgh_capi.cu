@@ -1,0 +1,325 @@
+// C ABI of the solver (declared in include/mgh.h): parameter validation, device memory of the
+// handle, and the entry points that sequence the kernels of the other translation units.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include <cmath>
+
+#include "mgh_engine.h"
+
+// The opaque handle of the C ABI is the engine's Handle.
+struct mgh_handle : public mgh::Handle {};
+
+namespace mgh {
+
+namespace {
+thread_local char g_last_error[512] = "";
+
+int coarse_dim(int n) { return (n - 1) / 2 + 1; }
+
+// Validate parameters; fills the level shapes when `lev` is non-null.
+mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullptr) {
+  if (!p) return MGH_INVALID_ARG;
+  if (p->nx_int < 1 || p->ny_int < 1 || p->abl < 0) return MGH_INVALID_ARG;
+  if (!(p->h > 0.0) || !(p->k > 0.0) || !(p->beta >= 0.0)) return MGH_INVALID_ARG;
+  if (p->levels < 2 || p->levels > kMaxLevels) return MGH_INVALID_ARG;
+  if (p->nu1 < 0 || p->nu1 > kMaxSweeps || p->nu2 < 0 || p->nu2 > kMaxSweeps) return MGH_INVALID_ARG;
+  if (!(p->omega > 0.0 && p->omega <= 1.0)) return MGH_INVALID_ARG;
+  if (p->restart < 1 || p->restart > kMaxRestart || p->maxit < 1 || !(p->tol > 0.0)) return MGH_INVALID_ARG;
+  if (p->precision != MGH_PREC_FP64 && p->precision != MGH_PREC_MIXED32) return MGH_INVALID_ARG;
+  if (p->batch_max < 1 || p->batch_max > 65535) return MGH_INVALID_ARG;
+  if (!std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) return MGH_INVALID_ARG;
+  const long long nx = p->nx_int + 2LL * p->abl, ny = p->ny_int + 2LL * p->abl;
+  if (nx > (1 << 20) || ny > (1 << 20) || nx * ny > (1LL << 31)) return MGH_INVALID_ARG;
+  int cx = (int)nx, cy = (int)ny;
+  for (int l = 0; l < p->levels; ++l) {
+    if (nx_l) { nx_l[l] = cx; ny_l[l] = cy; }
+    if (l + 1 < p->levels) { cx = coarse_dim(cx); cy = coarse_dim(cy); }
+  }
+  if ((long long)cx * cy > kMaxCoarse) return MGH_INVALID_ARG;
+  return MGH_OK;
+}
+
+size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Bytes of every device allocation of a handle, in allocation order.
+size_t workspace_bytes(const mgh_params& p) {
+  int nxl[kMaxLevels], nyl[kMaxLevels];
+  validate(&p, nxl, nyl);
+  const size_t B = p.batch_max, m = p.restart;
+  const size_t cs = p.precision == MGH_PREC_FP64 ? 16 : 8;
+  const size_t N = (size_t)nxl[0] * nyl[0];
+  size_t t = 0;
+  for (int l = 0; l < p.levels; ++l) {
+    const size_t n = (size_t)nxl[l] * nyl[l];
+    t += pad256(8 * n) + 2 * pad256(cs * n);
+    if (l >= 1) t += 2 * pad256(cs * n * B);             // b, vfin
+    if (l + 1 < p.levels) t += pad256(cs * n * B);       // vpre
+  }
+  const size_t nc = (size_t)nxl[p.levels - 1] * nyl[p.levels - 1];
+  const size_t W = 3 * (size_t)nxl[p.levels - 1] + 1;
+  t += pad256(8 * (size_t)p.nx_int * p.ny_int) + pad256(16 * N);
+  t += pad256(16 * nc * W) + pad256(4 * nc) + pad256(16 * nc * nc) + pad256(8 * nc * nc) + pad256(4);
+  t += pad256(16 * B * (m + 1) * N) + pad256(cs * B * m * N) + 3 * pad256(16 * B * N);
+  t += pad256(16 * B * m * (m + 1)) + 2 * pad256(16 * B * (m + 1)) + pad256(8 * B * m) + pad256(16 * B * m);
+  t += pad256(16 * B * (m + 1)) + pad256(16 * B * m) + pad256(8 * B * (m + 1)) + pad256(sizeof(RhsState) * B);
+  t += pad256(16 * (1216 + B) * (m + 2)) + pad256(8 * (B + 1));
+  return t;
+}
+
+template <typename T>
+mgh_status dev_alloc(T** p, size_t bytes) {
+  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 1));
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc", e, __FILE__, __LINE__);
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? MGH_OUT_OF_MEMORY : MGH_CUDA_ERROR;
+  }
+  return MGH_OK;
+}
+
+void free_handle(mgh_handle* h) {
+  if (!h) return;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    Level& lv = h->lev[l];
+    cudaFree(lv.c); cudaFree(lv.D); cudaFree(lv.wDinv); cudaFree(lv.b); cudaFree(lv.vpre); cudaFree(lv.vfin);
+  }
+  cudaFree(h->f_d); cudaFree(h->DA); cudaFree(h->band); cudaFree(h->piv); cudaFree(h->kinv64);
+  cudaFree(h->kinv32); cudaFree(h->lu_info); cudaFree(h->V); cudaFree(h->Z); cudaFree(h->W);
+  cudaFree(h->T1); cudaFree(h->T2); cudaFree(h->H); cudaFree(h->hcol); cudaFree(h->h2col); cudaFree(h->cs);
+  cudaFree(h->sn); cudaFree(h->g); cudaFree(h->y); cudaFree(h->vscale); cudaFree(h->st); cudaFree(h->partial);
+  cudaFree(h->dscratch);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  delete h;
+}
+
+bool batch_ok(const Handle* h, int B) { return h && B >= 1 && B <= h->Bmax; }
+
+}  // namespace
+
+void set_error(const char* what, cudaError_t e, const char* file, int line) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file,
+                line);
+}
+
+}  // namespace mgh
+
+using namespace mgh;
+
+extern "C" {
+
+void mgh_default_params(mgh_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nx_int = 128; p->ny_int = 128; p->abl = 16;
+  p->h = 1.0; p->k = 2.0 * 3.14159265358979323846 / 10.0; p->beta = 0.15;
+  p->shift_re = 1.0; p->shift_im = 0.5;
+  p->levels = 4; p->nu1 = 2; p->nu2 = 2; p->omega = 0.8;
+  p->restart = 20; p->maxit = 5000; p->tol = 1e-8;
+  p->precision = MGH_PREC_FP64; p->batch_max = 1;
+}
+
+mgh_status mgh_workspace_bytes(const mgh_params* p, size_t* bytes) {
+  if (!bytes) return MGH_INVALID_ARG;
+  MGH_TRY(validate(p));
+  *bytes = workspace_bytes(*p);
+  return MGH_OK;
+}
+
+mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) {
+  if (!out) return MGH_INVALID_ARG;
+  *out = nullptr;
+  int nxl[kMaxLevels], nyl[kMaxLevels];
+  MGH_TRY(validate(p, nxl, nyl));
+  mgh_handle* h = new (std::nothrow) mgh_handle();
+  if (!h) return MGH_OUT_OF_MEMORY;
+  h->p = *p;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->nx = nxl[0]; h->ny = nyl[0]; h->N = (size_t)h->nx * h->ny;
+  h->L = p->levels;
+  h->fp64 = p->precision == MGH_PREC_FP64;
+  h->csize = h->fp64 ? 16 : 8;
+  h->m = p->restart;
+  h->Bmax = p->batch_max;
+  const size_t B = h->Bmax, m = h->m, N = h->N, cs = h->csize;
+  mgh_status s = MGH_OK;
+#define ALLOC(ptr, bytes) do { s = dev_alloc(&(ptr), (bytes)); if (s != MGH_OK) { free_handle(h); return s; } } while (0)
+  double hl = p->h;
+  int sc = 1;
+  for (int l = 0; l < h->L; ++l) {
+    Level& lv = h->lev[l];
+    lv.nx = nxl[l]; lv.ny = nyl[l]; lv.h = hl; lv.scale = sc;
+    const size_t n = lv.n();
+    ALLOC(lv.c, 8 * n);
+    ALLOC(lv.D, cs * n);
+    ALLOC(lv.wDinv, cs * n);
+    if (l >= 1) { ALLOC(lv.b, cs * n * B); ALLOC(lv.vfin, cs * n * B); }
+    if (l + 1 < h->L) ALLOC(lv.vpre, cs * n * B);
+    hl *= 2.0; sc *= 2;
+  }
+  const Level& cl = h->lev[h->L - 1];
+  h->nc = (int)cl.n();
+  const size_t nc = h->nc, W = 3 * (size_t)cl.nx + 1;
+  ALLOC(h->f_d, 8 * (size_t)p->nx_int * p->ny_int);
+  ALLOC(h->DA, 16 * N);
+  ALLOC(h->band, 16 * nc * W);
+  ALLOC(h->piv, 4 * nc);
+  ALLOC(h->kinv64, 16 * nc * nc);
+  if (!h->fp64) ALLOC(h->kinv32, 8 * nc * nc);
+  ALLOC(h->lu_info, 4);
+  ALLOC(h->V, 16 * B * (m + 1) * N);
+  ALLOC(h->Z, cs * B * m * N);
+  ALLOC(h->W, 16 * B * N);
+  ALLOC(h->T1, 16 * B * N);
+  ALLOC(h->T2, 16 * B * N);
+  ALLOC(h->H, 16 * B * m * (m + 1));
+  ALLOC(h->hcol, 16 * B * (m + 1));
+  ALLOC(h->h2col, 16 * B * (m + 1));
+  ALLOC(h->cs, 8 * B * m);
+  ALLOC(h->sn, 16 * B * m);
+  ALLOC(h->g, 16 * B * (m + 1));
+  ALLOC(h->y, 16 * B * m);
+  ALLOC(h->vscale, 8 * B * (m + 1));
+  ALLOC(h->st, sizeof(RhsState) * B);
+  ALLOC(h->partial, 16 * (1216 + B) * (m + 2));
+  ALLOC(h->dscratch, 8 * (B + 1));
+#undef ALLOC
+  if (cudaMallocHost((void**)&h->st_host, sizeof(RhsState) * B) != cudaSuccess) {
+    h->st_host = nullptr;
+    free_handle(h);
+    return MGH_OUT_OF_MEMORY;
+  }
+  // start from f_d = 0 so that every later call finds a complete operator
+  cudaError_t e = cudaMemsetAsync(h->T1, 0, 8 * (size_t)p->nx_int * p->ny_int, h->stream);
+  if (e != cudaSuccess) { set_error("cudaMemsetAsync", e, __FILE__, __LINE__); free_handle(h); return MGH_CUDA_ERROR; }
+  s = setup_contrast(*h, (const double*)h->T1);
+  if (s != MGH_OK) { free_handle(h); return s; }
+  *out = h;
+  return MGH_OK;
+}
+
+void mgh_destroy(mgh_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_handle(h);
+}
+
+mgh_status mgh_set_contrast(mgh_handle* h, const double* f_d) {
+  if (!h || !f_d) return MGH_INVALID_ARG;
+  return setup_contrast(*h, f_d);
+}
+
+mgh_status mgh_incident_field(mgh_handle* h, const double* theta, int B, mgh_cdouble* u_in) {
+  if (!batch_ok(h, B) || !theta || !u_in) return MGH_INVALID_ARG;
+  return launch_incident(*h, theta, B, (cd*)u_in, false);
+}
+
+mgh_status mgh_rhs(mgh_handle* h, const double* theta, int B, mgh_cdouble* b) {
+  if (!batch_ok(h, B) || !theta || !b) return MGH_INVALID_ARG;
+  return launch_incident(*h, theta, B, (cd*)b, true);
+}
+
+mgh_status mgh_apply(mgh_handle* h, const mgh_cdouble* x, int B, mgh_cdouble* y) {
+  if (!batch_ok(h, B) || !x || !y || x == y) return MGH_INVALID_ARG;
+  return launch_apply_A(*h, (const cd*)x, B, (cd*)y);
+}
+
+mgh_status mgh_precondition(mgh_handle* h, const mgh_cdouble* b, int B, mgh_cdouble* z) {
+  if (!batch_ok(h, B) || !b || !z || (const void*)b == (const void*)z) return MGH_INVALID_ARG;
+  return vcycle(*h, (const cd*)b, h->N, nullptr, 0, z, h->N, true, B, nullptr);
+}
+
+mgh_status mgh_coarse_solve(mgh_handle* h, const mgh_cdouble* b, int B, mgh_cdouble* x) {
+  if (!batch_ok(h, B) || !b || !x || (const void*)b == (const void*)x) return MGH_INVALID_ARG;
+  return launch_coarse_apply(*h, b, (size_t)h->nc, x, (size_t)h->nc, B, nullptr, true);
+}
+
+mgh_status mgh_level_shape(const mgh_handle* h, int level, int* nx, int* ny, double* h_level) {
+  if (!h || level < 0 || level >= h->L) return MGH_INVALID_ARG;
+  if (nx) *nx = h->lev[level].nx;
+  if (ny) *ny = h->lev[level].ny;
+  if (h_level) *h_level = h->lev[level].h;
+  return MGH_OK;
+}
+
+mgh_status mgh_level_coefficient(mgh_handle* h, int level, double* c) {
+  if (!h || !c || level < 0 || level >= h->L) return MGH_INVALID_ARG;
+  MGH_CUDA(cudaMemcpyAsync(c, h->lev[level].c, 8 * h->lev[level].n(), cudaMemcpyDeviceToDevice, h->stream));
+  return MGH_OK;
+}
+
+mgh_status mgh_solve(mgh_handle* h, const mgh_cdouble* b, int B, mgh_cdouble* x, mgh_solve_info* info) {
+  if (!batch_ok(h, B) || !b || !x || (const void*)b == (const void*)x) return MGH_INVALID_ARG;
+  return fgmres_solve(*h, (const cd*)b, B, (cd*)x, info);
+}
+
+mgh_status mgh_forward(mgh_handle* h, const double* theta, int B, mgh_cdouble* u_sc, mgh_solve_info* info) {
+  if (!batch_ok(h, B) || !theta || !u_sc) return MGH_INVALID_ARG;
+  MGH_TRY(launch_incident(*h, theta, B, h->T1, true));
+  MGH_CUDA(cudaMemsetAsync(u_sc, 0, 16 * h->N * B, h->stream));
+  return fgmres_solve(*h, h->T1, B, (cd*)u_sc, info);
+}
+
+mgh_status mgh_crop(mgh_handle* h, const mgh_cdouble* u, int B, mgh_cdouble* u_int) {
+  if (!batch_ok(h, B) || !u || !u_int) return MGH_INVALID_ARG;
+  return launch_crop(*h, (const cd*)u, B, (cd*)u_int);
+}
+
+mgh_status mgh_sample(mgh_handle* h, const mgh_cdouble* u, int B, const int64_t* rec, int M, mgh_cdouble* out) {
+  if (!batch_ok(h, B) || !u || !rec || !out || M < 1) return MGH_INVALID_ARG;
+  return launch_sample(*h, (const cd*)u, B, rec, M, (cd*)out);
+}
+
+mgh_status mgh_scatter(mgh_handle* h, const mgh_cdouble* vals, int B, const int64_t* rec, int M, mgh_cdouble* G) {
+  if (!batch_ok(h, B) || !vals || !rec || !G || M < 1) return MGH_INVALID_ARG;
+  return launch_scatter(*h, (const cd*)vals, B, rec, M, (cd*)G);
+}
+
+mgh_status mgh_misfit(mgh_handle* h, const mgh_cdouble* u, const mgh_cdouble* y, int B, const int64_t* rec, int M,
+                      mgh_cdouble* r, mgh_cdouble* G, double* loss_host) {
+  if (!batch_ok(h, B) || !u || !y || !rec || M < 1) return MGH_INVALID_ARG;
+  MGH_TRY(launch_misfit(*h, (const cd*)u, (const cd*)y, B, rec, M, (cd*)r, (cd*)G, h->dscratch + B));
+  if (loss_host) {
+    MGH_CUDA(cudaMemcpyAsync(loss_host, h->dscratch + B, 8, cudaMemcpyDeviceToHost, h->stream));
+    MGH_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return MGH_OK;
+}
+
+mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u_sc, const mgh_cdouble* G, int B,
+                        double* grad, mgh_solve_info* info) {
+  if (!batch_ok(h, B) || !theta || !u_sc || !G || !grad) return MGH_INVALID_ARG;
+  MGH_TRY(launch_conj(*h, (const cd*)G, B, h->T1));
+  MGH_CUDA(cudaMemsetAsync(h->T2, 0, 16 * h->N * B, h->stream));
+  const mgh_status s = fgmres_solve(*h, h->T1, B, h->T2, info);
+  if (s != MGH_OK && s != MGH_NOT_CONVERGED) return s;
+  MGH_TRY(launch_gradient(*h, theta, (const cd*)u_sc, h->T2, B, grad));
+  return s;
+}
+
+uint64_t mgh_launch_count(const mgh_handle* h, int reset) {
+  if (!h) return 0;
+  const uint64_t n = h->launches;
+  if (reset) const_cast<mgh_handle*>(h)->launches = 0;
+  return n;
+}
+
+const char* mgh_status_string(mgh_status s) {
+  switch (s) {
+    case MGH_OK: return "ok";
+    case MGH_INVALID_ARG: return "invalid argument";
+    case MGH_NOT_CONVERGED: return "not converged";
+    case MGH_CUDA_ERROR: return "CUDA error";
+    case MGH_OUT_OF_MEMORY: return "out of device memory";
+    case MGH_TIMEOUT: return "device wait timed out";
+    case MGH_NOT_SUPPORTED: return "not supported";
+  }
+  return "unknown status";
+}
+
+const char* mgh_last_error(void) { return mgh::g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal host-side interface of the solver engine (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "mgh.h"
+#include "mgh_common.cuh"
+
+namespace mgh {
+
+constexpr int kMaxLevels = 12;
+constexpr int kMaxRestart = 32;
+constexpr int kMaxSweeps = 4;
+constexpr int kMaxCoarse = 4096;   // unknowns on the coarsest level (dense inverse kept on device)
+
+// Device arrays of one multigrid level.  Coefficient and diagonals are shared by every
+// right-hand side; the field buffers hold batch_max right-hand sides.
+struct Level {
+  int nx = 0, ny = 0, scale = 1;
+  double h = 1.0;
+  double* c = nullptr;       // real k0^2 eta^2 on this level (FP64 master copy)
+  void* D = nullptr;         // complex diagonal of K_kappa, in the cycle precision
+  void* wDinv = nullptr;     // omega / D, in the cycle precision
+  void* b = nullptr;         // right-hand side of this level (levels >= 1)
+  void* vpre = nullptr;      // iterate after pre-smoothing
+  void* vfin = nullptr;      // iterate after post-smoothing (levels >= 1)
+  size_t n() const { return (size_t)nx * ny; }
+};
+
+struct Handle {
+  mgh_params p{};
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0;
+  size_t N = 0;              // points of the extended grid
+  int L = 0;                 // levels
+  bool fp64 = true;          // cycle precision: double (true) or float (false)
+  size_t csize = 16;         // bytes per complex of the cycle precision
+  Level lev[kMaxLevels];
+  bool contrast_set = false;
+
+  // fine operator A (FP64)
+  double* f_d = nullptr;     // [ny_int][nx_int] contrast (device copy)
+  cd* DA = nullptr;          // diagonal of A
+
+  // coarsest level: dense inverse, stored transposed (column c of K^{-1} contiguous)
+  int nc = 0;
+  cd* band = nullptr;        // banded LU workspace (FP64)
+  int* piv = nullptr;
+  cd* kinv64 = nullptr;      // [nc][nc] FP64 transposed inverse
+  cf* kinv32 = nullptr;      // FP32 copy (mixed precision)
+  int* lu_info = nullptr;    // device status of the factorisation
+
+  // Krylov workspace
+  int m = 20;
+  int Bmax = 1;
+  cd* V = nullptr;           // [Bmax][m+1][N] Arnoldi basis (unnormalised; see vscale)
+  void* Z = nullptr;         // [Bmax][m][N] preconditioned vectors, cycle precision
+  cd* W = nullptr;           // [Bmax][N] A z_j
+  cd* T1 = nullptr;          // [Bmax][N] scratch field (right-hand sides built by forward/gradient)
+  cd* T2 = nullptr;          // [Bmax][N] scratch field
+  cd* H = nullptr;           // [Bmax][m+1][m] Hessenberg matrix (column-major per RHS: H[j*(m+1)+i])
+  cd* hcol = nullptr;        // [Bmax][m+1] dots of the current step
+  cd* h2col = nullptr;       // [Bmax][m+1] re-orthogonalisation dots
+  double* cs = nullptr;      // [Bmax][m] Givens cosines
+  cd* sn = nullptr;          // [Bmax][m] Givens sines
+  cd* g = nullptr;           // [Bmax][m+1] rotated right-hand side
+  cd* y = nullptr;           // [Bmax][m] least-squares solution
+  double* vscale = nullptr;  // [Bmax][m+1] multiplier that normalises V[b][i]
+  RhsState* st = nullptr;    // [Bmax]
+  RhsState* st_host = nullptr;  // pinned host mirror
+  cd* partial = nullptr;     // [Bmax][nblk][m+2] block partial sums
+  int nblk = 1;              // reduction blocks per right-hand side
+  double* dscratch = nullptr;   // small FP64 scratch (loss)
+
+  uint64_t launches = 0;
+};
+
+// mgh_setup.cu
+mgh_status setup_contrast(Handle& h, const double* f_d);
+mgh_status launch_incident(Handle& h, const double* theta, int B, cd* out, bool times_contrast);
+mgh_status launch_apply_A(Handle& h, const cd* x, int B, cd* y);
+mgh_status launch_crop(Handle& h, const cd* u, int B, cd* out);
+mgh_status launch_sample(Handle& h, const cd* u, int B, const int64_t* rec, int M, cd* out);
+mgh_status launch_scatter(Handle& h, const cd* vals, int B, const int64_t* rec, int M, cd* G);
+mgh_status launch_misfit(Handle& h, const cd* u, const cd* y, int B, const int64_t* rec, int M,
+                         cd* r, cd* G, double* loss_dev);
+mgh_status launch_conj(Handle& h, const cd* in, int B, cd* out);
+mgh_status launch_gradient(Handle& h, const double* theta, const cd* u_sc, const cd* z, int B,
+                           double* grad);
+mgh_status launch_coarse_apply(Handle& h, const void* b, size_t b_stride, void* x,
+                               size_t x_stride, int B, const RhsState* st, bool fp64_io);
+
+// mgh_mg.cu: one multigrid cycle on B right-hand sides.
+//   in      FP64 fine right-hand sides, rhs i at in + i*in_stride, each multiplied by
+//           in_scale[i*scale_stride] when in_scale != nullptr
+//   out     fine result, rhs i at out + i*out_stride, complex FP64 when out_fp64, otherwise
+//           in the cycle precision
+//   st      per-RHS state (a right-hand side with st[i].active == 0 is skipped) or nullptr
+mgh_status vcycle(Handle& h, const cd* in, size_t in_stride, const double* in_scale,
+                  size_t scale_stride, void* out, size_t out_stride, bool out_fp64, int B,
+                  const RhsState* st);
+
+// mgh_krylov.cu
+mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
+
+}  // namespace mgh

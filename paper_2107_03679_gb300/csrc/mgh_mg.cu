@@ -1,0 +1,350 @@
+// One multigrid cycle (Alg. 2, V-cycle, zero initial guess) on the shifted-Laplacian operator
+// K_kappa for a batch of right-hand sides, in complex FP32 or FP64.
+//
+// Each level other than the coarsest runs two fused, shared-memory tiled kernels:
+//   k_pre   nu1 damped-Jacobi sweeps from v = 0 (eq. dampedJ), the residual r = b - K v and
+//           its full-weighting restriction to the next level's right-hand side (Sec. IV-C);
+//           all sweeps are done on one tile with a halo of nu1 + 1 points (temporal blocking)
+//   k_post  bilinear prolongation of the coarse correction, v += P e (Sec. IV-C), then nu2
+//           damped-Jacobi sweeps on a tile with a halo of nu2 points
+// and the coarsest level applies the dense inverse of its operator (exact solve).
+//
+// Damped Jacobi is written v <- (1 - w) v + (w / D)(b + (sum of neighbours)/h^2), which is
+// v - w D^{-1}(K v - b) for K v = D v - (sum of neighbours)/h^2; w/D is precomputed per level.
+// Points outside the grid hold 0 in every tile buffer: the Sommerfeld closure already sits in D,
+// and the restriction counts out-of-grid fine samples as 0.
+#include "mgh_engine.h"
+
+namespace mgh {
+
+namespace {
+
+constexpr int kVThreads = 256;
+
+template <typename T, bool FP64_IN>
+__device__ __forceinline__ Cx<T> load_rhs(const void* __restrict__ b, size_t off, double sc) {
+  if constexpr (FP64_IN) {
+    const cd v = reinterpret_cast<const cd*>(b)[off];
+    return mk<T>(static_cast<T>(v.re * sc), static_cast<T>(v.im * sc));
+  } else {
+    return reinterpret_cast<const Cx<T>*>(b)[off];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> jacobi_point(const Cx<T>* v, int idx, int SW, Cx<T> b, Cx<T> wd,
+                                              T inv_h2, T om1) {
+  const Cx<T> s = v[idx - 1] + v[idx + 1] + v[idx - SW] + v[idx + SW];
+  const Cx<T> t = mk<T>(b.re + inv_h2 * s.re, b.im + inv_h2 * s.im);
+  const Cx<T> c = v[idx];
+  return mk<T>(om1 * c.re + wd.re * t.re - wd.im * t.im, om1 * c.im + wd.re * t.im + wd.im * t.re);
+}
+
+// Pre-smoothing + residual + full-weighting restriction on one TX x TY tile of level l.
+template <typename T, int NU, int TX, int TY, bool FP64_IN>
+__global__ void __launch_bounds__(kVThreads)
+k_pre(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
+      const Cx<T>* __restrict__ D, const Cx<T>* __restrict__ wDinv, Cx<T>* __restrict__ vpre,
+      size_t v_stride, Cx<T>* __restrict__ bc, size_t bc_stride, int nx, int ny, int nxc, int nyc,
+      T inv_h2, T om1, const RhsState* __restrict__ st) {
+  constexpr int H = NU + 1;
+  constexpr int SW = TX + 2 * H, SH = TY + 2 * H, S = SW * SH;
+  extern __shared__ unsigned char smem_raw[];
+  Cx<T>* sb = reinterpret_cast<Cx<T>*>(smem_raw);
+  Cx<T>* sw = sb + S;
+  Cx<T>* sd = sw + S;
+  Cx<T>* va = sd + S;
+  Cx<T>* vb = va + S;
+
+  const int rhs = blockIdx.z;
+  if (st && !st[rhs].active) return;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const double sc = (FP64_IN && bscale) ? bscale[rhs * scale_stride] : 1.0;
+  const size_t boff = rhs * b_stride;
+
+  for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
+    const int ly = idx / SW, lx = idx - ly * SW;
+    const int gx = x0 - H + lx, gy = y0 - H + ly;
+    Cx<T> b = czero<T>(), w = czero<T>(), d = czero<T>();
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+      const size_t q = (size_t)gy * nx + gx;
+      b = load_rhs<T, FP64_IN>(bin, boff + q, sc);
+      w = wDinv[q];
+      d = D[q];
+    }
+    sb[idx] = b; sw[idx] = w; sd[idx] = d;
+    if constexpr (NU >= 1) va[idx] = w * b;     // first sweep from v = 0
+  }
+  __syncthreads();
+
+  Cx<T>* vcur = va;
+  Cx<T>* vnxt = vb;
+#pragma unroll
+  for (int s = 2; s <= NU; ++s) {
+    const int lo = s - 1, W = SW - 2 * lo, Hh = SH - 2 * lo;
+    for (int t = threadIdx.x; t < W * Hh; t += kVThreads) {
+      const int ly = lo + t / W, lx = lo + t % W;
+      const int idx = ly * SW + lx;
+      vnxt[idx] = jacobi_point(vcur, idx, SW, sb[idx], sw[idx], inv_h2, om1);
+    }
+    __syncthreads();
+    Cx<T>* tmp = vcur; vcur = vnxt; vnxt = tmp;
+  }
+
+  // residual r = b - K v on fine [x0-1, x0+TX-1] x [y0-1, y0+TY-1] (local offset NU)
+  Cx<T>* r = vnxt;
+  {
+    constexpr int W = TX + 1, Hh = TY + 1;
+    for (int t = threadIdx.x; t < W * Hh; t += kVThreads) {
+      const int ly = NU + t / W, lx = NU + t % W;
+      const int idx = ly * SW + lx;
+      const int gx = x0 - H + lx, gy = y0 - H + ly;
+      Cx<T> rv = czero<T>();
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        if constexpr (NU >= 1) {
+          const Cx<T> s = vcur[idx - 1] + vcur[idx + 1] + vcur[idx - SW] + vcur[idx + SW];
+          const Cx<T> kv = sd[idx] * vcur[idx] - inv_h2 * s;
+          rv = sb[idx] - kv;
+        } else {
+          rv = sb[idx];
+        }
+      }
+      r[idx] = rv;
+    }
+  }
+  __syncthreads();
+
+  // restriction to the coarse points (2ci, 2cj) owned by this tile, and v on the owned points
+  {
+    constexpr int CW = TX / 2, CH = TY / 2;
+    const int ci0 = x0 / 2, cj0 = y0 / 2;
+    Cx<T>* bco = bc + rhs * bc_stride;
+    for (int t = threadIdx.x; t < CW * CH; t += kVThreads) {
+      const int ci = ci0 + t % CW, cj = cj0 + t / CW;
+      if (ci >= nxc || cj >= nyc) continue;
+      const int lx = 2 * ci - x0 + H, ly = 2 * cj - y0 + H;
+      const int idx = ly * SW + lx;
+      const Cx<T> e = r[idx - 1] + r[idx + 1] + r[idx - SW] + r[idx + SW];
+      const Cx<T> c = r[idx - SW - 1] + r[idx - SW + 1] + r[idx + SW - 1] + r[idx + SW + 1];
+      const T q16 = T(1) / T(16);
+      bco[(size_t)cj * nxc + ci] = mk<T>(q16 * (T(4) * r[idx].re + T(2) * e.re + c.re),
+                                         q16 * (T(4) * r[idx].im + T(2) * e.im + c.im));
+    }
+    Cx<T>* vo = vpre + rhs * v_stride;
+    for (int t = threadIdx.x; t < TX * TY; t += kVThreads) {
+      const int lx = H + t % TX, ly = H + t / TX;
+      const int gx = x0 + t % TX, gy = y0 + t / TX;
+      if (gx < nx && gy < ny) {
+        Cx<T> v = czero<T>();
+        if constexpr (NU >= 1) v = vcur[ly * SW + lx];
+        vo[(size_t)gy * nx + gx] = v;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int floor_half(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
+
+// Prolongation + correction + post-smoothing on one TX x TY tile of level l.
+template <typename T, int NU, int TX, int TY, bool FP64_IN, typename TOut>
+__global__ void __launch_bounds__(kVThreads)
+k_post(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
+       const Cx<T>* __restrict__ wDinv, const Cx<T>* __restrict__ vpre, size_t v_stride,
+       const Cx<T>* __restrict__ ec, size_t ec_stride, int nxc, int nyc, Cx<TOut>* __restrict__ out,
+       size_t out_stride, int nx, int ny, T inv_h2, T om1, const RhsState* __restrict__ st) {
+  constexpr int H = NU;
+  constexpr int SW = TX + 2 * H, SH = TY + 2 * H, S = SW * SH;
+  constexpr int CW = TX / 2 + H + 2, CH = TY / 2 + H + 2, CS = CW * CH;
+  extern __shared__ unsigned char smem_raw[];
+  Cx<T>* sb = reinterpret_cast<Cx<T>*>(smem_raw);
+  Cx<T>* sw = sb + S;
+  Cx<T>* va = sw + S;
+  Cx<T>* vb = va + S;
+  Cx<T>* se = vb + S;
+
+  const int rhs = blockIdx.z;
+  if (st && !st[rhs].active) return;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int cx0 = floor_half(x0 - H - 1), cy0 = floor_half(y0 - H - 1);
+  const double sc = (FP64_IN && bscale) ? bscale[rhs * scale_stride] : 1.0;
+  const size_t boff = rhs * b_stride;
+  const Cx<T>* vp = vpre + rhs * v_stride;
+  const Cx<T>* eco = ec + rhs * ec_stride;
+
+  for (int t = threadIdx.x; t < CS; t += kVThreads) {
+    const int cj = cy0 + t / CW, ci = cx0 + t % CW;
+    se[t] = (ci >= 0 && ci < nxc && cj >= 0 && cj < nyc) ? eco[(size_t)cj * nxc + ci] : czero<T>();
+  }
+  for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
+    const int ly = idx / SW, lx = idx - ly * SW;
+    const int gx = x0 - H + lx, gy = y0 - H + ly;
+    Cx<T> b = czero<T>(), w = czero<T>(), v = czero<T>();
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+      const size_t q = (size_t)gy * nx + gx;
+      if constexpr (NU >= 1) {
+        b = load_rhs<T, FP64_IN>(bin, boff + q, sc);
+        w = wDinv[q];
+      }
+      v = vp[q];
+    }
+    sb[idx] = b; sw[idx] = w; vb[idx] = v;
+  }
+  __syncthreads();
+
+  // v = v_pre + P e on every in-grid point of the tile (bilinear weights per fine parity)
+  for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
+    const int ly = idx / SW, lx = idx - ly * SW;
+    const int gx = x0 - H + lx, gy = y0 - H + ly;
+    Cx<T> v = czero<T>();
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+      const int ia = (gx >> 1) - cx0, ja = (gy >> 1) - cy0;
+      Cx<T> p;
+      const bool ox = gx & 1, oy = gy & 1;
+      if (!ox && !oy) {
+        p = se[ja * CW + ia];
+      } else if (ox && !oy) {
+        const Cx<T> s = se[ja * CW + ia] + se[ja * CW + ia + 1];
+        p = T(0.5) * s;
+      } else if (!ox && oy) {
+        const Cx<T> s = se[ja * CW + ia] + se[(ja + 1) * CW + ia];
+        p = T(0.5) * s;
+      } else {
+        const Cx<T> s = se[ja * CW + ia] + se[ja * CW + ia + 1] + se[(ja + 1) * CW + ia] + se[(ja + 1) * CW + ia + 1];
+        p = T(0.25) * s;
+      }
+      v = vb[idx] + p;
+    }
+    va[idx] = v;
+  }
+  __syncthreads();
+
+  Cx<T>* vcur = va;
+  Cx<T>* vnxt = vb;
+#pragma unroll
+  for (int s = 1; s <= NU; ++s) {
+    const int lo = s, W = SW - 2 * lo, Hh = SH - 2 * lo;
+    for (int t = threadIdx.x; t < W * Hh; t += kVThreads) {
+      const int ly = lo + t / W, lx = lo + t % W;
+      const int idx = ly * SW + lx;
+      vnxt[idx] = jacobi_point(vcur, idx, SW, sb[idx], sw[idx], inv_h2, om1);
+    }
+    __syncthreads();
+    Cx<T>* tmp = vcur; vcur = vnxt; vnxt = tmp;
+  }
+
+  Cx<TOut>* o = out + rhs * out_stride;
+  for (int t = threadIdx.x; t < TX * TY; t += kVThreads) {
+    const int gx = x0 + t % TX, gy = y0 + t / TX;
+    if (gx < nx && gy < ny) o[(size_t)gy * nx + gx] = ccast<TOut>(vcur[(H + t / TX) * SW + H + t % TX]);
+  }
+}
+
+template <typename T> struct Tile;
+template <> struct Tile<float> { static constexpr int X = 64, Y = 16; };
+template <> struct Tile<double> { static constexpr int X = 32, Y = 16; };
+
+template <typename T, int NU, bool FP64_IN>
+size_t pre_smem() {
+  constexpr int H = NU + 1, SW = Tile<T>::X + 2 * H, SH = Tile<T>::Y + 2 * H;
+  return 5 * sizeof(Cx<T>) * SW * SH;
+}
+template <typename T, int NU>
+size_t post_smem() {
+  constexpr int H = NU, SW = Tile<T>::X + 2 * H, SH = Tile<T>::Y + 2 * H;
+  constexpr int CW = Tile<T>::X / 2 + H + 2, CH = Tile<T>::Y / 2 + H + 2;
+  return sizeof(Cx<T>) * (4 * SW * SH + CW * CH);
+}
+
+template <typename T, int NU, bool FP64_IN>
+mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
+                         size_t scale_stride, int B, const RhsState* st) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  constexpr int TX = Tile<T>::X, TY = Tile<T>::Y;
+  const size_t smem = pre_smem<T, NU, FP64_IN>();
+  auto kern = k_pre<T, NU, TX, TY, FP64_IN>;
+  MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY, B);
+  const T ih2 = static_cast<T>(1.0 / (lv.h * lv.h));
+  const T om1 = static_cast<T>(1.0 - h.p.omega);
+  kern<<<grid, kVThreads, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const Cx<T>*)lv.D,
+                                            (const Cx<T>*)lv.wDinv, (Cx<T>*)lv.vpre, lv.n(),
+                                            (Cx<T>*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx, cl.ny, ih2, om1, st);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  return MGH_OK;
+}
+
+template <typename T, int NU, bool FP64_IN, typename TOut>
+mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
+                          size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  constexpr int TX = Tile<T>::X, TY = Tile<T>::Y;
+  const size_t smem = post_smem<T, NU>();
+  auto kern = k_post<T, NU, TX, TY, FP64_IN, TOut>;
+  MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY, B);
+  const T ih2 = static_cast<T>(1.0 / (lv.h * lv.h));
+  const T om1 = static_cast<T>(1.0 - h.p.omega);
+  kern<<<grid, kVThreads, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const Cx<T>*)lv.wDinv,
+                                            (const Cx<T>*)lv.vpre, lv.n(), (const Cx<T>*)cl.vfin, cl.n(),
+                                            cl.nx, cl.ny, out, out_stride, lv.nx, lv.ny, ih2, om1, st);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  return MGH_OK;
+}
+
+template <typename T, bool FP64_IN>
+mgh_status launch_pre(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
+                      size_t scale_stride, int B, const RhsState* st) {
+  switch (h.p.nu1) {
+    case 0: return launch_pre_nu<T, 0, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 1: return launch_pre_nu<T, 1, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 2: return launch_pre_nu<T, 2, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 3: return launch_pre_nu<T, 3, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 4: return launch_pre_nu<T, 4, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+  }
+  return MGH_INVALID_ARG;
+}
+
+template <typename T, bool FP64_IN, typename TOut>
+mgh_status launch_post(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
+                       size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st) {
+  switch (h.p.nu2) {
+    case 0: return launch_post_nu<T, 0, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 1: return launch_post_nu<T, 1, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 2: return launch_post_nu<T, 2, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 3: return launch_post_nu<T, 3, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 4: return launch_post_nu<T, 4, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+  }
+  return MGH_INVALID_ARG;
+}
+
+template <typename T>
+mgh_status vcycle_t(Handle& h, const cd* in, size_t in_stride, const double* in_scale, size_t scale_stride,
+                    void* out, size_t out_stride, bool out_fp64, int B, const RhsState* st) {
+  const int L = h.L;
+  // down: level 0 reads the FP64 input, coarser levels their restricted right-hand side
+  MGH_TRY((launch_pre<T, true>(h, 0, in, in_stride, in_scale, scale_stride, B, st)));
+  for (int l = 1; l + 1 < L; ++l)
+    MGH_TRY((launch_pre<T, false>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, B, st)));
+  // coarsest: exact solve
+  const Level& cl = h.lev[L - 1];
+  MGH_TRY(launch_coarse_apply(h, cl.b, cl.n(), cl.vfin, cl.n(), B, st, sizeof(T) == 8));
+  // up
+  for (int l = L - 2; l >= 1; --l)
+    MGH_TRY((launch_post<T, false, T>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, (Cx<T>*)h.lev[l].vfin,
+                                       h.lev[l].n(), B, st)));
+  if (out_fp64)
+    return launch_post<T, true, double>(h, 0, in, in_stride, in_scale, scale_stride, (cd*)out, out_stride, B, st);
+  return launch_post<T, true, T>(h, 0, in, in_stride, in_scale, scale_stride, (Cx<T>*)out, out_stride, B, st);
+}
+
+}  // namespace
+
+mgh_status vcycle(Handle& h, const cd* in, size_t in_stride, const double* in_scale, size_t scale_stride,
+                  void* out, size_t out_stride, bool out_fp64, int B, const RhsState* st) {
+  if (h.fp64) return vcycle_t<double>(h, in, in_stride, in_scale, scale_stride, out, out_stride, out_fp64, B, st);
+  return vcycle_t<float>(h, in, in_stride, in_scale, scale_stride, out, out_stride, out_fp64, B, st);
+}
+
+}  // namespace mgh

@@ -1,0 +1,214 @@
+"""Torch-facing wrapper of the C ABI: owns one solver handle and passes tensors to it.
+
+Tensors are plumbing only (device memory and the CUDA stream); every operation is one C call
+into libmgh.so.  Complex fields are torch.complex128 tensors (interleaved re/im doubles, the
+layout of mgh_cdouble), shaped [B, ny, nx] on the extended grid.
+"""
+from __future__ import annotations
+
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import capi
+
+
+class Solver:
+    """Batched MG-preconditioned FGMRES solver for one discretised Helmholtz problem (Sec. IV)."""
+
+    def __init__(self, nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: float = 0.15,
+                 shift=(1.0, 0.5), levels: int = 4, nu1: int = 1, nu2: int = 1, omega: float = 0.8,
+                 restart: int = 20, maxit: int = 5000, tol: float = 1e-6, precision: str = "mixed32",
+                 batch_max: int = 1, device: Optional[torch.device] = None, stream=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p = capi.mgh_params()
+        p.nx_int, p.ny_int, p.abl = nx_int, ny_int, abl
+        p.h, p.k, p.beta = h, k, beta
+        p.shift_re, p.shift_im = float(shift[0]), float(shift[1])
+        p.levels, p.nu1, p.nu2, p.omega = levels, nu1, nu2, omega
+        p.restart, p.maxit, p.tol = restart, maxit, tol
+        p.precision = capi.PRECISIONS[precision]
+        p.batch_max = batch_max
+        self.params = p
+        self.precision = precision
+        self.nx_int, self.ny_int, self.abl = nx_int, ny_int, abl
+        self.nx, self.ny = nx_int + 2 * abl, ny_int + 2 * abl
+        self.N = self.nx * self.ny
+        self.h, self.k = h, k
+        self.batch_max = batch_max
+        with torch.cuda.device(self.device):
+            self._h = capi.mgh_create(p, self.stream.cuda_stream)
+        self._f_d = None
+
+    @classmethod
+    def from_workload(cls, w, batch_max: Optional[int] = None, precision: Optional[str] = None, **kw):
+        args = dict(nx_int=w.nx_int, ny_int=w.ny_int, abl=w.abl, h=w.h, k=w.k, beta=w.beta,
+                    shift=(w.shift_re, w.shift_im), levels=w.levels, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
+                    restart=w.restart, tol=w.tol, precision=precision or w.precision,
+                    batch_max=batch_max or w.n_angles)
+        args.update(kw)
+        return cls(**args)
+
+    # ------------------------------------------------------------------ helpers
+    def close(self):
+        if getattr(self, "_h", None):
+            capi.mgh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field(self, B: int) -> torch.Tensor:
+        return torch.empty((B, self.ny, self.nx), dtype=torch.complex128, device=self.device)
+
+    def _dev(self, t: torch.Tensor, dtype) -> torch.Tensor:
+        t = t.to(device=self.device, dtype=dtype)
+        return t.contiguous()
+
+    def _B(self, t: torch.Tensor) -> int:
+        B = t.shape[0] if t.dim() >= 1 else 1
+        if B < 1 or B > self.batch_max:
+            raise ValueError(f"batch {B} outside [1, {self.batch_max}]")
+        return B
+
+    # ------------------------------------------------------------------ operations
+    def set_contrast(self, f_d: torch.Tensor) -> None:
+        f = self._dev(f_d, torch.float64)
+        if tuple(f.shape) != (self.ny_int, self.nx_int):
+            raise ValueError(f"f_d must be [{self.ny_int}, {self.nx_int}]")
+        capi.mgh_set_contrast(self._h, capi._ptr(f))
+        self._f_d = f
+
+    def incident_field(self, theta: torch.Tensor) -> torch.Tensor:
+        th = self._dev(theta, torch.float64).reshape(-1)
+        out = self.field(th.numel())
+        capi.mgh_incident_field(self._h, capi._ptr(th), self._B(th), capi._ptr(out))
+        return out
+
+    def rhs(self, theta: torch.Tensor) -> torch.Tensor:
+        th = self._dev(theta, torch.float64).reshape(-1)
+        out = self.field(th.numel())
+        capi.mgh_rhs(self._h, capi._ptr(th), self._B(th), capi._ptr(out))
+        return out
+
+    def apply(self, x: torch.Tensor) -> torch.Tensor:
+        x = self._dev(x, torch.complex128)
+        y = torch.empty_like(x)
+        capi.mgh_apply(self._h, capi._ptr(x, numel=self.N), self._B(x), capi._ptr(y))
+        return y
+
+    def precondition(self, b: torch.Tensor) -> torch.Tensor:
+        b = self._dev(b, torch.complex128)
+        z = torch.empty_like(b)
+        capi.mgh_precondition(self._h, capi._ptr(b, numel=self.N), self._B(b), capi._ptr(z))
+        return z
+
+    def level_shape(self, level: int):
+        return capi.mgh_level_shape(self._h, level)
+
+    def level_coefficient(self, level: int) -> torch.Tensor:
+        nx, ny, _ = self.level_shape(level)
+        c = torch.empty((ny, nx), dtype=torch.float64, device=self.device)
+        capi.mgh_level_coefficient(self._h, level, capi._ptr(c))
+        return c
+
+    def coarse_solve(self, b: torch.Tensor) -> torch.Tensor:
+        b = self._dev(b, torch.complex128)
+        x = torch.empty_like(b)
+        capi.mgh_coarse_solve(self._h, capi._ptr(b), self._B(b), capi._ptr(x))
+        return x
+
+    def solve(self, b: torch.Tensor, x0: Optional[torch.Tensor] = None):
+        b = self._dev(b, torch.complex128)
+        x = torch.zeros_like(b) if x0 is None else self._dev(x0, torch.complex128).clone()
+        infos = capi.mgh_solve(self._h, capi._ptr(b, numel=self.N), self._B(b), capi._ptr(x))
+        return x, infos
+
+    def forward(self, theta: torch.Tensor, out: Optional[torch.Tensor] = None):
+        th = self._dev(theta, torch.float64).reshape(-1)
+        u = self.field(th.numel()) if out is None else out
+        infos = capi.mgh_forward(self._h, capi._ptr(th), self._B(th), capi._ptr(u, torch.complex128))
+        return u, infos
+
+    def crop(self, u: torch.Tensor) -> torch.Tensor:
+        u = self._dev(u, torch.complex128)
+        B = self._B(u)
+        out = torch.empty((B, self.ny_int, self.nx_int), dtype=torch.complex128, device=self.device)
+        capi.mgh_crop(self._h, capi._ptr(u), B, capi._ptr(out))
+        return out
+
+    def sample(self, u: torch.Tensor, rec: torch.Tensor) -> torch.Tensor:
+        u = self._dev(u, torch.complex128)
+        rec = self._dev(rec, torch.int64)
+        B = self._B(u)
+        out = torch.empty((B, rec.numel()), dtype=torch.complex128, device=self.device)
+        capi.mgh_sample(self._h, capi._ptr(u), B, capi._ptr(rec), rec.numel(), capi._ptr(out))
+        return out
+
+    def scatter(self, vals: torch.Tensor, rec: torch.Tensor) -> torch.Tensor:
+        vals = self._dev(vals, torch.complex128)
+        rec = self._dev(rec, torch.int64)
+        B = self._B(vals)
+        G = self.field(B)
+        capi.mgh_scatter(self._h, capi._ptr(vals), B, capi._ptr(rec), rec.numel(), capi._ptr(G))
+        return G
+
+    def misfit(self, u: torch.Tensor, y: torch.Tensor, rec: torch.Tensor):
+        """r = S u - y, G = S^T r, loss = 1/2 sum |r|^2 (Sec. V)."""
+        u = self._dev(u, torch.complex128)
+        y = self._dev(y, torch.complex128)
+        rec = self._dev(rec, torch.int64)
+        B = self._B(u)
+        r = torch.empty((B, rec.numel()), dtype=torch.complex128, device=self.device)
+        G = self.field(B)
+        loss = capi.mgh_misfit(self._h, capi._ptr(u), capi._ptr(y), B, capi._ptr(rec), rec.numel(),
+                               capi._ptr(r), capi._ptr(G))
+        return r, G, loss
+
+    def gradient(self, theta: torch.Tensor, u_sc: torch.Tensor, G: torch.Tensor):
+        """grad f_d of a real loss with dL/du_sc = G (PyTorch convention), via one adjoint solve per angle."""
+        th = self._dev(theta, torch.float64).reshape(-1)
+        u_sc = self._dev(u_sc, torch.complex128)
+        G = self._dev(G, torch.complex128)
+        grad = torch.empty((self.ny_int, self.nx_int), dtype=torch.float64, device=self.device)
+        infos = capi.mgh_gradient(self._h, capi._ptr(th), capi._ptr(u_sc), capi._ptr(G), self._B(th),
+                                  capi._ptr(grad))
+        return grad, infos
+
+    def launch_count(self, reset: bool = False) -> int:
+        return capi.mgh_launch_count(self._h, reset)
+
+
+class ScatteredField(torch.autograd.Function):
+    """u_rec = S A(f_d)^{-1} (k^2 f_d u_in(theta)): receiver samples of the scattered fields.
+
+    backward takes G_rec = dL/du_rec in PyTorch's complex convention, scatters it onto the grid
+    (S^T), and returns dL/df_d from one adjoint solve per angle (Prop. 1), all in the CUDA library.
+    """
+
+    @staticmethod
+    def forward(ctx, f_d: torch.Tensor, solver: Solver, theta: torch.Tensor, rec: torch.Tensor):
+        solver.set_contrast(f_d.detach())
+        u_sc, infos = solver.forward(theta)
+        u_rec = solver.sample(u_sc, rec)
+        ctx.solver = solver
+        ctx.infos = infos
+        ctx.save_for_backward(f_d.detach(), theta, u_sc, rec)
+        return u_rec
+
+    @staticmethod
+    def backward(ctx, g_rec: torch.Tensor):
+        f_d, theta, u_sc, rec = ctx.saved_tensors
+        solver: Solver = ctx.solver
+        solver.set_contrast(f_d)
+        G = solver.scatter(g_rec.contiguous(), rec)
+        grad, _ = solver.gradient(theta, u_sc, G)
+        return grad.to(f_d.dtype), None, None, None
+
+
+def scattered_field(f_d: torch.Tensor, solver: Solver, theta: torch.Tensor, rec: torch.Tensor) -> torch.Tensor:
+    return ScatteredField.apply(f_d, solver, theta, rec)
