@@ -1,0 +1,448 @@
+#!/usr/bin/env python
+"""Benchmark of the batched multigrid-preconditioned Helmholtz solver.
+
+Metric: Helmholtz solves per second to relative residual 1e-6 (batched angles), with the
+achieved HBM bandwidth of the dominant kernel against the measured peak.
+
+One step is one pass over every stage of the hot path for one batch of illuminations of the
+batched-forward workload (512^2 interior + 32-cell absorbing layer, 60 plane waves, contrast
+from 6 seeded ellipses, FP32 V-cycle with 6 levels, FP64 FGMRES(20), tol 1e-6):
+  set the contrast and rebuild the hierarchy; form the 60 right-hand sides and solve them;
+  crop to the interior and sample the receivers; evaluate the data misfit; solve the 60
+  adjoint systems and form the gradient in the contrast.  A step therefore completes 120
+  Helmholtz solves, every one of them to true relative residual <= 1e-6.
+
+Under torchrun each rank runs its own batch (independent problems, weak scaling, no
+collective on the data path); the timing is the maximum over ranks.
+`--impl reference` times the FP64 CPU oracle on the host cores instead (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Helmholtz solves/s to rel-res 1e-6 (batched angles); V-cycle HBM GB/s vs peak"
+UNIT = "solves/s"
+ITER_FIXTURE = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mgh", "reference"], default="mgh")
+    ap.add_argument("--workload", default="ellipses576")
+    ap.add_argument("--precision", choices=["mixed32", "fp64"], default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--sample-steps", type=int, default=60, help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+# --------------------------------------------------------------------------- inputs
+def make_inputs(w):
+    """Seeded synthetic inputs: ground truth phantom, the iterate the step is evaluated at,
+    angles and receivers (the data are produced on the device from the ground truth)."""
+    import numpy as np
+    import workloads as W
+    f_gt = W.phantom(w)
+    f_step = 0.9 * f_gt
+    th = W.angles(w)
+    rec = W.receivers(w, f_gt)
+    return f_gt, f_step, th, rec
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- algorithmic bytes
+def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict) -> dict:
+    """Minimal DRAM bytes of each kernel class from the engine counters (fields read once,
+    per-grid coefficient arrays counted once per launch).  N = fine points, cs = bytes of one
+    complex number of the multigrid precision."""
+    steps = prof["arnoldi_steps"]
+    c16 = 16
+    out = {
+        # level-0 pre-smoothing + residual + restriction: read b (FP64), write v (cs), write the
+        # restricted residual (cs/4 per fine point); D and w/D once per launch
+        "vcycle_pre_l0": steps * N * (c16 + cs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
+        # level-0 prolongation + correction + post-smoothing: read b (FP64), v (cs), coarse e
+        # (cs/4), write z (cs); w/D once per launch
+        "vcycle_post_l0": steps * N * (c16 + 2 * cs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
+        # fused w = A z_j + dots: read z (cs) and j+1 basis vectors (FP64), write w (FP64); D_A per launch
+        "matvec_dots": steps * N * (cs + c16) + prof["basis_reads"] * N * c16 + launches["matvec_dots"] * c16 * N,
+        # update: read w and j+1 basis vectors, write v_{j+1}
+        "gs_update": steps * N * 2 * c16 + prof["basis_reads"] * N * c16,
+        "true_residual": prof["residuals"] * N * 3 * c16,
+        "x_update": prof["updates"] * N * 2 * c16 + prof["update_reads"] * N * cs,
+    }
+    return out
+
+
+# --------------------------------------------------------------------------- CPU oracle sample
+def cpu_sample_main(args):
+    """Run in a subprocess with one BLAS thread: time `sample_steps` FGMRES steps of the FP64
+    oracle on angle 0 of the workload and print seconds per Arnoldi step."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    w = W.WORKLOADS[args.workload]
+    _, f_step, th, _ = make_inputs(w)
+    p = O.Problem.from_workload(w)
+    t0 = time.perf_counter()
+    s = O.MGHSolver(p, f_step, w.levels, w.nu1, w.nu2, w.omega, complex(w.shift_re, w.shift_im), w.restart,
+                    w.tol, maxit=args.sample_steps)
+    t_setup = time.perf_counter() - t0
+    b = O.rhs(p, f_step, float(th[0]))
+    t0 = time.perf_counter()
+    _, info = s.solve(b)
+    t = time.perf_counter() - t0
+    print(json.dumps({"sec_per_step": t / max(info.iterations, 1), "steps": info.iterations, "setup_s": t_setup,
+                      "solve_s": t}))
+
+
+def oracle_iterations_per_solve(workload: str):
+    if not os.path.exists(ITER_FIXTURE):
+        return None
+    with open(ITER_FIXTURE) as fh:
+        d = json.load(fh)
+    e = d.get(workload)
+    if not e:
+        return None
+    return 0.5 * (e["forward_iterations"] + e["adjoint_iterations"])
+
+
+def run_cpu_sample(workload: str, sample_steps: int):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
+                        "--sample-steps", str(sample_steps)], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(f"cpu sample failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_record(workload: str, sample_steps: int):
+    its = oracle_iterations_per_solve(workload)
+    smp = run_cpu_sample(workload, sample_steps)
+    if its is None:
+        return None
+    value = 1.0 / (smp["sec_per_step"] * its)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle, 1 thread: {smp['steps']} FGMRES steps of angle 0 "
+                       f"({smp['solve_s']:.1f} s, {smp['sec_per_step'] * 1e3:.0f} ms/step), scaled by the oracle's own "
+                       f"{its:.0f} steps per solve (forward/adjoint mean, {os.path.relpath(ITER_FIXTURE, ROOT)})")}
+
+
+# --------------------------------------------------------------------------- reference arm
+def reference_main(args, rank, world):
+    if rank != 0:
+        return
+    import workloads as W
+    w = W.WORKLOADS[args.workload]
+    its = oracle_iterations_per_solve(args.workload)
+    if its is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle iteration fixture for {args.workload}"}))
+        return
+    sample_steps = 40
+    for _ in range(args.warmup):
+        run_cpu_sample(args.workload, sample_steps)
+    times = []
+    for _ in range(args.steps):
+        smp = run_cpu_sample(args.workload, sample_steps)
+        times.append(smp["sec_per_step"])
+    sec = sum(times) / len(times)
+    value = 1.0 / (sec * its)
+    sample = (f"FP64 numpy oracle, 1 thread: {sample_steps} FGMRES steps of angle 0 per step, "
+              f"scaled by {its:.0f} oracle steps per solve")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * sample_steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny}", "angles": w.n_angles},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------- GPU arm
+def gpu_main(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2107_03679_gb300 import Solver
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = W.WORKLOADS[args.workload]
+    precision = args.precision or w.precision
+    f_gt, f_step, th, rec = make_inputs(w)
+    B = w.n_angles
+    solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=20000)
+    stream = solver.stream
+    d_th = torch.from_numpy(th).to(dev)
+    d_rec = torch.from_numpy(rec).to(dev)
+    d_fgt = torch.from_numpy(f_gt).to(dev)
+    d_f = torch.from_numpy(f_step).to(dev)
+    # synthetic measurements: receiver samples of the ground-truth phantom's fields
+    solver.set_contrast(d_fgt)
+    u_gt, _ = solver.forward(d_th)
+    d_y = solver.sample(u_gt, d_rec)
+    del u_gt
+    u = solver.field(B)
+
+    def step(f_dev, y_dev):
+        solver.set_contrast(f_dev)                               # contrast, hierarchy, coarsest inverse
+        _, inf_f = solver.forward(d_th, out=u)                   # right-hand sides + forward solves
+        u_int = solver.crop(u)                                   # truncation to the interior
+        _, G, loss = solver.misfit(u, y_dev, d_rec)              # receiver sampling, residual, loss
+        g, inf_a = solver.gradient(d_th, u, G)                   # adjoint solves + gradient
+        return g, loss, inf_f, inf_a, u_int
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    infos = []
+    for _ in range(args.warmup):
+        _, _, a, b, _ = step(d_f, d_y)
+        infos += a + b
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0] or 0)
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local_rank)
+    solver.profile_enable(True)
+    l0 = solver.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    timed_infos = []
+    for _ in range(args.steps):
+        _, loss, a, b, _ = step(d_f, d_y)
+        timed_infos += a + b
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    launches = solver.launch_count() - l0
+    prof = solver.profile_read()
+    solver.profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    solves_rank = 2 * B * args.steps
+    value = world * solves_rank / (ms_max / 1e3)
+    conv = all(i["converged"] for i in timed_infos)
+    worst = max(i["rel_residual"] for i in timed_infos)
+    its = [i["iterations"] for i in timed_infos]
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_f = torch.from_numpy(f_step).pin_memory()
+        h_y = d_y.cpu().pin_memory()
+        h_g = torch.empty((w.ny_int, w.nx_int), dtype=torch.float64).pin_memory()
+        h_s = torch.empty((B, rec.size), dtype=torch.complex128).pin_memory()
+        h2d = h_f.numel() * 8 + h_y.numel() * 16
+        d2h = h_g.numel() * 8 + h_s.numel() * 16 + 8
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            f_dev = h_f.to(dev, non_blocking=True)
+            y_dev = h_y.to(dev, non_blocking=True)
+            g, loss, _, _, _ = step(f_dev, y_dev)
+            h_g.copy_(g, non_blocking=True)
+            h_s.copy_(solver.sample(u, d_rec), non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * solves_rank / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel class (CUDA events over the timed region)
+    cs = 16 if precision == "fp64" else 8
+    N = solver.N
+    alg = algorithmic_bytes(prof, N, cs, prof["launches"])
+    ms_cls = prof["ms"]
+    dom = max(ms_cls, key=lambda k: ms_cls[k])
+    peak, peak_kind = load_peaks()
+    kernels = {}
+    for k, v in ms_cls.items():
+        if v <= 0:
+            continue
+        e = {"ms": round(v, 3), "share": round(v / sum(ms_cls.values()), 4), "launches": prof["launches"][k]}
+        if k in alg:
+            e["GBps"] = round(alg[k] / (v / 1e3) / 1e9, 1)
+        kernels[k] = e
+    vc_bytes = alg["vcycle_pre_l0"] + alg["vcycle_post_l0"]
+    vc_ms = ms_cls["vcycle_pre_l0"] + ms_cls["vcycle_post_l0"]
+    if dom in alg:
+        achieved = alg[dom] / (ms_cls[dom] / 1e3) / 1e9
+        n_l = max(prof["launches"][dom], 1)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": round(alg[dom] / n_l)}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                "traffic": None, "peak_kind": peak_kind}
+    roof["vcycle_fine_GBps"] = round(vc_bytes / (vc_ms / 1e3) / 1e9, 1) if vc_ms > 0 else None
+    roof["vcycle_fine_frac"] = round(vc_bytes / (vc_ms / 1e3) / 1e9 / peak, 4) if vc_ms > 0 else None
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = cpu_baseline_record(args.workload, sample_steps=200)
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"error": str(ex)[:200]}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if precision == "mixed32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
+                   "angles_per_gpu": B, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
+                   "restart": w.restart, "tol": w.tol, "shift": [w.shift_re, w.shift_im],
+                   "step": "set_contrast + 60 forward + crop/sample/misfit + 60 adjoint solves + gradient",
+                   "solves_per_step": 2 * B, "l2": "inputs larger than L2 (Krylov basis "
+                   f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "kernels": kernels,
+        "iterations": {"mean": round(sum(its) / len(its), 1), "min": min(its), "max": max(its)},
+        "converged": conv, "worst_rel_residual": worst,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.cpu_sample:
+        cpu_sample_main(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "reference":
+            dist.init_process_group("gloo")
+        else:
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+    try:
+        if args.impl == "reference":
+            reference_main(args, rank, world)
+        else:
+            gpu_main(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -172,6 +172,33 @@ mgh_status mgh_misfit(mgh_handle* h, const mgh_cdouble* u, const mgh_cdouble* y,
 mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u_sc,
                         const mgh_cdouble* G, int B, double* grad, mgh_solve_info* info);
 
+/* Device-time profile of a handle.  Kernel classes (index into ms/launches):
+ *   0 level-0 pre-smoothing + residual + restriction   5 second Gram-Schmidt pass
+ *   1 level-0 prolongation + correction + smoothing    6 per-RHS reductions and Givens updates
+ *   2 coarser levels and the coarsest solve            7 true residuals
+ *   3 fused A z_j + Gram-Schmidt dots                   8 iterate updates x += Z y
+ *   4 Gram-Schmidt update + re-orthogonalisation dots   9 everything else (set-up, right-hand sides, ...)
+ * Counters let a caller turn times into bytes: every Arnoldi step runs one multigrid cycle, a
+ * Gram-Schmidt pass at step j reads j+1 basis vectors. */
+#define MGH_PROFILE_CLASSES 10
+typedef struct {
+  double ms[MGH_PROFILE_CLASSES];          /* summed device time, CUDA events on the handle's stream */
+  uint64_t launches[MGH_PROFILE_CLASSES];  /* kernel launches per class */
+  uint64_t arnoldi_steps;                  /* Arnoldi steps summed over right-hand sides */
+  uint64_t basis_reads;                    /* sum over steps of j+1 (first pass) */
+  uint64_t reorth_reads;                   /* sum over second passes of j+1 */
+  uint64_t residuals;                      /* true residual evaluations, summed over right-hand sides */
+  uint64_t updates;                        /* iterate updates, summed over right-hand sides */
+  uint64_t update_reads;                   /* preconditioned vectors read by iterate updates */
+} mgh_profile;
+
+/* Start (enable != 0) or stop recording; starting clears the profile.  While on, every launch
+ * is bracketed by two CUDA events on the handle's stream. */
+mgh_status mgh_profile_enable(mgh_handle* h, int enable);
+
+/* Synchronise the handle's stream and return the profile accumulated since it was enabled. */
+mgh_status mgh_profile_read(mgh_handle* h, mgh_profile* out);
+
 /* Kernel launches issued by this handle since creation (or since the last reset). */
 uint64_t mgh_launch_count(const mgh_handle* h, int reset);
 

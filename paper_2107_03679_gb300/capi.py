@@ -34,6 +34,18 @@ class mgh_solve_info(ctypes.Structure):
                 ("rel_residual", ctypes.c_double)]
 
 
+MGH_PROFILE_CLASSES = 10
+PROFILE_CLASS_NAMES = ["vcycle_pre_l0", "vcycle_post_l0", "vcycle_coarse", "matvec_dots", "gs_update",
+                       "gs_reorth", "reduce_givens", "true_residual", "x_update", "other"]
+
+
+class mgh_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * MGH_PROFILE_CLASSES), ("launches", ctypes.c_uint64 * MGH_PROFILE_CLASSES),
+                ("arnoldi_steps", ctypes.c_uint64), ("basis_reads", ctypes.c_uint64),
+                ("reorth_reads", ctypes.c_uint64), ("residuals", ctypes.c_uint64),
+                ("updates", ctypes.c_uint64), ("update_reads", ctypes.c_uint64)]
+
+
 class MGHError(RuntimeError):
     def __init__(self, fn: str, status: int):
         msg = _lib.mgh_status_string(status).decode()
@@ -71,6 +83,8 @@ def _load():
         "mgh_scatter": (S, [P, P, I, P, I, P]),
         "mgh_misfit": (S, [P, P, P, I, P, I, P, P, ctypes.POINTER(D)]),
         "mgh_gradient": (S, [P, P, P, P, I, P, info_p]),
+        "mgh_profile_enable": (S, [P, I]),
+        "mgh_profile_read": (S, [P, ctypes.POINTER(mgh_profile)]),
         "mgh_launch_count": (ctypes.c_uint64, [P, I]),
         "mgh_status_string": (ctypes.c_char_p, [S]),
         "mgh_last_error": (ctypes.c_char_p, []),
@@ -89,7 +103,7 @@ EXPORTED = [
     "mgh_default_params", "mgh_workspace_bytes", "mgh_create", "mgh_destroy", "mgh_set_contrast",
     "mgh_incident_field", "mgh_rhs", "mgh_apply", "mgh_precondition", "mgh_coarse_solve",
     "mgh_level_shape", "mgh_level_coefficient", "mgh_solve", "mgh_forward", "mgh_crop", "mgh_sample",
-    "mgh_scatter", "mgh_misfit", "mgh_gradient", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
+    "mgh_scatter", "mgh_misfit", "mgh_gradient", "mgh_profile_enable", "mgh_profile_read", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
 ]
 
 
@@ -217,6 +231,20 @@ def mgh_gradient(h, theta, u_sc, G, B, grad, allow_not_converged=True):
     st = _lib.mgh_gradient(h, theta, u_sc, G, B, grad, info)
     _check("mgh_gradient", st, (MGH_OK, MGH_NOT_CONVERGED) if allow_not_converged else (MGH_OK,))
     return _infos_to_list(info)
+
+
+def mgh_profile_enable(h, enable=True):
+    _check("mgh_profile_enable", _lib.mgh_profile_enable(h, 1 if enable else 0))
+
+
+def mgh_profile_read(h) -> dict:
+    p = mgh_profile()
+    _check("mgh_profile_read", _lib.mgh_profile_read(h, ctypes.byref(p)))
+    return dict(ms={n: p.ms[i] for i, n in enumerate(PROFILE_CLASS_NAMES)},
+                launches={n: int(p.launches[i]) for i, n in enumerate(PROFILE_CLASS_NAMES)},
+                arnoldi_steps=int(p.arnoldi_steps), basis_reads=int(p.basis_reads),
+                reorth_reads=int(p.reorth_reads), residuals=int(p.residuals), updates=int(p.updates),
+                update_reads=int(p.update_reads))
 
 
 def mgh_launch_count(h, reset=False) -> int:

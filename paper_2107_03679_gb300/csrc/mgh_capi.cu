@@ -93,12 +93,46 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->sn); cudaFree(h->g); cudaFree(h->y); cudaFree(h->vscale); cudaFree(h->st); cudaFree(h->partial);
   cudaFree(h->dscratch);
   if (h->st_host) cudaFreeHost(h->st_host);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
 }
 
 bool batch_ok(const Handle* h, int B) { return h && B >= 1 && B <= h->Bmax; }
 
 }  // namespace
+
+ProfScope::ProfScope(Handle& hh, int cls) : h(hh) {
+  if (!h.prof) return;
+  if (h.ev_used + 2 > h.ev.size()) {
+    const size_t grow = std::max<size_t>(256, h.ev.size());
+    for (size_t i = 0; i < grow; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;   // profiling degrades, the launch still runs
+      h.ev.push_back(e);
+    }
+  }
+  slot = (int)h.ev_used;
+  h.ev_used += 2;
+  if (h.ev_cls.size() < h.ev_used / 2) h.ev_cls.resize(h.ev_used / 2);
+  h.ev_cls[slot / 2] = cls;
+  cudaEventRecord(h.ev[slot], h.stream);
+}
+
+ProfScope::~ProfScope() {
+  if (slot >= 0) cudaEventRecord(h.ev[slot + 1], h.stream);
+}
+
+mgh_status prof_flush(Handle& h) {
+  for (size_t i = 0; i + 1 < h.ev_used; i += 2) {
+    float ms = 0.f;
+    MGH_CUDA(cudaEventElapsedTime(&ms, h.ev[i], h.ev[i + 1]));
+    const int c = h.ev_cls[i / 2];
+    h.acc.ms[c] += ms;
+    h.acc.launches[c] += 1;
+  }
+  h.ev_used = 0;
+  return MGH_OK;
+}
 
 void set_error(const char* what, cudaError_t e, const char* file, int line) {
   std::snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file,
@@ -298,6 +332,23 @@ mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u
   if (s != MGH_OK && s != MGH_NOT_CONVERGED) return s;
   MGH_TRY(launch_gradient(*h, theta, (const cd*)u_sc, h->T2, B, grad));
   return s;
+}
+
+mgh_status mgh_profile_enable(mgh_handle* h, int enable) {
+  if (!h) return MGH_INVALID_ARG;
+  MGH_CUDA(cudaStreamSynchronize(h->stream));
+  MGH_TRY(prof_flush(*h));
+  h->acc = mgh_profile{};
+  h->prof = enable != 0;
+  return MGH_OK;
+}
+
+mgh_status mgh_profile_read(mgh_handle* h, mgh_profile* out) {
+  if (!h || !out) return MGH_INVALID_ARG;
+  MGH_CUDA(cudaStreamSynchronize(h->stream));
+  MGH_TRY(prof_flush(*h));
+  *out = h->acc;
+  return MGH_OK;
 }
 
 uint64_t mgh_launch_count(const mgh_handle* h, int reset) {

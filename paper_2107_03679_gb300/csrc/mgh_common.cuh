@@ -70,7 +70,11 @@ struct RhsState {
   int iterations;    // total Arnoldi steps
   int restarts;      // completed cycles
   int reorth;        // 1 if the current step needs a second Gram-Schmidt pass
-  int pad;
+  int vsum;          // sum over steps of j+1 (basis vectors read per Gram-Schmidt pass)
+  int rsum;          // the same for second passes
+  int nres;          // true residual evaluations
+  int nupd;          // iterate updates
+  int zsum;          // preconditioned vectors read by iterate updates
   double bnorm;      // ||b||
   double rnorm;      // last true residual norm
   double wnorm2;     // ||A z_j||^2 of the current step

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "mgh.h"
 #include "mgh_common.cuh"
@@ -75,6 +76,24 @@ struct Handle {
   double* dscratch = nullptr;   // small FP64 scratch (loss)
 
   uint64_t launches = 0;
+
+  // profiling (mgh_profile_enable): event pairs around launches, resolved at read time
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;     // pool, two per recorded launch
+  std::vector<int> ev_cls;         // class of each recorded pair
+  size_t ev_used = 0;
+  mgh_profile acc{};
+};
+
+enum ProfClass { P_PRE0 = 0, P_POST0, P_COARSE, P_MATVEC_DOTS, P_UPDATE, P_REORTH, P_REDUCE, P_RESIDUAL,
+                 P_XUPDATE, P_OTHER };
+
+// Brackets the launches issued during its lifetime with CUDA events when profiling is on.
+struct ProfScope {
+  Handle& h;
+  int slot = -1;
+  ProfScope(Handle& hh, int cls);
+  ~ProfScope();
 };
 
 // mgh_setup.cu
@@ -101,6 +120,9 @@ mgh_status launch_coarse_apply(Handle& h, const void* b, size_t b_stride, void* 
 mgh_status vcycle(Handle& h, const cd* in, size_t in_stride, const double* in_scale,
                   size_t scale_stride, void* out, size_t out_stride, bool out_fp64, int B,
                   const RhsState* st);
+
+// mgh_capi.cu: resolve the recorded event pairs of a synchronised stream into h.acc
+mgh_status prof_flush(Handle& h);
 
 // mgh_krylov.cu
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);

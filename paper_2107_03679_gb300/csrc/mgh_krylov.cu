@@ -213,7 +213,10 @@ __global__ void k_fin_reorth(KArgs a, int j, const cd* __restrict__ partial, con
   sum_partials(a, partial, rhs, j + 2, sh);
   for (int i = threadIdx.x; i <= j; i += blockDim.x)
     hcol[(size_t)rhs * (a.m + 1) + i] = hcol[(size_t)rhs * (a.m + 1) + i] + h2col[(size_t)rhs * (a.m + 1) + i];
-  if (threadIdx.x == 0) st[rhs].norm2 = sh[j + 1].re;
+  if (threadIdx.x == 0) {
+    st[rhs].norm2 = sh[j + 1].re;
+    st[rhs].rsum += j + 1;
+  }
 }
 
 // Givens update of column j of the Hessenberg matrix and of the rotated right-hand side g;
@@ -255,6 +258,7 @@ __global__ void k_givens(KArgs a, int j, const cd* __restrict__ hcol, cd* __rest
   for (int i = 0; i <= j; ++i) Hc[i] = col[i];
   RhsState& S = st[rhs];
   S.iterations += 1;
+  S.vsum += j + 1;
   S.jend = j + 1;
   const double est = sqrt(cabs2(gg[j + 1])) / S.bnorm;
   if (hn > 0.0) vscale[(size_t)rhs * (m + 1) + j + 1] = 1.0 / hn;
@@ -263,10 +267,12 @@ __global__ void k_givens(KArgs a, int j, const cd* __restrict__ hcol, cd* __rest
 
 // Back substitution H(0:jend,0:jend) y = g(0:jend); one thread per right-hand side.
 __global__ void k_lsq(KArgs a, const cd* __restrict__ H, const cd* __restrict__ g, cd* __restrict__ y,
-                      const RhsState* __restrict__ st, int B) {
+                      RhsState* __restrict__ st, int B) {
   const int rhs = blockIdx.x * blockDim.x + threadIdx.x;
   if (rhs >= B || st[rhs].done || st[rhs].jend == 0) return;
   const int m = a.m, je = st[rhs].jend;
+  st[rhs].nupd += 1;
+  st[rhs].zsum += je;
   const cd* Hb = H + (size_t)rhs * m * (m + 1);
   const cd* gg = g + (size_t)rhs * (m + 1);
   cd* yy = y + (size_t)rhs * m;
@@ -339,6 +345,7 @@ __global__ void k_cycle_start(KArgs a, const cd* __restrict__ partial, double* _
   sum_partials(a, partial, rhs, 2, sh);
   if (threadIdx.x != 0) return;
   RhsState& S = st[rhs];
+  S.nres += 1;
   if (first) {
     S.bnorm = sqrt(sh[1].re);
     S.iterations = 0;
@@ -377,22 +384,44 @@ __global__ void k_state_reset(RhsState* st, int B) {
 // ---------------------------------------------------------------- host-side dispatch on NV
 template <typename TZ, int NV>
 mgh_status step_nv(Handle& h, const KArgs& a, int j, int B) {
-  dim3 grid(a.nblk, B);
-  k_matvec_dots<TZ, NV><<<grid, kKThreads, 0, h.stream>>>(a, j, (const Cx<TZ>*)h.Z, h.DA, h.V, h.W, h.partial, h.st);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_fin_dots<<<B, 64, 0, h.stream>>>(a, j, h.partial, h.vscale, h.hcol, h.st);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_update<NV><<<grid, kKThreads, 0, h.stream>>>(a, j, h.hcol, h.vscale, h.V, h.W, h.partial, h.st);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_fin_update<<<B, 64, 0, h.stream>>>(a, j, h.partial, h.vscale, h.h2col, h.st);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_reorth<NV><<<grid, kKThreads, 0, h.stream>>>(a, j, h.h2col, h.vscale, h.V, h.partial, h.st);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_fin_reorth<<<B, 64, 0, h.stream>>>(a, j, h.partial, h.h2col, h.hcol, h.st);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_givens<<<(B + 63) / 64, 64, 0, h.stream>>>(a, j, h.hcol, h.H, h.cs, h.sn, h.g, h.vscale, h.st, B, h.p.tol,
-                                               h.p.maxit);
-  MGH_CHECK_LAUNCH(); h.launches++;
+  const dim3 grid(a.nblk, B);
+  {
+    ProfScope ps(h, P_MATVEC_DOTS);
+    k_matvec_dots<TZ, NV><<<grid, kKThreads, 0, h.stream>>>(a, j, (const Cx<TZ>*)h.Z, h.DA, h.V, h.W, h.partial,
+                                                            h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_fin_dots<<<B, 64, 0, h.stream>>>(a, j, h.partial, h.vscale, h.hcol, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_UPDATE);
+    k_update<NV><<<grid, kKThreads, 0, h.stream>>>(a, j, h.hcol, h.vscale, h.V, h.W, h.partial, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_fin_update<<<B, 64, 0, h.stream>>>(a, j, h.partial, h.vscale, h.h2col, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REORTH);
+    k_reorth<NV><<<grid, kKThreads, 0, h.stream>>>(a, j, h.h2col, h.vscale, h.V, h.partial, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_fin_reorth<<<B, 64, 0, h.stream>>>(a, j, h.partial, h.h2col, h.hcol, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_givens<<<(B + 63) / 64, 64, 0, h.stream>>>(a, j, h.hcol, h.H, h.cs, h.sn, h.g, h.vscale, h.st, B, h.p.tol,
+                                                 h.p.maxit);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
   return MGH_OK;
 }
 
@@ -413,6 +442,7 @@ template <typename TZ>
 mgh_status xupdate(Handle& h, const KArgs& a, int B, cd* x) {
   dim3 grid(a.nblk, B);
   const int m = a.m;
+  ProfScope ps(h, P_XUPDATE);
   if (m <= 4) k_xupdate<TZ, 4><<<grid, kKThreads, 0, h.stream>>>(a, (const Cx<TZ>*)h.Z, h.y, x, h.st);
   else if (m <= 8) k_xupdate<TZ, 8><<<grid, kKThreads, 0, h.stream>>>(a, (const Cx<TZ>*)h.Z, h.y, x, h.st);
   else if (m <= 16) k_xupdate<TZ, 16><<<grid, kKThreads, 0, h.stream>>>(a, (const Cx<TZ>*)h.Z, h.y, x, h.st);
@@ -430,33 +460,61 @@ mgh_status fgmres_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) 
   a.chunk = (h.N + a.nblk - 1) / a.nblk;
   a.inv_h2 = 1.0 / (h.p.h * h.p.h);
   const dim3 grid(a.nblk, B);
-  k_state_reset<<<(B + 63) / 64, 64, 0, h.stream>>>(h.st, B);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.V, h.partial, h.st);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 1);
-  MGH_CHECK_LAUNCH(); h.launches++;
-  k_zero_if_b_zero<<<grid, kKThreads, 0, h.stream>>>(a, x, h.st);
-  MGH_CHECK_LAUNCH(); h.launches++;
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_state_reset<<<(B + 63) / 64, 64, 0, h.stream>>>(h.st, B);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_RESIDUAL);
+    k_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.V, h.partial, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 1);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_OTHER);
+    k_zero_if_b_zero<<<grid, kKThreads, 0, h.stream>>>(a, x, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
   for (;;) {
     MGH_CUDA(cudaMemcpyAsync(h.st_host, h.st, sizeof(RhsState) * B, cudaMemcpyDeviceToHost, h.stream));
     MGH_CUDA(cudaStreamSynchronize(h.stream));
+    MGH_TRY(prof_flush(h));
     bool any = false;
     for (int i = 0; i < B; ++i) any |= (h.st_host[i].done == 0);
     if (!any) break;
     for (int j = 0; j < a.m; ++j) MGH_TRY(arnoldi_step<TZ>(h, a, j, B));
-    k_lsq<<<(B + 63) / 64, 64, 0, h.stream>>>(a, h.H, h.g, h.y, h.st, B);
-    MGH_CHECK_LAUNCH(); h.launches++;
+    {
+      ProfScope ps(h, P_REDUCE);
+      k_lsq<<<(B + 63) / 64, 64, 0, h.stream>>>(a, h.H, h.g, h.y, h.st, B);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
     MGH_TRY(xupdate<TZ>(h, a, B, x));
-    k_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.V, h.partial, h.st);
-    MGH_CHECK_LAUNCH(); h.launches++;
-    k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 0);
-    MGH_CHECK_LAUNCH(); h.launches++;
+    {
+      ProfScope ps(h, P_RESIDUAL);
+      k_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.V, h.partial, h.st);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    {
+      ProfScope ps(h, P_REDUCE);
+      k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 0);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
   }
   bool all_conv = true;
   for (int i = 0; i < B; ++i) {
     const RhsState& S = h.st_host[i];
     all_conv &= (S.converged != 0);
+    h.acc.arnoldi_steps += S.iterations;
+    h.acc.basis_reads += S.vsum;
+    h.acc.reorth_reads += S.rsum;
+    h.acc.residuals += S.nres;
+    h.acc.updates += S.nupd;
+    h.acc.update_reads += S.zsum;
     if (info) {
       info[i].iterations = S.iterations;
       info[i].restarts = S.restarts;

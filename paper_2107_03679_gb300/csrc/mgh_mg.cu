@@ -267,6 +267,7 @@ mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, con
   dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY, B);
   const T ih2 = static_cast<T>(1.0 / (lv.h * lv.h));
   const T om1 = static_cast<T>(1.0 - h.p.omega);
+  ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
   kern<<<grid, kVThreads, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const Cx<T>*)lv.D,
                                             (const Cx<T>*)lv.wDinv, (Cx<T>*)lv.vpre, lv.n(),
                                             (Cx<T>*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx, cl.ny, ih2, om1, st);
@@ -286,6 +287,7 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
   dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY, B);
   const T ih2 = static_cast<T>(1.0 / (lv.h * lv.h));
   const T om1 = static_cast<T>(1.0 - h.p.omega);
+  ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
   kern<<<grid, kVThreads, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const Cx<T>*)lv.wDinv,
                                             (const Cx<T>*)lv.vpre, lv.n(), (const Cx<T>*)cl.vfin, cl.n(),
                                             cl.nx, cl.ny, out, out_stride, lv.nx, lv.ny, ih2, om1, st);

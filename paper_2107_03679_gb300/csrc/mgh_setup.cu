@@ -419,6 +419,7 @@ mgh_status setup_contrast(Handle& h, const double* f_d) {
   int info = 0;
   MGH_CUDA(cudaMemcpyAsync(&info, h.lu_info, sizeof(int), cudaMemcpyDeviceToHost, s));
   MGH_CUDA(cudaStreamSynchronize(s));
+  MGH_TRY(prof_flush(h));
   if (info != 0) return MGH_INVALID_ARG;   // singular coarsest operator
   h.contrast_set = true;
   return MGH_OK;
@@ -428,6 +429,7 @@ mgh_status launch_coarse_apply(Handle& h, const void* b, size_t b_stride, void* 
                                const RhsState* st, bool fp64_io) {
   const int n = h.nc;
   dim3 grid((n + 127) / 128, B);
+  ProfScope ps(h, st ? P_COARSE : P_OTHER);
   if (fp64_io) {
     MGH_CUDA(cudaFuncSetAttribute(k_coarse_apply<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(cd) * n)));

@@ -179,6 +179,12 @@ class Solver:
                                   capi._ptr(grad))
         return grad, infos
 
+    def profile_enable(self, enable: bool = True) -> None:
+        capi.mgh_profile_enable(self._h, enable)
+
+    def profile_read(self) -> dict:
+        return capi.mgh_profile_read(self._h)
+
     def launch_count(self, reset: bool = False) -> int:
         return capi.mgh_launch_count(self._h, reset)
 
