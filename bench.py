@@ -45,6 +45,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["mgh", "reference"], default="mgh")
     ap.add_argument("--workload", default="ellipses576")
     ap.add_argument("--precision", choices=["mixed32", "fp64"], default=None)
+    ap.add_argument("--angles", type=int, default=None,
+                    help="use only the first N illumination angles (smaller case for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -257,7 +259,9 @@ def gpu_main(args, rank, world, local_rank):
     w = W.WORKLOADS[args.workload]
     precision = args.precision or w.precision
     f_gt, f_step, th, rec = make_inputs(w)
-    B = w.n_angles
+    if args.angles:
+        th = th[:args.angles]
+    B = len(th)
     solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=20000)
     stream = solver.stream
     d_th = torch.from_numpy(th).to(dev)
@@ -400,9 +404,9 @@ def gpu_main(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if precision == "mixed32" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
-                   "angles_per_gpu": B, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
+                   "angles_per_gpu": B, "angles_total": B * world, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
                    "restart": w.restart, "tol": w.tol, "shift": [w.shift_re, w.shift_im],
-                   "step": "set_contrast + 60 forward + crop/sample/misfit + 60 adjoint solves + gradient",
+                   "step": f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient",
                    "solves_per_step": 2 * B, "l2": "inputs larger than L2 (Krylov basis "
                    f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
