@@ -47,6 +47,10 @@ def parse_args(argv=None):
     ap.add_argument("--precision", choices=["mixed32", "fp64"], default=None)
     ap.add_argument("--angles", type=int, default=None,
                     help="use only the first N illumination angles (smaller case for profiling)")
+    ap.add_argument("--restart", type=int, default=None, help="GMRES restart length (default: the workload's)")
+    ap.add_argument("--nu", type=int, default=None, help="pre- and post-smoothing sweeps (default: the workload's)")
+    ap.add_argument("--arnoldi", choices=["df", "fp64"], default="df",
+                    help="mixed precision Arnoldi arithmetic: double-float on FP32 pipes or native FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -257,12 +261,16 @@ def gpu_main(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     w = W.WORKLOADS[args.workload]
+    if args.restart:
+        w.restart = args.restart
+    if args.nu is not None:
+        w.nu1 = w.nu2 = args.nu
     precision = args.precision or w.precision
     f_gt, f_step, th, rec = make_inputs(w)
     if args.angles:
         th = th[:args.angles]
     B = len(th)
-    solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=20000)
+    solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=20000, arnoldi=args.arnoldi)
     stream = solver.stream
     d_th = torch.from_numpy(th).to(dev)
     d_rec = torch.from_numpy(rec).to(dev)
@@ -405,7 +413,7 @@ def gpu_main(args, rank, world, local_rank):
         "dtype": "f32+f64" if precision == "mixed32" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
                    "angles_per_gpu": B, "angles_total": B * world, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
-                   "restart": w.restart, "tol": w.tol, "shift": [w.shift_re, w.shift_im],
+                   "restart": w.restart, "tol": w.tol, "arnoldi": args.arnoldi if precision == "mixed32" else "fp64", "shift": [w.shift_re, w.shift_im],
                    "step": f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient",
                    "solves_per_step": 2 * B, "l2": "inputs larger than L2 (Krylov basis "
                    f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}"},

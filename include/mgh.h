@@ -55,6 +55,12 @@ typedef enum {
   MGH_PREC_MIXED32 = 1      /* multigrid cycle in complex FP32, FP64 outer Krylov and residuals */
 } mgh_precision;
 
+typedef enum {
+  MGH_ARNOLDI_DF = 0,       /* mixed precision: Arnoldi vectors and Gram-Schmidt arithmetic in
+                               double-float (pairs of FP32, ~48-bit significand) on the FP32 pipes */
+  MGH_ARNOLDI_FP64 = 1      /* native FP64 Gram-Schmidt (always used when precision is FP64) */
+} mgh_arnoldi;
+
 /* Solver parameters.  Lengths are in the same unit as h (grid cells when h = 1). */
 typedef struct {
   int nx_int, ny_int;       /* interior Omega size in grid points */
@@ -66,11 +72,12 @@ typedef struct {
   int levels;               /* multigrid levels including the finest, >= 1 (Alg. 2) */
   int nu1, nu2;             /* pre- and post-relaxation sweeps, 0..4 (Alg. 2) */
   double omega;             /* damped-Jacobi weight omega_S in (0, 1] (eq. dampedJ) */
-  int restart;              /* GMRES restart length m, 1..32 */
+  int restart;              /* GMRES restart length m, 1..32 (1..20 with MGH_ARNOLDI_DF) */
   int maxit;                /* maximum Arnoldi steps per right-hand side */
   double tol;               /* stop when ||b - A x||_2 <= tol * ||b||_2 (true FP64 residual) */
   int precision;            /* mgh_precision */
   int batch_max;            /* largest batch B any later call may use; sizes the workspace */
+  int arnoldi;              /* mgh_arnoldi, used when precision is MGH_PREC_MIXED32 */
 } mgh_params;
 
 typedef struct {

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(_HERE, "libmgh.so")
 MGH_OK, MGH_INVALID_ARG, MGH_NOT_CONVERGED, MGH_CUDA_ERROR, MGH_OUT_OF_MEMORY, MGH_TIMEOUT, MGH_NOT_SUPPORTED = range(7)
 MGH_PREC_FP64, MGH_PREC_MIXED32 = 0, 1
 PRECISIONS = {"fp64": MGH_PREC_FP64, "mixed32": MGH_PREC_MIXED32}
+MGH_ARNOLDI_DF, MGH_ARNOLDI_FP64 = 0, 1
+ARNOLDI = {"df": MGH_ARNOLDI_DF, "fp64": MGH_ARNOLDI_FP64}
 
 
 class mgh_params(ctypes.Structure):
@@ -25,7 +27,7 @@ class mgh_params(ctypes.Structure):
         ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
         ("omega", ctypes.c_double),
         ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
-        ("precision", ctypes.c_int), ("batch_max", ctypes.c_int),
+        ("precision", ctypes.c_int), ("batch_max", ctypes.c_int), ("arnoldi", ctypes.c_int),
     ]
 
 

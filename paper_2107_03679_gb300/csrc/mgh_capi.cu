@@ -31,6 +31,9 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
   if (p->restart < 1 || p->restart > kMaxRestart || p->maxit < 1 || !(p->tol > 0.0)) return MGH_INVALID_ARG;
   if (p->precision != MGH_PREC_FP64 && p->precision != MGH_PREC_MIXED32) return MGH_INVALID_ARG;
   if (p->batch_max < 1 || p->batch_max > 65535) return MGH_INVALID_ARG;
+  if (p->arnoldi != MGH_ARNOLDI_DF && p->arnoldi != MGH_ARNOLDI_FP64) return MGH_INVALID_ARG;
+  if (p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_DF && p->restart > kMaxRestartDf)
+    return MGH_INVALID_ARG;
   if (!std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) return MGH_INVALID_ARG;
   const long long nx = p->nx_int + 2LL * p->abl, ny = p->ny_int + 2LL * p->abl;
   if (nx > (1 << 20) || ny > (1 << 20) || nx * ny > (1LL << 31)) return MGH_INVALID_ARG;
@@ -66,7 +69,8 @@ size_t workspace_bytes(const mgh_params& p) {
   t += pad256(16 * B * (m + 1) * N) + pad256(cs * B * m * N) + 3 * pad256(16 * B * N);
   t += pad256(16 * B * m * (m + 1)) + 2 * pad256(16 * B * (m + 1)) + pad256(8 * B * m) + pad256(16 * B * m);
   t += pad256(16 * B * (m + 1)) + pad256(16 * B * m) + pad256(8 * B * (m + 1)) + pad256(sizeof(RhsState) * B);
-  t += pad256(16 * (1216 + B) * (m + 2)) + pad256(8 * (B + 1));
+  t += pad256(16 * (1216 + B) * (2 * m + 4)) + pad256(8 * (B + 1));
+  t += pad256(16 * N) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m);   // DAdf, hpend, coef
   return t;
 }
 
@@ -91,7 +95,7 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->kinv32); cudaFree(h->lu_info); cudaFree(h->V); cudaFree(h->Z); cudaFree(h->W);
   cudaFree(h->T1); cudaFree(h->T2); cudaFree(h->H); cudaFree(h->hcol); cudaFree(h->h2col); cudaFree(h->cs);
   cudaFree(h->sn); cudaFree(h->g); cudaFree(h->y); cudaFree(h->vscale); cudaFree(h->st); cudaFree(h->partial);
-  cudaFree(h->dscratch);
+  cudaFree(h->dscratch); cudaFree(h->DAdf); cudaFree(h->hpend); cudaFree(h->coef);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -218,7 +222,10 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->y, 16 * B * m);
   ALLOC(h->vscale, 8 * B * (m + 1));
   ALLOC(h->st, sizeof(RhsState) * B);
-  ALLOC(h->partial, 16 * (1216 + B) * (m + 2));
+  ALLOC(h->partial, 16 * (1216 + B) * (2 * m + 4));
+  ALLOC(h->DAdf, 16 * N);
+  ALLOC(h->hpend, 16 * B * (m + 1));
+  ALLOC(h->coef, 16 * B * 2 * m);
   ALLOC(h->dscratch, 8 * (B + 1));
 #undef ALLOC
   if (cudaMallocHost((void**)&h->st_host, sizeof(RhsState) * B) != cudaSuccess) {

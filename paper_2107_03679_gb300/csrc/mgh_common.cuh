@@ -79,6 +79,8 @@ struct RhsState {
   double rnorm;      // last true residual norm
   double wnorm2;     // ||A z_j||^2 of the current step
   double norm2;      // ||w'||^2 after orthogonalisation
+  double inv_nu;     // 1 / ||u_j - Q_j s|| of the current step (mixed path)
+  double hjj_re, hjj_im;  // <q_j, w> of the current step (mixed path)
 };
 
 }  // namespace mgh

@@ -13,6 +13,7 @@ namespace mgh {
 
 constexpr int kMaxLevels = 12;
 constexpr int kMaxRestart = 32;
+constexpr int kMaxRestartDf = 20;  // restart limit of the double-float Arnoldi (register budget)
 constexpr int kMaxSweeps = 4;
 constexpr int kMaxCoarse = 4096;   // unknowns on the coarsest level (dense inverse kept on device)
 
@@ -44,6 +45,7 @@ struct Handle {
   // fine operator A (FP64)
   double* f_d = nullptr;     // [ny_int][nx_int] contrast (device copy)
   cd* DA = nullptr;          // diagonal of A
+  float2* DAdf = nullptr;    // the same as double-float planes [2][N] (hi, lo) for the mixed path
 
   // coarsest level: dense inverse, stored transposed (column c of K^{-1} contiguous)
   int nc = 0;
@@ -71,7 +73,9 @@ struct Handle {
   double* vscale = nullptr;  // [Bmax][m+1] multiplier that normalises V[b][i]
   RhsState* st = nullptr;    // [Bmax]
   RhsState* st_host = nullptr;  // pinned host mirror
-  cd* partial = nullptr;     // [Bmax][nblk][m+2] block partial sums
+  cd* hpend = nullptr;       // [Bmax][m+1] column j of H before its delayed correction (mixed path)
+  cd* coef = nullptr;        // [Bmax][2m] Gram-Schmidt coefficients of the current step (mixed path)
+  cd* partial = nullptr;     // [nblk*B][2m+4] block partial sums
   int nblk = 1;              // reduction blocks per right-hand side
   double* dscratch = nullptr;   // small FP64 scratch (loss)
 
@@ -123,6 +127,11 @@ mgh_status vcycle(Handle& h, const cd* in, size_t in_stride, const double* in_sc
 
 // mgh_capi.cu: resolve the recorded event pairs of a synchronised stream into h.acc
 mgh_status prof_flush(Handle& h);
+
+// FP32 multigrid cycle whose level-0 input is an FP32 field (the hi plane of a double-float
+// basis vector) scaled per RHS; output in FP32.
+mgh_status vcycle_f32in(Handle& h, const cf* in, size_t in_stride, const double* in_scale,
+                        size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st);
 
 // mgh_krylov.cu
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);

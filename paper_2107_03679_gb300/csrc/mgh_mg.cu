@@ -21,13 +21,16 @@ namespace {
 
 constexpr int kVThreads = 256;
 
-template <typename T, bool FP64_IN>
+// Right-hand side of a level: complex TIn (FP64 input, FP32 hi plane of a double-float
+// basis vector, or the level's own precision) times a per-RHS scale, converted to T.
+template <typename T, typename TIn>
 __device__ __forceinline__ Cx<T> load_rhs(const void* __restrict__ b, size_t off, double sc) {
-  if constexpr (FP64_IN) {
-    const cd v = reinterpret_cast<const cd*>(b)[off];
+  const Cx<TIn> v = reinterpret_cast<const Cx<TIn>*>(b)[off];
+  if constexpr (sizeof(TIn) == 8) {
     return mk<T>(static_cast<T>(v.re * sc), static_cast<T>(v.im * sc));
   } else {
-    return reinterpret_cast<const Cx<T>*>(b)[off];
+    const T s = static_cast<T>(sc);
+    return mk<T>(static_cast<T>(v.re) * s, static_cast<T>(v.im) * s);
   }
 }
 
@@ -41,7 +44,7 @@ __device__ __forceinline__ Cx<T> jacobi_point(const Cx<T>* v, int idx, int SW, C
 }
 
 // Pre-smoothing + residual + full-weighting restriction on one TX x TY tile of level l.
-template <typename T, int NU, int TX, int TY, bool FP64_IN>
+template <typename T, int NU, int TX, int TY, typename TIn>
 __global__ void __launch_bounds__(kVThreads)
 k_pre(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
       const Cx<T>* __restrict__ D, const Cx<T>* __restrict__ wDinv, Cx<T>* __restrict__ vpre,
@@ -59,7 +62,7 @@ k_pre(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ 
   const int rhs = blockIdx.z;
   if (st && !st[rhs].active) return;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const double sc = (FP64_IN && bscale) ? bscale[rhs * scale_stride] : 1.0;
+  const double sc = bscale ? bscale[rhs * scale_stride] : 1.0;
   const size_t boff = rhs * b_stride;
 
   for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
@@ -68,7 +71,7 @@ k_pre(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ 
     Cx<T> b = czero<T>(), w = czero<T>(), d = czero<T>();
     if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
       const size_t q = (size_t)gy * nx + gx;
-      b = load_rhs<T, FP64_IN>(bin, boff + q, sc);
+      b = load_rhs<T, TIn>(bin, boff + q, sc);
       w = wDinv[q];
       d = D[q];
     }
@@ -146,7 +149,7 @@ k_pre(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ 
 __device__ __forceinline__ int floor_half(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
 
 // Prolongation + correction + post-smoothing on one TX x TY tile of level l.
-template <typename T, int NU, int TX, int TY, bool FP64_IN, typename TOut>
+template <typename T, int NU, int TX, int TY, typename TIn, typename TOut>
 __global__ void __launch_bounds__(kVThreads)
 k_post(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
        const Cx<T>* __restrict__ wDinv, const Cx<T>* __restrict__ vpre, size_t v_stride,
@@ -166,7 +169,7 @@ k_post(const void* __restrict__ bin, size_t b_stride, const double* __restrict__
   if (st && !st[rhs].active) return;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int cx0 = floor_half(x0 - H - 1), cy0 = floor_half(y0 - H - 1);
-  const double sc = (FP64_IN && bscale) ? bscale[rhs * scale_stride] : 1.0;
+  const double sc = bscale ? bscale[rhs * scale_stride] : 1.0;
   const size_t boff = rhs * b_stride;
   const Cx<T>* vp = vpre + rhs * v_stride;
   const Cx<T>* eco = ec + rhs * ec_stride;
@@ -182,7 +185,7 @@ k_post(const void* __restrict__ bin, size_t b_stride, const double* __restrict__
     if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
       const size_t q = (size_t)gy * nx + gx;
       if constexpr (NU >= 1) {
-        b = load_rhs<T, FP64_IN>(bin, boff + q, sc);
+        b = load_rhs<T, TIn>(bin, boff + q, sc);
         w = wDinv[q];
       }
       v = vp[q];
@@ -243,7 +246,7 @@ template <typename T> struct Tile;
 template <> struct Tile<float> { static constexpr int X = 64, Y = 16; };
 template <> struct Tile<double> { static constexpr int X = 32, Y = 16; };
 
-template <typename T, int NU, bool FP64_IN>
+template <typename T, int NU>
 size_t pre_smem() {
   constexpr int H = NU + 1, SW = Tile<T>::X + 2 * H, SH = Tile<T>::Y + 2 * H;
   return 5 * sizeof(Cx<T>) * SW * SH;
@@ -255,14 +258,14 @@ size_t post_smem() {
   return sizeof(Cx<T>) * (4 * SW * SH + CW * CH);
 }
 
-template <typename T, int NU, bool FP64_IN>
+template <typename T, int NU, typename TIn>
 mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
                          size_t scale_stride, int B, const RhsState* st) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
   constexpr int TX = Tile<T>::X, TY = Tile<T>::Y;
-  const size_t smem = pre_smem<T, NU, FP64_IN>();
-  auto kern = k_pre<T, NU, TX, TY, FP64_IN>;
+  const size_t smem = pre_smem<T, NU>();
+  auto kern = k_pre<T, NU, TX, TY, TIn>;
   MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY, B);
   const T ih2 = static_cast<T>(1.0 / (lv.h * lv.h));
@@ -275,14 +278,14 @@ mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, con
   return MGH_OK;
 }
 
-template <typename T, int NU, bool FP64_IN, typename TOut>
+template <typename T, int NU, typename TIn, typename TOut>
 mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
                           size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
   constexpr int TX = Tile<T>::X, TY = Tile<T>::Y;
   const size_t smem = post_smem<T, NU>();
-  auto kern = k_post<T, NU, TX, TY, FP64_IN, TOut>;
+  auto kern = k_post<T, NU, TX, TY, TIn, TOut>;
   MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY, B);
   const T ih2 = static_cast<T>(1.0 / (lv.h * lv.h));
@@ -295,58 +298,64 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
   return MGH_OK;
 }
 
-template <typename T, bool FP64_IN>
+template <typename T, typename TIn>
 mgh_status launch_pre(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
                       size_t scale_stride, int B, const RhsState* st) {
   switch (h.p.nu1) {
-    case 0: return launch_pre_nu<T, 0, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
-    case 1: return launch_pre_nu<T, 1, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
-    case 2: return launch_pre_nu<T, 2, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
-    case 3: return launch_pre_nu<T, 3, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
-    case 4: return launch_pre_nu<T, 4, FP64_IN>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 0: return launch_pre_nu<T, 0, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 1: return launch_pre_nu<T, 1, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 2: return launch_pre_nu<T, 2, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 3: return launch_pre_nu<T, 3, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 4: return launch_pre_nu<T, 4, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
   }
   return MGH_INVALID_ARG;
 }
 
-template <typename T, bool FP64_IN, typename TOut>
+template <typename T, typename TIn, typename TOut>
 mgh_status launch_post(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
                        size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st) {
   switch (h.p.nu2) {
-    case 0: return launch_post_nu<T, 0, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
-    case 1: return launch_post_nu<T, 1, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
-    case 2: return launch_post_nu<T, 2, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
-    case 3: return launch_post_nu<T, 3, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
-    case 4: return launch_post_nu<T, 4, FP64_IN, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 0: return launch_post_nu<T, 0, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 1: return launch_post_nu<T, 1, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 2: return launch_post_nu<T, 2, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 3: return launch_post_nu<T, 3, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 4: return launch_post_nu<T, 4, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
   }
   return MGH_INVALID_ARG;
 }
 
-template <typename T>
-mgh_status vcycle_t(Handle& h, const cd* in, size_t in_stride, const double* in_scale, size_t scale_stride,
+template <typename T, typename TIn>
+mgh_status vcycle_t(Handle& h, const void* in, size_t in_stride, const double* in_scale, size_t scale_stride,
                     void* out, size_t out_stride, bool out_fp64, int B, const RhsState* st) {
   const int L = h.L;
-  // down: level 0 reads the FP64 input, coarser levels their restricted right-hand side
-  MGH_TRY((launch_pre<T, true>(h, 0, in, in_stride, in_scale, scale_stride, B, st)));
+  // down: level 0 reads the input, coarser levels their restricted right-hand side
+  MGH_TRY((launch_pre<T, TIn>(h, 0, in, in_stride, in_scale, scale_stride, B, st)));
   for (int l = 1; l + 1 < L; ++l)
-    MGH_TRY((launch_pre<T, false>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, B, st)));
+    MGH_TRY((launch_pre<T, T>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, B, st)));
   // coarsest: exact solve
   const Level& cl = h.lev[L - 1];
   MGH_TRY(launch_coarse_apply(h, cl.b, cl.n(), cl.vfin, cl.n(), B, st, sizeof(T) == 8));
   // up
   for (int l = L - 2; l >= 1; --l)
-    MGH_TRY((launch_post<T, false, T>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, (Cx<T>*)h.lev[l].vfin,
-                                       h.lev[l].n(), B, st)));
+    MGH_TRY((launch_post<T, T, T>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, (Cx<T>*)h.lev[l].vfin,
+                                  h.lev[l].n(), B, st)));
   if (out_fp64)
-    return launch_post<T, true, double>(h, 0, in, in_stride, in_scale, scale_stride, (cd*)out, out_stride, B, st);
-  return launch_post<T, true, T>(h, 0, in, in_stride, in_scale, scale_stride, (Cx<T>*)out, out_stride, B, st);
+    return launch_post<T, TIn, double>(h, 0, in, in_stride, in_scale, scale_stride, (cd*)out, out_stride, B, st);
+  return launch_post<T, TIn, T>(h, 0, in, in_stride, in_scale, scale_stride, (Cx<T>*)out, out_stride, B, st);
 }
 
 }  // namespace
 
 mgh_status vcycle(Handle& h, const cd* in, size_t in_stride, const double* in_scale, size_t scale_stride,
                   void* out, size_t out_stride, bool out_fp64, int B, const RhsState* st) {
-  if (h.fp64) return vcycle_t<double>(h, in, in_stride, in_scale, scale_stride, out, out_stride, out_fp64, B, st);
-  return vcycle_t<float>(h, in, in_stride, in_scale, scale_stride, out, out_stride, out_fp64, B, st);
+  if (h.fp64)
+    return vcycle_t<double, double>(h, in, in_stride, in_scale, scale_stride, out, out_stride, out_fp64, B, st);
+  return vcycle_t<float, double>(h, in, in_stride, in_scale, scale_stride, out, out_stride, out_fp64, B, st);
+}
+
+mgh_status vcycle_f32in(Handle& h, const cf* in, size_t in_stride, const double* in_scale, size_t scale_stride,
+                        cf* out, size_t out_stride, int B, const RhsState* st) {
+  return vcycle_t<float, float>(h, in, in_stride, in_scale, scale_stride, out, out_stride, false, B, st);
 }
 
 }  // namespace mgh

@@ -213,6 +213,16 @@ __global__ void k_band_inverse(const cd* __restrict__ band, const int* __restric
   for (int r = lane; r < n; r += 32) kinvT[(size_t)k * n + r] = y[r];
 }
 
+// Split a complex FP64 array into double-float planes: hi[q] = (float)v, lo[q] = (float)(v - hi).
+__global__ void k_split_df(const cd* __restrict__ a, float2* __restrict__ hi, float2* __restrict__ lo, size_t n) {
+  const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const cd v = a[q];
+  const float rh = (float)v.re, ih = (float)v.im;
+  hi[q] = make_float2(rh, ih);
+  lo[q] = make_float2((float)(v.re - (double)rh), (float)(v.im - (double)ih));
+}
+
 __global__ void k_to_float(const cd* __restrict__ a, cf* __restrict__ b, size_t n) {
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (q < n) b[q] = ccast<float>(a[q]);
@@ -385,6 +395,8 @@ mgh_status setup_contrast(Handle& h, const double* f_d) {
   // fine operator A (unshifted)
   da.nx = h.nx; da.ny = h.ny; da.scale = 1; da.h = p.h; da.kap_re = 1.0; da.kap_im = 0.0;
   k_level_diag<double><<<blocks_for(h.N), kThreads, 0, s>>>(h.lev[0].c, da, h.DA, nullptr);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  k_split_df<<<blocks_for(h.N), kThreads, 0, s>>>(h.DA, h.DAdf, h.DAdf + h.N, h.N);
   MGH_CHECK_LAUNCH(); h.launches++;
   // K_kappa on every level
   da.kap_re = p.shift_re; da.kap_im = p.shift_im;
