@@ -140,12 +140,27 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- algorithmic bytes
-def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict) -> dict:
+def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, df: bool) -> dict:
     """Minimal DRAM bytes of each kernel class from the engine counters (fields read once,
     per-grid coefficient arrays counted once per launch).  N = fine points, cs = bytes of one
     complex number of the multigrid precision."""
     steps = prof["arnoldi_steps"]
     c16 = 16
+    if df:
+        # double-float Arnoldi (mixed path): the V-cycle reads the 8-byte hi plane of u_j
+        return {
+            "vcycle_pre_l0": steps * N * (8 + cs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
+            "vcycle_post_l0": steps * N * (8 + 2 * cs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
+            # pass 1: read z_j (FP32) and u_j, write w, read the j final basis vectors; D_A planes per launch
+            "matvec_dots": steps * N * (cs + 2 * c16) + prof["basis_reads"] * N * c16
+            + launches["matvec_dots"] * c16 * N,
+            # pass 2: read u_j and w, write q_j and u_{j+1}, read the j final basis vectors
+            "gs_update": steps * N * 4 * c16 + prof["basis_reads"] * N * c16,
+            # cycle tail: read u_m and the m basis vectors
+            "gs_reorth": prof["reorth_reads"] * N * c16 + prof["updates"] * N * c16,
+            "true_residual": prof["residuals"] * N * 3 * c16,
+            "x_update": prof["updates"] * N * 2 * c16 + prof["update_reads"] * N * cs,
+        }
     out = {
         # level-0 pre-smoothing + residual + restriction: read b (FP64), write v (cs), write the
         # restricted residual (cs/4 per fine point); D and w/D once per launch
@@ -373,7 +388,7 @@ def gpu_main(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel class (CUDA events over the timed region)
     cs = 16 if precision == "fp64" else 8
     N = solver.N
-    alg = algorithmic_bytes(prof, N, cs, prof["launches"])
+    alg = algorithmic_bytes(prof, N, cs, prof["launches"], precision == "mixed32" and args.arnoldi == "df")
     ms_cls = prof["ms"]
     dom = max(ms_cls, key=lambda k: ms_cls[k])
     peak, peak_kind = load_peaks()

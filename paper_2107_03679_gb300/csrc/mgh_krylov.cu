@@ -722,6 +722,7 @@ __global__ void k_df_scalars(KArgs a, int j, int tail, const cd* __restrict__ pa
   if (threadIdx.x != 0) return;
   const int m = a.m;
   RhsState& S = st[rhs];
+  if (tail) S.rsum += j;
   const cd* s = sh;
   const cd* t = sh + j;
   const double alpha = sh[2 * j].re;

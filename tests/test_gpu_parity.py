@@ -130,6 +130,30 @@ def test_solve_matches_direct_solve(precision, tol, bound):
         assert true <= tol * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("restart", [4, 10, 20])
+def test_mixed_arnoldi_variants_agree(restart):
+    """Double-float Arnoldi (FP32 pipes) and native-FP64 Arnoldi reach the same solution."""
+    torch = torch_cuda()
+    w = ragged(precision="mixed32", levels=4, nu1=1, nu2=1, tol=1e-10, restart=restart)
+    p, f, o = oracle_solver(w)
+    th = W.angles(w)
+    b = np.stack([O.rhs(p, f, t) for t in th])
+    out = {}
+    for ar in ("df", "fp64"):
+        s = make_solver(w, B=3, maxit=3000, arnoldi=ar)
+        s.set_contrast(to_t(f, torch))
+        x, infos = s.solve(to_t(b, torch))
+        assert all(i["converged"] for i in infos), (ar, infos)
+        out[ar] = (x.cpu().numpy(), [i["iterations"] for i in infos])
+    for q in range(3):
+        ref = O.direct_solve(p, o.D, b[q])
+        assert rel(out["df"][0][q], ref) < 1e-5
+        assert rel(out["df"][0][q], out["fp64"][0][q]) < 1e-5
+    # same Krylov method: iteration counts within a few steps
+    for a, c in zip(out["df"][1], out["fp64"][1]):
+        assert abs(a - c) <= max(3, 0.1 * c)
+
+
 def test_forward_matches_oracle_forward():
     torch = torch_cuda()
     w = ragged(precision="fp64", tol=1e-11)
