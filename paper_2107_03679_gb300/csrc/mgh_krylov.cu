@@ -89,8 +89,10 @@ k_matvec_dots(KArgs a, int j, const Cx<TZ>* __restrict__ Z, const cd* __restrict
   for (int i = 0; i < NV; ++i) acc[i] = czero<double>();
   double nrm = 0.0;
   const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
-  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads) {
-    const int m = (int)(q % a.nx), n = (int)(q / a.nx);
+  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
+  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
     cd s = czero<double>();
     if (m > 0) s = s + load_z(z, q - 1);
     if (m < a.nx - 1) s = s + load_z(z, q + 1);
@@ -322,8 +324,10 @@ k_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const cd
   cd acc[1] = {czero<double>()};
   double bn = 0.0;
   const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
-  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads) {
-    const int m = (int)(q % a.nx), n = (int)(q / a.nx);
+  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
+  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
     cd s = czero<double>();
     if (m > 0) s = s + xb[q - 1];
     if (m < a.nx - 1) s = s + xb[q + 1];
@@ -581,8 +585,10 @@ k_df_pass1(KArgs a, int j, const cf* __restrict__ Z, const float2* __restrict__ 
   df alpha = {0.f, 0.f};
   cdf beta = cdf_zero();
   const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
-  for (size_t q = p0 + threadIdx.x; q < p1; q += kDfThreads) {
-    const int m = (int)(q % a.nx), n = (int)(q / a.nx);
+  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
+  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kDfThreads, m += kDfThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
     // neighbour sum of the FP32 z, exactly in df
     df sr = {0.f, 0.f}, si = {0.f, 0.f};
     if (m > 0) { const cf v = z[q - 1]; df_add1(sr, v.re); df_add1(si, v.im); }
@@ -874,8 +880,10 @@ k_df_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const
   cd acc[1] = {czero<double>()};
   double bn = 0.0;
   const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
-  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads) {
-    const int m = (int)(q % a.nx), n = (int)(q / a.nx);
+  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
+  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
     cd s = czero<double>();
     if (m > 0) s = s + xb[q - 1];
     if (m < a.nx - 1) s = s + xb[q + 1];
@@ -890,6 +898,39 @@ k_df_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const
     bn += cabs2(bv);
   }
   block_reduce_store<1>(acc, 1, bn, 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
+}
+
+// x += sum_{i < jend} y_i z_i with the sum formed in double-float (z_i FP32), added to FP64 x.
+template <int NV>
+__global__ void __launch_bounds__(kKThreads)
+k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, cd* __restrict__ x,
+             const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y;
+  if (st[rhs].done || st[rhs].jend == 0) return;
+  const int je = st[rhs].jend;
+  __shared__ cdf ys[NV];
+  if (threadIdx.x < NV && (int)threadIdx.x < je) ys[threadIdx.x] = cdf_from(y[(size_t)rhs * a.m + threadIdx.x]);
+  __syncthreads();
+  const cf* Zb = Z + (size_t)rhs * a.m * a.N;
+  cd* xb = x + (size_t)rhs * a.N;
+  const size_t p0 = blockIdx.x * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads) {
+    df sr = {0.f, 0.f}, si = {0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (i < je) {
+        const cf z = Zb[(size_t)i * a.N + q];
+        df_fma1(sr, ys[i].re.hi, ys[i].re.lo, z.re);
+        df_fma1(sr, -ys[i].im.hi, -ys[i].im.lo, z.im);
+        df_fma1(si, ys[i].re.hi, ys[i].re.lo, z.im);
+        df_fma1(si, ys[i].im.hi, ys[i].im.lo, z.re);
+      }
+    }
+    cd v = xb[q];
+    v.re += df_to_double(sr);
+    v.im += df_to_double(si);
+    xb[q] = v;
+  }
 }
 
 template <int NV>
@@ -997,7 +1038,16 @@ mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info)
       k_lsq<<<(B + 63) / 64, 64, 0, h.stream>>>(a, h.H, h.g, h.y, h.st, B);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
-    MGH_TRY(xupdate<float>(h, a, B, x));
+    {
+      ProfScope ps(h, P_XUPDATE);
+      const int m = a.m;
+      if (m <= 4) k_df_xupdate<4><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+      else if (m <= 8) k_df_xupdate<8><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+      else if (m <= 12) k_df_xupdate<12><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+      else if (m <= 16) k_df_xupdate<16><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+      else k_df_xupdate<kMaxRestartDf><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
     {
       ProfScope ps(h, P_RESIDUAL);
       k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, Vd, h.partial, h.st);

@@ -57,7 +57,7 @@ __global__ void k_fine_coef(const double* __restrict__ f_d, double* __restrict__
                             int abl, int nx_int, int ny_int, double k2) {
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (q >= (size_t)nx * ny) return;
-  const int m = (int)(q % nx), n = (int)(q / nx);
+  const int n = (int)((unsigned)q / (unsigned)nx), m = (int)((unsigned)q - (unsigned)n * (unsigned)nx);
   const int mi = m - abl, ni = n - abl;
   double v = k2;
   if (mi >= 0 && mi < nx_int && ni >= 0 && ni < ny_int) v = k2 * (1.0 + f_d[(size_t)ni * nx_int + mi]);
@@ -70,7 +70,7 @@ __global__ void k_restrict_coef(const double* __restrict__ cf_, double* __restri
                                 int nxc, int nyc, double k2) {
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (q >= (size_t)nxc * nyc) return;
-  const int i = (int)(q % nxc), j = (int)(q / nxc);
+  const int j = (int)((unsigned)q / (unsigned)nxc), i = (int)((unsigned)q - (unsigned)j * (unsigned)nxc);
   if (i == 0 || j == 0 || i == nxc - 1 || j == nyc - 1) { cc[q] = k2; return; }
   double s = 0.0;
   for (int dn = -1; dn <= 1; ++dn)
@@ -88,7 +88,7 @@ __global__ void k_level_diag(const double* __restrict__ c, DiagArgs a, Cx<T>* __
                              Cx<T>* __restrict__ wDinv) {
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (q >= (size_t)a.nx * a.ny) return;
-  const int i = (int)(q % a.nx), j = (int)(q / a.nx);
+  const int j = (int)((unsigned)q / (unsigned)a.nx), i = (int)((unsigned)q - (unsigned)j * (unsigned)a.nx);
   const cd d = level_diag(a, i, j, c[q]);
   D[q] = ccast<T>(d);
   if (wDinv) {
@@ -261,7 +261,7 @@ __global__ void k_incident(const double* __restrict__ theta, const double* __res
   const size_t N = (size_t)nx * ny;
   if (q >= N) return;
   const int rhs = blockIdx.y;
-  const int m = (int)(q % nx), n = (int)(q / nx);
+  const int n = (int)((unsigned)q / (unsigned)nx), m = (int)((unsigned)q - (unsigned)n * (unsigned)nx);
   double s = 1.0;
   if (f_d) {
     const int mi = m - abl, ni = n - abl;
@@ -280,7 +280,7 @@ __global__ void k_apply_A(const cd* __restrict__ DA, const cd* __restrict__ x, c
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   const size_t N = (size_t)nx * ny;
   if (q >= N) return;
-  const int m = (int)(q % nx), n = (int)(q / nx);
+  const int n = (int)((unsigned)q / (unsigned)nx), m = (int)((unsigned)q - (unsigned)n * (unsigned)nx);
   const cd* xb = x + blockIdx.y * N;
   cd s = czero<double>();
   if (m > 0) s = s + xb[q - 1];
@@ -295,7 +295,7 @@ __global__ void k_crop(const cd* __restrict__ u, cd* __restrict__ out, int nx, i
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   const size_t Ni = (size_t)nx_int * ny_int;
   if (q >= Ni) return;
-  const int mi = (int)(q % nx_int), ni = (int)(q / nx_int);
+  const int ni = (int)((unsigned)q / (unsigned)nx_int), mi = (int)((unsigned)q - (unsigned)ni * (unsigned)nx_int);
   out[blockIdx.y * Ni + q] = u[blockIdx.y * (size_t)nx * ny + (size_t)(ni + abl) * nx + mi + abl];
 }
 
@@ -355,7 +355,7 @@ __global__ void k_gradient(const double* __restrict__ theta, const cd* __restric
                            int ny_int, double h, double k, double* __restrict__ grad) {
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (q >= (size_t)nx_int * ny_int) return;
-  const int mi = (int)(q % nx_int), ni = (int)(q / nx_int);
+  const int ni = (int)((unsigned)q / (unsigned)nx_int), mi = (int)((unsigned)q - (unsigned)ni * (unsigned)nx_int);
   const int m = mi + abl, n = ni + abl;
   const size_t N = (size_t)nx * ny, p = (size_t)n * nx + m;
   double acc = 0.0;

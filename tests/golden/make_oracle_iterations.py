@@ -37,7 +37,8 @@ def main(name):
     G[rec] = np.conj(r)
     _, info_a = s.solve(G.reshape(p.ny, p.nx))
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
-    data[name] = {"angle_index": 0, "contrast": "0.9 x ground-truth phantom", "tol": w.tol,
+    data[name] = {"angle_index": 0, "contrast": "0.9 x ground-truth phantom", "tol": w.tol, "restart": w.restart,
+                  "levels": w.levels, "nu": [w.nu1, w.nu2],
                   "forward_iterations": info_f.iterations, "adjoint_iterations": info_a.iterations,
                   "forward_converged": info_f.converged, "adjoint_converged": info_a.converged}
     with open(OUT, "w") as fh:
