@@ -206,6 +206,24 @@ mgh_status mgh_profile_enable(mgh_handle* h, int enable);
 /* Synchronise the handle's stream and return the profile accumulated since it was enabled. */
 mgh_status mgh_profile_read(mgh_handle* h, mgh_profile* out);
 
+/* Allocation-free variant of mgh_misfit (the paper has no counterpart: it is a service of this
+ * library).  For callers that cannot allocate device memory: for example code whose device
+ * memory is all handed out by a pool it does not own, or that must not call cudaMalloc because
+ * cudaMalloc may synchronise the device.  No handle is needed and nothing is allocated: the
+ * per-RHS partial losses live in a static device array of this library (32 KiB per GPU, held
+ * until the process exits).
+ *   nx, ny       extended grid size of the fields (u and G are [B][ny][nx])
+ *   u, y, rec, M, r, G   as in mgh_misfit (device; r and G may be NULL; receivers distinct)
+ *   B            1..4096 right-hand sides; larger B returns MGH_INVALID_ARG
+ *   loss_dev     device double receiving 1/2 sum_q ||S u_q - y_q||^2
+ *   cuda_stream  cudaStream_t the work is queued on (NULL = legacy default stream)
+ * The first call on a device looks up the static array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (different streams, no ordering between them) race on it. */
+mgh_status mgh_misfit_noalloc(int nx, int ny, const mgh_cdouble* u, const mgh_cdouble* y, int B,
+                              const int64_t* rec, int M, mgh_cdouble* r, mgh_cdouble* G,
+                              double* loss_dev, void* cuda_stream);
+
 /* Kernel launches issued by this handle since creation (or since the last reset). */
 uint64_t mgh_launch_count(const mgh_handle* h, int reset);
 

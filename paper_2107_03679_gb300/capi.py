@@ -84,6 +84,7 @@ def _load():
         "mgh_sample": (S, [P, P, I, P, I, P]),
         "mgh_scatter": (S, [P, P, I, P, I, P]),
         "mgh_misfit": (S, [P, P, P, I, P, I, P, P, ctypes.POINTER(D)]),
+        "mgh_misfit_noalloc": (S, [I, I, P, P, I, P, I, P, P, P, P]),
         "mgh_gradient": (S, [P, P, P, P, I, P, info_p]),
         "mgh_profile_enable": (S, [P, I]),
         "mgh_profile_read": (S, [P, ctypes.POINTER(mgh_profile)]),
@@ -105,7 +106,7 @@ EXPORTED = [
     "mgh_default_params", "mgh_workspace_bytes", "mgh_create", "mgh_destroy", "mgh_set_contrast",
     "mgh_incident_field", "mgh_rhs", "mgh_apply", "mgh_precondition", "mgh_coarse_solve",
     "mgh_level_shape", "mgh_level_coefficient", "mgh_solve", "mgh_forward", "mgh_crop", "mgh_sample",
-    "mgh_scatter", "mgh_misfit", "mgh_gradient", "mgh_profile_enable", "mgh_profile_read", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
+    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_profile_enable", "mgh_profile_read", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
 ]
 
 
@@ -226,6 +227,11 @@ def mgh_misfit(h, u, y, B, rec, M, r, G, want_loss=True):
     loss = ctypes.c_double(0.0)
     _check("mgh_misfit", _lib.mgh_misfit(h, u, y, B, rec, M, r, G, ctypes.byref(loss) if want_loss else None))
     return loss.value
+
+
+def mgh_misfit_noalloc(nx, ny, u, y, B, rec, M, r, G, loss_dev, stream):
+    _check("mgh_misfit_noalloc", _lib.mgh_misfit_noalloc(nx, ny, u, y, B, rec, M, r, G, loss_dev,
+                                                         ctypes.c_void_p(stream)))
 
 
 def mgh_gradient(h, theta, u_sc, G, B, grad, allow_not_converged=True):
