@@ -54,7 +54,7 @@ size_t workspace_bytes(const mgh_params& p) {
   validate(&p, nxl, nyl);
   const size_t B = p.batch_max, m = p.restart;
   const size_t cs = p.precision == MGH_PREC_FP64 ? 16 : 8;
-  const size_t N = (size_t)nxl[0] * nyl[0];
+  const size_t N = (size_t)nxl[0] * nyl[0], Np = (N + 63) / 64 * 64;
   size_t t = 0;
   for (int l = 0; l < p.levels; ++l) {
     const size_t n = (size_t)nxl[l] * nyl[l];
@@ -66,11 +66,11 @@ size_t workspace_bytes(const mgh_params& p) {
   const size_t W = 3 * (size_t)nxl[p.levels - 1] + 1;
   t += pad256(8 * (size_t)p.nx_int * p.ny_int) + pad256(16 * N);
   t += pad256(16 * nc * W) + pad256(4 * nc) + pad256(16 * nc * nc) + pad256(8 * nc * nc) + pad256(4);
-  t += pad256(16 * B * (m + 1) * N) + pad256(cs * B * m * N) + 3 * pad256(16 * B * N);
+  t += pad256(16 * B * (m + 1) * Np) + pad256(cs * B * m * N) + pad256(16 * B * Np) + 2 * pad256(16 * B * N);
   t += pad256(16 * B * m * (m + 1)) + 2 * pad256(16 * B * (m + 1)) + pad256(8 * B * m) + pad256(16 * B * m);
   t += pad256(16 * B * (m + 1)) + pad256(16 * B * m) + pad256(8 * B * (m + 1)) + pad256(sizeof(RhsState) * B);
   t += pad256(16 * (1216 + B) * (2 * m + 4)) + pad256(8 * (B + 1));
-  t += pad256(16 * N) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m);   // DAdf, hpend, coef
+  t += pad256(16 * Np) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m) + pad256(4);   // DAdf, hpend, coef, err
   return t;
 }
 
@@ -96,6 +96,7 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->T1); cudaFree(h->T2); cudaFree(h->H); cudaFree(h->hcol); cudaFree(h->h2col); cudaFree(h->cs);
   cudaFree(h->sn); cudaFree(h->g); cudaFree(h->y); cudaFree(h->vscale); cudaFree(h->st); cudaFree(h->partial);
   cudaFree(h->dscratch); cudaFree(h->DAdf); cudaFree(h->hpend); cudaFree(h->coef);
+  cudaFree(h->dev_err);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -177,12 +178,13 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   h->p = *p;
   h->stream = (cudaStream_t)cuda_stream;
   h->nx = nxl[0]; h->ny = nyl[0]; h->N = (size_t)h->nx * h->ny;
+  h->Np = (h->N + 63) / 64 * 64;
   h->L = p->levels;
   h->fp64 = p->precision == MGH_PREC_FP64;
   h->csize = h->fp64 ? 16 : 8;
   h->m = p->restart;
   h->Bmax = p->batch_max;
-  const size_t B = h->Bmax, m = h->m, N = h->N, cs = h->csize;
+  const size_t B = h->Bmax, m = h->m, N = h->N, Np = h->Np, cs = h->csize;
   mgh_status s = MGH_OK;
 #define ALLOC(ptr, bytes) do { s = dev_alloc(&(ptr), (bytes)); if (s != MGH_OK) { free_handle(h); return s; } } while (0)
   double hl = p->h;
@@ -208,9 +210,9 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->kinv64, 16 * nc * nc);
   if (!h->fp64) ALLOC(h->kinv32, 8 * nc * nc);
   ALLOC(h->lu_info, 4);
-  ALLOC(h->V, 16 * B * (m + 1) * N);
+  ALLOC(h->V, 16 * B * (m + 1) * Np);
   ALLOC(h->Z, cs * B * m * N);
-  ALLOC(h->W, 16 * B * N);
+  ALLOC(h->W, 16 * B * Np);
   ALLOC(h->T1, 16 * B * N);
   ALLOC(h->T2, 16 * B * N);
   ALLOC(h->H, 16 * B * m * (m + 1));
@@ -223,7 +225,8 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->vscale, 8 * B * (m + 1));
   ALLOC(h->st, sizeof(RhsState) * B);
   ALLOC(h->partial, 16 * (1216 + B) * (2 * m + 4));
-  ALLOC(h->DAdf, 16 * N);
+  ALLOC(h->DAdf, 16 * Np);
+  ALLOC(h->dev_err, 4);
   ALLOC(h->hpend, 16 * B * (m + 1));
   ALLOC(h->coef, 16 * B * 2 * m);
   ALLOC(h->dscratch, 8 * (B + 1));

@@ -36,6 +36,7 @@ struct Handle {
   cudaStream_t stream = nullptr;
   int nx = 0, ny = 0;
   size_t N = 0;              // points of the extended grid
+  size_t Np = 0;             // plane stride of double-float fields: N rounded up to 64 points
   int L = 0;                 // levels
   bool fp64 = true;          // cycle precision: double (true) or float (false)
   size_t csize = 16;         // bytes per complex of the cycle precision
@@ -78,6 +79,7 @@ struct Handle {
   cd* partial = nullptr;     // [nblk*B][2m+4] block partial sums
   int nblk = 1;              // reduction blocks per right-hand side
   double* dscratch = nullptr;   // small FP64 scratch (loss)
+  int* dev_err = nullptr;       // device error word written by kernels with bounded waits
 
   uint64_t launches = 0;
 
@@ -132,6 +134,11 @@ mgh_status prof_flush(Handle& h);
 // basis vector) scaled per RHS; output in FP32.
 mgh_status vcycle_f32in(Handle& h, const cf* in, size_t in_stride, const double* in_scale,
                         size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st);
+
+// mgh_krylov_df.cu: mixed-precision engine with double-float Arnoldi
+mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
+// device flag set by a kernel whose bounded wait gave up (0 = none)
+constexpr int kErrTimeout = 1;
 
 // mgh_krylov.cu
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);

@@ -1,0 +1,723 @@
+// Mixed-precision FGMRES engine: Arnoldi in double-float arithmetic on the FP32 pipes, with
+// classical Gram-Schmidt whose second pass is delayed by one step (low-synchronisation GMRES;
+// Swirydowicz et al. 2020, Bielich et al. 2022), so that each Arnoldi step reads the basis twice.
+//
+//   step j holds q_0..q_{j-1} (final, orthonormal) and u_j, the candidate left by step j-1
+//   (orthogonalised once).  z_j = M^{-1}(u_j / ||u_j||), w = A z_j.
+//   pass 1   one sweep computes s = Q^H u_j, t = Q^H w, alpha = ||u_j||^2, beta = u_j^H w
+//   scalars  nu = sqrt(alpha - ||s||^2); q_j = (u_j - Q s)/nu; h_{:,j} = (t, (beta - s^H t)/nu);
+//            column j-1 is finalised with the correction s and h_{j,j-1} = nu, then rotated
+//   pass 2   one sweep writes q_j over u_j and u_{j+1} = w - Q t - h_jj q_j
+//
+// The relation A z_j = sum_{i<=j+1} h_ij q_i holds exactly for the stored z_j, which is what
+// flexible GMRES needs; the least-squares problem and the stopping estimate lag one step behind
+// the preconditioner application.  A tail pass at the end of a cycle finalises the last column.
+//
+// Each block streams its contiguous chunk of points through a ring of shared-memory stages
+// filled by bulk copies (TMA, cp.async.bulk) that complete on mbarriers, so loads of later tiles
+// are in flight while the FP32 pipes work on the current one.  Double-float fields (basis
+// vectors, w, the operator diagonal) are pairs of float2 planes (hi, lo) with plane stride Np.
+#include <cmath>
+
+#include "mgh_df.cuh"
+#include "mgh_krylov_common.cuh"
+#include "mgh_tma.cuh"
+
+namespace mgh {
+
+namespace {
+
+constexpr int kDfThreads = kTile;      // one point per thread per tile
+constexpr int kMaxStages = 4;
+constexpr int kMaxPlanes = 2 * kMaxRestartDf + 4;
+constexpr int kSmemHeader = 512;      // mbarriers + plane pointer table, before the stage buffers
+constexpr size_t kStageBudget = 96 * 1024;   // two blocks of 256 threads fit on one SM
+
+// ---------------------------------------------------------------- double-float reductions
+__device__ __forceinline__ df df_add(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  df r;
+  two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+// Stage buffer and pipeline bookkeeping of one block.
+struct Pipe {
+  uint64_t* bar;
+  const float2** src;
+  float2* buf;
+  int S, P, ntiles;
+  size_t p0, p1;
+
+  __device__ __forceinline__ float2* plane(int slot, int p) const {
+    return buf + ((size_t)slot * P + p) * kTile;
+  }
+
+  // Thread 0: queue the bulk copies of tile k into its slot.
+  __device__ __forceinline__ void issue(int k) const {
+    const int slot = k % S;
+    const size_t start = p0 + (size_t)k * kTile;
+    const int n = (int)((p1 - start) < (size_t)kTile ? (p1 - start) : (size_t)kTile);
+    const uint32_t bytes = (uint32_t)(((n + 1) & ~1) * sizeof(float2));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[slot], bytes * (uint32_t)P);
+    for (int p = 0; p < P; ++p) bulk_load(plane(slot, p), src[p] + start, bytes, &bar[slot]);
+  }
+};
+
+// Set up barriers and the first S tiles; returns the pipeline view of shared memory.
+__device__ __forceinline__ Pipe pipe_begin(unsigned char* smem, int S, int P, size_t p0, size_t p1) {
+  Pipe pp;
+  pp.bar = reinterpret_cast<uint64_t*>(smem);
+  pp.src = reinterpret_cast<const float2**>(smem + 64);
+  pp.buf = reinterpret_cast<float2*>(smem + kSmemHeader);
+  pp.S = S;
+  pp.P = P;
+  pp.p0 = p0;
+  pp.p1 = p1;
+  pp.ntiles = p1 > p0 ? (int)((p1 - p0 + kTile - 1) / kTile) : 0;
+  return pp;
+}
+
+__device__ __forceinline__ void pipe_start(const Pipe& pp) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < pp.S; ++s) mbar_init(&pp.bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < pp.S && k < pp.ntiles; ++k) pp.issue(k);
+}
+
+// Wait for tile k.  On timeout every thread returns false together after the block has
+// drained the copies it still has in flight (bounded) and raised the error word.
+__device__ __forceinline__ bool pipe_wait(const Pipe& pp, int k, int* err) {
+  const bool ok = mbar_wait(&pp.bar[k % pp.S], (uint32_t)((k / pp.S) & 1), kWaitLimitNs);
+  if (!__syncthreads_or(!ok)) return true;
+  if (threadIdx.x == 0) {
+    atomicExch(err, kErrTimeout);
+    for (int kk = k; kk < k + pp.S && kk < pp.ntiles; ++kk)
+      mbar_wait(&pp.bar[kk % pp.S], (uint32_t)((kk / pp.S) & 1), kWaitLimitNs);
+  }
+  __syncthreads();
+  return false;
+}
+
+// After all threads finished reading tile k: refill its slot with tile k + S.
+__device__ __forceinline__ void pipe_release(const Pipe& pp, int k) {
+  __syncthreads();
+  if (threadIdx.x == 0 && k + pp.S < pp.ntiles) pp.issue(k + pp.S);
+}
+
+__device__ __forceinline__ const float2* vplane(const float2* V, const KArgs& a, int rhs, int i, int h) {
+  return V + (((size_t)rhs * (a.m + 1) + i) * 2 + h) * a.Np;
+}
+
+// Reduce `nv` df values per thread (vals[0..nv)) over the block and write them, converted to
+// FP64, to out[dst(c)] for c < nv.  Static shared scratch of kMaxVals per warp.
+constexpr int kMaxVals = 4 * kMaxRestartDf + 4;
+
+template <typename Dst>
+__device__ __forceinline__ void block_reduce_df(const df* vals, int nv, Dst dst) {
+  __shared__ float2 sh[kDfThreads / 32][kMaxVals];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = 0; c < nv; ++c) {
+    const df v = warp_sum_df(vals[c]);
+    if (lane == 0) sh[warp][c] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nv; c += kDfThreads) {
+    df acc = {sh[0][c].x, sh[0][c].y};
+    for (int w = 1; w < kDfThreads / 32; ++w) acc = df_add(acc, df{sh[w][c].x, sh[w][c].y});
+    *dst(c) = df_to_double(acc);
+  }
+}
+
+// ---------------------------------------------------------------- pass 1
+// Planes: u_j (hi, lo), D_A (hi, lo), q_0 .. q_{j-1} (hi, lo each).
+// Partial slots: s at [0, j), t at [j, 2j), alpha at 2j, beta at 2j+1.
+template <int NV>
+__global__ void __launch_bounds__(kDfThreads)
+k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __restrict__ DAdf,
+           const float2* __restrict__ V, float2* __restrict__ W, cd* __restrict__ partial,
+           const RhsState* __restrict__ st, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (!st[rhs].active) return;
+  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  const int P = 4 + 2 * j;
+  Pipe pp = pipe_begin(smem, S, P, p0, p1);
+  if (threadIdx.x == 0) {
+    pp.src[0] = vplane(V, a, rhs, j, 0);
+    pp.src[1] = vplane(V, a, rhs, j, 1);
+    pp.src[2] = DAdf;
+    pp.src[3] = DAdf + a.Np;
+    for (int i = 0; i < j; ++i) {
+      pp.src[4 + 2 * i] = vplane(V, a, rhs, i, 0);
+      pp.src[5 + 2 * i] = vplane(V, a, rhs, i, 1);
+    }
+  }
+  pipe_start(pp);
+  const cf* z = Z + ((size_t)rhs * a.m + j) * a.N;
+  float2* wh = W + (size_t)rhs * 2 * a.Np;
+  float2* wl = wh + a.Np;
+  const df ih = df_from_double(a.inv_h2);
+  cdf s[NV], t[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) { s[i] = cdf_zero(); t[i] = cdf_zero(); }
+  df alpha = {0.f, 0.f};
+  cdf beta = cdf_zero();
+  const unsigned q0 = (unsigned)(p0 + threadIdx.x);
+  int n = (int)(q0 / (unsigned)a.nx);
+  int m = (int)(q0 - (unsigned)n * (unsigned)a.nx);
+  for (int k = 0; k < pp.ntiles; ++k, m += kTile) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
+    if (!pipe_wait(pp, k, err)) return;
+    const int slot = k % S;
+    const size_t q = p0 + (size_t)k * kTile + threadIdx.x;
+    if (q < p1) {
+      df sr = {0.f, 0.f}, si = {0.f, 0.f};
+      if (m > 0) { const cf v = z[q - 1]; df_add1(sr, v.re); df_add1(si, v.im); }
+      if (m < a.nx - 1) { const cf v = z[q + 1]; df_add1(sr, v.re); df_add1(si, v.im); }
+      if (n > 0) { const cf v = z[q - a.nx]; df_add1(sr, v.re); df_add1(si, v.im); }
+      if (n < a.ny - 1) { const cf v = z[q + a.nx]; df_add1(sr, v.re); df_add1(si, v.im); }
+      const cf zc = z[q];
+      const float2 dh = pp.plane(slot, 2)[threadIdx.x], dl = pp.plane(slot, 3)[threadIdx.x];
+      cdf w = cdf_zero();
+      // w = D z - (1/h^2) (sum of neighbours)
+      df_fma1(w.re, dh.x, dl.x, zc.re);
+      df_fma1(w.re, -dh.y, -dl.y, zc.im);
+      df_fma1(w.im, dh.x, dl.x, zc.im);
+      df_fma1(w.im, dh.y, dl.y, zc.re);
+      df_fma(w.re, -ih.hi, -ih.lo, sr.hi, sr.lo);
+      df_fma(w.im, -ih.hi, -ih.lo, si.hi, si.lo);
+      w.re = df_norm(w.re);
+      w.im = df_norm(w.im);
+      wh[q] = make_float2(w.re.hi, w.im.hi);
+      wl[q] = make_float2(w.re.lo, w.im.lo);
+      const float2 uh = pp.plane(slot, 0)[threadIdx.x], ul = pp.plane(slot, 1)[threadIdx.x];
+      cdf u;
+      u.re.hi = uh.x; u.im.hi = uh.y; u.re.lo = ul.x; u.im.lo = ul.y;
+      cdf_abs2_acc(alpha, u);
+      cdf_dot_acc(beta, u, w);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        if (i < j) {
+          const float2 qh = pp.plane(slot, 4 + 2 * i)[threadIdx.x], ql = pp.plane(slot, 5 + 2 * i)[threadIdx.x];
+          cdf qi;
+          qi.re.hi = qh.x; qi.im.hi = qh.y; qi.re.lo = ql.x; qi.im.lo = ql.y;
+          cdf_dot_acc(s[i], qi, u);
+          cdf_dot_acc(t[i], qi, w);
+        }
+      }
+    }
+    pipe_release(pp, k);
+  }
+  df vals[4 * NV + 3];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    vals[4 * i] = s[i].re; vals[4 * i + 1] = s[i].im; vals[4 * i + 2] = t[i].re; vals[4 * i + 3] = t[i].im;
+  }
+  // compact: the first 4j entries are the live dots, then alpha, beta
+  vals[4 * j] = alpha;
+  vals[4 * j + 1] = beta.re;
+  vals[4 * j + 2] = beta.im;
+  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
+  block_reduce_df(vals, 4 * j + 3, [&](int c) -> double* {
+    if (c < 4 * j) {
+      const int i = c >> 2, part = c & 3;   // s.re s.im t.re t.im
+      return reinterpret_cast<double*>(out + (part < 2 ? i : j + i)) + (part & 1);
+    }
+    if (c == 4 * j) { out[2 * j].im = 0.0; return reinterpret_cast<double*>(out + 2 * j); }
+    return reinterpret_cast<double*>(out + 2 * j + 1) + (c - 4 * j - 1);
+  });
+}
+
+// ---------------------------------------------------------------- cycle tail
+// s = Q_m^H u_m and alpha = ||u_m||^2; planes u (hi, lo), q_0 .. q_{j-1}; slots as in pass 1.
+template <int NV>
+__global__ void __launch_bounds__(kDfThreads)
+k_df_tail(KArgs a, int j, int S, const float2* __restrict__ V, cd* __restrict__ partial,
+          const RhsState* __restrict__ st, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (!st[rhs].active) return;
+  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  const int P = 2 + 2 * j;
+  Pipe pp = pipe_begin(smem, S, P, p0, p1);
+  if (threadIdx.x == 0) {
+    pp.src[0] = vplane(V, a, rhs, j, 0);
+    pp.src[1] = vplane(V, a, rhs, j, 1);
+    for (int i = 0; i < j; ++i) {
+      pp.src[2 + 2 * i] = vplane(V, a, rhs, i, 0);
+      pp.src[3 + 2 * i] = vplane(V, a, rhs, i, 1);
+    }
+  }
+  pipe_start(pp);
+  cdf s[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) s[i] = cdf_zero();
+  df alpha = {0.f, 0.f};
+  for (int k = 0; k < pp.ntiles; ++k) {
+    if (!pipe_wait(pp, k, err)) return;
+    const int slot = k % S;
+    const size_t q = p0 + (size_t)k * kTile + threadIdx.x;
+    if (q < p1) {
+      const float2 uh = pp.plane(slot, 0)[threadIdx.x], ul = pp.plane(slot, 1)[threadIdx.x];
+      cdf u;
+      u.re.hi = uh.x; u.im.hi = uh.y; u.re.lo = ul.x; u.im.lo = ul.y;
+      cdf_abs2_acc(alpha, u);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        if (i < j) {
+          const float2 qh = pp.plane(slot, 2 + 2 * i)[threadIdx.x], ql = pp.plane(slot, 3 + 2 * i)[threadIdx.x];
+          cdf qi;
+          qi.re.hi = qh.x; qi.im.hi = qh.y; qi.re.lo = ql.x; qi.im.lo = ql.y;
+          cdf_dot_acc(s[i], qi, u);
+        }
+      }
+    }
+    pipe_release(pp, k);
+  }
+  df vals[2 * NV + 1];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) { vals[2 * i] = s[i].re; vals[2 * i + 1] = s[i].im; }
+  vals[2 * j] = alpha;
+  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
+  block_reduce_df(vals, 2 * j + 1, [&](int c) -> double* {
+    if (c < 2 * j) return reinterpret_cast<double*>(out + (c >> 1)) + (c & 1);
+    out[2 * j].im = 0.0;
+    return reinterpret_cast<double*>(out + 2 * j);
+  });
+  if (threadIdx.x < j) out[j + threadIdx.x] = czero<double>();
+  if (threadIdx.x == 0) out[2 * j + 1] = czero<double>();
+}
+
+// ---------------------------------------------------------------- scalars (one block per RHS)
+// Delayed correction and Givens rotation of column j-1, stopping test, pass-2 coefficients.
+__global__ void k_df_scalars(KArgs a, int j, int tail, const cd* __restrict__ partial, cd* __restrict__ H,
+                             double* __restrict__ cs, cd* __restrict__ sn, cd* __restrict__ g, cd* __restrict__ hpend,
+                             cd* __restrict__ coef, RhsState* __restrict__ st, double tol, int maxit) {
+  __shared__ cd sh[2 * kMaxRestart + 4];
+  const int rhs = blockIdx.x;
+  if (!st[rhs].active) return;
+  for (int c = threadIdx.x; c < 2 * j + 2; c += blockDim.x) {
+    cd acc = czero<double>();
+    for (int b = 0; b < a.nblk; ++b) acc = acc + partial[((size_t)rhs * a.nblk + b) * a.pstride + c];
+    sh[c] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int m = a.m;
+  RhsState& S = st[rhs];
+  if (tail) S.rsum += j;
+  const cd* s = sh;
+  const cd* t = sh + j;
+  const double alpha = sh[2 * j].re;
+  const cd beta = sh[2 * j + 1];
+  double ss = 0.0;
+  for (int i = 0; i < j; ++i) ss += cabs2(s[i]);
+  const double nu2 = alpha - ss;
+  const bool breakdown = !(nu2 > 1e-28 * alpha);
+  const double nu = breakdown ? 0.0 : sqrt(nu2);
+  if (j >= 1) {
+    cd col[kMaxRestart + 1];
+    const cd* pend = hpend + (size_t)rhs * (m + 1);
+    for (int i = 0; i < j; ++i) col[i] = pend[i] + s[i];
+    col[j] = mk<double>(nu, 0.0);
+    const int c = j - 1;
+    double* c_ = cs + (size_t)rhs * m;
+    cd* s_ = sn + (size_t)rhs * m;
+    for (int i = 0; i < c; ++i) {
+      const cd tt = c_[i] * col[i] + s_[i] * col[i + 1];
+      col[i + 1] = (-1.0 * cconj(s_[i])) * col[i] + c_[i] * col[i + 1];
+      col[i] = tt;
+    }
+    const cd aa = col[c], bb = col[c + 1];
+    double cc;
+    cd sv;
+    if (bb.re == 0.0 && bb.im == 0.0) { cc = 1.0; sv = czero<double>(); }
+    else if (aa.re == 0.0 && aa.im == 0.0) { cc = 0.0; sv = mk<double>(1.0, 0.0); }
+    else {
+      const double na = sqrt(cabs2(aa)), rho = sqrt(cabs2(aa) + cabs2(bb));
+      cc = na / rho;
+      sv = (1.0 / (na * rho)) * (aa * cconj(bb));
+    }
+    col[c] = cc * col[c] + sv * col[c + 1];
+    c_[c] = cc;
+    s_[c] = sv;
+    cd* gg = g + (size_t)rhs * (m + 1);
+    gg[c + 1] = (-1.0 * cconj(sv)) * gg[c];
+    gg[c] = cc * gg[c];
+    cd* Hc = H + ((size_t)rhs * m + c) * (m + 1);
+    for (int i = 0; i <= c; ++i) Hc[i] = col[i];
+    S.iterations += 1;
+    S.jend = j;
+    const double est = sqrt(cabs2(gg[c + 1])) / S.bnorm;
+    if (tail || !(est > tol) || S.iterations >= maxit || breakdown) { S.active = 0; return; }
+  } else if (breakdown) {
+    S.active = 0;
+    S.jend = 0;
+    return;
+  }
+  cd hjj = beta;
+  for (int i = 0; i < j; ++i) hjj = hjj - cconj(s[i]) * t[i];
+  hjj = (1.0 / nu) * hjj;
+  cd* pend = hpend + (size_t)rhs * (m + 1);
+  cd* cf_ = coef + (size_t)rhs * 2 * m;
+  for (int i = 0; i < j; ++i) { pend[i] = t[i]; cf_[i] = s[i]; cf_[m + i] = t[i]; }
+  pend[j] = hjj;
+  S.inv_nu = 1.0 / nu;
+  S.hjj_re = hjj.re;
+  S.hjj_im = hjj.im;
+  S.vsum += j;
+}
+
+// ---------------------------------------------------------------- pass 2
+// Planes: u_j (hi, lo), w (hi, lo), q_0 .. q_{j-1}.  Writes q_j over u_j and u_{j+1} into slot
+// j+1; partial ||u_{j+1}||^2 in slot 0.
+template <int NV>
+__global__ void __launch_bounds__(kDfThreads)
+k_df_pass2(KArgs a, int j, int S, const cd* __restrict__ coef, float2* __restrict__ V, const float2* __restrict__ W,
+           cd* __restrict__ partial, const RhsState* __restrict__ st, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  const RhsState& SS = st[rhs];
+  if (!SS.active) return;
+  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  const int P = 4 + 2 * j;
+  Pipe pp = pipe_begin(smem, S, P, p0, p1);
+  __shared__ cdf cs_[NV], ct_[NV];
+  if (threadIdx.x == 0) {
+    pp.src[0] = vplane(V, a, rhs, j, 0);
+    pp.src[1] = vplane(V, a, rhs, j, 1);
+    pp.src[2] = W + (size_t)rhs * 2 * a.Np;
+    pp.src[3] = W + ((size_t)rhs * 2 + 1) * a.Np;
+    for (int i = 0; i < j; ++i) {
+      pp.src[4 + 2 * i] = vplane(V, a, rhs, i, 0);
+      pp.src[5 + 2 * i] = vplane(V, a, rhs, i, 1);
+    }
+  }
+  const cd* cf_ = coef + (size_t)rhs * 2 * a.m;
+  for (int i = threadIdx.x; i < j; i += kDfThreads) {
+    cs_[i] = cdf_from(cf_[i]);
+    ct_[i] = cdf_from(cf_[a.m + i]);
+  }
+  pipe_start(pp);   // its __syncthreads also publishes cs_/ct_
+  const df inv_nu = df_from_double(SS.inv_nu);
+  cdf hjj;
+  hjj.re = df_from_double(SS.hjj_re);
+  hjj.im = df_from_double(SS.hjj_im);
+  float2* uh_g = V + (((size_t)rhs * (a.m + 1) + j) * 2) * a.Np;
+  float2* ul_g = uh_g + a.Np;
+  float2* nh_g = V + (((size_t)rhs * (a.m + 1) + j + 1) * 2) * a.Np;
+  float2* nl_g = nh_g + a.Np;
+  df nrm = {0.f, 0.f};
+  for (int k = 0; k < pp.ntiles; ++k) {
+    if (!pipe_wait(pp, k, err)) return;
+    const int slot = k % S;
+    const size_t q = p0 + (size_t)k * kTile + threadIdx.x;
+    if (q < p1) {
+      const float2 a0 = pp.plane(slot, 0)[threadIdx.x], a1 = pp.plane(slot, 1)[threadIdx.x];
+      const float2 b0 = pp.plane(slot, 2)[threadIdx.x], b1 = pp.plane(slot, 3)[threadIdx.x];
+      cdf u, w;
+      u.re.hi = a0.x; u.im.hi = a0.y; u.re.lo = a1.x; u.im.lo = a1.y;
+      w.re.hi = b0.x; w.im.hi = b0.y; w.re.lo = b1.x; w.im.lo = b1.y;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        if (i < j) {
+          const float2 qh = pp.plane(slot, 4 + 2 * i)[threadIdx.x], ql = pp.plane(slot, 5 + 2 * i)[threadIdx.x];
+          cdf qi;
+          qi.re.hi = qh.x; qi.im.hi = qh.y; qi.re.lo = ql.x; qi.im.lo = ql.y;
+          cdf_sub_mul(u, cs_[i], qi);
+          cdf_sub_mul(w, ct_[i], qi);
+        }
+      }
+      u.re = df_norm(u.re);
+      u.im = df_norm(u.im);
+      cdf qj = cdf_zero();
+      df_fma(qj.re, u.re.hi, u.re.lo, inv_nu.hi, inv_nu.lo);
+      df_fma(qj.im, u.im.hi, u.im.lo, inv_nu.hi, inv_nu.lo);
+      qj.re = df_norm(qj.re);
+      qj.im = df_norm(qj.im);
+      uh_g[q] = make_float2(qj.re.hi, qj.im.hi);
+      ul_g[q] = make_float2(qj.re.lo, qj.im.lo);
+      cdf_sub_mul(w, hjj, qj);
+      w.re = df_norm(w.re);
+      w.im = df_norm(w.im);
+      nh_g[q] = make_float2(w.re.hi, w.im.hi);
+      nl_g[q] = make_float2(w.re.lo, w.im.lo);
+      cdf_abs2_acc(nrm, w);
+    }
+    pipe_release(pp, k);
+  }
+  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
+  block_reduce_df(&nrm, 1, [&](int) -> double* { out[0].im = 0.0; return reinterpret_cast<double*>(out); });
+}
+
+// 1/||u_{j+1}|| for the next preconditioner input.
+__global__ void k_df_unorm(KArgs a, int j, const cd* __restrict__ partial, double* __restrict__ vscale,
+                           const RhsState* __restrict__ st) {
+  __shared__ cd sh[1];
+  const int rhs = blockIdx.x;
+  if (!st[rhs].active) return;
+  sum_partials(a, partial, rhs, 1, sh);
+  if (threadIdx.x == 0) {
+    const double n2 = sh[0].re;
+    vscale[(size_t)rhs * (a.m + 1) + j + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+  }
+}
+
+// r = b - A x in FP64, stored as the double-float candidate u_0 in basis slot 0;
+// partial ||r||^2 (slot 0) and ||b||^2 (slot 1).
+__global__ void __launch_bounds__(kKThreads)
+k_df_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const cd* __restrict__ DA,
+              float2* __restrict__ V, cd* __restrict__ partial, const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (st[rhs].done) return;
+  const cd* xb = x + (size_t)rhs * a.N;
+  const cd* bb = b + (size_t)rhs * a.N;
+  float2* rh = V + ((size_t)rhs * (a.m + 1) * 2) * a.Np;
+  float2* rl = rh + a.Np;
+  cd acc[1] = {czero<double>()};
+  double bn = 0.0;
+  const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
+  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
+    cd s = czero<double>();
+    if (m > 0) s = s + xb[q - 1];
+    if (m < a.nx - 1) s = s + xb[q + 1];
+    if (n > 0) s = s + xb[q - a.nx];
+    if (n < a.ny - 1) s = s + xb[q + a.nx];
+    const cd bv = bb[q];
+    const cd rv = bv - (DA[q] * xb[q] - a.inv_h2 * s);
+    const cdf r = cdf_from(rv);
+    rh[q] = make_float2(r.re.hi, r.im.hi);
+    rl[q] = make_float2(r.re.lo, r.im.lo);
+    acc[0].re += cabs2(rv);
+    bn += cabs2(bv);
+  }
+  block_reduce_store<1>(acc, 1, bn, 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
+}
+
+// x += sum_{i < jend} y_i z_i with the sum formed in double-float (z_i FP32), added to FP64 x.
+template <int NV>
+__global__ void __launch_bounds__(kKThreads)
+k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, cd* __restrict__ x,
+             const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y;
+  if (st[rhs].done || st[rhs].jend == 0) return;
+  const int je = st[rhs].jend;
+  __shared__ cdf ys[NV];
+  if (threadIdx.x < NV && (int)threadIdx.x < je) ys[threadIdx.x] = cdf_from(y[(size_t)rhs * a.m + threadIdx.x]);
+  __syncthreads();
+  const cf* Zb = Z + (size_t)rhs * a.m * a.N;
+  cd* xb = x + (size_t)rhs * a.N;
+  const size_t p0 = blockIdx.x * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads) {
+    df sr = {0.f, 0.f}, si = {0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (i < je) {
+        const cf z = Zb[(size_t)i * a.N + q];
+        df_fma1(sr, ys[i].re.hi, ys[i].re.lo, z.re);
+        df_fma1(sr, -ys[i].im.hi, -ys[i].im.lo, z.im);
+        df_fma1(si, ys[i].re.hi, ys[i].re.lo, z.im);
+        df_fma1(si, ys[i].im.hi, ys[i].im.lo, z.re);
+      }
+    }
+    cd v = xb[q];
+    v.re += df_to_double(sr);
+    v.im += df_to_double(si);
+    xb[q] = v;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+// Stages of the shared-memory ring for P planes and the dynamic shared memory they need.
+int stages_for(int P) {
+  const size_t stage = (size_t)P * kTile * sizeof(float2);
+  int S = (int)(kStageBudget / stage);
+  return S < 2 ? 2 : (S > kMaxStages ? kMaxStages : S);
+}
+size_t smem_for(int P, int S) { return kSmemHeader + (size_t)S * P * kTile * sizeof(float2); }
+
+template <typename K>
+mgh_status set_smem(K kern) {
+  MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_for(kMaxPlanes, 2) + 1024));
+  return MGH_OK;
+}
+
+template <int NV>
+mgh_status df_step_nv(Handle& h, const KArgs& a, int j, int B) {
+  static bool init = false;
+  if (!init) {
+    MGH_TRY(set_smem(k_df_pass1<NV>));
+    MGH_TRY(set_smem(k_df_pass2<NV>));
+    MGH_TRY(set_smem(k_df_tail<NV>));
+    init = true;
+  }
+  const dim3 grid(a.nblk, B);
+  float2* V = reinterpret_cast<float2*>(h.V);
+  float2* W = reinterpret_cast<float2*>(h.W);
+  {
+    const int P = 4 + 2 * j, S = stages_for(P);
+    ProfScope ps(h, P_MATVEC_DOTS);
+    k_df_pass1<NV><<<grid, kDfThreads, smem_for(P, S), h.stream>>>(a, j, S, (const cf*)h.Z, h.DAdf, V, W,
+                                                                    h.partial, h.st, h.dev_err);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_df_scalars<<<B, 64, 0, h.stream>>>(a, j, 0, h.partial, h.H, h.cs, h.sn, h.g, h.hpend, h.coef, h.st,
+                                         h.p.tol, h.p.maxit);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    const int P = 4 + 2 * j, S = stages_for(P);
+    ProfScope ps(h, P_UPDATE);
+    k_df_pass2<NV><<<grid, kDfThreads, smem_for(P, S), h.stream>>>(a, j, S, h.coef, V, W, h.partial, h.st,
+                                                                    h.dev_err);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_df_unorm<<<B, 32, 0, h.stream>>>(a, j, h.partial, h.vscale, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  return MGH_OK;
+}
+
+template <int NV>
+mgh_status df_tail_nv(Handle& h, const KArgs& a, int j, int B) {
+  static bool init = false;
+  if (!init) {
+    MGH_TRY(set_smem(k_df_tail<NV>));
+    init = true;
+  }
+  const dim3 grid(a.nblk, B);
+  {
+    const int P = 2 + 2 * j, S = stages_for(P);
+    ProfScope ps(h, P_REORTH);
+    k_df_tail<NV><<<grid, kDfThreads, smem_for(P, S), h.stream>>>(a, j, S, reinterpret_cast<const float2*>(h.V),
+                                                                   h.partial, h.st, h.dev_err);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_df_scalars<<<B, 64, 0, h.stream>>>(a, j, 1, h.partial, h.H, h.cs, h.sn, h.g, h.hpend, h.coef, h.st,
+                                         h.p.tol, h.p.maxit);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  return MGH_OK;
+}
+
+mgh_status df_arnoldi_step(Handle& h, const KArgs& a, int j, int B) {
+  // z_j = M^{-1}(u_j / ||u_j||), reading only the hi plane of u_j
+  const cf* uhi = reinterpret_cast<const cf*>(reinterpret_cast<const float2*>(h.V) + (size_t)j * 2 * a.Np);
+  MGH_TRY(vcycle_f32in(h, uhi, (size_t)(a.m + 1) * 2 * a.Np, h.vscale + j, (size_t)(a.m + 1),
+                       (cf*)h.Z + (size_t)j * a.N, (size_t)a.m * a.N, B, h.st));
+  if (j <= 4) return df_step_nv<4>(h, a, j, B);
+  if (j <= 8) return df_step_nv<8>(h, a, j, B);
+  if (j <= 12) return df_step_nv<12>(h, a, j, B);
+  if (j <= 16) return df_step_nv<16>(h, a, j, B);
+  return df_step_nv<kMaxRestartDf>(h, a, j, B);
+}
+
+mgh_status df_tail(Handle& h, const KArgs& a, int j, int B) {
+  if (j <= 4) return df_tail_nv<4>(h, a, j, B);
+  if (j <= 8) return df_tail_nv<8>(h, a, j, B);
+  if (j <= 12) return df_tail_nv<12>(h, a, j, B);
+  if (j <= 16) return df_tail_nv<16>(h, a, j, B);
+  return df_tail_nv<kMaxRestartDf>(h, a, j, B);
+}
+
+mgh_status df_xupdate(Handle& h, const KArgs& a, int B, cd* x) {
+  const dim3 grid(a.nblk, B);
+  ProfScope ps(h, P_XUPDATE);
+  const int m = a.m;
+  if (m <= 4) k_df_xupdate<4><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+  else if (m <= 8) k_df_xupdate<8><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+  else if (m <= 12) k_df_xupdate<12><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+  else if (m <= 16) k_df_xupdate<16><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+  else k_df_xupdate<kMaxRestartDf><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  return MGH_OK;
+}
+
+}  // namespace
+
+mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
+  KArgs a = make_kargs(h, B);
+  const dim3 grid(a.nblk, B);
+  float2* V = reinterpret_cast<float2*>(h.V);
+  MGH_CUDA(cudaMemsetAsync(h.dev_err, 0, sizeof(int), h.stream));
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_state_reset<<<(B + 63) / 64, 64, 0, h.stream>>>(h.st, B);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_RESIDUAL);
+    k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, V, h.partial, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 1);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_OTHER);
+    k_zero_if_b_zero<<<grid, kKThreads, 0, h.stream>>>(a, x, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  int err_host = 0;
+  for (;;) {
+    MGH_CUDA(cudaMemcpyAsync(h.st_host, h.st, sizeof(RhsState) * B, cudaMemcpyDeviceToHost, h.stream));
+    MGH_CUDA(cudaMemcpyAsync(&err_host, h.dev_err, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    MGH_CUDA(cudaStreamSynchronize(h.stream));
+    MGH_TRY(prof_flush(h));
+    if (err_host) return MGH_TIMEOUT;
+    bool any = false;
+    for (int i = 0; i < B; ++i) any |= (h.st_host[i].done == 0);
+    if (!any) break;
+    for (int j = 0; j < a.m; ++j) MGH_TRY(df_arnoldi_step(h, a, j, B));
+    MGH_TRY(df_tail(h, a, a.m, B));
+    {
+      ProfScope ps(h, P_REDUCE);
+      k_lsq<<<(B + 63) / 64, 64, 0, h.stream>>>(a, h.H, h.g, h.y, h.st, B);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    MGH_TRY(df_xupdate(h, a, B, x));
+    {
+      ProfScope ps(h, P_RESIDUAL);
+      k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, V, h.partial, h.st);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    {
+      ProfScope ps(h, P_REDUCE);
+      k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 0);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+  }
+  return finish_solve(h, B, info);
+}
+
+}  // namespace mgh

@@ -396,7 +396,7 @@ mgh_status setup_contrast(Handle& h, const double* f_d) {
   da.nx = h.nx; da.ny = h.ny; da.scale = 1; da.h = p.h; da.kap_re = 1.0; da.kap_im = 0.0;
   k_level_diag<double><<<blocks_for(h.N), kThreads, 0, s>>>(h.lev[0].c, da, h.DA, nullptr);
   MGH_CHECK_LAUNCH(); h.launches++;
-  k_split_df<<<blocks_for(h.N), kThreads, 0, s>>>(h.DA, h.DAdf, h.DAdf + h.N, h.N);
+  k_split_df<<<blocks_for(h.N), kThreads, 0, s>>>(h.DA, h.DAdf, h.DAdf + h.Np, h.N);
   MGH_CHECK_LAUNCH(); h.launches++;
   // K_kappa on every level
   da.kap_re = p.shift_re; da.kap_im = p.shift_im;
