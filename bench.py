@@ -158,7 +158,9 @@ def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, df: bool) -> 
             "gs_update": steps * N * 4 * c16 + prof["basis_reads"] * N * c16,
             # cycle tail: read u_m and the m basis vectors
             "gs_reorth": prof["reorth_reads"] * N * c16 + prof["updates"] * N * c16,
+            # double-float residual: read x and b, write u_0 (FP64 acceptance checks are rare)
             "true_residual": prof["residuals"] * N * 3 * c16,
+            # double-float iterate update: read and write x, read jend preconditioned vectors
             "x_update": prof["updates"] * N * 2 * c16 + prof["update_reads"] * N * cs,
         }
     out = {

@@ -71,6 +71,7 @@ size_t workspace_bytes(const mgh_params& p) {
   t += pad256(16 * B * (m + 1)) + pad256(16 * B * m) + pad256(8 * B * (m + 1)) + pad256(sizeof(RhsState) * B);
   t += pad256(16 * (1216 + B) * (2 * m + 4)) + pad256(8 * (B + 1));
   t += pad256(16 * Np) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m) + pad256(4);   // DAdf, hpend, coef, err
+  if (p.precision != MGH_PREC_FP64) t += 2 * pad256(16 * B * Np);                        // xdf, bdf
   return t;
 }
 
@@ -96,7 +97,7 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->T1); cudaFree(h->T2); cudaFree(h->H); cudaFree(h->hcol); cudaFree(h->h2col); cudaFree(h->cs);
   cudaFree(h->sn); cudaFree(h->g); cudaFree(h->y); cudaFree(h->vscale); cudaFree(h->st); cudaFree(h->partial);
   cudaFree(h->dscratch); cudaFree(h->DAdf); cudaFree(h->hpend); cudaFree(h->coef);
-  cudaFree(h->dev_err);
+  cudaFree(h->dev_err); cudaFree(h->xdf); cudaFree(h->bdf);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -227,6 +228,7 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->partial, 16 * (1216 + B) * (2 * m + 4));
   ALLOC(h->DAdf, 16 * Np);
   ALLOC(h->dev_err, 4);
+  if (!h->fp64) { ALLOC(h->xdf, 16 * B * Np); ALLOC(h->bdf, 16 * B * Np); }
   ALLOC(h->hpend, 16 * B * (m + 1));
   ALLOC(h->coef, 16 * B * 2 * m);
   ALLOC(h->dscratch, 8 * (B + 1));

@@ -75,12 +75,15 @@ struct RhsState {
   int nres;          // true residual evaluations
   int nupd;          // iterate updates
   int zsum;          // preconditioned vectors read by iterate updates
+  int verify;        // mixed path: the double-float residual met the target, FP64 check pending
+  int nverify;       // FP64 verifications run
   double bnorm;      // ||b||
   double rnorm;      // last true residual norm
   double wnorm2;     // ||A z_j||^2 of the current step
   double norm2;      // ||w'||^2 after orthogonalisation
   double inv_nu;     // 1 / ||u_j - Q_j s|| of the current step (mixed path)
   double hjj_re, hjj_im;  // <q_j, w> of the current step (mixed path)
+  double tol_scale;  // mixed path: factor on tol for the double-float residual (tightened if the FP64 check fails)
 };
 
 }  // namespace mgh

@@ -46,7 +46,9 @@ struct Handle {
   // fine operator A (FP64)
   double* f_d = nullptr;     // [ny_int][nx_int] contrast (device copy)
   cd* DA = nullptr;          // diagonal of A
-  float2* DAdf = nullptr;    // the same as double-float planes [2][N] (hi, lo) for the mixed path
+  float2* DAdf = nullptr;    // the same as double-float planes [2][Np] (hi, lo) for the mixed path
+  float2* xdf = nullptr;     // [Bmax][2][Np] iterate of the mixed path in double-float
+  float2* bdf = nullptr;     // [Bmax][2][Np] right-hand side of the mixed path in double-float
 
   // coarsest level: dense inverse, stored transposed (column c of K^{-1} contiguous)
   int nc = 0;

@@ -481,19 +481,122 @@ __global__ void k_df_unorm(KArgs a, int j, const cd* __restrict__ partial, doubl
   }
 }
 
-// r = b - A x in FP64, stored as the double-float candidate u_0 in basis slot 0;
-// partial ||r||^2 (slot 0) and ||b||^2 (slot 1).
+// FP64 fields [B][N] -> double-float planes [B][2][Np].
+__global__ void k_df_split(const cd* __restrict__ a, float2* __restrict__ out, size_t N, size_t Np) {
+  const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  const int rhs = blockIdx.y;
+  const cdf v = cdf_from(a[rhs * N + q]);
+  float2* h = out + (size_t)rhs * 2 * Np;
+  h[q] = make_float2(v.re.hi, v.im.hi);
+  h[q + Np] = make_float2(v.re.lo, v.im.lo);
+}
+
+// Double-float planes -> FP64 x (every RHS when all != 0, else those awaiting verification).
+__global__ void k_df_join(const float2* __restrict__ xdf, cd* __restrict__ x, size_t N, size_t Np,
+                          const RhsState* __restrict__ st, int all) {
+  const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (q >= N || (!all && !st[rhs].verify)) return;
+  if (st[rhs].bnorm == 0.0) { x[rhs * N + q] = czero<double>(); return; }   // b = 0 gives x = 0
+  const float2* h = xdf + (size_t)rhs * 2 * Np;
+  const float2 a = h[q], b = h[q + Np];
+  x[rhs * N + q] = mk<double>((double)a.x + (double)b.x, (double)a.y + (double)b.y);
+}
+
+__device__ __forceinline__ cdf load_df(const float2* __restrict__ h, size_t Np, size_t q) {
+  const float2 a = h[q], b = h[q + Np];
+  cdf r;
+  r.re.hi = a.x; r.im.hi = a.y; r.re.lo = b.x; r.im.lo = b.y;
+  return r;
+}
+
+// r = b - A x in double-float (x, b double-float planes), written as the candidate u_0 in basis
+// slot 0; partial ||r||^2 (slot 0) and ||b||^2 (slot 1).
 __global__ void __launch_bounds__(kKThreads)
-k_df_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const cd* __restrict__ DA,
+k_df_residual(KArgs a, const float2* __restrict__ bdf, const float2* __restrict__ xdf, const float2* __restrict__ DAdf,
               float2* __restrict__ V, cd* __restrict__ partial, const RhsState* __restrict__ st) {
   const int rhs = blockIdx.y, blk = blockIdx.x;
   if (st[rhs].done) return;
-  const cd* xb = x + (size_t)rhs * a.N;
-  const cd* bb = b + (size_t)rhs * a.N;
+  const float2* xb = xdf + (size_t)rhs * 2 * a.Np;
+  const float2* bb = bdf + (size_t)rhs * 2 * a.Np;
   float2* rh = V + ((size_t)rhs * (a.m + 1) * 2) * a.Np;
   float2* rl = rh + a.Np;
+  const df ih = df_from_double(a.inv_h2);
+  df rn = {0.f, 0.f}, bn = {0.f, 0.f};
+  const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
+  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
+    cdf sum = cdf_zero();
+    if (m > 0) { const cdf v = load_df(xb, a.Np, q - 1); df_fma(sum.re, v.re.hi, v.re.lo, 1.f, 0.f); df_fma(sum.im, v.im.hi, v.im.lo, 1.f, 0.f); }
+    if (m < a.nx - 1) { const cdf v = load_df(xb, a.Np, q + 1); df_fma(sum.re, v.re.hi, v.re.lo, 1.f, 0.f); df_fma(sum.im, v.im.hi, v.im.lo, 1.f, 0.f); }
+    if (n > 0) { const cdf v = load_df(xb, a.Np, q - a.nx); df_fma(sum.re, v.re.hi, v.re.lo, 1.f, 0.f); df_fma(sum.im, v.im.hi, v.im.lo, 1.f, 0.f); }
+    if (n < a.ny - 1) { const cdf v = load_df(xb, a.Np, q + a.nx); df_fma(sum.re, v.re.hi, v.re.lo, 1.f, 0.f); df_fma(sum.im, v.im.hi, v.im.lo, 1.f, 0.f); }
+    sum.re = df_norm(sum.re);
+    sum.im = df_norm(sum.im);
+    const cdf xc = load_df(xb, a.Np, q);
+    const cdf D = load_df(DAdf, a.Np, q);
+    cdf r = load_df(bb, a.Np, q);
+    cdf_abs2_acc(bn, r);
+    // r = b - D x + (1/h^2) sum
+    cdf_sub_mul(r, D, xc);
+    df_fma(r.re, ih.hi, ih.lo, sum.re.hi, sum.re.lo);
+    df_fma(r.im, ih.hi, ih.lo, sum.im.hi, sum.im.lo);
+    r.re = df_norm(r.re);
+    r.im = df_norm(r.im);
+    rh[q] = make_float2(r.re.hi, r.im.hi);
+    rl[q] = make_float2(r.re.lo, r.im.lo);
+    cdf_abs2_acc(rn, r);
+  }
+  cd acc[1] = {mk<double>(df_to_double(rn), 0.0)};
+  block_reduce_store<1>(acc, 1, df_to_double(bn), 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
+}
+
+// Cycle start from the double-float residual: a right-hand side whose residual meets its target
+// waits for the FP64 verification instead of starting a cycle.
+__global__ void k_df_cycle_start(KArgs a, const cd* __restrict__ partial, double* __restrict__ vscale,
+                                 cd* __restrict__ g, RhsState* __restrict__ st, double tol, int maxit, int first) {
+  __shared__ cd sh[2];
+  const int rhs = blockIdx.x;
+  if (st[rhs].done) return;
+  sum_partials(a, partial, rhs, 2, sh);
+  if (threadIdx.x != 0) return;
+  RhsState& S = st[rhs];
+  S.nres += 1;
+  if (first) {
+    S.bnorm = sqrt(sh[1].re);
+    S.iterations = 0;
+    S.restarts = 0;
+    S.tol_scale = 1.0;
+  } else {
+    S.restarts += 1;
+  }
+  const double rn = sqrt(sh[0].re);
+  S.rnorm = rn;
+  S.jend = 0;
+  S.active = 0;
+  S.verify = 0;
+  if (S.bnorm == 0.0) { S.done = 1; S.converged = 1; return; }
+  if (rn <= tol * S.tol_scale * S.bnorm) { S.verify = 1; return; }
+  if (S.iterations >= maxit || !(rn == rn)) { S.done = 1; S.converged = 0; return; }
+  S.active = 1;
+  vscale[(size_t)rhs * (a.m + 1)] = 1.0 / rn;
+  cd* gg = g + (size_t)rhs * (a.m + 1);
+  gg[0] = mk<double>(rn, 0.0);
+  for (int i = 1; i <= a.m; ++i) gg[i] = czero<double>();
+}
+
+// FP64 true residual ||b - A x||^2 of the right-hand sides awaiting verification (slot 0).
+__global__ void __launch_bounds__(kKThreads)
+k_verify_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const cd* __restrict__ DA,
+                  cd* __restrict__ partial, const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (!st[rhs].verify) return;
+  const cd* xb = x + (size_t)rhs * a.N;
+  const cd* bb = b + (size_t)rhs * a.N;
   cd acc[1] = {czero<double>()};
-  double bn = 0.0;
   const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
   int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
   int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
@@ -504,21 +607,39 @@ k_df_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const
     if (m < a.nx - 1) s = s + xb[q + 1];
     if (n > 0) s = s + xb[q - a.nx];
     if (n < a.ny - 1) s = s + xb[q + a.nx];
-    const cd bv = bb[q];
-    const cd rv = bv - (DA[q] * xb[q] - a.inv_h2 * s);
-    const cdf r = cdf_from(rv);
-    rh[q] = make_float2(r.re.hi, r.im.hi);
-    rl[q] = make_float2(r.re.lo, r.im.lo);
+    const cd rv = bb[q] - (DA[q] * xb[q] - a.inv_h2 * s);
     acc[0].re += cabs2(rv);
-    bn += cabs2(bv);
   }
-  block_reduce_store<1>(acc, 1, bn, 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
+  block_reduce_store<1>(acc, 1, 0.0, 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
 }
 
-// x += sum_{i < jend} y_i z_i with the sum formed in double-float (z_i FP32), added to FP64 x.
+// Accept on the FP64 residual, or tighten the double-float target and start another cycle.
+__global__ void k_verify_decide(KArgs a, const cd* __restrict__ partial, double* __restrict__ vscale,
+                                cd* __restrict__ g, RhsState* __restrict__ st, double tol, int maxit) {
+  __shared__ cd sh[1];
+  const int rhs = blockIdx.x;
+  if (!st[rhs].verify) return;
+  sum_partials(a, partial, rhs, 1, sh);
+  if (threadIdx.x != 0) return;
+  RhsState& S = st[rhs];
+  S.verify = 0;
+  S.nverify += 1;
+  const double r64 = sqrt(sh[0].re);
+  if (r64 <= tol * S.bnorm) { S.done = 1; S.converged = 1; S.rnorm = r64; return; }
+  S.tol_scale *= 0.1;
+  if (S.iterations >= maxit || !(r64 == r64)) { S.done = 1; S.converged = 0; S.rnorm = r64; return; }
+  // continue from the double-float residual already in basis slot 0
+  S.active = 1;
+  vscale[(size_t)rhs * (a.m + 1)] = 1.0 / S.rnorm;
+  cd* gg = g + (size_t)rhs * (a.m + 1);
+  gg[0] = mk<double>(S.rnorm, 0.0);
+  for (int i = 1; i <= a.m; ++i) gg[i] = czero<double>();
+}
+
+// x += sum_{i < jend} y_i z_i, all in double-float (x planes, z FP32, y split to double-float).
 template <int NV>
 __global__ void __launch_bounds__(kKThreads)
-k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, cd* __restrict__ x,
+k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, float2* __restrict__ xdf,
              const RhsState* __restrict__ st) {
   const int rhs = blockIdx.y;
   if (st[rhs].done || st[rhs].jend == 0) return;
@@ -527,24 +648,25 @@ k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, cd* __
   if (threadIdx.x < NV && (int)threadIdx.x < je) ys[threadIdx.x] = cdf_from(y[(size_t)rhs * a.m + threadIdx.x]);
   __syncthreads();
   const cf* Zb = Z + (size_t)rhs * a.m * a.N;
-  cd* xb = x + (size_t)rhs * a.N;
+  float2* xh = xdf + (size_t)rhs * 2 * a.Np;
+  float2* xl = xh + a.Np;
   const size_t p0 = blockIdx.x * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
   for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads) {
-    df sr = {0.f, 0.f}, si = {0.f, 0.f};
+    cdf v = load_df(xh, a.Np, q);
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       if (i < je) {
         const cf z = Zb[(size_t)i * a.N + q];
-        df_fma1(sr, ys[i].re.hi, ys[i].re.lo, z.re);
-        df_fma1(sr, -ys[i].im.hi, -ys[i].im.lo, z.im);
-        df_fma1(si, ys[i].re.hi, ys[i].re.lo, z.im);
-        df_fma1(si, ys[i].im.hi, ys[i].im.lo, z.re);
+        df_fma1(v.re, ys[i].re.hi, ys[i].re.lo, z.re);
+        df_fma1(v.re, -ys[i].im.hi, -ys[i].im.lo, z.im);
+        df_fma1(v.im, ys[i].re.hi, ys[i].re.lo, z.im);
+        df_fma1(v.im, ys[i].im.hi, ys[i].im.lo, z.re);
       }
     }
-    cd v = xb[q];
-    v.re += df_to_double(sr);
-    v.im += df_to_double(si);
-    xb[q] = v;
+    v.re = df_norm(v.re);
+    v.im = df_norm(v.im);
+    xh[q] = make_float2(v.re.hi, v.im.hi);
+    xl[q] = make_float2(v.re.lo, v.im.lo);
   }
 }
 
@@ -648,10 +770,11 @@ mgh_status df_tail(Handle& h, const KArgs& a, int j, int B) {
   return df_tail_nv<kMaxRestartDf>(h, a, j, B);
 }
 
-mgh_status df_xupdate(Handle& h, const KArgs& a, int B, cd* x) {
+mgh_status df_xupdate(Handle& h, const KArgs& a, int B) {
   const dim3 grid(a.nblk, B);
   ProfScope ps(h, P_XUPDATE);
   const int m = a.m;
+  float2* x = h.xdf;
   if (m <= 4) k_df_xupdate<4><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
   else if (m <= 8) k_df_xupdate<8><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
   else if (m <= 12) k_df_xupdate<12><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
@@ -666,28 +789,49 @@ mgh_status df_xupdate(Handle& h, const KArgs& a, int B, cd* x) {
 mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
   KArgs a = make_kargs(h, B);
   const dim3 grid(a.nblk, B);
+  const dim3 pgrid((unsigned)((a.N + 255) / 256), B);
   float2* V = reinterpret_cast<float2*>(h.V);
   MGH_CUDA(cudaMemsetAsync(h.dev_err, 0, sizeof(int), h.stream));
+  // start: state, double-float copies of b and x0, first residual in double-float
+  auto residual_and_start = [&](int first) -> mgh_status {
+    {
+      ProfScope ps(h, P_RESIDUAL);
+      k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, h.bdf, h.xdf, h.DAdf, V, h.partial, h.st);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    {
+      ProfScope ps(h, P_REDUCE);
+      k_df_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, first);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    {
+      // FP64 acceptance test of the right-hand sides whose double-float residual met the target
+      ProfScope ps(h, P_RESIDUAL);
+      k_df_join<<<pgrid, 256, 0, h.stream>>>(h.xdf, x, a.N, a.Np, h.st, 0);
+      MGH_CHECK_LAUNCH(); h.launches++;
+      k_verify_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.partial, h.st);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    {
+      ProfScope ps(h, P_REDUCE);
+      k_verify_decide<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    return MGH_OK;
+  };
   {
     ProfScope ps(h, P_REDUCE);
     k_state_reset<<<(B + 63) / 64, 64, 0, h.stream>>>(h.st, B);
     MGH_CHECK_LAUNCH(); h.launches++;
   }
   {
-    ProfScope ps(h, P_RESIDUAL);
-    k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, V, h.partial, h.st);
-    MGH_CHECK_LAUNCH(); h.launches++;
-  }
-  {
-    ProfScope ps(h, P_REDUCE);
-    k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 1);
-    MGH_CHECK_LAUNCH(); h.launches++;
-  }
-  {
     ProfScope ps(h, P_OTHER);
-    k_zero_if_b_zero<<<grid, kKThreads, 0, h.stream>>>(a, x, h.st);
+    k_df_split<<<pgrid, 256, 0, h.stream>>>(b, h.bdf, a.N, a.Np);
+    MGH_CHECK_LAUNCH(); h.launches++;
+    k_df_split<<<pgrid, 256, 0, h.stream>>>(x, h.xdf, a.N, a.Np);
     MGH_CHECK_LAUNCH(); h.launches++;
   }
+  MGH_TRY(residual_and_start(1));
   int err_host = 0;
   for (;;) {
     MGH_CUDA(cudaMemcpyAsync(h.st_host, h.st, sizeof(RhsState) * B, cudaMemcpyDeviceToHost, h.stream));
@@ -705,18 +849,16 @@ mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info)
       k_lsq<<<(B + 63) / 64, 64, 0, h.stream>>>(a, h.H, h.g, h.y, h.st, B);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
-    MGH_TRY(df_xupdate(h, a, B, x));
-    {
-      ProfScope ps(h, P_RESIDUAL);
-      k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, V, h.partial, h.st);
-      MGH_CHECK_LAUNCH(); h.launches++;
-    }
-    {
-      ProfScope ps(h, P_REDUCE);
-      k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 0);
-      MGH_CHECK_LAUNCH(); h.launches++;
-    }
+    MGH_TRY(df_xupdate(h, a, B));
+    MGH_TRY(residual_and_start(0));
   }
+  {
+    // every RHS leaves with its double-float iterate rounded to FP64
+    ProfScope ps(h, P_OTHER);
+    k_df_join<<<pgrid, 256, 0, h.stream>>>(h.xdf, x, a.N, a.Np, h.st, 1);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  MGH_CUDA(cudaStreamSynchronize(h.stream));
   return finish_solve(h, B, info);
 }
 
