@@ -92,34 +92,41 @@ __device__ __forceinline__ Pipe pipe_begin(unsigned char* smem, int S, int P, si
   return pp;
 }
 
-__device__ __forceinline__ void pipe_start(const Pipe& pp) {
+__device__ __forceinline__ void pipe_start(const Pipe& pp, int* fail) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < pp.S; ++s) mbar_init(&pp.bar[s], 1);
     fence_mbar_init();
+    *fail = 0;
   }
   __syncthreads();
   if (threadIdx.x == 0)
     for (int k = 0; k < pp.S && k < pp.ntiles; ++k) pp.issue(k);
 }
 
-// Wait for tile k.  On timeout every thread returns false together after the block has
-// drained the copies it still has in flight (bounded) and raised the error word.
-__device__ __forceinline__ bool pipe_wait(const Pipe& pp, int k, int* err) {
+// Wait for tile k (each thread on its own, bounded).  A thread that gives up raises the block's
+// failure flag; the flag is read by every thread after the next barrier (pipe_release).
+__device__ __forceinline__ bool pipe_wait(const Pipe& pp, int k, int* fail) {
   const bool ok = mbar_wait(&pp.bar[k % pp.S], (uint32_t)((k / pp.S) & 1), kWaitLimitNs);
-  if (!__syncthreads_or(!ok)) return true;
-  if (threadIdx.x == 0) {
-    atomicExch(err, kErrTimeout);
-    for (int kk = k; kk < k + pp.S && kk < pp.ntiles; ++kk)
-      mbar_wait(&pp.bar[kk % pp.S], (uint32_t)((kk / pp.S) & 1), kWaitLimitNs);
-  }
-  __syncthreads();
-  return false;
+  if (!ok) *fail = 1;
+  return ok;
 }
 
-// After all threads finished reading tile k: refill its slot with tile k + S.
-__device__ __forceinline__ void pipe_release(const Pipe& pp, int k) {
+// After all threads finished with tile k: refill its slot with tile k + S.  Returns false (for
+// every thread together) if some thread's wait gave up: the block then drains the copies it
+// still has in flight (bounded), raises the error word and must return.
+__device__ __forceinline__ bool pipe_release(const Pipe& pp, int k, const int* fail, int* err) {
   __syncthreads();
+  if (*fail) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, kErrTimeout);
+      for (int kk = k; kk < k + pp.S && kk < pp.ntiles; ++kk)
+        mbar_wait(&pp.bar[kk % pp.S], (uint32_t)((kk / pp.S) & 1), kWaitLimitNs);
+    }
+    __syncthreads();
+    return false;
+  }
   if (threadIdx.x == 0 && k + pp.S < pp.ntiles) pp.issue(k + pp.S);
+  return true;
 }
 
 __device__ __forceinline__ const float2* vplane(const float2* V, const KArgs& a, int rhs, int i, int h) {
@@ -170,7 +177,8 @@ k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __rest
       pp.src[5 + 2 * i] = vplane(V, a, rhs, i, 1);
     }
   }
-  pipe_start(pp);
+  int* fail = reinterpret_cast<int*>(smem + kSmemHeader - 16);
+  pipe_start(pp, fail);
   const cf* z = Z + ((size_t)rhs * a.m + j) * a.N;
   float2* wh = W + (size_t)rhs * 2 * a.Np;
   float2* wl = wh + a.Np;
@@ -180,21 +188,40 @@ k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __rest
   for (int i = 0; i < NV; ++i) { s[i] = cdf_zero(); t[i] = cdf_zero(); }
   df alpha = {0.f, 0.f};
   cdf beta = cdf_zero();
+  // the five stencil values of z for this thread's point of a tile (0 for missing neighbours,
+  // which adds nothing to the neighbour sum); loaded one tile ahead of their use
+  struct Stencil { cf c, w, e, s, n; };
+  auto load_stencil = [&](int k, int m, int n) {
+    Stencil v;
+    v.c = v.w = v.e = v.s = v.n = mk<float>(0.f, 0.f);
+    const size_t q = p0 + (size_t)k * kTile + threadIdx.x;
+    if (k < pp.ntiles && q < p1) {
+      v.c = z[q];
+      if (m > 0) v.w = z[q - 1];
+      if (m < a.nx - 1) v.e = z[q + 1];
+      if (n > 0) v.s = z[q - a.nx];
+      if (n < a.ny - 1) v.n = z[q + a.nx];
+    }
+    return v;
+  };
   const unsigned q0 = (unsigned)(p0 + threadIdx.x);
   int n = (int)(q0 / (unsigned)a.nx);
   int m = (int)(q0 - (unsigned)n * (unsigned)a.nx);
-  for (int k = 0; k < pp.ntiles; ++k, m += kTile) {
-    while (m >= a.nx) { m -= a.nx; ++n; }
-    if (!pipe_wait(pp, k, err)) return;
+  Stencil zs = load_stencil(0, m, n);
+  for (int k = 0; k < pp.ntiles; ++k) {
+    int mn = m + kTile, nn = n;
+    while (mn >= a.nx) { mn -= a.nx; ++nn; }
+    const Stencil zn = load_stencil(k + 1, mn, nn);
+    const bool ready = pipe_wait(pp, k, fail);
     const int slot = k % S;
     const size_t q = p0 + (size_t)k * kTile + threadIdx.x;
-    if (q < p1) {
+    if (ready && q < p1) {
       df sr = {0.f, 0.f}, si = {0.f, 0.f};
-      if (m > 0) { const cf v = z[q - 1]; df_add1(sr, v.re); df_add1(si, v.im); }
-      if (m < a.nx - 1) { const cf v = z[q + 1]; df_add1(sr, v.re); df_add1(si, v.im); }
-      if (n > 0) { const cf v = z[q - a.nx]; df_add1(sr, v.re); df_add1(si, v.im); }
-      if (n < a.ny - 1) { const cf v = z[q + a.nx]; df_add1(sr, v.re); df_add1(si, v.im); }
-      const cf zc = z[q];
+      df_add1(sr, zs.w.re); df_add1(si, zs.w.im);
+      df_add1(sr, zs.e.re); df_add1(si, zs.e.im);
+      df_add1(sr, zs.s.re); df_add1(si, zs.s.im);
+      df_add1(sr, zs.n.re); df_add1(si, zs.n.im);
+      const cf zc = zs.c;
       const float2 dh = pp.plane(slot, 2)[threadIdx.x], dl = pp.plane(slot, 3)[threadIdx.x];
       cdf w = cdf_zero();
       // w = D z - (1/h^2) (sum of neighbours)
@@ -224,7 +251,10 @@ k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __rest
         }
       }
     }
-    pipe_release(pp, k);
+    if (!pipe_release(pp, k, fail, err)) return;
+    zs = zn;
+    m = mn;
+    n = nn;
   }
   df vals[4 * NV + 3];
 #pragma unroll
@@ -266,16 +296,17 @@ k_df_tail(KArgs a, int j, int S, const float2* __restrict__ V, cd* __restrict__ 
       pp.src[3 + 2 * i] = vplane(V, a, rhs, i, 1);
     }
   }
-  pipe_start(pp);
+  int* fail = reinterpret_cast<int*>(smem + kSmemHeader - 16);
+  pipe_start(pp, fail);
   cdf s[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) s[i] = cdf_zero();
   df alpha = {0.f, 0.f};
   for (int k = 0; k < pp.ntiles; ++k) {
-    if (!pipe_wait(pp, k, err)) return;
+    const bool ready = pipe_wait(pp, k, fail);
     const int slot = k % S;
     const size_t q = p0 + (size_t)k * kTile + threadIdx.x;
-    if (q < p1) {
+    if (ready && q < p1) {
       const float2 uh = pp.plane(slot, 0)[threadIdx.x], ul = pp.plane(slot, 1)[threadIdx.x];
       cdf u;
       u.re.hi = uh.x; u.im.hi = uh.y; u.re.lo = ul.x; u.im.lo = ul.y;
@@ -290,7 +321,7 @@ k_df_tail(KArgs a, int j, int S, const float2* __restrict__ V, cd* __restrict__ 
         }
       }
     }
-    pipe_release(pp, k);
+    if (!pipe_release(pp, k, fail, err)) return;
   }
   df vals[2 * NV + 1];
 #pragma unroll
@@ -416,7 +447,8 @@ k_df_pass2(KArgs a, int j, int S, const cd* __restrict__ coef, float2* __restric
     cs_[i] = cdf_from(cf_[i]);
     ct_[i] = cdf_from(cf_[a.m + i]);
   }
-  pipe_start(pp);   // its __syncthreads also publishes cs_/ct_
+  int* fail = reinterpret_cast<int*>(smem + kSmemHeader - 16);
+  pipe_start(pp, fail);   // its __syncthreads also publishes cs_/ct_
   const df inv_nu = df_from_double(SS.inv_nu);
   cdf hjj;
   hjj.re = df_from_double(SS.hjj_re);
@@ -427,10 +459,10 @@ k_df_pass2(KArgs a, int j, int S, const cd* __restrict__ coef, float2* __restric
   float2* nl_g = nh_g + a.Np;
   df nrm = {0.f, 0.f};
   for (int k = 0; k < pp.ntiles; ++k) {
-    if (!pipe_wait(pp, k, err)) return;
+    const bool ready = pipe_wait(pp, k, fail);
     const int slot = k % S;
     const size_t q = p0 + (size_t)k * kTile + threadIdx.x;
-    if (q < p1) {
+    if (ready && q < p1) {
       const float2 a0 = pp.plane(slot, 0)[threadIdx.x], a1 = pp.plane(slot, 1)[threadIdx.x];
       const float2 b0 = pp.plane(slot, 2)[threadIdx.x], b1 = pp.plane(slot, 3)[threadIdx.x];
       cdf u, w;
@@ -462,7 +494,7 @@ k_df_pass2(KArgs a, int j, int S, const cd* __restrict__ coef, float2* __restric
       nl_g[q] = make_float2(w.re.lo, w.im.lo);
       cdf_abs2_acc(nrm, w);
     }
-    pipe_release(pp, k);
+    if (!pipe_release(pp, k, fail, err)) return;
   }
   cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
   block_reduce_df(&nrm, 1, [&](int) -> double* { out[0].im = 0.0; return reinterpret_cast<double*>(out); });

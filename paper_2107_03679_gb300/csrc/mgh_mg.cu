@@ -65,18 +65,31 @@ k_pre(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ 
   const double sc = bscale ? bscale[rhs * scale_stride] : 1.0;
   const size_t boff = rhs * b_stride;
 
-  for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
-    const int ly = idx / SW, lx = idx - ly * SW;
-    const int gx = x0 - H + lx, gy = y0 - H + ly;
-    Cx<T> b = czero<T>(), w = czero<T>(), d = czero<T>();
-    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-      const size_t q = (size_t)gy * nx + gx;
-      b = load_rhs<T, TIn>(bin, boff + q, sc);
-      w = wDinv[q];
-      d = D[q];
+  // tile load: every global load of this thread is issued before the first shared store
+  constexpr int NL = (S + kVThreads - 1) / kVThreads;
+  {
+    Cx<T> rb[NL], rw[NL], rd[NL];
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+      const int idx = threadIdx.x + r * kVThreads;
+      rb[r] = czero<T>(); rw[r] = czero<T>(); rd[r] = czero<T>();
+      const int ly = idx / SW, lx = idx - ly * SW;
+      const int gx = x0 - H + lx, gy = y0 - H + ly;
+      if (idx < S && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        const size_t q = (size_t)gy * nx + gx;
+        rb[r] = load_rhs<T, TIn>(bin, boff + q, sc);
+        rw[r] = wDinv[q];
+        rd[r] = D[q];
+      }
     }
-    sb[idx] = b; sw[idx] = w; sd[idx] = d;
-    if constexpr (NU >= 1) va[idx] = w * b;     // first sweep from v = 0
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+      const int idx = threadIdx.x + r * kVThreads;
+      if (idx < S) {
+        sb[idx] = rb[r]; sw[idx] = rw[r]; sd[idx] = rd[r];
+        if constexpr (NU >= 1) va[idx] = rw[r] * rb[r];     // first sweep from v = 0
+      }
+    }
   }
   __syncthreads();
 
@@ -174,23 +187,43 @@ k_post(const void* __restrict__ bin, size_t b_stride, const double* __restrict__
   const Cx<T>* vp = vpre + rhs * v_stride;
   const Cx<T>* eco = ec + rhs * ec_stride;
 
-  for (int t = threadIdx.x; t < CS; t += kVThreads) {
-    const int cj = cy0 + t / CW, ci = cx0 + t % CW;
-    se[t] = (ci >= 0 && ci < nxc && cj >= 0 && cj < nyc) ? eco[(size_t)cj * nxc + ci] : czero<T>();
-  }
-  for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
-    const int ly = idx / SW, lx = idx - ly * SW;
-    const int gx = x0 - H + lx, gy = y0 - H + ly;
-    Cx<T> b = czero<T>(), w = czero<T>(), v = czero<T>();
-    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-      const size_t q = (size_t)gy * nx + gx;
-      if constexpr (NU >= 1) {
-        b = load_rhs<T, TIn>(bin, boff + q, sc);
-        w = wDinv[q];
-      }
-      v = vp[q];
+  // tile load: every global load of this thread is issued before the first shared store
+  constexpr int NC = (CS + kVThreads - 1) / kVThreads;
+  constexpr int NL = (S + kVThreads - 1) / kVThreads;
+  {
+    Cx<T> re[NC], rb[NL], rw[NL], rv[NL];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+      const int t = threadIdx.x + r * kVThreads;
+      const int cj = cy0 + t / CW, ci = cx0 + t % CW;
+      re[r] = czero<T>();
+      if (t < CS && ci >= 0 && ci < nxc && cj >= 0 && cj < nyc) re[r] = eco[(size_t)cj * nxc + ci];
     }
-    sb[idx] = b; sw[idx] = w; vb[idx] = v;
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+      const int idx = threadIdx.x + r * kVThreads;
+      rb[r] = czero<T>(); rw[r] = czero<T>(); rv[r] = czero<T>();
+      const int ly = idx / SW, lx = idx - ly * SW;
+      const int gx = x0 - H + lx, gy = y0 - H + ly;
+      if (idx < S && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        const size_t q = (size_t)gy * nx + gx;
+        if constexpr (NU >= 1) {
+          rb[r] = load_rhs<T, TIn>(bin, boff + q, sc);
+          rw[r] = wDinv[q];
+        }
+        rv[r] = vp[q];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+      const int t = threadIdx.x + r * kVThreads;
+      if (t < CS) se[t] = re[r];
+    }
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+      const int idx = threadIdx.x + r * kVThreads;
+      if (idx < S) { sb[idx] = rb[r]; sw[idx] = rw[r]; vb[idx] = rv[r]; }
+    }
   }
   __syncthreads();
 
