@@ -78,15 +78,16 @@ WORKLOADS = {
                         levels=4, nu1=2, nu2=2, restart=20, tol=1e-8, precision="fp64"),
     # Batched forward, mixed precision: 512^2 + 32, sum of 6 random ellipses, 60 angles.
     # GMRES restart 8: on this workload the oracle needs 649 / 655 / 666 / 667 / 692 steps for
-    # m = 20 / 16 / 10 / 8 / 5, while the cost of a step grows with m.
+    # m = 20 / 16 / 10 / 8 / 5 (nu = 1), while the cost of a step grows with m.  Two smoothing
+    # sweeps: 603 steps per solve on the GPU against 675 with one and 625 with three.
     "ellipses576": Workload("ellipses576", 512, 512, 32, 10.0, 60, -60.0, 60.0,
-                            "ellipses", 2, levels=6, nu1=1, nu2=1, restart=8, tol=1e-6),
+                            "ellipses", 2, levels=6, nu1=2, nu2=2, restart=8, tol=1e-6),
     # Strong scattering: 1024^2 + 48, cell-like phantom, 120 angles, 12 ppw.
     "cell1120": Workload("cell1120", 1024, 1024, 48, 12.0, 120, -70.0, 70.0,
-                         "cell", 3, levels=6, nu1=1, nu2=1, restart=8, tol=1e-6),
+                         "cell", 3, levels=7, nu1=2, nu2=2, restart=8, tol=1e-6),
     # Differentiation: 512^2 + 32, ground-truth ellipse, 60 angles, receivers on a line.
     "grad576": Workload("grad576", 512, 512, 32, 10.0, 60, -60.0, 60.0,
-                        "gt_ellipse", 4, levels=6, nu1=1, nu2=1, restart=8, tol=1e-6),
+                        "gt_ellipse", 4, levels=6, nu1=2, nu2=2, restart=8, tol=1e-6),
 }
 
 
