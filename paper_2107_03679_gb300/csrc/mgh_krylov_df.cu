@@ -2,16 +2,19 @@
 // classical Gram-Schmidt whose second pass is delayed by one step (low-synchronisation GMRES;
 // Swirydowicz et al. 2020, Bielich et al. 2022), so that each Arnoldi step reads the basis twice.
 //
-//   step j holds q_0..q_{j-1} (final, orthonormal) and u_j, the candidate left by step j-1
-//   (orthogonalised once).  z_j = M^{-1}(u_j / ||u_j||), w = A z_j.
-//   pass 1   one sweep computes s = Q^H u_j, t = Q^H w, alpha = ||u_j||^2, beta = u_j^H w
+//   step j holds q_0..q_{j-1} (final, orthonormal), u_j (the candidate left by step j-1,
+//   orthogonalised once) and, from the pass that wrote u_j, s = Q^H u_j and alpha = ||u_j||^2.
+//   z_j = M^{-1}(u_j / ||u_j||), w = A z_j.
+//   pass 1   one sweep: w = A z_j, t = Q^H w, beta = u_j^H w
 //   scalars  nu = sqrt(alpha - ||s||^2); q_j = (u_j - Q s)/nu; h_{:,j} = (t, (beta - s^H t)/nu);
 //            column j-1 is finalised with the correction s and h_{j,j-1} = nu, then rotated
-//   pass 2   one sweep writes q_j over u_j and u_{j+1} = w - Q t - h_jj q_j
+//   pass 2   one sweep writes q_j over u_j and u_{j+1} = w - Q t - h_jj q_j, and accumulates
+//            the next step's s' = [Q q_j]^H u_{j+1} and alpha' = ||u_{j+1}||^2
 //
 // The relation A z_j = sum_{i<=j+1} h_ij q_i holds exactly for the stored z_j, which is what
 // flexible GMRES needs; the least-squares problem and the stopping estimate lag one step behind
-// the preconditioner application.  A tail pass at the end of a cycle finalises the last column.
+// the preconditioner application.  At the end of a cycle the last column is finalised from the
+// last pass 2's dots, with no extra sweep.
 //
 // Each block streams its contiguous chunk of points through a ring of shared-memory stages
 // filled by bulk copies (TMA, cp.async.bulk) that complete on mbarriers, so loads of later tiles
@@ -153,9 +156,13 @@ __device__ __forceinline__ void block_reduce_df(const df* vals, int nv, Dst dst)
   }
 }
 
+// Partial-sum slots (per block, stride pstride = 2m+4):
+//   region A (pass 1):  t = Q_j^H w at [0, j), beta = u_j^H w at j
+//   region B (pass 2):  s = Q_{j+1}^H u_{j+1} at kB + [0, j+1), alpha = ||u_{j+1}||^2 at kB + j + 1
+__host__ __device__ __forceinline__ int region_b(int m) { return m + 2; }
+
 // ---------------------------------------------------------------- pass 1
 // Planes: u_j (hi, lo), D_A (hi, lo), q_0 .. q_{j-1} (hi, lo each).
-// Partial slots: s at [0, j), t at [j, 2j), alpha at 2j, beta at 2j+1.
 template <int NV>
 __global__ void __launch_bounds__(kDfThreads)
 k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __restrict__ DAdf,
@@ -183,10 +190,9 @@ k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __rest
   float2* wh = W + (size_t)rhs * 2 * a.Np;
   float2* wl = wh + a.Np;
   const df ih = df_from_double(a.inv_h2);
-  cdf s[NV], t[NV];
+  cdf t[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) { s[i] = cdf_zero(); t[i] = cdf_zero(); }
-  df alpha = {0.f, 0.f};
+  for (int i = 0; i < NV; ++i) t[i] = cdf_zero();
   cdf beta = cdf_zero();
   // the five stencil values of z for this thread's point of a tile (0 for missing neighbours,
   // which adds nothing to the neighbour sum); loaded one tile ahead of their use
@@ -238,7 +244,6 @@ k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __rest
       const float2 uh = pp.plane(slot, 0)[threadIdx.x], ul = pp.plane(slot, 1)[threadIdx.x];
       cdf u;
       u.re.hi = uh.x; u.im.hi = uh.y; u.re.lo = ul.x; u.im.lo = ul.y;
-      cdf_abs2_acc(alpha, u);
       cdf_dot_acc(beta, u, w);
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
@@ -246,7 +251,6 @@ k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __rest
           const float2 qh = pp.plane(slot, 4 + 2 * i)[threadIdx.x], ql = pp.plane(slot, 5 + 2 * i)[threadIdx.x];
           cdf qi;
           qi.re.hi = qh.x; qi.im.hi = qh.y; qi.re.lo = ql.x; qi.im.lo = ql.y;
-          cdf_dot_acc(s[i], qi, u);
           cdf_dot_acc(t[i], qi, w);
         }
       }
@@ -256,109 +260,41 @@ k_df_pass1(KArgs a, int j, int S, const cf* __restrict__ Z, const float2* __rest
     m = mn;
     n = nn;
   }
-  df vals[4 * NV + 3];
+  df vals[2 * NV + 2];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    vals[4 * i] = s[i].re; vals[4 * i + 1] = s[i].im; vals[4 * i + 2] = t[i].re; vals[4 * i + 3] = t[i].im;
-  }
-  // compact: the first 4j entries are the live dots, then alpha, beta
-  vals[4 * j] = alpha;
-  vals[4 * j + 1] = beta.re;
-  vals[4 * j + 2] = beta.im;
+  for (int i = 0; i < NV; ++i) { vals[2 * i] = t[i].re; vals[2 * i + 1] = t[i].im; }
+  vals[2 * j] = beta.re;
+  vals[2 * j + 1] = beta.im;
   cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
-  block_reduce_df(vals, 4 * j + 3, [&](int c) -> double* {
-    if (c < 4 * j) {
-      const int i = c >> 2, part = c & 3;   // s.re s.im t.re t.im
-      return reinterpret_cast<double*>(out + (part < 2 ? i : j + i)) + (part & 1);
-    }
-    if (c == 4 * j) { out[2 * j].im = 0.0; return reinterpret_cast<double*>(out + 2 * j); }
-    return reinterpret_cast<double*>(out + 2 * j + 1) + (c - 4 * j - 1);
-  });
-}
-
-// ---------------------------------------------------------------- cycle tail
-// s = Q_m^H u_m and alpha = ||u_m||^2; planes u (hi, lo), q_0 .. q_{j-1}; slots as in pass 1.
-template <int NV>
-__global__ void __launch_bounds__(kDfThreads)
-k_df_tail(KArgs a, int j, int S, const float2* __restrict__ V, cd* __restrict__ partial,
-          const RhsState* __restrict__ st, int* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int rhs = blockIdx.y, blk = blockIdx.x;
-  if (!st[rhs].active) return;
-  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
-  const int P = 2 + 2 * j;
-  Pipe pp = pipe_begin(smem, S, P, p0, p1);
-  if (threadIdx.x == 0) {
-    pp.src[0] = vplane(V, a, rhs, j, 0);
-    pp.src[1] = vplane(V, a, rhs, j, 1);
-    for (int i = 0; i < j; ++i) {
-      pp.src[2 + 2 * i] = vplane(V, a, rhs, i, 0);
-      pp.src[3 + 2 * i] = vplane(V, a, rhs, i, 1);
-    }
-  }
-  int* fail = reinterpret_cast<int*>(smem + kSmemHeader - 16);
-  pipe_start(pp, fail);
-  cdf s[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) s[i] = cdf_zero();
-  df alpha = {0.f, 0.f};
-  for (int k = 0; k < pp.ntiles; ++k) {
-    const bool ready = pipe_wait(pp, k, fail);
-    const int slot = k % S;
-    const size_t q = p0 + (size_t)k * kTile + threadIdx.x;
-    if (ready && q < p1) {
-      const float2 uh = pp.plane(slot, 0)[threadIdx.x], ul = pp.plane(slot, 1)[threadIdx.x];
-      cdf u;
-      u.re.hi = uh.x; u.im.hi = uh.y; u.re.lo = ul.x; u.im.lo = ul.y;
-      cdf_abs2_acc(alpha, u);
-#pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        if (i < j) {
-          const float2 qh = pp.plane(slot, 2 + 2 * i)[threadIdx.x], ql = pp.plane(slot, 3 + 2 * i)[threadIdx.x];
-          cdf qi;
-          qi.re.hi = qh.x; qi.im.hi = qh.y; qi.re.lo = ql.x; qi.im.lo = ql.y;
-          cdf_dot_acc(s[i], qi, u);
-        }
-      }
-    }
-    if (!pipe_release(pp, k, fail, err)) return;
-  }
-  df vals[2 * NV + 1];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) { vals[2 * i] = s[i].re; vals[2 * i + 1] = s[i].im; }
-  vals[2 * j] = alpha;
-  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
-  block_reduce_df(vals, 2 * j + 1, [&](int c) -> double* {
-    if (c < 2 * j) return reinterpret_cast<double*>(out + (c >> 1)) + (c & 1);
-    out[2 * j].im = 0.0;
-    return reinterpret_cast<double*>(out + 2 * j);
-  });
-  if (threadIdx.x < j) out[j + threadIdx.x] = czero<double>();
-  if (threadIdx.x == 0) out[2 * j + 1] = czero<double>();
+  block_reduce_df(vals, 2 * j + 2, [&](int c) -> double* { return reinterpret_cast<double*>(out + (c >> 1)) + (c & 1); });
 }
 
 // ---------------------------------------------------------------- scalars (one block per RHS)
 // Delayed correction and Givens rotation of column j-1, stopping test, pass-2 coefficients.
+// tail != 0 (j = m): only column m-1 is finalised, from the last pass 2's region B.
 __global__ void k_df_scalars(KArgs a, int j, int tail, const cd* __restrict__ partial, cd* __restrict__ H,
                              double* __restrict__ cs, cd* __restrict__ sn, cd* __restrict__ g, cd* __restrict__ hpend,
                              cd* __restrict__ coef, RhsState* __restrict__ st, double tol, int maxit) {
-  __shared__ cd sh[2 * kMaxRestart + 4];
+  __shared__ cd shA[kMaxRestart + 2], shB[kMaxRestart + 2];
   const int rhs = blockIdx.x;
   if (!st[rhs].active) return;
-  for (int c = threadIdx.x; c < 2 * j + 2; c += blockDim.x) {
+  const int kB = region_b(a.m);
+  const int nA = tail ? 0 : j + 1;      // t, beta
+  const int nB = j >= 1 ? j + 1 : 0;    // s, alpha (from the previous pass 2)
+  for (int c = threadIdx.x; c < nA + nB; c += blockDim.x) {
+    const int slot = c < nA ? c : kB + (c - nA);
     cd acc = czero<double>();
-    for (int b = 0; b < a.nblk; ++b) acc = acc + partial[((size_t)rhs * a.nblk + b) * a.pstride + c];
-    sh[c] = acc;
+    for (int b = 0; b < a.nblk; ++b) acc = acc + partial[((size_t)rhs * a.nblk + b) * a.pstride + slot];
+    if (c < nA) shA[c] = acc; else shB[c - nA] = acc;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
   const int m = a.m;
   RhsState& S = st[rhs];
-  if (tail) S.rsum += j;
-  const cd* s = sh;
-  const cd* t = sh + j;
-  const double alpha = sh[2 * j].re;
-  const cd beta = sh[2 * j + 1];
+  const cd* t = shA;
+  const cd beta = tail ? czero<double>() : shA[j];
+  const cd* s = shB;
+  const double alpha = j >= 1 ? shB[j].re : S.rnorm * S.rnorm;
   double ss = 0.0;
   for (int i = 0; i < j; ++i) ss += cabs2(s[i]);
   const double nu2 = alpha - ss;
@@ -419,7 +355,8 @@ __global__ void k_df_scalars(KArgs a, int j, int tail, const cd* __restrict__ pa
 
 // ---------------------------------------------------------------- pass 2
 // Planes: u_j (hi, lo), w (hi, lo), q_0 .. q_{j-1}.  Writes q_j over u_j and u_{j+1} into slot
-// j+1; partial ||u_{j+1}||^2 in slot 0.
+// j+1, and accumulates the next step's second-pass dots s' = Q_{j+1}^H u_{j+1} (q_j included)
+// and alpha' = ||u_{j+1}||^2 into region B.
 template <int NV>
 __global__ void __launch_bounds__(kDfThreads)
 k_df_pass2(KArgs a, int j, int S, const cd* __restrict__ coef, float2* __restrict__ V, const float2* __restrict__ W,
@@ -457,6 +394,9 @@ k_df_pass2(KArgs a, int j, int S, const cd* __restrict__ coef, float2* __restric
   float2* ul_g = uh_g + a.Np;
   float2* nh_g = V + (((size_t)rhs * (a.m + 1) + j + 1) * 2) * a.Np;
   float2* nl_g = nh_g + a.Np;
+  cdf sd[NV + 1];
+#pragma unroll
+  for (int i = 0; i <= NV; ++i) sd[i] = cdf_zero();
   df nrm = {0.f, 0.f};
   for (int k = 0; k < pp.ntiles; ++k) {
     const bool ready = pipe_wait(pp, k, fail);
@@ -493,24 +433,43 @@ k_df_pass2(KArgs a, int j, int S, const cd* __restrict__ coef, float2* __restric
       nh_g[q] = make_float2(w.re.hi, w.im.hi);
       nl_g[q] = make_float2(w.re.lo, w.im.lo);
       cdf_abs2_acc(nrm, w);
+      // second-pass dots of the new candidate against q_0 .. q_j
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        if (i < j) {
+          const float2 qh = pp.plane(slot, 4 + 2 * i)[threadIdx.x], ql = pp.plane(slot, 5 + 2 * i)[threadIdx.x];
+          cdf qi;
+          qi.re.hi = qh.x; qi.im.hi = qh.y; qi.re.lo = ql.x; qi.im.lo = ql.y;
+          cdf_dot_acc(sd[i], qi, w);
+        }
+      }
+      cdf_dot_acc(sd[NV], qj, w);
     }
     if (!pipe_release(pp, k, fail, err)) return;
   }
-  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
-  block_reduce_df(&nrm, 1, [&](int) -> double* { out[0].im = 0.0; return reinterpret_cast<double*>(out); });
+  df vals[2 * NV + 3];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) { vals[2 * i] = sd[i].re; vals[2 * i + 1] = sd[i].im; }
+  // compact: dots with q_0..q_{j-1}, then q_j, then alpha'
+  vals[2 * j] = sd[NV].re;
+  vals[2 * j + 1] = sd[NV].im;
+  vals[2 * j + 2] = nrm;
+  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride + region_b(a.m);
+  block_reduce_df(vals, 2 * j + 3, [&](int c) -> double* {
+    if (c == 2 * j + 2) { out[j + 1].im = 0.0; return reinterpret_cast<double*>(out + j + 1); }
+    return reinterpret_cast<double*>(out + (c >> 1)) + (c & 1);
+  });
 }
 
-// 1/||u_{j+1}|| for the next preconditioner input.
+// 1/||u_{j+1}|| for the next preconditioner input (alpha' of region B).
 __global__ void k_df_unorm(KArgs a, int j, const cd* __restrict__ partial, double* __restrict__ vscale,
                            const RhsState* __restrict__ st) {
-  __shared__ cd sh[1];
   const int rhs = blockIdx.x;
-  if (!st[rhs].active) return;
-  sum_partials(a, partial, rhs, 1, sh);
-  if (threadIdx.x == 0) {
-    const double n2 = sh[0].re;
-    vscale[(size_t)rhs * (a.m + 1) + j + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
-  }
+  if (!st[rhs].active || threadIdx.x != 0) return;
+  double n2 = 0.0;
+  const int slot = region_b(a.m) + j + 1;
+  for (int b = 0; b < a.nblk; ++b) n2 += partial[((size_t)rhs * a.nblk + b) * a.pstride + slot].re;
+  vscale[(size_t)rhs * (a.m + 1) + j + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
 }
 
 // FP64 fields [B][N] -> double-float planes [B][2][Np].
@@ -724,7 +683,6 @@ mgh_status df_step_nv(Handle& h, const KArgs& a, int j, int B) {
   if (!init) {
     MGH_TRY(set_smem(k_df_pass1<NV>));
     MGH_TRY(set_smem(k_df_pass2<NV>));
-    MGH_TRY(set_smem(k_df_tail<NV>));
     init = true;
   }
   const dim3 grid(a.nblk, B);
@@ -758,30 +716,6 @@ mgh_status df_step_nv(Handle& h, const KArgs& a, int j, int B) {
   return MGH_OK;
 }
 
-template <int NV>
-mgh_status df_tail_nv(Handle& h, const KArgs& a, int j, int B) {
-  static bool init = false;
-  if (!init) {
-    MGH_TRY(set_smem(k_df_tail<NV>));
-    init = true;
-  }
-  const dim3 grid(a.nblk, B);
-  {
-    const int P = 2 + 2 * j, S = stages_for(P);
-    ProfScope ps(h, P_REORTH);
-    k_df_tail<NV><<<grid, kDfThreads, smem_for(P, S), h.stream>>>(a, j, S, reinterpret_cast<const float2*>(h.V),
-                                                                   h.partial, h.st, h.dev_err);
-    MGH_CHECK_LAUNCH(); h.launches++;
-  }
-  {
-    ProfScope ps(h, P_REDUCE);
-    k_df_scalars<<<B, 64, 0, h.stream>>>(a, j, 1, h.partial, h.H, h.cs, h.sn, h.g, h.hpend, h.coef, h.st,
-                                         h.p.tol, h.p.maxit);
-    MGH_CHECK_LAUNCH(); h.launches++;
-  }
-  return MGH_OK;
-}
-
 mgh_status df_arnoldi_step(Handle& h, const KArgs& a, int j, int B) {
   // z_j = M^{-1}(u_j / ||u_j||), reading only the hi plane of u_j
   const cf* uhi = reinterpret_cast<const cf*>(reinterpret_cast<const float2*>(h.V) + (size_t)j * 2 * a.Np);
@@ -794,12 +728,13 @@ mgh_status df_arnoldi_step(Handle& h, const KArgs& a, int j, int B) {
   return df_step_nv<kMaxRestartDf>(h, a, j, B);
 }
 
-mgh_status df_tail(Handle& h, const KArgs& a, int j, int B) {
-  if (j <= 4) return df_tail_nv<4>(h, a, j, B);
-  if (j <= 8) return df_tail_nv<8>(h, a, j, B);
-  if (j <= 12) return df_tail_nv<12>(h, a, j, B);
-  if (j <= 16) return df_tail_nv<16>(h, a, j, B);
-  return df_tail_nv<kMaxRestartDf>(h, a, j, B);
+// End of a cycle: finalise the last column from the second-pass dots of the last pass 2.
+mgh_status df_tail(Handle& h, const KArgs& a, int B) {
+  ProfScope ps(h, P_REDUCE);
+  k_df_scalars<<<B, 64, 0, h.stream>>>(a, a.m, 1, h.partial, h.H, h.cs, h.sn, h.g, h.hpend, h.coef, h.st,
+                                       h.p.tol, h.p.maxit);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  return MGH_OK;
 }
 
 mgh_status df_xupdate(Handle& h, const KArgs& a, int B) {
@@ -875,7 +810,7 @@ mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info)
     for (int i = 0; i < B; ++i) any |= (h.st_host[i].done == 0);
     if (!any) break;
     for (int j = 0; j < a.m; ++j) MGH_TRY(df_arnoldi_step(h, a, j, B));
-    MGH_TRY(df_tail(h, a, a.m, B));
+    MGH_TRY(df_tail(h, a, B));
     {
       ProfScope ps(h, P_REDUCE);
       k_lsq<<<(B + 63) / 64, 64, 0, h.stream>>>(a, h.H, h.g, h.y, h.st, B);
