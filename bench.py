@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--nu", type=int, default=None, help="pre- and post-smoothing sweeps (default: the workload's)")
     ap.add_argument("--arnoldi", choices=["df", "fp64"], default="df",
                     help="mixed precision Arnoldi arithmetic: double-float on FP32 pipes or native FP64")
+    ap.add_argument("--descent", type=int, default=0,
+                    help="instead of the throughput line: N projected gradient-descent steps from f = 0")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -446,6 +448,133 @@ def gpu_main(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------------------- gradient descent
+def descent_main(args, rank, world, local_rank):
+    """Projected gradient descent f <- max(0, f - gamma g) on the data term, from f = 0, with the
+    gradient of every step from the forward and adjoint solves of all angles (Prop. 1).  The
+    step gamma is fixed after the first gradient so that the first update moves f by at most
+    0.02 (the nonnegativity constraint of the MAP problem in Sec. V)."""
+    import torch
+    import workloads as W
+    from paper_2107_03679_gb300 import Solver
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = W.WORKLOADS[args.workload]
+    precision = args.precision or w.precision
+    f_gt, _, th, rec = make_inputs(w)
+    B = len(th)
+    s = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=20000, arnoldi=args.arnoldi)
+    d_th = torch.from_numpy(th).to(dev)
+    d_rec = torch.from_numpy(rec).to(dev)
+    s.set_contrast(torch.from_numpy(f_gt).to(dev))
+    u, _ = s.forward(d_th)
+    y_clean = s.sample(u, d_rec)
+    import workloads as Wm
+    sigma = 0.01 * float(torch.sqrt((y_clean.abs() ** 2).mean()))
+    y = y_clean + torch.from_numpy(Wm.complex_noise(tuple(y_clean.shape), sigma, 44)).to(dev)
+    f = torch.zeros_like(torch.from_numpy(f_gt)).to(dev)
+    losses, errs, its = [], [], []
+    gamma = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(args.descent + 1):
+        s.set_contrast(f)
+        u, inf_f = s.forward(d_th, out=u)
+        _, G, loss = s.misfit(u, y, d_rec)
+        losses.append(loss)
+        errs.append(float(torch.linalg.norm(f - torch.from_numpy(f_gt).to(dev)) / torch.linalg.norm(torch.from_numpy(f_gt).to(dev))))
+        if it == args.descent:
+            break
+        g, inf_a = s.gradient(d_th, u, G)
+        its.append(sum(i["iterations"] for i in inf_f + inf_a) / (2 * B))
+        if gamma is None:
+            gamma = 0.02 / float(g.abs().max())
+        f = torch.clamp(f - gamma * g, min=0.0)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    if rank == 0:
+        print(json.dumps({"metric": "projected gradient descent on the data term", "workload": args.workload,
+                          "precision": precision, "steps": args.descent, "gamma": gamma, "loss": losses,
+                          "relative_error_to_ground_truth": errs, "mean_iterations_per_solve": its,
+                          "seconds": round(sec, 2), "noise": "1% complex Gaussian (seed 44)"}))
+    s.close()
+
+
+# --------------------------------------------------------------------------- uneven batch
+def uneven_main(args, rank, world, local_rank):
+    """Four grids of different sizes solved together: one solver handle and one CUDA stream per
+    grid, driven from one host thread each so that their kernels overlap on the GPU."""
+    import threading as th
+    import torch
+    import workloads as W
+    from paper_2107_03679_gb300 import Solver
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    precision = args.precision or "mixed32"
+    jobs = []
+    for w in W.uneven_workloads():
+        stream = torch.cuda.Stream(dev)
+        f_gt, f_step, thetas, rec = make_inputs(w)
+        with torch.cuda.stream(stream):
+            s = Solver.from_workload(w, batch_max=len(thetas), precision=precision, device=dev, maxit=50000,
+                                     stream=stream, arnoldi=args.arnoldi)
+            d = dict(w=w, s=s, stream=stream, th=torch.from_numpy(thetas).to(dev), rec=torch.from_numpy(rec).to(dev),
+                     f=torch.from_numpy(f_step).to(dev))
+            s.set_contrast(torch.from_numpy(f_gt).to(dev))
+            u, _ = s.forward(d["th"])
+            d["y"] = s.sample(u, d["rec"])
+            d["u"] = u
+        jobs.append(d)
+    torch.cuda.synchronize()
+
+    def run_one(d, out):
+        with torch.cuda.stream(d["stream"]):
+            s = d["s"]
+            s.set_contrast(d["f"])
+            _, inf_f = s.forward(d["th"], out=d["u"])
+            _, G, _ = s.misfit(d["u"], d["y"], d["rec"])
+            _, inf_a = s.gradient(d["th"], d["u"], G)
+        out.extend(inf_f + inf_a)
+
+    def step():
+        outs = [[] for _ in jobs]
+        ts = [th.Thread(target=run_one, args=(d, o)) for d, o in zip(jobs, outs)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        return outs
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per = None
+    for _ in range(args.steps):
+        per = step()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    solves = sum(2 * d["th"].numel() for d in jobs) * args.steps
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": round(solves / sec, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "uneven", "grids": [f"{d['w'].nx}x{d['w'].ny}:{d['th'].numel()}" for d in jobs],
+                   "precision": precision, "timing": "host wall clock around all streams"},
+        "per_grid": [{"grid": f"{d['w'].nx}x{d['w'].ny}", "angles": d["th"].numel(),
+                      "iterations_mean": round(sum(i["iterations"] for i in o) / len(o), 1),
+                      "converged": all(i["converged"] for i in o)} for d, o in zip(jobs, per)],
+    }
+    print(json.dumps(line))
+    for d in jobs:
+        d["s"].close()
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.cpu_sample:
@@ -465,6 +594,10 @@ def main(argv=None):
     try:
         if args.impl == "reference":
             reference_main(args, rank, world)
+        elif args.workload == "uneven":
+            uneven_main(args, rank, world, local_rank)
+        elif args.descent:
+            descent_main(args, rank, world, local_rank)
         else:
             gpu_main(args, rank, world, local_rank)
     finally:

@@ -302,3 +302,39 @@ def test_ellipses576_full_size_residual_property():
         true = np.linalg.norm(b - O.apply_operator(D, uq, p.h)) / np.linalg.norm(b)
         assert true <= w.tol * (1 + 1e-6), (q, true)
         assert abs(true - infos[q]["rel_residual"]) <= 1e-3 * w.tol
+
+
+def test_gradient_twenty_directions_against_central_differences():
+    """Differentiation check of the data-term gradient on 20 seeded random directions: the CUDA
+    forward/adjoint gradient (FP64, tight tolerance) against central differences of the loss
+    computed with the CUDA forward solves, and against the oracle gradient."""
+    torch = torch_cuda()
+    w = W.Workload("fd20", 48, 48, 6, 8.0, 6, -60.0, 60.0, "gt_ellipse", 4, levels=3, nu1=2, nu2=2,
+                   precision="fp64", tol=1e-12)
+    s = make_solver(w, B=6, maxit=5000)
+    p, f_gt, o = oracle_solver(w, tol=1e-13)
+    th = W.angles(w)
+    rec = W.receivers(w, f_gt)
+    y = O.sample(o.forward(th)[0], rec) + W.complex_noise((len(th), rec.size), 0.01, 4)
+    f = 0.7 * f_gt
+    d_th, d_rec, d_y = to_t(th, torch), to_t(rec, torch), to_t(y, torch)
+
+    def loss_at(ff):
+        s.set_contrast(to_t(ff, torch))
+        u, infos = s.forward(d_th)
+        assert all(i["converged"] for i in infos)
+        return s.misfit(u, d_y, d_rec)
+
+    _, G, loss = loss_at(f)
+    u, _ = s.forward(d_th)
+    g, _ = s.gradient(d_th, u, G)
+    g = g.cpu().numpy()
+    _, _, o2 = oracle_solver(w, tol=1e-13, f=f)
+    _, g_ref, _ = o2.gradient(th, rec, y)
+    assert rel(g, g_ref) < 1e-8
+    rng = np.random.default_rng(20)
+    eps = 1e-5
+    for _ in range(20):
+        d = rng.standard_normal(f.shape)
+        fd = (loss_at(f + eps * d)[2] - loss_at(f - eps * d)[2]) / (2 * eps)
+        assert float(np.sum(g * d)) == pytest.approx(fd, rel=1e-5, abs=1e-10)

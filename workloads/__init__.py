@@ -91,6 +91,15 @@ WORKLOADS = {
 }
 
 
+def uneven_workloads() -> List[Workload]:
+    """Uneven batch: four grids solved together, each with its own angles (absorbing layer of
+    n/16 cells per side, 10 points per wavelength, seeded ellipse phantoms with n/n_b <= 1.2).
+    Levels are chosen so that the coarsest grid has 18-36 points per side."""
+    spec = [(256, 90, 5, 51), (384, 60, 5, 52), (768, 40, 6, 53), (2048, 16, 8, 54)]
+    return [Workload(f"uneven{n}", n, n, n // 16, 10.0, b, -60.0, 60.0, "ellipses", seed, levels=lv,
+                     nu1=2, nu2=2, restart=8, tol=1e-6) for n, b, lv, seed in spec]
+
+
 def small_workload(name: str = "small", n_int: int = 40, abl: int = 6, ppw: float = 10.0,
                    n_angles: int = 3, levels: int = 3, phantom: str = "ellipses",
                    seed: int = 7, precision: str = "fp64", **kw) -> Workload:
