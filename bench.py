@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--nu", type=int, default=None, help="pre- and post-smoothing sweeps (default: the workload's)")
     ap.add_argument("--arnoldi", choices=["df", "fp64"], default="df",
                     help="mixed precision Arnoldi arithmetic: double-float on FP32 pipes or native FP64")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick nu and the restart length with the autotuner (cached) before timing")
     ap.add_argument("--descent", type=int, default=0,
                     help="instead of the throughput line: N projected gradient-descent steps from f = 0")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -289,6 +291,12 @@ def gpu_main(args, rank, world, local_rank):
     if args.angles:
         th = th[:args.angles]
     B = len(th)
+    tuned = None
+    if args.autotune:
+        from paper_2107_03679_gb300.autotune import tune
+        tuned, trials = tune(w, torch.from_numpy(f_step).to(dev), torch.from_numpy(th), dev, precision=precision)
+        w.nu1 = w.nu2 = tuned["nu"]
+        w.restart = tuned["restart"]
     solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=20000, arnoldi=args.arnoldi)
     stream = solver.stream
     d_th = torch.from_numpy(th).to(dev)
@@ -441,6 +449,7 @@ def gpu_main(args, rank, world, local_rank):
         "iterations": {"mean": round(sum(its) / len(its), 1), "min": min(its), "max": max(its)},
         "converged": conv, "worst_rel_residual": worst,
         "gpu_launches": int(launches),
+        "autotuned": tuned,
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,

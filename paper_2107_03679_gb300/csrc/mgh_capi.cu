@@ -178,6 +178,12 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   if (!h) return MGH_OUT_OF_MEMORY;
   h->p = *p;
   h->stream = (cudaStream_t)cuda_stream;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (h->num_sms < 1) h->num_sms = 1;
+  }
   h->nx = nxl[0]; h->ny = nyl[0]; h->N = (size_t)h->nx * h->ny;
   h->Np = (h->N + 63) / 64 * 64;
   h->L = p->levels;

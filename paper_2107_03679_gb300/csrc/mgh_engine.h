@@ -34,6 +34,7 @@ struct Level {
 struct Handle {
   mgh_params p{};
   cudaStream_t stream = nullptr;
+  int num_sms = 1;           // multiprocessors of the handle's device
   int nx = 0, ny = 0;
   size_t N = 0;              // points of the extended grid
   size_t Np = 0;             // plane stride of double-float fields: N rounded up to 64 points

@@ -13,6 +13,8 @@
 // v - w D^{-1}(K v - b) for K v = D v - (sum of neighbours)/h^2; w/D is precomputed per level.
 // Points outside the grid hold 0 in every tile buffer: the Sommerfeld closure already sits in D,
 // and the restriction counts out-of-grid fine samples as 0.
+#include <type_traits>
+
 #include "mgh_engine.h"
 
 namespace mgh {
@@ -275,6 +277,253 @@ k_post(const void* __restrict__ bin, size_t b_stride, const double* __restrict__
   }
 }
 
+// ---------------------------------------------------------------- streaming FP32 level kernels
+// Persistent variants of k_pre / k_post for FP32 levels (inputs already FP32): each block walks
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... (RHS-major, then y, then x) and copies the next
+// tile's inputs into the other half of a double buffer with cp.async (zero-filled outside the
+// grid) while it computes the current tile, so the tile loads no longer stall the block.
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8u : 0u) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+struct TileWalk {
+  int ntx, nty, per_rhs, total;
+  const RhsState* st;
+  __device__ __forceinline__ int next(int t, int step) const {
+    while (t < total && st && !st[t / per_rhs].active) t += step;
+    return t;
+  }
+};
+
+template <int NU, int TX, int TY>
+__global__ void __launch_bounds__(kVThreads)
+k_pre_s(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
+        const cf* __restrict__ D, const cf* __restrict__ wDinv, cf* __restrict__ vpre, size_t v_stride,
+        cf* __restrict__ bc, size_t bc_stride, int nx, int ny, int nxc, int nyc, float inv_h2, float om1,
+        TileWalk tw) {
+  constexpr int H = NU + 1;
+  constexpr int SW = TX + 2 * H, SH = TY + 2 * H, S = SW * SH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf* in = reinterpret_cast<cf*>(smem_raw);          // [2][3][S]: b, w/D, D
+  cf* va = in + 6 * S;
+  cf* vb = va + S;
+  const int step = gridDim.x;
+
+  auto issue = [&](int t, int buf) {
+    const int rhs = t / tw.per_rhs, r = t - rhs * tw.per_rhs;
+    const int y0 = (r / tw.ntx) * TY, x0 = (r % tw.ntx) * TX;
+    const cf* bb = bin + rhs * b_stride;
+    cf* sb = in + (2 * buf * 3 + 0) * S;
+    for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
+      const int ly = idx / SW, lx = idx - ly * SW;
+      const int gx = x0 - H + lx, gy = y0 - H + ly;
+      const bool ok = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+      const size_t q = ok ? (size_t)gy * nx + gx : 0;
+      cp_async8(sb + idx, bb + q, ok);
+      cp_async8(sb + S + idx, wDinv + q, ok);
+      cp_async8(sb + 2 * S + idx, D + q, ok);
+    }
+  };
+  int t = tw.next(blockIdx.x, step);
+  if (t < tw.total) issue(t, 0);
+  cp_async_commit();
+  int buf = 0;
+  while (t < tw.total) {
+    const int tn = tw.next(t + step, step);
+    if (tn < tw.total) issue(tn, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const cf* sb = in + (2 * buf * 3 + 0) * S;
+    const cf* sw = sb + S;
+    const cf* sd = sb + 2 * S;
+    const int rhs = t / tw.per_rhs, r = t - rhs * tw.per_rhs;
+    const int y0 = (r / tw.ntx) * TY, x0 = (r % tw.ntx) * TX;
+    const float sc = bscale ? (float)bscale[rhs * scale_stride] : 1.f;
+    cf* vcur = va;
+    cf* vnxt = vb;
+    if constexpr (NU >= 1) {
+      for (int idx = threadIdx.x; idx < S; idx += kVThreads) va[idx] = sw[idx] * (sc * sb[idx]);   // first sweep from 0
+      __syncthreads();
+    }
+#pragma unroll
+    for (int sw_i = 2; sw_i <= NU; ++sw_i) {
+      const int lo = sw_i - 1, W = SW - 2 * lo, Hh = SH - 2 * lo;
+      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+        const int ly = lo + u / W, lx = lo + u % W;
+        const int idx = ly * SW + lx;
+        vnxt[idx] = jacobi_point(vcur, idx, SW, sc * sb[idx], sw[idx], inv_h2, om1);
+      }
+      __syncthreads();
+      cf* tmp = vcur; vcur = vnxt; vnxt = tmp;
+    }
+    cf* rr = vnxt;
+    {
+      constexpr int W = TX + 1, Hh = TY + 1;
+      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+        const int ly = NU + u / W, lx = NU + u % W;
+        const int idx = ly * SW + lx;
+        const int gx = x0 - H + lx, gy = y0 - H + ly;
+        cf rv = czero<float>();
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+          if constexpr (NU >= 1) {
+            const cf s4 = vcur[idx - 1] + vcur[idx + 1] + vcur[idx - SW] + vcur[idx + SW];
+            const cf kv = sd[idx] * vcur[idx] - inv_h2 * s4;
+            rv = sc * sb[idx] - kv;
+          } else {
+            rv = sc * sb[idx];
+          }
+        }
+        rr[idx] = rv;
+      }
+    }
+    __syncthreads();
+    {
+      constexpr int CW = TX / 2, CH = TY / 2;
+      const int ci0 = x0 / 2, cj0 = y0 / 2;
+      cf* bco = bc + rhs * bc_stride;
+      for (int u = threadIdx.x; u < CW * CH; u += kVThreads) {
+        const int ci = ci0 + u % CW, cj = cj0 + u / CW;
+        if (ci >= nxc || cj >= nyc) continue;
+        const int idx = (2 * cj - y0 + H) * SW + 2 * ci - x0 + H;
+        const cf e = rr[idx - 1] + rr[idx + 1] + rr[idx - SW] + rr[idx + SW];
+        const cf c = rr[idx - SW - 1] + rr[idx - SW + 1] + rr[idx + SW - 1] + rr[idx + SW + 1];
+        bco[(size_t)cj * nxc + ci] = mk<float>(0.0625f * (4.f * rr[idx].re + 2.f * e.re + c.re),
+                                               0.0625f * (4.f * rr[idx].im + 2.f * e.im + c.im));
+      }
+      cf* vo = vpre + rhs * v_stride;
+      for (int u = threadIdx.x; u < TX * TY; u += kVThreads) {
+        const int gx = x0 + u % TX, gy = y0 + u / TX;
+        if (gx < nx && gy < ny) {
+          cf v = czero<float>();
+          if constexpr (NU >= 1) v = vcur[(H + u / TX) * SW + H + u % TX];
+          vo[(size_t)gy * nx + gx] = v;
+        }
+      }
+    }
+    __syncthreads();
+    t = tn;
+    buf ^= 1;
+  }
+}
+
+template <int NU, int TX, int TY>
+__global__ void __launch_bounds__(kVThreads)
+k_post_s(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
+         const cf* __restrict__ wDinv, const cf* __restrict__ vpre, size_t v_stride, const cf* __restrict__ ec,
+         size_t ec_stride, int nxc, int nyc, cf* __restrict__ out, size_t out_stride, int nx, int ny,
+         float inv_h2, float om1, TileWalk tw) {
+  constexpr int H = NU;
+  constexpr int SW = TX + 2 * H, SH = TY + 2 * H, S = SW * SH;
+  constexpr int CW = TX / 2 + H + 2, CH = TY / 2 + H + 2, CS = CW * CH;
+  constexpr int STAGE = 3 * S + CS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf* in = reinterpret_cast<cf*>(smem_raw);          // [2][STAGE]: v_pre, b, w/D, coarse e
+  cf* va = in + 2 * STAGE;
+  cf* vb = va + S;
+  const int step = gridDim.x;
+
+  auto issue = [&](int t, int buf) {
+    const int rhs = t / tw.per_rhs, r = t - rhs * tw.per_rhs;
+    const int y0 = (r / tw.ntx) * TY, x0 = (r % tw.ntx) * TX;
+    const int cx0 = floor_half(x0 - H - 1), cy0 = floor_half(y0 - H - 1);
+    cf* base = in + buf * STAGE;
+    const cf* vp = vpre + rhs * v_stride;
+    const cf* bb = bin + rhs * b_stride;
+    for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
+      const int ly = idx / SW, lx = idx - ly * SW;
+      const int gx = x0 - H + lx, gy = y0 - H + ly;
+      const bool ok = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+      const size_t q = ok ? (size_t)gy * nx + gx : 0;
+      cp_async8(base + idx, vp + q, ok);
+      if constexpr (NU >= 1) {
+        cp_async8(base + S + idx, bb + q, ok);
+        cp_async8(base + 2 * S + idx, wDinv + q, ok);
+      }
+    }
+    const cf* eco = ec + rhs * ec_stride;
+    for (int u = threadIdx.x; u < CS; u += kVThreads) {
+      const int cj = cy0 + u / CW, ci = cx0 + u % CW;
+      const bool ok = ci >= 0 && ci < nxc && cj >= 0 && cj < nyc;
+      cp_async8(base + 3 * S + u, eco + (ok ? (size_t)cj * nxc + ci : 0), ok);
+    }
+  };
+  int t = tw.next(blockIdx.x, step);
+  if (t < tw.total) issue(t, 0);
+  cp_async_commit();
+  int buf = 0;
+  while (t < tw.total) {
+    const int tn = tw.next(t + step, step);
+    if (tn < tw.total) issue(tn, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const cf* svp = in + buf * STAGE;
+    const cf* sb = svp + S;
+    const cf* sw = svp + 2 * S;
+    const cf* se = svp + 3 * S;
+    const int rhs = t / tw.per_rhs, r = t - rhs * tw.per_rhs;
+    const int y0 = (r / tw.ntx) * TY, x0 = (r % tw.ntx) * TX;
+    const int cx0 = floor_half(x0 - H - 1), cy0 = floor_half(y0 - H - 1);
+    const float sc = bscale ? (float)bscale[rhs * scale_stride] : 1.f;
+    // v = v_pre + P e
+    for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
+      const int ly = idx / SW, lx = idx - ly * SW;
+      const int gx = x0 - H + lx, gy = y0 - H + ly;
+      cf v = czero<float>();
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        const int ia = (gx >> 1) - cx0, ja = (gy >> 1) - cy0;
+        const bool ox = gx & 1, oy = gy & 1;
+        cf p;
+        if (!ox && !oy) p = se[ja * CW + ia];
+        else if (ox && !oy) p = 0.5f * (se[ja * CW + ia] + se[ja * CW + ia + 1]);
+        else if (!ox && oy) p = 0.5f * (se[ja * CW + ia] + se[(ja + 1) * CW + ia]);
+        else p = 0.25f * (se[ja * CW + ia] + se[ja * CW + ia + 1] + se[(ja + 1) * CW + ia] + se[(ja + 1) * CW + ia + 1]);
+        v = svp[idx] + p;
+      }
+      va[idx] = v;
+    }
+    __syncthreads();
+    cf* vcur = va;
+    cf* vnxt = vb;
+#pragma unroll
+    for (int s_i = 1; s_i <= NU; ++s_i) {
+      const int lo = s_i, W = SW - 2 * lo, Hh = SH - 2 * lo;
+      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+        const int ly = lo + u / W, lx = lo + u % W;
+        const int idx = ly * SW + lx;
+        vnxt[idx] = jacobi_point(vcur, idx, SW, sc * sb[idx], sw[idx], inv_h2, om1);
+      }
+      __syncthreads();
+      cf* tmp = vcur; vcur = vnxt; vnxt = tmp;
+    }
+    cf* o = out + rhs * out_stride;
+    for (int u = threadIdx.x; u < TX * TY; u += kVThreads) {
+      const int gx = x0 + u % TX, gy = y0 + u / TX;
+      if (gx < nx && gy < ny) o[(size_t)gy * nx + gx] = vcur[(H + u / TX) * SW + H + u % TX];
+    }
+    __syncthreads();
+    t = tn;
+    buf ^= 1;
+  }
+}
+
+template <int NU>
+size_t pre_s_smem() {
+  constexpr int H = NU + 1, SW = 64 + 2 * H, SH = 16 + 2 * H;
+  return sizeof(cf) * 8 * SW * SH;
+}
+template <int NU>
+size_t post_s_smem() {
+  constexpr int H = NU, SW = 64 + 2 * H, SH = 16 + 2 * H;
+  constexpr int CW = 32 + H + 2, CH = 8 + H + 2;
+  return sizeof(cf) * (2 * (3 * SW * SH + CW * CH) + 2 * SW * SH);
+}
+
 template <typename T> struct Tile;
 template <> struct Tile<float> { static constexpr int X = 64, Y = 16; };
 template <> struct Tile<double> { static constexpr int X = 32, Y = 16; };
@@ -291,11 +540,37 @@ size_t post_smem() {
   return sizeof(Cx<T>) * (4 * SW * SH + CW * CH);
 }
 
+// Persistent grid size of a streaming kernel: resident blocks per SM times SMs, at most `tiles`.
+template <typename K>
+int persistent_blocks(Handle& h, K kern, size_t smem, int tiles) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVThreads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int n = per_sm * h.num_sms;
+  return n < tiles ? n : tiles;
+}
+
 template <typename T, int NU, typename TIn>
 mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
                          size_t scale_stride, int B, const RhsState* st) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
+  if constexpr (std::is_same<T, float>::value && std::is_same<TIn, float>::value) {
+    const size_t smem = pre_s_smem<NU>();
+    auto kern = k_pre_s<NU, 64, 16>;
+    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TileWalk tw;
+    tw.ntx = (lv.nx + 63) / 64; tw.nty = (lv.ny + 15) / 16; tw.per_rhs = tw.ntx * tw.nty; tw.total = tw.per_rhs * B;
+    tw.st = st;
+    const int grid = persistent_blocks(h, kern, smem, tw.total);
+    ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
+    kern<<<grid, kVThreads, smem, h.stream>>>((const cf*)bin, b_stride, bscale, scale_stride, (const cf*)lv.D,
+                                              (const cf*)lv.wDinv, (cf*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx,
+                                              lv.ny, cl.nx, cl.ny, (float)(1.0 / (lv.h * lv.h)),
+                                              (float)(1.0 - h.p.omega), tw);
+    MGH_CHECK_LAUNCH(); h.launches++;
+    return MGH_OK;
+  }
   constexpr int TX = Tile<T>::X, TY = Tile<T>::Y;
   const size_t smem = pre_smem<T, NU>();
   auto kern = k_pre<T, NU, TX, TY, TIn>;
@@ -316,6 +591,23 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
                           size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
+  if constexpr (std::is_same<T, float>::value && std::is_same<TIn, float>::value &&
+                std::is_same<TOut, float>::value) {
+    const size_t smem = post_s_smem<NU>();
+    auto kern = k_post_s<NU, 64, 16>;
+    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TileWalk tw;
+    tw.ntx = (lv.nx + 63) / 64; tw.nty = (lv.ny + 15) / 16; tw.per_rhs = tw.ntx * tw.nty; tw.total = tw.per_rhs * B;
+    tw.st = st;
+    const int grid = persistent_blocks(h, kern, smem, tw.total);
+    ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
+    kern<<<grid, kVThreads, smem, h.stream>>>((const cf*)bin, b_stride, bscale, scale_stride, (const cf*)lv.wDinv,
+                                              (const cf*)lv.vpre, lv.n(), (const cf*)cl.vfin, cl.n(), cl.nx, cl.ny,
+                                              (cf*)out, out_stride, lv.nx, lv.ny, (float)(1.0 / (lv.h * lv.h)),
+                                              (float)(1.0 - h.p.omega), tw);
+    MGH_CHECK_LAUNCH(); h.launches++;
+    return MGH_OK;
+  }
   constexpr int TX = Tile<T>::X, TY = Tile<T>::Y;
   const size_t smem = post_smem<T, NU>();
   auto kern = k_post<T, NU, TX, TY, TIn, TOut>;
