@@ -100,6 +100,8 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->dev_err); cudaFree(h->xdf); cudaFree(h->bdf);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  delete[] h->tma;
+  delete[] h->tma_in;
   delete h;
 }
 
@@ -244,6 +246,8 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
     free_handle(h);
     return MGH_OUT_OF_MEMORY;
   }
+  s = build_vcycle_tma(*h);
+  if (s != MGH_OK) { free_handle(h); return s; }
   // start from f_d = 0 so that every later call finds a complete operator
   cudaError_t e = cudaMemsetAsync(h->T1, 0, 8 * (size_t)p->nx_int * p->ny_int, h->stream);
   if (e != cudaSuccess) { set_error("cudaMemsetAsync", e, __FILE__, __LINE__); free_handle(h); return MGH_CUDA_ERROR; }

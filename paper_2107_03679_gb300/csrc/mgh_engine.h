@@ -1,6 +1,7 @@
 // Internal host-side interface of the solver engine (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>            // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -29,6 +30,13 @@ struct Level {
   void* vpre = nullptr;      // iterate after pre-smoothing
   void* vfin = nullptr;      // iterate after post-smoothing (levels >= 1)
   size_t n() const { return (size_t)nx * ny; }
+};
+
+// Tensor maps of one FP32 multigrid level for the TMA level kernels (valid when *_ok).
+struct LevelTma {
+  bool pre_ok = false, post_ok = false;
+  CUtensorMap pre_b, pre_w, pre_d;          // pre_b for levels >= 1
+  CUtensorMap post_b, post_w, post_v, post_e;
 };
 
 struct Handle {
@@ -86,6 +94,11 @@ struct Handle {
 
   uint64_t launches = 0;
 
+  // TMA tensor maps of the FP32 cycle (built at create when the encoder is available)
+  LevelTma* tma = nullptr;        // [kMaxLevels]
+  CUtensorMap* tma_in = nullptr;  // [2*m]: level-0 input (hi plane of basis slot j) for pre [j], post [m+j]
+  bool tma_in_ok = false;
+
   // profiling (mgh_profile_enable): event pairs around launches, resolved at read time
   bool prof = false;
   std::vector<cudaEvent_t> ev;     // pool, two per recorded launch
@@ -136,7 +149,10 @@ mgh_status prof_flush(Handle& h);
 // FP32 multigrid cycle whose level-0 input is an FP32 field (the hi plane of a double-float
 // basis vector) scaled per RHS; output in FP32.
 mgh_status vcycle_f32in(Handle& h, const cf* in, size_t in_stride, const double* in_scale,
-                        size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st);
+                        size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st,
+                        int in_slot);
+// Build the tensor maps of the FP32 level kernels (no-op when tensor maps are unavailable).
+mgh_status build_vcycle_tma(Handle& h);
 
 // mgh_krylov_df.cu: mixed-precision engine with double-float Arnoldi
 mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);

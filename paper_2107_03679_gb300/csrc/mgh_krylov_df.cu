@@ -720,7 +720,7 @@ mgh_status df_arnoldi_step(Handle& h, const KArgs& a, int j, int B) {
   // z_j = M^{-1}(u_j / ||u_j||), reading only the hi plane of u_j
   const cf* uhi = reinterpret_cast<const cf*>(reinterpret_cast<const float2*>(h.V) + (size_t)j * 2 * a.Np);
   MGH_TRY(vcycle_f32in(h, uhi, (size_t)(a.m + 1) * 2 * a.Np, h.vscale + j, (size_t)(a.m + 1),
-                       (cf*)h.Z + (size_t)j * a.N, (size_t)a.m * a.N, B, h.st));
+                       (cf*)h.Z + (size_t)j * a.N, (size_t)a.m * a.N, B, h.st, j));
   if (j <= 4) return df_step_nv<4>(h, a, j, B);
   if (j <= 8) return df_step_nv<8>(h, a, j, B);
   if (j <= 12) return df_step_nv<12>(h, a, j, B);

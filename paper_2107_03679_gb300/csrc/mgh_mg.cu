@@ -13,9 +13,12 @@
 // v - w D^{-1}(K v - b) for K v = D v - (sum of neighbours)/h^2; w/D is precomputed per level.
 // Points outside the grid hold 0 in every tile buffer: the Sommerfeld closure already sits in D,
 // and the restriction counts out-of-grid fine samples as 0.
+#include <cudaTypedefs.h>
+#include <new>
 #include <type_traits>
 
 #include "mgh_engine.h"
+#include "mgh_tma.cuh"
 
 namespace mgh {
 
@@ -54,7 +57,7 @@ k_pre(const void* __restrict__ bin, size_t b_stride, const double* __restrict__ 
       T inv_h2, T om1, const RhsState* __restrict__ st) {
   constexpr int H = NU + 1;
   constexpr int SW = TX + 2 * H, SH = TY + 2 * H, S = SW * SH;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Cx<T>* sb = reinterpret_cast<Cx<T>*>(smem_raw);
   Cx<T>* sw = sb + S;
   Cx<T>* sd = sw + S;
@@ -173,7 +176,7 @@ k_post(const void* __restrict__ bin, size_t b_stride, const double* __restrict__
   constexpr int H = NU;
   constexpr int SW = TX + 2 * H, SH = TY + 2 * H, S = SW * SH;
   constexpr int CW = TX / 2 + H + 2, CH = TY / 2 + H + 2, CS = CW * CH;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Cx<T>* sb = reinterpret_cast<Cx<T>*>(smem_raw);
   Cx<T>* sw = sb + S;
   Cx<T>* va = sw + S;
@@ -307,7 +310,7 @@ k_pre_s(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__ 
         TileWalk tw) {
   constexpr int H = NU + 1;
   constexpr int SW = TX + 2 * H, SH = TY + 2 * H, S = SW * SH;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cf* in = reinterpret_cast<cf*>(smem_raw);          // [2][3][S]: b, w/D, D
   cf* va = in + 6 * S;
   cf* vb = va + S;
@@ -421,7 +424,7 @@ k_post_s(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__
   constexpr int SW = TX + 2 * H, SH = TY + 2 * H, S = SW * SH;
   constexpr int CW = TX / 2 + H + 2, CH = TY / 2 + H + 2, CS = CW * CH;
   constexpr int STAGE = 3 * S + CS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cf* in = reinterpret_cast<cf*>(smem_raw);          // [2][STAGE]: v_pre, b, w/D, coarse e
   cf* va = in + 2 * STAGE;
   cf* vb = va + S;
@@ -512,6 +515,282 @@ k_post_s(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__
   }
 }
 
+// ---------------------------------------------------------------- TMA tensor-tile level kernels
+// The same persistent double-buffered scheme with the tile inputs fetched by the tensor-memory
+// accelerator: one thread issues a 2-D or 3-D tensor copy per input array and stage, points
+// outside the grid arrive as zeros, and the copies complete on an mbarrier per stage.  A box
+// must start at an even x (8-byte elements, 16-byte rule), so the x halo is rounded up to an
+// even width.  Used for FP32 levels of even width; odd widths use the cp.async kernels.
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared arrays start on 128-byte boundaries (16 complex FP32 values).
+__host__ __device__ constexpr int pad16(int n) { return (n + 15) & ~15; }
+
+template <int NU, int TX, int TY>
+struct PreGeom {
+  static constexpr int H = NU + 1, HX = (H + 1) & ~1;
+  static constexpr int SW = TX + 2 * HX, SH = TY + 2 * H, S = SW * SH, SP = pad16(S);
+  static constexpr size_t smem() { return 128 + sizeof(cf) * (2 * 3 * SP + 2 * SP); }
+};
+
+template <int NU, int TX, int TY>
+__global__ void __launch_bounds__(kVThreads)
+k_pre_t(const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtensorMap tm_w,
+        const __grid_constant__ CUtensorMap tm_d, const double* __restrict__ bscale, size_t scale_stride,
+        cf* __restrict__ vpre, size_t v_stride, cf* __restrict__ bc, size_t bc_stride, int nx, int ny, int nxc,
+        int nyc, float inv_h2, float om1, TileWalk tw, int* __restrict__ err) {
+  using G = PreGeom<NU, TX, TY>;
+  constexpr int H = G::H, HX = G::HX, SW = G::SW, SH = G::SH, S = G::S, SP = G::SP;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  __shared__ int fail;
+  cf* in = reinterpret_cast<cf*>(smem_raw + 128);  // [2][3][SP]: b, w/D, D
+  cf* va = in + 6 * SP;
+  cf* vb = va + SP;
+  const int step = gridDim.x;
+  constexpr uint32_t kBytes = 3u * S * sizeof(cf);
+  auto issue = [&](int t, int buf) {
+    const int rhs = t / tw.per_rhs, r = t - rhs * tw.per_rhs;
+    const int y0 = (r / tw.ntx) * TY, x0 = (r % tw.ntx) * TX;
+    cf* base = in + buf * 3 * SP;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[buf], kBytes);
+    tma_load_3d(base, &tm_b, x0 - HX, y0 - H, rhs, &bar[buf]);
+    tma_load_2d(base + SP, &tm_w, x0 - HX, y0 - H, &bar[buf]);
+    tma_load_2d(base + 2 * SP, &tm_d, x0 - HX, y0 - H, &bar[buf]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    fail = 0;
+  }
+  __syncthreads();
+  int t = tw.next(blockIdx.x, step);
+  if (threadIdx.x == 0 && t < tw.total) issue(t, 0);
+  int buf = 0, k = 0;
+  uint32_t phase[2] = {0u, 0u};
+  while (t < tw.total) {
+    const int tn = tw.next(t + step, step);
+    if (threadIdx.x == 0 && tn < tw.total) issue(tn, buf ^ 1);
+    if (!mbar_wait(&bar[buf], phase[buf], kWaitLimitNs)) fail = 1;
+    phase[buf] ^= 1u;
+    __syncthreads();
+    if (fail) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, kErrTimeout);
+        if (tn < tw.total) mbar_wait(&bar[buf ^ 1], phase[buf ^ 1], kWaitLimitNs);
+      }
+      __syncthreads();
+      return;
+    }
+    const cf* sb = in + buf * 3 * SP;
+    const cf* sw = sb + SP;
+    const cf* sd = sb + 2 * SP;
+    const int rhs = t / tw.per_rhs, r = t - rhs * tw.per_rhs;
+    const int y0 = (r / tw.ntx) * TY, x0 = (r % tw.ntx) * TX;
+    const float sc = bscale ? (float)bscale[rhs * scale_stride] : 1.f;
+    cf* vcur = va;
+    cf* vnxt = vb;
+    if constexpr (NU >= 1) {
+      for (int idx = threadIdx.x; idx < S; idx += kVThreads) va[idx] = sw[idx] * (sc * sb[idx]);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int s_i = 2; s_i <= NU; ++s_i) {
+      const int lo = s_i - 1, W = SW - 2 * lo, Hh = SH - 2 * lo;
+      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+        const int ly = lo + u / W, lx = lo + u % W;
+        const int idx = ly * SW + lx;
+        vnxt[idx] = jacobi_point(vcur, idx, SW, sc * sb[idx], sw[idx], inv_h2, om1);
+      }
+      __syncthreads();
+      cf* tmp = vcur; vcur = vnxt; vnxt = tmp;
+    }
+    cf* rr = vnxt;
+    {
+      constexpr int W = TX + 1, Hh = TY + 1;
+      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+        const int ly = H - 1 + u / W, lx = HX - 1 + u % W;
+        const int idx = ly * SW + lx;
+        const int gx = x0 - HX + lx, gy = y0 - H + ly;
+        cf rv = czero<float>();
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+          if constexpr (NU >= 1) {
+            const cf s4 = vcur[idx - 1] + vcur[idx + 1] + vcur[idx - SW] + vcur[idx + SW];
+            const cf kv = sd[idx] * vcur[idx] - inv_h2 * s4;
+            rv = sc * sb[idx] - kv;
+          } else {
+            rv = sc * sb[idx];
+          }
+        }
+        rr[idx] = rv;
+      }
+    }
+    __syncthreads();
+    {
+      constexpr int CW = TX / 2, CH = TY / 2;
+      const int ci0 = x0 / 2, cj0 = y0 / 2;
+      cf* bco = bc + rhs * bc_stride;
+      for (int u = threadIdx.x; u < CW * CH; u += kVThreads) {
+        const int ci = ci0 + u % CW, cj = cj0 + u / CW;
+        if (ci >= nxc || cj >= nyc) continue;
+        const int idx = (2 * cj - y0 + H) * SW + 2 * ci - x0 + HX;
+        const cf e = rr[idx - 1] + rr[idx + 1] + rr[idx - SW] + rr[idx + SW];
+        const cf c = rr[idx - SW - 1] + rr[idx - SW + 1] + rr[idx + SW - 1] + rr[idx + SW + 1];
+        bco[(size_t)cj * nxc + ci] = mk<float>(0.0625f * (4.f * rr[idx].re + 2.f * e.re + c.re),
+                                               0.0625f * (4.f * rr[idx].im + 2.f * e.im + c.im));
+      }
+      cf* vo = vpre + rhs * v_stride;
+      for (int u = threadIdx.x; u < TX * TY; u += kVThreads) {
+        const int gx = x0 + u % TX, gy = y0 + u / TX;
+        if (gx < nx && gy < ny) {
+          cf v = czero<float>();
+          if constexpr (NU >= 1) v = vcur[(H + u / TX) * SW + HX + u % TX];
+          vo[(size_t)gy * nx + gx] = v;
+        }
+      }
+    }
+    __syncthreads();
+    t = tn;
+    buf ^= 1;
+    ++k;
+  }
+}
+
+template <int NU, int TX, int TY>
+struct PostGeom {
+  static constexpr int H = NU, HX = (NU + 1) & ~1;
+  static constexpr int SW = TX + 2 * HX, SH = TY + 2 * H, S = SW * SH, SP = pad16(S);
+  static constexpr int CW = ((TX / 2 + HX + 3) + 1) & ~1, CH = TY / 2 + H + 2, CS = CW * CH, CSP = pad16(CS);
+  static constexpr int STAGE = 3 * SP + CSP;
+  static constexpr size_t smem() { return 128 + sizeof(cf) * (2 * STAGE + 2 * SP); }
+};
+
+template <int NU, int TX, int TY>
+__global__ void __launch_bounds__(kVThreads)
+k_post_t(const __grid_constant__ CUtensorMap tm_v, const __grid_constant__ CUtensorMap tm_b,
+         const __grid_constant__ CUtensorMap tm_w, const __grid_constant__ CUtensorMap tm_e,
+         const double* __restrict__ bscale, size_t scale_stride, cf* __restrict__ out, size_t out_stride, int nx,
+         int ny, float inv_h2, float om1, TileWalk tw, int* __restrict__ err) {
+  using G = PostGeom<NU, TX, TY>;
+  constexpr int H = G::H, HX = G::HX, SW = G::SW, SH = G::SH, S = G::S, SP = G::SP, CW = G::CW, CS = G::CS,
+                STAGE = G::STAGE;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  __shared__ int fail;
+  cf* in = reinterpret_cast<cf*>(smem_raw + 128);  // [2][STAGE]: v_pre, b, w/D, coarse e
+  cf* va = in + 2 * STAGE;
+  cf* vb = va + SP;
+  const int step = gridDim.x;
+  constexpr uint32_t kBytes = (uint32_t)((NU >= 1 ? 3 * S : S) + CS) * sizeof(cf);
+  auto coarse_origin = [&](int x0, int y0, int& cx0, int& cy0) {
+    cx0 = floor_half(x0 - H - 1);
+    cx0 -= (cx0 & 1);            // even start for the 16-byte rule
+    cy0 = floor_half(y0 - H - 1);
+  };
+  auto issue = [&](int t, int buf) {
+    const int rhs = t / tw.per_rhs, r = t - rhs * tw.per_rhs;
+    const int y0 = (r / tw.ntx) * TY, x0 = (r % tw.ntx) * TX;
+    int cx0, cy0;
+    coarse_origin(x0, y0, cx0, cy0);
+    cf* base = in + buf * STAGE;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[buf], kBytes);
+    tma_load_3d(base, &tm_v, x0 - HX, y0 - H, rhs, &bar[buf]);
+    if constexpr (NU >= 1) {
+      tma_load_3d(base + SP, &tm_b, x0 - HX, y0 - H, rhs, &bar[buf]);
+      tma_load_2d(base + 2 * SP, &tm_w, x0 - HX, y0 - H, &bar[buf]);
+    }
+    tma_load_3d(base + 3 * SP, &tm_e, cx0, cy0, rhs, &bar[buf]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    fail = 0;
+  }
+  __syncthreads();
+  int t = tw.next(blockIdx.x, step);
+  if (threadIdx.x == 0 && t < tw.total) issue(t, 0);
+  int buf = 0;
+  uint32_t phase[2] = {0u, 0u};
+  while (t < tw.total) {
+    const int tn = tw.next(t + step, step);
+    if (threadIdx.x == 0 && tn < tw.total) issue(tn, buf ^ 1);
+    if (!mbar_wait(&bar[buf], phase[buf], kWaitLimitNs)) fail = 1;
+    phase[buf] ^= 1u;
+    __syncthreads();
+    if (fail) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, kErrTimeout);
+        if (tn < tw.total) mbar_wait(&bar[buf ^ 1], phase[buf ^ 1], kWaitLimitNs);
+      }
+      __syncthreads();
+      return;
+    }
+    const cf* svp = in + buf * STAGE;
+    const cf* sb = svp + SP;
+    const cf* sw = svp + 2 * SP;
+    const cf* se = svp + 3 * SP;
+    const int rhs = t / tw.per_rhs, r = t - rhs * tw.per_rhs;
+    const int y0 = (r / tw.ntx) * TY, x0 = (r % tw.ntx) * TX;
+    int cx0, cy0;
+    coarse_origin(x0, y0, cx0, cy0);
+    const float sc = bscale ? (float)bscale[rhs * scale_stride] : 1.f;
+    for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
+      const int ly = idx / SW, lx = idx - ly * SW;
+      const int gx = x0 - HX + lx, gy = y0 - H + ly;
+      cf v = czero<float>();
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        const int ia = (gx >> 1) - cx0, ja = (gy >> 1) - cy0;
+        const bool ox = gx & 1, oy = gy & 1;
+        cf p;
+        if (!ox && !oy) p = se[ja * CW + ia];
+        else if (ox && !oy) p = 0.5f * (se[ja * CW + ia] + se[ja * CW + ia + 1]);
+        else if (!ox && oy) p = 0.5f * (se[ja * CW + ia] + se[(ja + 1) * CW + ia]);
+        else p = 0.25f * (se[ja * CW + ia] + se[ja * CW + ia + 1] + se[(ja + 1) * CW + ia] + se[(ja + 1) * CW + ia + 1]);
+        v = svp[idx] + p;
+      }
+      va[idx] = v;
+    }
+    __syncthreads();
+    cf* vcur = va;
+    cf* vnxt = vb;
+#pragma unroll
+    for (int s_i = 1; s_i <= NU; ++s_i) {
+      const int lo = s_i, W = SW - 2 * lo, Hh = SH - 2 * lo;
+      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+        const int ly = lo + u / W, lx = lo + u % W;
+        const int idx = ly * SW + lx;
+        vnxt[idx] = jacobi_point(vcur, idx, SW, sc * sb[idx], sw[idx], inv_h2, om1);
+      }
+      __syncthreads();
+      cf* tmp = vcur; vcur = vnxt; vnxt = tmp;
+    }
+    cf* o = out + rhs * out_stride;
+    for (int u = threadIdx.x; u < TX * TY; u += kVThreads) {
+      const int gx = x0 + u % TX, gy = y0 + u / TX;
+      if (gx < nx && gy < ny) o[(size_t)gy * nx + gx] = vcur[(H + u / TX) * SW + HX + u % TX];
+    }
+    __syncthreads();
+    t = tn;
+    buf ^= 1;
+  }
+}
+
 template <int NU>
 size_t pre_s_smem() {
   constexpr int H = NU + 1, SW = 64 + 2 * H, SH = 16 + 2 * H;
@@ -552,10 +831,32 @@ int persistent_blocks(Handle& h, K kern, size_t smem, int tiles) {
 
 template <typename T, int NU, typename TIn>
 mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
-                         size_t scale_stride, int B, const RhsState* st) {
+                         size_t scale_stride, int B, const RhsState* st, int in_slot) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
   if constexpr (std::is_same<T, float>::value && std::is_same<TIn, float>::value) {
+    const bool tma = h.tma && h.tma[l].pre_ok && (l > 0 || (in_slot >= 0 && h.tma_in_ok));
+    if (tma) {
+      using G = PreGeom<NU, 64, 16>;
+      auto kern = k_pre_t<NU, 64, 16>;
+      static bool attr = false;
+      if (!attr) {
+        MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem()));
+        attr = true;
+      }
+      TileWalk tw;
+      tw.ntx = (lv.nx + 63) / 64; tw.nty = (lv.ny + 15) / 16; tw.per_rhs = tw.ntx * tw.nty; tw.total = tw.per_rhs * B;
+      tw.st = st;
+      const int grid = persistent_blocks(h, kern, G::smem(), tw.total);
+      const CUtensorMap& mb = l == 0 ? h.tma_in[in_slot] : h.tma[l].pre_b;
+      ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
+      kern<<<grid, kVThreads, G::smem(), h.stream>>>(mb, h.tma[l].pre_w, h.tma[l].pre_d, bscale, scale_stride,
+                                                     (cf*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx,
+                                                     cl.ny, (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega),
+                                                     tw, h.dev_err);
+      MGH_CHECK_LAUNCH(); h.launches++;
+      return MGH_OK;
+    }
     const size_t smem = pre_s_smem<NU>();
     auto kern = k_pre_s<NU, 64, 16>;
     MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -588,11 +889,34 @@ mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, con
 
 template <typename T, int NU, typename TIn, typename TOut>
 mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
-                          size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st) {
+                          size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st,
+                          int in_slot) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
   if constexpr (std::is_same<T, float>::value && std::is_same<TIn, float>::value &&
                 std::is_same<TOut, float>::value) {
+    const bool tma = h.tma && h.tma[l].post_ok && (l > 0 || (in_slot >= 0 && h.tma_in_ok));
+    if (tma) {
+      using G = PostGeom<NU, 64, 16>;
+      auto kern = k_post_t<NU, 64, 16>;
+      static bool attr = false;
+      if (!attr) {
+        MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem()));
+        attr = true;
+      }
+      TileWalk tw;
+      tw.ntx = (lv.nx + 63) / 64; tw.nty = (lv.ny + 15) / 16; tw.per_rhs = tw.ntx * tw.nty; tw.total = tw.per_rhs * B;
+      tw.st = st;
+      const int grid = persistent_blocks(h, kern, G::smem(), tw.total);
+      const CUtensorMap& mb = l == 0 ? h.tma_in[h.m + in_slot] : h.tma[l].post_b;
+      ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
+      kern<<<grid, kVThreads, G::smem(), h.stream>>>(h.tma[l].post_v, mb, h.tma[l].post_w, h.tma[l].post_e, bscale,
+                                                     scale_stride, (cf*)out, out_stride, lv.nx, lv.ny,
+                                                     (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega), tw,
+                                                     h.dev_err);
+      MGH_CHECK_LAUNCH(); h.launches++;
+      return MGH_OK;
+    }
     const size_t smem = post_s_smem<NU>();
     auto kern = k_post_s<NU, 64, 16>;
     MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -625,36 +949,37 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
 
 template <typename T, typename TIn>
 mgh_status launch_pre(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
-                      size_t scale_stride, int B, const RhsState* st) {
+                      size_t scale_stride, int B, const RhsState* st, int in_slot = -1) {
   switch (h.p.nu1) {
-    case 0: return launch_pre_nu<T, 0, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
-    case 1: return launch_pre_nu<T, 1, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
-    case 2: return launch_pre_nu<T, 2, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
-    case 3: return launch_pre_nu<T, 3, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
-    case 4: return launch_pre_nu<T, 4, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st);
+    case 0: return launch_pre_nu<T, 0, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st, in_slot);
+    case 1: return launch_pre_nu<T, 1, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st, in_slot);
+    case 2: return launch_pre_nu<T, 2, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st, in_slot);
+    case 3: return launch_pre_nu<T, 3, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st, in_slot);
+    case 4: return launch_pre_nu<T, 4, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st, in_slot);
   }
   return MGH_INVALID_ARG;
 }
 
 template <typename T, typename TIn, typename TOut>
 mgh_status launch_post(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
-                       size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st) {
+                       size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st,
+                       int in_slot = -1) {
   switch (h.p.nu2) {
-    case 0: return launch_post_nu<T, 0, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
-    case 1: return launch_post_nu<T, 1, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
-    case 2: return launch_post_nu<T, 2, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
-    case 3: return launch_post_nu<T, 3, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
-    case 4: return launch_post_nu<T, 4, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    case 0: return launch_post_nu<T, 0, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st, in_slot);
+    case 1: return launch_post_nu<T, 1, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st, in_slot);
+    case 2: return launch_post_nu<T, 2, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st, in_slot);
+    case 3: return launch_post_nu<T, 3, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st, in_slot);
+    case 4: return launch_post_nu<T, 4, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st, in_slot);
   }
   return MGH_INVALID_ARG;
 }
 
 template <typename T, typename TIn>
 mgh_status vcycle_t(Handle& h, const void* in, size_t in_stride, const double* in_scale, size_t scale_stride,
-                    void* out, size_t out_stride, bool out_fp64, int B, const RhsState* st) {
+                    void* out, size_t out_stride, bool out_fp64, int B, const RhsState* st, int in_slot = -1) {
   const int L = h.L;
   // down: level 0 reads the input, coarser levels their restricted right-hand side
-  MGH_TRY((launch_pre<T, TIn>(h, 0, in, in_stride, in_scale, scale_stride, B, st)));
+  MGH_TRY((launch_pre<T, TIn>(h, 0, in, in_stride, in_scale, scale_stride, B, st, in_slot)));
   for (int l = 1; l + 1 < L; ++l)
     MGH_TRY((launch_pre<T, T>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, B, st)));
   // coarsest: exact solve
@@ -666,7 +991,8 @@ mgh_status vcycle_t(Handle& h, const void* in, size_t in_stride, const double* i
                                   h.lev[l].n(), B, st)));
   if (out_fp64)
     return launch_post<T, TIn, double>(h, 0, in, in_stride, in_scale, scale_stride, (cd*)out, out_stride, B, st);
-  return launch_post<T, TIn, T>(h, 0, in, in_stride, in_scale, scale_stride, (Cx<T>*)out, out_stride, B, st);
+  return launch_post<T, TIn, T>(h, 0, in, in_stride, in_scale, scale_stride, (Cx<T>*)out, out_stride, B, st,
+                                in_slot);
 }
 
 }  // namespace
@@ -679,8 +1005,94 @@ mgh_status vcycle(Handle& h, const cd* in, size_t in_stride, const double* in_sc
 }
 
 mgh_status vcycle_f32in(Handle& h, const cf* in, size_t in_stride, const double* in_scale, size_t scale_stride,
-                        cf* out, size_t out_stride, int B, const RhsState* st) {
-  return vcycle_t<float, float>(h, in, in_stride, in_scale, scale_stride, out, out_stride, false, B, st);
+                        cf* out, size_t out_stride, int B, const RhsState* st, int in_slot) {
+  return vcycle_t<float, float>(h, in, in_stride, in_scale, scale_stride, out, out_stride, false, B, st, in_slot);
+}
+
+// ---------------------------------------------------------------- tensor maps
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map over complex FP32 data (8-byte elements): dims (nx, ny[, nz]), byte strides of
+// rows and planes, box (bx, by[, 1]).  False if the 16-byte rules of the encoder are not met.
+bool encode_map(CUtensorMap* map, const void* base, int rank, uint64_t nx, uint64_t ny, uint64_t nz,
+                uint64_t row_bytes, uint64_t plane_bytes, uint32_t bx, uint32_t by) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15) || (rank == 3 && (plane_bytes & 15))) return false;
+  if ((bx * 8) % 16 || bx > 256 || by > 256) return false;
+  cuuint64_t dims[3] = {nx, ny, nz};
+  cuuint64_t strides[2] = {row_bytes, plane_bytes};
+  cuuint32_t box[3] = {bx, by, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
+                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Box geometry of the TMA level kernels for nu sweeps (mirrors PreGeom / PostGeom).
+struct BoxDims { int sw, sh, cw, ch; };
+BoxDims pre_box(int nu) {
+  const int H = nu + 1, HX = (H + 1) & ~1;
+  return {64 + 2 * HX, 16 + 2 * H, 0, 0};
+}
+BoxDims post_box(int nu) {
+  const int H = nu, HX = (nu + 1) & ~1;
+  return {64 + 2 * HX, 16 + 2 * H, ((32 + HX + 3) + 1) & ~1, 8 + H + 2};
+}
+
+}  // namespace
+
+mgh_status build_vcycle_tma(Handle& h) {
+  if (h.fp64 || !tensor_map_encoder()) return MGH_OK;
+  h.tma = new (std::nothrow) LevelTma[kMaxLevels];
+  h.tma_in = new (std::nothrow) CUtensorMap[2 * h.m];
+  if (!h.tma || !h.tma_in) return MGH_OUT_OF_MEMORY;
+  const BoxDims bp = pre_box(h.p.nu1), bq = post_box(h.p.nu2);
+  const uint64_t B = h.Bmax;
+  for (int l = 0; l + 1 < h.L; ++l) {
+    const Level& lv = h.lev[l];
+    const Level& cl = h.lev[l + 1];
+    LevelTma& t = h.tma[l];
+    const uint64_t row = (uint64_t)lv.nx * 8, plane = (uint64_t)lv.n() * 8;
+    bool ok = (lv.nx % 2 == 0);
+    ok = ok && encode_map(&t.pre_w, lv.wDinv, 2, lv.nx, lv.ny, 1, row, 0, bp.sw, bp.sh);
+    ok = ok && encode_map(&t.pre_d, lv.D, 2, lv.nx, lv.ny, 1, row, 0, bp.sw, bp.sh);
+    if (l >= 1) ok = ok && encode_map(&t.pre_b, lv.b, 3, lv.nx, lv.ny, B, row, plane, bp.sw, bp.sh);
+    t.pre_ok = ok;
+    bool okp = (lv.nx % 2 == 0) && (cl.nx % 2 == 0);
+    okp = okp && encode_map(&t.post_w, lv.wDinv, 2, lv.nx, lv.ny, 1, row, 0, bq.sw, bq.sh);
+    okp = okp && encode_map(&t.post_v, lv.vpre, 3, lv.nx, lv.ny, B, row, plane, bq.sw, bq.sh);
+    if (l >= 1) okp = okp && encode_map(&t.post_b, lv.b, 3, lv.nx, lv.ny, B, row, plane, bq.sw, bq.sh);
+    okp = okp && encode_map(&t.post_e, cl.vfin, 3, cl.nx, cl.ny, B, (uint64_t)cl.nx * 8, (uint64_t)cl.n() * 8,
+                            bq.cw, bq.ch);
+    t.post_ok = okp;
+  }
+  // level-0 inputs: the hi plane of basis slot j of every right-hand side
+  bool ok = (h.nx % 2 == 0);
+  const float2* V = reinterpret_cast<const float2*>(h.V);
+  const uint64_t rhs_bytes = (uint64_t)(h.m + 1) * 2 * h.Np * 8;
+  for (int j = 0; j < h.m && ok; ++j) {
+    const float2* base = V + (size_t)j * 2 * h.Np;
+    ok = encode_map(&h.tma_in[j], base, 3, h.nx, h.ny, B, (uint64_t)h.nx * 8, rhs_bytes, bp.sw, bp.sh) &&
+         encode_map(&h.tma_in[h.m + j], base, 3, h.nx, h.ny, B, (uint64_t)h.nx * 8, rhs_bytes, bq.sw, bq.sh);
+  }
+  h.tma_in_ok = ok;
+  return MGH_OK;
 }
 
 }  // namespace mgh
