@@ -49,6 +49,8 @@ def parse_args(argv=None):
                     help="use only the first N illumination angles (smaller case for profiling)")
     ap.add_argument("--restart", type=int, default=None, help="GMRES restart length (default: the workload's)")
     ap.add_argument("--nu", type=int, default=None, help="pre- and post-smoothing sweeps (default: the workload's)")
+    ap.add_argument("--levels", type=int, default=None, help="multigrid levels (default: the workload's)")
+    ap.add_argument("--maxit", type=int, default=20000, help="Arnoldi steps per solve before giving up")
     ap.add_argument("--arnoldi", choices=["df", "fp64"], default="df",
                     help="mixed precision Arnoldi arithmetic: double-float on FP32 pipes or native FP64")
     ap.add_argument("--autotune", action="store_true",
@@ -286,6 +288,8 @@ def gpu_main(args, rank, world, local_rank):
         w.restart = args.restart
     if args.nu is not None:
         w.nu1 = w.nu2 = args.nu
+    if args.levels:
+        w.levels = args.levels
     precision = args.precision or w.precision
     f_gt, f_step, th, rec = make_inputs(w)
     if args.angles:
@@ -297,7 +301,7 @@ def gpu_main(args, rank, world, local_rank):
         tuned, trials = tune(w, torch.from_numpy(f_step).to(dev), torch.from_numpy(th), dev, precision=precision)
         w.nu1 = w.nu2 = tuned["nu"]
         w.restart = tuned["restart"]
-    solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=20000, arnoldi=args.arnoldi)
+    solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=args.maxit, arnoldi=args.arnoldi)
     stream = solver.stream
     d_th = torch.from_numpy(th).to(dev)
     d_rec = torch.from_numpy(rec).to(dev)
