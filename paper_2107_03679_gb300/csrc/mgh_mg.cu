@@ -25,6 +25,7 @@ namespace mgh {
 namespace {
 
 constexpr int kVThreads = 256;
+constexpr int kVcThreadsTma = 512;   // threads of the TMA level kernels (one tile per block)
 
 // Right-hand side of a level: complex TIn (FP64 input, FP32 hi plane of a double-float
 // basis vector, or the level's own precision) times a per-RHS scale, converted to T.
@@ -545,8 +546,8 @@ struct PreGeom {
   static constexpr size_t smem() { return 128 + sizeof(cf) * (2 * 3 * SP + 2 * SP); }
 };
 
-template <int NU, int TX, int TY>
-__global__ void __launch_bounds__(kVThreads)
+template <int NU, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
 k_pre_t(const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtensorMap tm_w,
         const __grid_constant__ CUtensorMap tm_d, const double* __restrict__ bscale, size_t scale_stride,
         cf* __restrict__ vpre, size_t v_stride, cf* __restrict__ bc, size_t bc_stride, int nx, int ny, int nxc,
@@ -605,13 +606,13 @@ k_pre_t(const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtens
     cf* vcur = va;
     cf* vnxt = vb;
     if constexpr (NU >= 1) {
-      for (int idx = threadIdx.x; idx < S; idx += kVThreads) va[idx] = sw[idx] * (sc * sb[idx]);
+      for (int idx = threadIdx.x; idx < S; idx += NT) va[idx] = sw[idx] * (sc * sb[idx]);
       __syncthreads();
     }
 #pragma unroll
     for (int s_i = 2; s_i <= NU; ++s_i) {
       const int lo = s_i - 1, W = SW - 2 * lo, Hh = SH - 2 * lo;
-      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+      for (int u = threadIdx.x; u < W * Hh; u += NT) {
         const int ly = lo + u / W, lx = lo + u % W;
         const int idx = ly * SW + lx;
         vnxt[idx] = jacobi_point(vcur, idx, SW, sc * sb[idx], sw[idx], inv_h2, om1);
@@ -622,7 +623,7 @@ k_pre_t(const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtens
     cf* rr = vnxt;
     {
       constexpr int W = TX + 1, Hh = TY + 1;
-      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+      for (int u = threadIdx.x; u < W * Hh; u += NT) {
         const int ly = H - 1 + u / W, lx = HX - 1 + u % W;
         const int idx = ly * SW + lx;
         const int gx = x0 - HX + lx, gy = y0 - H + ly;
@@ -644,7 +645,7 @@ k_pre_t(const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtens
       constexpr int CW = TX / 2, CH = TY / 2;
       const int ci0 = x0 / 2, cj0 = y0 / 2;
       cf* bco = bc + rhs * bc_stride;
-      for (int u = threadIdx.x; u < CW * CH; u += kVThreads) {
+      for (int u = threadIdx.x; u < CW * CH; u += NT) {
         const int ci = ci0 + u % CW, cj = cj0 + u / CW;
         if (ci >= nxc || cj >= nyc) continue;
         const int idx = (2 * cj - y0 + H) * SW + 2 * ci - x0 + HX;
@@ -654,7 +655,7 @@ k_pre_t(const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtens
                                                0.0625f * (4.f * rr[idx].im + 2.f * e.im + c.im));
       }
       cf* vo = vpre + rhs * v_stride;
-      for (int u = threadIdx.x; u < TX * TY; u += kVThreads) {
+      for (int u = threadIdx.x; u < TX * TY; u += NT) {
         const int gx = x0 + u % TX, gy = y0 + u / TX;
         if (gx < nx && gy < ny) {
           cf v = czero<float>();
@@ -679,8 +680,8 @@ struct PostGeom {
   static constexpr size_t smem() { return 128 + sizeof(cf) * (2 * STAGE + 2 * SP); }
 };
 
-template <int NU, int TX, int TY>
-__global__ void __launch_bounds__(kVThreads)
+template <int NU, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
 k_post_t(const __grid_constant__ CUtensorMap tm_v, const __grid_constant__ CUtensorMap tm_b,
          const __grid_constant__ CUtensorMap tm_w, const __grid_constant__ CUtensorMap tm_e,
          const double* __restrict__ bscale, size_t scale_stride, cf* __restrict__ out, size_t out_stride, int nx,
@@ -750,7 +751,7 @@ k_post_t(const __grid_constant__ CUtensorMap tm_v, const __grid_constant__ CUten
     int cx0, cy0;
     coarse_origin(x0, y0, cx0, cy0);
     const float sc = bscale ? (float)bscale[rhs * scale_stride] : 1.f;
-    for (int idx = threadIdx.x; idx < S; idx += kVThreads) {
+    for (int idx = threadIdx.x; idx < S; idx += NT) {
       const int ly = idx / SW, lx = idx - ly * SW;
       const int gx = x0 - HX + lx, gy = y0 - H + ly;
       cf v = czero<float>();
@@ -772,7 +773,7 @@ k_post_t(const __grid_constant__ CUtensorMap tm_v, const __grid_constant__ CUten
 #pragma unroll
     for (int s_i = 1; s_i <= NU; ++s_i) {
       const int lo = s_i, W = SW - 2 * lo, Hh = SH - 2 * lo;
-      for (int u = threadIdx.x; u < W * Hh; u += kVThreads) {
+      for (int u = threadIdx.x; u < W * Hh; u += NT) {
         const int ly = lo + u / W, lx = lo + u % W;
         const int idx = ly * SW + lx;
         vnxt[idx] = jacobi_point(vcur, idx, SW, sc * sb[idx], sw[idx], inv_h2, om1);
@@ -781,7 +782,7 @@ k_post_t(const __grid_constant__ CUtensorMap tm_v, const __grid_constant__ CUten
       cf* tmp = vcur; vcur = vnxt; vnxt = tmp;
     }
     cf* o = out + rhs * out_stride;
-    for (int u = threadIdx.x; u < TX * TY; u += kVThreads) {
+    for (int u = threadIdx.x; u < TX * TY; u += NT) {
       const int gx = x0 + u % TX, gy = y0 + u / TX;
       if (gx < nx && gy < ny) o[(size_t)gy * nx + gx] = vcur[(H + u / TX) * SW + HX + u % TX];
     }
@@ -821,9 +822,9 @@ size_t post_smem() {
 
 // Persistent grid size of a streaming kernel: resident blocks per SM times SMs, at most `tiles`.
 template <typename K>
-int persistent_blocks(Handle& h, K kern, size_t smem, int tiles) {
+int persistent_blocks(Handle& h, K kern, size_t smem, int tiles, int threads = kVThreads) {
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVThreads, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int n = per_sm * h.num_sms;
   return n < tiles ? n : tiles;
@@ -838,7 +839,7 @@ mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, con
     const bool tma = h.tma && h.tma[l].pre_ok && (l > 0 || (in_slot >= 0 && h.tma_in_ok));
     if (tma) {
       using G = PreGeom<NU, 64, 16>;
-      auto kern = k_pre_t<NU, 64, 16>;
+      auto kern = k_pre_t<NU, 64, 16, kVcThreadsTma>;
       static bool attr = false;
       if (!attr) {
         MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem()));
@@ -847,10 +848,10 @@ mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, con
       TileWalk tw;
       tw.ntx = (lv.nx + 63) / 64; tw.nty = (lv.ny + 15) / 16; tw.per_rhs = tw.ntx * tw.nty; tw.total = tw.per_rhs * B;
       tw.st = st;
-      const int grid = persistent_blocks(h, kern, G::smem(), tw.total);
+      const int grid = persistent_blocks(h, kern, G::smem(), tw.total, kVcThreadsTma);
       const CUtensorMap& mb = l == 0 ? h.tma_in[in_slot] : h.tma[l].pre_b;
       ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
-      kern<<<grid, kVThreads, G::smem(), h.stream>>>(mb, h.tma[l].pre_w, h.tma[l].pre_d, bscale, scale_stride,
+      kern<<<grid, kVcThreadsTma, G::smem(), h.stream>>>(mb, h.tma[l].pre_w, h.tma[l].pre_d, bscale, scale_stride,
                                                      (cf*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx,
                                                      cl.ny, (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega),
                                                      tw, h.dev_err);
@@ -898,7 +899,7 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
     const bool tma = h.tma && h.tma[l].post_ok && (l > 0 || (in_slot >= 0 && h.tma_in_ok));
     if (tma) {
       using G = PostGeom<NU, 64, 16>;
-      auto kern = k_post_t<NU, 64, 16>;
+      auto kern = k_post_t<NU, 64, 16, kVcThreadsTma>;
       static bool attr = false;
       if (!attr) {
         MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem()));
@@ -907,10 +908,10 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
       TileWalk tw;
       tw.ntx = (lv.nx + 63) / 64; tw.nty = (lv.ny + 15) / 16; tw.per_rhs = tw.ntx * tw.nty; tw.total = tw.per_rhs * B;
       tw.st = st;
-      const int grid = persistent_blocks(h, kern, G::smem(), tw.total);
+      const int grid = persistent_blocks(h, kern, G::smem(), tw.total, kVcThreadsTma);
       const CUtensorMap& mb = l == 0 ? h.tma_in[h.m + in_slot] : h.tma[l].post_b;
       ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
-      kern<<<grid, kVThreads, G::smem(), h.stream>>>(h.tma[l].post_v, mb, h.tma[l].post_w, h.tma[l].post_e, bscale,
+      kern<<<grid, kVcThreadsTma, G::smem(), h.stream>>>(h.tma[l].post_v, mb, h.tma[l].post_w, h.tma[l].post_e, bscale,
                                                      scale_stride, (cf*)out, out_stride, lv.nx, lv.ny,
                                                      (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega), tw,
                                                      h.dev_err);
