@@ -65,7 +65,7 @@ size_t workspace_bytes(const mgh_params& p) {
   const size_t nc = (size_t)nxl[p.levels - 1] * nyl[p.levels - 1];
   const size_t W = 3 * (size_t)nxl[p.levels - 1] + 1;
   t += pad256(8 * (size_t)p.nx_int * p.ny_int) + pad256(16 * N);
-  t += pad256(16 * nc * W) + pad256(4 * nc) + pad256(16 * nc * nc) + pad256(8 * nc * nc) + pad256(4);
+  t += pad256(16 * nc * W) + pad256(4 * nc) + 2 * pad256(16 * nc * nc) + pad256(8 * nc * nc) + pad256(4);
   t += pad256(16 * B * (m + 1) * Np) + pad256(cs * B * m * N) + pad256(16 * B * Np) + 2 * pad256(16 * B * N);
   t += pad256(16 * B * m * (m + 1)) + 2 * pad256(16 * B * (m + 1)) + pad256(8 * B * m) + pad256(16 * B * m);
   t += pad256(16 * B * (m + 1)) + pad256(16 * B * m) + pad256(8 * B * (m + 1)) + pad256(sizeof(RhsState) * B);
@@ -92,7 +92,7 @@ void free_handle(mgh_handle* h) {
     Level& lv = h->lev[l];
     cudaFree(lv.c); cudaFree(lv.D); cudaFree(lv.wDinv); cudaFree(lv.b); cudaFree(lv.vpre); cudaFree(lv.vfin);
   }
-  cudaFree(h->f_d); cudaFree(h->DA); cudaFree(h->band); cudaFree(h->piv); cudaFree(h->kinv64);
+  cudaFree(h->f_d); cudaFree(h->DA); cudaFree(h->band); cudaFree(h->piv); cudaFree(h->kinv64); cudaFree(h->kinv64r);
   cudaFree(h->kinv32); cudaFree(h->lu_info); cudaFree(h->V); cudaFree(h->Z); cudaFree(h->W);
   cudaFree(h->T1); cudaFree(h->T2); cudaFree(h->H); cudaFree(h->hcol); cudaFree(h->h2col); cudaFree(h->cs);
   cudaFree(h->sn); cudaFree(h->g); cudaFree(h->y); cudaFree(h->vscale); cudaFree(h->st); cudaFree(h->partial);
@@ -217,6 +217,7 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->band, 16 * nc * W);
   ALLOC(h->piv, 4 * nc);
   ALLOC(h->kinv64, 16 * nc * nc);
+  ALLOC(h->kinv64r, 16 * nc * nc);
   if (!h->fp64) ALLOC(h->kinv32, 8 * nc * nc);
   ALLOC(h->lu_info, 4);
   ALLOC(h->V, 16 * B * (m + 1) * Np);

@@ -63,8 +63,9 @@ struct Handle {
   int nc = 0;
   cd* band = nullptr;        // banded LU workspace (FP64)
   int* piv = nullptr;
-  cd* kinv64 = nullptr;      // [nc][nc] FP64 transposed inverse
-  cf* kinv32 = nullptr;      // FP32 copy (mixed precision)
+  cd* kinv64 = nullptr;      // [nc][nc] FP64 inverse, transposed (column c contiguous)
+  cd* kinv64r = nullptr;     // [nc][nc] FP64 inverse, row-major
+  cf* kinv32 = nullptr;      // [nc][nc] FP32 inverse, row-major (mixed precision)
   int* lu_info = nullptr;    // device status of the factorisation
 
   // Krylov workspace

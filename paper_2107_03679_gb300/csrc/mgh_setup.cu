@@ -223,33 +223,55 @@ __global__ void k_split_df(const cd* __restrict__ a, float2* __restrict__ hi, fl
   lo[q] = make_float2((float)(v.re - (double)rh), (float)(v.im - (double)ih));
 }
 
-__global__ void k_to_float(const cd* __restrict__ a, cf* __restrict__ b, size_t n) {
+
+// Row-major copies of the transposed inverse: Kr[r][c] = kinvT[c][r] (FP64 and FP32).
+__global__ void k_transpose_inv(const cd* __restrict__ kinvT, int n, cd* __restrict__ k64r, cf* __restrict__ k32r) {
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (q < n) b[q] = ccast<float>(a[q]);
+  if (q >= (size_t)n * n) return;
+  const int r = (int)(q / n), c = (int)(q % n);
+  const cd v = kinvT[(size_t)c * n + r];
+  k64r[q] = v;
+  if (k32r) k32r[q] = ccast<float>(v);
 }
 
-// x[r] = sum_c K^{-1}[r][c] b[c] for one right-hand side per blockIdx.y; b staged in shared memory.
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// x[q][r] = sum_c K^{-1}[r][c] b[q][c]: one warp per (row, right-hand side), the lanes split the
+// columns (coalesced reads of the row-major inverse and of b), two independent accumulators.
 template <typename TK, typename TIO>
-__global__ void k_coarse_apply(const Cx<TK>* __restrict__ kinvT, int n, const Cx<TIO>* __restrict__ b,
-                               size_t b_stride, Cx<TIO>* __restrict__ x, size_t x_stride,
-                               const RhsState* __restrict__ st) {
-  extern __shared__ unsigned char smem_raw[];
-  Cx<TK>* sb = reinterpret_cast<Cx<TK>*>(smem_raw);
-  const int rhs = blockIdx.y;
+__global__ void k_coarse_apply_w(const Cx<TK>* __restrict__ Kr, int n, int B, const Cx<TIO>* __restrict__ b,
+                                 size_t b_stride, Cx<TIO>* __restrict__ x, size_t x_stride,
+                                 const RhsState* __restrict__ st) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (long long)n * B) return;
+  const int rhs = (int)(warp / n), r = (int)(warp - (long long)rhs * n);
   if (st && !st[rhs].active) return;
   const Cx<TIO>* bb = b + rhs * b_stride;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) sb[c] = ccast<TK>(bb[c]);
-  __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  Cx<TK> acc = czero<TK>();
-  for (int c = 0; c < n; ++c) {
-    const Cx<TK> kv = kinvT[(size_t)c * n + r];
-    const Cx<TK> bv = sb[c];
-    acc.re = fma(kv.re, bv.re, fma(-kv.im, bv.im, acc.re));
-    acc.im = fma(kv.re, bv.im, fma(kv.im, bv.re, acc.im));
+  const Cx<TK>* row = Kr + (size_t)r * n;
+  TK a0r = 0, a0i = 0, a1r = 0, a1i = 0;
+  int c = lane;
+  for (; c + 32 < n; c += 64) {
+    const Cx<TK> k0 = row[c], k1 = row[c + 32];
+    const Cx<TK> b0 = ccast<TK>(bb[c]), b1 = ccast<TK>(bb[c + 32]);
+    a0r = fma(k0.re, b0.re, fma(-k0.im, b0.im, a0r));
+    a0i = fma(k0.re, b0.im, fma(k0.im, b0.re, a0i));
+    a1r = fma(k1.re, b1.re, fma(-k1.im, b1.im, a1r));
+    a1i = fma(k1.re, b1.im, fma(k1.im, b1.re, a1i));
   }
-  x[rhs * x_stride + r] = ccast<TIO>(acc);
+  if (c < n) {
+    const Cx<TK> k0 = row[c];
+    const Cx<TK> b0 = ccast<TK>(bb[c]);
+    a0r = fma(k0.re, b0.re, fma(-k0.im, b0.im, a0r));
+    a0i = fma(k0.re, b0.im, fma(k0.im, b0.re, a0i));
+  }
+  const TK sr = warp_sum_t<TK>(a0r + a1r), si = warp_sum_t<TK>(a0i + a1i);
+  if (lane == 0) x[rhs * x_stride + r] = ccast<TIO>(mk<TK>(sr, si));
 }
 
 // ---------------------------------------------------------------- forward-model kernels
@@ -424,10 +446,8 @@ mgh_status setup_contrast(Handle& h, const double* f_d) {
   MGH_CUDA(cudaFuncSetAttribute(k_band_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(cd) * n)));
   k_band_inverse<<<n, 32, sizeof(cd) * n, s>>>(h.band, h.piv, n, kl, ku, h.kinv64);
   MGH_CHECK_LAUNCH(); h.launches++;
-  if (!h.fp64) {
-    k_to_float<<<blocks_for((size_t)n * n), kThreads, 0, s>>>(h.kinv64, h.kinv32, (size_t)n * n);
-    MGH_CHECK_LAUNCH(); h.launches++;
-  }
+  k_transpose_inv<<<blocks_for((size_t)n * n), kThreads, 0, s>>>(h.kinv64, n, h.kinv64r, h.fp64 ? nullptr : h.kinv32);
+  MGH_CHECK_LAUNCH(); h.launches++;
   int info = 0;
   MGH_CUDA(cudaMemcpyAsync(&info, h.lu_info, sizeof(int), cudaMemcpyDeviceToHost, s));
   MGH_CUDA(cudaStreamSynchronize(s));
@@ -440,16 +460,15 @@ mgh_status setup_contrast(Handle& h, const double* f_d) {
 mgh_status launch_coarse_apply(Handle& h, const void* b, size_t b_stride, void* x, size_t x_stride, int B,
                                const RhsState* st, bool fp64_io) {
   const int n = h.nc;
-  dim3 grid((n + 127) / 128, B);
+  const long long warps = (long long)n * B;
+  const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
   ProfScope ps(h, st ? P_COARSE : P_OTHER);
   if (fp64_io) {
-    MGH_CUDA(cudaFuncSetAttribute(k_coarse_apply<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(cd) * n)));
-    k_coarse_apply<double, double><<<grid, 128, sizeof(cd) * n, h.stream>>>(
-        h.kinv64, n, (const cd*)b, b_stride, (cd*)x, x_stride, st);
+    k_coarse_apply_w<double, double><<<grid, 256, 0, h.stream>>>(h.kinv64r, n, B, (const cd*)b, b_stride, (cd*)x,
+                                                                 x_stride, st);
   } else {
-    k_coarse_apply<float, float><<<grid, 128, sizeof(cf) * n, h.stream>>>(
-        h.kinv32, n, (const cf*)b, b_stride, (cf*)x, x_stride, st);
+    k_coarse_apply_w<float, float><<<grid, 256, 0, h.stream>>>(h.kinv32, n, B, (const cf*)b, b_stride, (cf*)x,
+                                                               x_stride, st);
   }
   MGH_CHECK_LAUNCH(); h.launches++;
   return MGH_OK;
