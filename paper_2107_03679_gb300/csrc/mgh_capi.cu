@@ -2,6 +2,7 @@
 // handle, and the entry points that sequence the kernels of the other translation units.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -247,6 +248,19 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
     free_handle(h);
     return MGH_OUT_OF_MEMORY;
   }
+  // level-kernel selection (environment): MGH_VCYCLE=tile picks the shared-memory tile kernels
+  // for the FP32 levels; MGH_WAVE_SEG sets the rows per warp of the wavefront kernels,
+  // MGH_WAVE_MIN_NX the narrowest level that uses them, MGH_WAVE_PF their load depth in rows,
+  // MGH_WAVE_WARPS their warps per block and MGH_WAVE_RING the length of their shared-memory row
+  // rings in unroll periods (0: loads prefetched into registers); MGH_WAVE_FILL=bulk fills the
+  // rings with bulk copies issued by one lane instead of per-lane cp.async copies
+  if (const char* e = std::getenv("MGH_VCYCLE")) h->vc_wave = std::strcmp(e, "tile") != 0;
+  if (const char* e = std::getenv("MGH_WAVE_SEG")) h->wave_seg = std::max(0, std::atoi(e));
+  if (const char* e = std::getenv("MGH_WAVE_MIN_NX")) h->wave_min_nx = std::max(0, std::atoi(e));
+  if (const char* e = std::getenv("MGH_WAVE_PF")) h->wave_pf = std::atoi(e) == 2 ? 2 : 1;
+  if (const char* e = std::getenv("MGH_WAVE_WARPS")) h->wave_warps = std::atoi(e) == 2 ? 2 : 4;
+  if (const char* e = std::getenv("MGH_WAVE_RING")) h->wave_ring = std::max(0, std::atoi(e));
+  if (const char* e = std::getenv("MGH_WAVE_FILL")) h->wave_lane_ring = std::strcmp(e, "bulk") != 0;
   s = build_vcycle_tma(*h);
   if (s != MGH_OK) { free_handle(h); return s; }
   // start from f_d = 0 so that every later call finds a complete operator

@@ -48,6 +48,14 @@ struct Handle {
   size_t Np = 0;             // plane stride of double-float fields: N rounded up to 64 points
   int L = 0;                 // levels
   bool fp64 = true;          // cycle precision: double (true) or float (false)
+  bool vc_wave = true;       // FP32 levels: wavefront kernels (else shared-memory tiles)
+  int wave_seg = 0;          // rows per warp segment of the wavefront kernels (0: automatic)
+  int wave_min_nx = 0;       // levels narrower than this use the tiled kernels
+  int wave_pf = 1;           // rows of loads in flight per warp (1 or 2; 16-byte path only)
+  int wave_warps = 4;        // warps per block of the wavefront kernels (2 or 4)
+  int wave_ring = 1;         // shared-memory row ring of the wavefront kernels, in unroll periods
+                             // (1 or 2; 0: loads prefetched into registers)
+  bool wave_lane_ring = true;  // rings filled per lane by cp.async (else by bulk copies)
   size_t csize = 16;         // bytes per complex of the cycle precision
   Level lev[kMaxLevels];
   bool contrast_set = false;

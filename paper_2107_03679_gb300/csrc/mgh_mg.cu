@@ -19,6 +19,7 @@
 
 #include "mgh_engine.h"
 #include "mgh_tma.cuh"
+#include "mgh_wave.cuh"
 
 namespace mgh {
 
@@ -830,12 +831,228 @@ int persistent_blocks(Handle& h, K kern, size_t smem, int tiles, int threads = k
   return n < tiles ? n : tiles;
 }
 
+// ---------------------------------------------------------------- wavefront level kernels (host side)
+bool a16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Rows per warp segment: about the longest of 64, 32, 16, 8 that still gives the GPU three waves
+// of warps (longer segments repeat fewer halo rows, shorter ones fill small levels), moved down
+// to an even length whose step count (seg + extra) wastes at most one step of the last unrolled
+// period of P steps.
+int wave_seg(const Handle& h, int ny, int nstrips, int B, int extra, int P) {
+  int seg = 64;
+  if (h.wave_seg > 0) {
+    seg = (h.wave_seg + 1) & ~1;
+  } else {
+    const long target = 3L * h.num_sms * 16;
+    while (seg > 8 && (long)nstrips * ((ny + seg - 1) / seg) * B < target) seg /= 2;
+  }
+  for (int s = seg; s >= 4; s -= 2)
+    if ((P - (s + extra) % P) % P <= 1) return s;
+  return seg;
+}
+
+bool use_wave(const Handle& h, int l) { return h.vc_wave && h.lev[l].nx >= h.wave_min_nx; }
+
+template <int NU, bool V4, int PF, int NW>
+void pre_wave_go(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale, size_t scale_stride, int B,
+                 const RhsState* st, int nstrips, int nwarps, int seg) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  wave::k_pre_w<NU, V4, PF, NW><<<grid, 32 * NW, 0, h.stream>>>(
+      bin, b_stride, bscale, scale_stride, (const cf*)lv.D, (const cf*)lv.wDinv, (cf*)lv.vpre, lv.n(), (cf*)cl.b,
+      cl.n(), lv.nx, lv.ny, cl.nx, (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega), nstrips, nwarps, seg, st);
+}
+
+template <int NU, bool V4, int PF, int NW>
+void post_wave_go(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale, size_t scale_stride,
+                  cf* out, size_t out_stride, int B, const RhsState* st, int nstrips, int nwarps, int seg) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  wave::k_post_w<NU, V4, PF, NW><<<grid, 32 * NW, 0, h.stream>>>(
+      bin, b_stride, bscale, scale_stride, (const cf*)lv.wDinv, (const cf*)lv.vpre, lv.n(), (const cf*)cl.vfin,
+      cl.n(), cl.nx, cl.ny, out, out_stride, lv.nx, lv.ny, (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega),
+      nstrips, nwarps, seg, st);
+}
+
+template <int NU, int NW, int MS>
+mgh_status pre_ring_go(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale, size_t scale_stride,
+                       int B, const RhsState* st, int nstrips, int nwarps, int seg) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  auto kern = wave::k_pre_wt<NU, NW, MS>;
+  constexpr int S = wave::RingLen<wave::PreW<NU, 1>::P, NU, MS>::S;
+  constexpr size_t smem = wave::RingSmem<NW, S>::bytes();
+  static bool attr = false;
+  if (!attr) {
+    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.D, (const cf*)lv.wDinv,
+                                          (cf*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx,
+                                          (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega), nstrips, nwarps,
+                                          seg, st, h.dev_err);
+  return MGH_OK;
+}
+
+template <int NU, int NW, int MS>
+mgh_status post_ring_go(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale,
+                        size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st, int nstrips,
+                        int nwarps, int seg) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  auto kern = wave::k_post_wt<NU, NW, MS>;
+  constexpr int S = wave::RingLen<wave::PostW<NU, 1>::P, NU, MS>::S;
+  constexpr size_t smem = wave::RingSmem<NW, S>::bytes();
+  static bool attr = false;
+  if (!attr) {
+    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.wDinv,
+                                          (const cf*)lv.vpre, lv.n(), (const cf*)cl.vfin, cl.n(), cl.nx, cl.ny, out,
+                                          out_stride, lv.nx, lv.ny, (float)(1.0 / (lv.h * lv.h)),
+                                          (float)(1.0 - h.p.omega), nstrips, nwarps, seg, st, h.dev_err);
+  return MGH_OK;
+}
+
+template <int NU, int NW, int MS>
+mgh_status pre_lane_go(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale, size_t scale_stride,
+                       int B, const RhsState* st, int nstrips, int nwarps, int seg) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  auto kern = wave::k_pre_wa<NU, NW, MS>;
+  constexpr int S = wave::RingLen<wave::PreW<NU, 1>::P, NU, MS>::S;
+  constexpr size_t smem = wave::LaneRingSmem<NW, S>::bytes();
+  static bool attr = false;
+  if (!attr) {
+    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.D, (const cf*)lv.wDinv,
+                                          (cf*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx,
+                                          (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega), nstrips, nwarps,
+                                          seg, st);
+  return MGH_OK;
+}
+
+template <int NU, int NW, int MS>
+mgh_status post_lane_go(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale,
+                        size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st, int nstrips,
+                        int nwarps, int seg) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  auto kern = wave::k_post_wa<NU, NW, MS>;
+  constexpr int S = wave::RingLen<wave::PostW<NU, 1>::P, NU, MS>::S;
+  constexpr size_t smem = wave::LaneRingSmem<NW, S>::bytes();
+  static bool attr = false;
+  if (!attr) {
+    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.wDinv,
+                                          (const cf*)lv.vpre, lv.n(), (const cf*)cl.vfin, cl.n(), cl.nx, cl.ny, out,
+                                          out_stride, lv.nx, lv.ny, (float)(1.0 / (lv.h * lv.h)),
+                                          (float)(1.0 - h.p.omega), nstrips, nwarps, seg, st);
+  return MGH_OK;
+}
+
+// Ring variants: ring length multiplier (1 or 2 unroll periods) and warps per block.
+#define MGH_RING_DISPATCH(GO, NU, MS, NW, ...)                                                   \
+  ((MS) >= 2 ? ((NW) == 2 ? GO<NU, 2, 2>(__VA_ARGS__) : GO<NU, 4, 2>(__VA_ARGS__))            \
+             : ((NW) == 2 ? GO<NU, 2, 1>(__VA_ARGS__) : GO<NU, 4, 1>(__VA_ARGS__)))
+
+// Variant dispatch: 16-byte vector accesses or not, prefetch depth 1 or 2, 2 or 4 warps per block.
+#define MGH_WAVE_DISPATCH(GO, NU, V4, PF, NW, ...)                         \
+  do {                                                                     \
+    if (V4) {                                                              \
+      if (PF == 2) {                                                       \
+        if (NW == 2) GO<NU, true, 2, 2>(__VA_ARGS__); else GO<NU, true, 2, 4>(__VA_ARGS__);    \
+      } else {                                                             \
+        if (NW == 2) GO<NU, true, 1, 2>(__VA_ARGS__); else GO<NU, true, 1, 4>(__VA_ARGS__);    \
+      }                                                                    \
+    } else {                                                               \
+      if (NW == 2) GO<NU, false, 1, 2>(__VA_ARGS__); else GO<NU, false, 1, 4>(__VA_ARGS__);    \
+    }                                                                      \
+  } while (0)
+
+template <int NU>
+mgh_status launch_pre_wave(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale,
+                           size_t scale_stride, int B, const RhsState* st) {
+  const Level& lv = h.lev[l];
+  using G = wave::PreW<NU, 2>;   // period of the PF = 2 variant (a multiple of the PF = 1 one)
+  const bool v4 = lv.nx % 2 == 0 && b_stride % 2 == 0 && lv.n() % 2 == 0 && a16(bin) && a16(lv.D) &&
+                  a16(lv.wDinv) && a16(lv.vpre);
+  const bool ring = v4 && h.wave_ring > 0;
+  const int period = !ring ? G::P
+                           : (h.wave_ring >= 2 ? wave::RingLen<wave::PreW<NU, 1>::P, NU, 2>::S
+                                               : wave::RingLen<wave::PreW<NU, 1>::P, NU, 1>::S);
+  const int nstrips = (lv.nx + G::XO - 1) / G::XO;
+  const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * G::H - 1, period);
+  const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
+  ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
+  if (ring) {
+    if (h.wave_lane_ring)
+      MGH_TRY(MGH_RING_DISPATCH(pre_lane_go, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,
+                                scale_stride, B, st, nstrips, nwarps, seg));
+    else
+      MGH_TRY(MGH_RING_DISPATCH(pre_ring_go, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,
+                                scale_stride, B, st, nstrips, nwarps, seg));
+    MGH_CHECK_LAUNCH(); h.launches++;
+    return MGH_OK;
+  }
+  MGH_WAVE_DISPATCH(pre_wave_go, NU, v4, h.wave_pf, h.wave_warps, h, l, bin, b_stride, bscale, scale_stride, B, st,
+                    nstrips, nwarps, seg);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  return MGH_OK;
+}
+
+template <int NU>
+mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale,
+                            size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st) {
+  const Level& lv = h.lev[l];
+  using G = wave::PostW<NU, 2>;
+  const bool v4 = lv.nx % 2 == 0 && b_stride % 2 == 0 && out_stride % 2 == 0 && lv.n() % 2 == 0 && a16(bin) &&
+                  a16(out) && a16(lv.wDinv) && a16(lv.vpre);
+  const bool ring = v4 && h.wave_ring > 0;
+  const int period = !ring ? G::P
+                           : (h.wave_ring >= 2 ? wave::RingLen<wave::PostW<NU, 1>::P, NU, 2>::S
+                                               : wave::RingLen<wave::PostW<NU, 1>::P, NU, 1>::S);
+  const int nstrips = (lv.nx + G::XO - 1) / G::XO;
+  const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * NU, period);
+  const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
+  ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
+  if (ring) {
+    if (h.wave_lane_ring)
+      MGH_TRY(MGH_RING_DISPATCH(post_lane_go, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,
+                                scale_stride, out, out_stride, B, st, nstrips, nwarps, seg));
+    else
+      MGH_TRY(MGH_RING_DISPATCH(post_ring_go, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,
+                                scale_stride, out, out_stride, B, st, nstrips, nwarps, seg));
+    MGH_CHECK_LAUNCH(); h.launches++;
+    return MGH_OK;
+  }
+  MGH_WAVE_DISPATCH(post_wave_go, NU, v4, h.wave_pf, h.wave_warps, h, l, bin, b_stride, bscale, scale_stride, out,
+                    out_stride, B, st, nstrips, nwarps, seg);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  return MGH_OK;
+}
+
 template <typename T, int NU, typename TIn>
 mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
                          size_t scale_stride, int B, const RhsState* st, int in_slot) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
   if constexpr (std::is_same<T, float>::value && std::is_same<TIn, float>::value) {
+    if constexpr (NU >= 1) {
+      if (use_wave(h, l))
+        return launch_pre_wave<NU>(h, l, (const cf*)bin, b_stride, bscale, scale_stride, B, st);
+    }
     const bool tma = h.tma && h.tma[l].pre_ok && (l > 0 || (in_slot >= 0 && h.tma_in_ok));
     if (tma) {
       using G = PreGeom<NU, 64, 16>;
@@ -896,6 +1113,10 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
   const Level& cl = h.lev[l + 1];
   if constexpr (std::is_same<T, float>::value && std::is_same<TIn, float>::value &&
                 std::is_same<TOut, float>::value) {
+    if constexpr (NU >= 1) {
+      if (use_wave(h, l))
+        return launch_post_wave<NU>(h, l, (const cf*)bin, b_stride, bscale, scale_stride, out, out_stride, B, st);
+    }
     const bool tma = h.tma && h.tma[l].post_ok && (l > 0 || (in_slot >= 0 && h.tma_in_ok));
     if (tma) {
       using G = PostGeom<NU, 64, 16>;
