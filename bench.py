@@ -51,7 +51,7 @@ def parse_args(argv=None):
     ap.add_argument("--nu", type=int, default=None, help="pre- and post-smoothing sweeps (default: the workload's)")
     ap.add_argument("--levels", type=int, default=None, help="multigrid levels (default: the workload's)")
     ap.add_argument("--maxit", type=int, default=20000, help="Arnoldi steps per solve before giving up")
-    ap.add_argument("--arnoldi", choices=["df", "fp64"], default="df",
+    ap.add_argument("--arnoldi", choices=["df", "fp64", "sstep"], default="df",
                     help="mixed precision Arnoldi arithmetic: double-float on FP32 pipes or native FP64")
     ap.add_argument("--autotune", action="store_true",
                     help="pick nu and the restart length with the autotuner (cached) before timing")
@@ -146,13 +146,26 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- algorithmic bytes
-def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, df: bool) -> dict:
+def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str) -> dict:
     """Minimal DRAM bytes of each kernel class from the engine counters (fields read once,
     per-grid coefficient arrays counted once per launch).  N = fine points, cs = bytes of one
-    complex number of the multigrid precision."""
+    complex number of the multigrid precision; engine = "df", "sstep" or "fp64"."""
     steps = prof["arnoldi_steps"]
     c16 = 16
-    if df:
+    if engine == "sstep":
+        # s-step cycles: every step of a cycle runs (cycle_steps), one Gram sweep per cycle
+        run = prof["cycle_steps"]
+        return {
+            "vcycle_pre_l0": run * N * (8 + cs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
+            "vcycle_post_l0": run * N * (8 + 2 * cs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
+            # v_{k+1} = A z_k: read z_k (FP32), write v_{k+1} (double-float); D_A planes per launch
+            "matvec_dots": run * N * (cs + c16) + launches["matvec_dots"] * c16 * N,
+            # Gram sweep: read the m + 1 basis vectors
+            "gs_update": prof["gram_reads"] * N * c16,
+            "true_residual": prof["residuals"] * N * 3 * c16,
+            "x_update": prof["updates"] * N * 2 * c16 + prof["update_reads"] * N * cs,
+        }
+    if engine == "df":
         # double-float Arnoldi (mixed path): the V-cycle reads the 8-byte hi plane of u_j
         return {
             "vcycle_pre_l0": steps * N * (8 + cs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
@@ -404,7 +417,7 @@ def gpu_main(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel class (CUDA events over the timed region)
     cs = 16 if precision == "fp64" else 8
     N = solver.N
-    alg = algorithmic_bytes(prof, N, cs, prof["launches"], precision == "mixed32" and args.arnoldi == "df")
+    alg = algorithmic_bytes(prof, N, cs, prof["launches"], args.arnoldi if precision == "mixed32" else "fp64")
     ms_cls = prof["ms"]
     dom = max(ms_cls, key=lambda k: ms_cls[k])
     peak, peak_kind = load_peaks()

@@ -58,7 +58,12 @@ typedef enum {
 typedef enum {
   MGH_ARNOLDI_DF = 0,       /* mixed precision: Arnoldi vectors and Gram-Schmidt arithmetic in
                                double-float (pairs of FP32, ~48-bit significand) on the FP32 pipes */
-  MGH_ARNOLDI_FP64 = 1      /* native FP64 Gram-Schmidt (always used when precision is FP64) */
+  MGH_ARNOLDI_FP64 = 1,     /* native FP64 Gram-Schmidt (always used when precision is FP64) */
+  MGH_ARNOLDI_SSTEP = 2     /* mixed precision, restart <= 8: each cycle builds the monomial basis
+                               v_{k+1} = A M^{-1} v_k (double-float), orthogonalises it at once by a
+                               Cholesky factor of its Gram matrix (double-float sums, FP64 factor),
+                               and solves the cycle's least-squares problem on that factor; one
+                               sweep over the basis per cycle instead of two per step */
 } mgh_arnoldi;
 
 /* Solver parameters.  Lengths are in the same unit as h (grid cells when h = 1). */
@@ -72,7 +77,8 @@ typedef struct {
   int levels;               /* multigrid levels including the finest, >= 1 (Alg. 2) */
   int nu1, nu2;             /* pre- and post-relaxation sweeps, 0..4 (Alg. 2) */
   double omega;             /* damped-Jacobi weight omega_S in (0, 1] (eq. dampedJ) */
-  int restart;              /* GMRES restart length m, 1..32 (1..20 with MGH_ARNOLDI_DF) */
+  int restart;              /* GMRES restart length m, 1..32 (1..20 with MGH_ARNOLDI_DF, 1..8 with
+                               MGH_ARNOLDI_SSTEP) */
   int maxit;                /* maximum Arnoldi steps per right-hand side */
   double tol;               /* stop when ||b - A x||_2 <= tol * ||b||_2 (true FP64 residual) */
   int precision;            /* mgh_precision */
@@ -197,6 +203,10 @@ typedef struct {
   uint64_t residuals;                      /* true residual evaluations, summed over right-hand sides */
   uint64_t updates;                        /* iterate updates, summed over right-hand sides */
   uint64_t update_reads;                   /* preconditioned vectors read by iterate updates */
+  uint64_t cycle_steps;                    /* multigrid cycles + matvecs run, summed over right-hand sides
+                                              (MGH_ARNOLDI_SSTEP runs every step of a cycle, also past
+                                              the step that met the tolerance) */
+  uint64_t gram_reads;                     /* basis vectors read by Gram sweeps (MGH_ARNOLDI_SSTEP) */
 } mgh_profile;
 
 /* Start (enable != 0) or stop recording; starting clears the profile.  While on, every launch

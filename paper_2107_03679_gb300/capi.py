@@ -15,8 +15,8 @@ LIB_PATH = os.path.join(_HERE, "libmgh.so")
 MGH_OK, MGH_INVALID_ARG, MGH_NOT_CONVERGED, MGH_CUDA_ERROR, MGH_OUT_OF_MEMORY, MGH_TIMEOUT, MGH_NOT_SUPPORTED = range(7)
 MGH_PREC_FP64, MGH_PREC_MIXED32 = 0, 1
 PRECISIONS = {"fp64": MGH_PREC_FP64, "mixed32": MGH_PREC_MIXED32}
-MGH_ARNOLDI_DF, MGH_ARNOLDI_FP64 = 0, 1
-ARNOLDI = {"df": MGH_ARNOLDI_DF, "fp64": MGH_ARNOLDI_FP64}
+MGH_ARNOLDI_DF, MGH_ARNOLDI_FP64, MGH_ARNOLDI_SSTEP = 0, 1, 2
+ARNOLDI = {"df": MGH_ARNOLDI_DF, "fp64": MGH_ARNOLDI_FP64, "sstep": MGH_ARNOLDI_SSTEP}
 
 
 class mgh_params(ctypes.Structure):
@@ -45,7 +45,8 @@ class mgh_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * MGH_PROFILE_CLASSES), ("launches", ctypes.c_uint64 * MGH_PROFILE_CLASSES),
                 ("arnoldi_steps", ctypes.c_uint64), ("basis_reads", ctypes.c_uint64),
                 ("reorth_reads", ctypes.c_uint64), ("residuals", ctypes.c_uint64),
-                ("updates", ctypes.c_uint64), ("update_reads", ctypes.c_uint64)]
+                ("updates", ctypes.c_uint64), ("update_reads", ctypes.c_uint64),
+                ("cycle_steps", ctypes.c_uint64), ("gram_reads", ctypes.c_uint64)]
 
 
 class MGHError(RuntimeError):
@@ -252,7 +253,7 @@ def mgh_profile_read(h) -> dict:
                 launches={n: int(p.launches[i]) for i, n in enumerate(PROFILE_CLASS_NAMES)},
                 arnoldi_steps=int(p.arnoldi_steps), basis_reads=int(p.basis_reads),
                 reorth_reads=int(p.reorth_reads), residuals=int(p.residuals), updates=int(p.updates),
-                update_reads=int(p.update_reads))
+                update_reads=int(p.update_reads), cycle_steps=int(p.cycle_steps), gram_reads=int(p.gram_reads))
 
 
 def mgh_launch_count(h, reset=False) -> int:

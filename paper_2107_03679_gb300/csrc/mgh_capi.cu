@@ -32,8 +32,11 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
   if (p->restart < 1 || p->restart > kMaxRestart || p->maxit < 1 || !(p->tol > 0.0)) return MGH_INVALID_ARG;
   if (p->precision != MGH_PREC_FP64 && p->precision != MGH_PREC_MIXED32) return MGH_INVALID_ARG;
   if (p->batch_max < 1 || p->batch_max > 65535) return MGH_INVALID_ARG;
-  if (p->arnoldi != MGH_ARNOLDI_DF && p->arnoldi != MGH_ARNOLDI_FP64) return MGH_INVALID_ARG;
+  if (p->arnoldi != MGH_ARNOLDI_DF && p->arnoldi != MGH_ARNOLDI_FP64 && p->arnoldi != MGH_ARNOLDI_SSTEP)
+    return MGH_INVALID_ARG;
   if (p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_DF && p->restart > kMaxRestartDf)
+    return MGH_INVALID_ARG;
+  if (p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_SSTEP && p->restart > kMaxRestartSs)
     return MGH_INVALID_ARG;
   if (!std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) return MGH_INVALID_ARG;
   const long long nx = p->nx_int + 2LL * p->abl, ny = p->ny_int + 2LL * p->abl;
@@ -70,7 +73,7 @@ size_t workspace_bytes(const mgh_params& p) {
   t += pad256(16 * B * (m + 1) * Np) + pad256(cs * B * m * N) + pad256(16 * B * Np) + 2 * pad256(16 * B * N);
   t += pad256(16 * B * m * (m + 1)) + 2 * pad256(16 * B * (m + 1)) + pad256(8 * B * m) + pad256(16 * B * m);
   t += pad256(16 * B * (m + 1)) + pad256(16 * B * m) + pad256(8 * B * (m + 1)) + pad256(sizeof(RhsState) * B);
-  t += pad256(16 * (1216 + B) * (2 * m + 4)) + pad256(8 * (B + 1));
+  t += pad256(16 * (1216 + B) * partial_stride(m)) + pad256(8 * (B + 1));
   t += pad256(16 * Np) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m) + pad256(4);   // DAdf, hpend, coef, err
   if (p.precision != MGH_PREC_FP64) t += 2 * pad256(16 * B * Np);                        // xdf, bdf
   return t;
@@ -235,7 +238,7 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->y, 16 * B * m);
   ALLOC(h->vscale, 8 * B * (m + 1));
   ALLOC(h->st, sizeof(RhsState) * B);
-  ALLOC(h->partial, 16 * (1216 + B) * (2 * m + 4));
+  ALLOC(h->partial, 16 * (1216 + B) * partial_stride(m));
   ALLOC(h->DAdf, 16 * Np);
   ALLOC(h->dev_err, 4);
   if (!h->fp64) { ALLOC(h->xdf, 16 * B * Np); ALLOC(h->bdf, 16 * B * Np); }

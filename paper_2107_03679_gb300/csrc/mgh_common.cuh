@@ -77,6 +77,8 @@ struct RhsState {
   int zsum;          // preconditioned vectors read by iterate updates
   int verify;        // mixed path: the double-float residual met the target, FP64 check pending
   int nverify;       // FP64 verifications run
+  int csteps;        // s-step engine: multigrid cycles + matvecs run (all steps of every cycle)
+  int gsum;          // s-step engine: basis vectors read by the Gram sweeps
   double bnorm;      // ||b||
   double rnorm;      // last true residual norm
   double wnorm2;     // ||A z_j||^2 of the current step

@@ -15,6 +15,14 @@ namespace mgh {
 constexpr int kMaxLevels = 12;
 constexpr int kMaxRestart = 32;
 constexpr int kMaxRestartDf = 20;  // restart limit of the double-float Arnoldi (register budget)
+constexpr int kMaxRestartSs = 8;   // restart limit of the s-step engine (Gram sums held in registers)
+
+// Complex slots per block in the partial-sum buffer: two Gram-Schmidt regions of m + 2, or the
+// (m + 1)(m + 2) / 2 entries of an s-step Gram matrix.
+inline int partial_stride(int m) {
+  const int a = 2 * m + 4, b = (m + 1) * (m + 2) / 2;
+  return a > b ? a : b;
+}
 constexpr int kMaxSweeps = 4;
 constexpr int kMaxCoarse = 4096;   // unknowns on the coarsest level (dense inverse kept on device)
 
@@ -165,6 +173,7 @@ mgh_status build_vcycle_tma(Handle& h);
 
 // mgh_krylov_df.cu: mixed-precision engine with double-float Arnoldi
 mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
+mgh_status fgmres_ss(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
 // device flag set by a kernel whose bounded wait gave up (0 = none)
 constexpr int kErrTimeout = 1;
 

@@ -402,6 +402,7 @@ mgh_status fgmres_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) 
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
   if (h.fp64) return fgmres_t<double>(h, b, B, x, info);
   if (h.p.arnoldi == MGH_ARNOLDI_FP64) return fgmres_t<float>(h, b, B, x, info);
+  if (h.p.arnoldi == MGH_ARNOLDI_SSTEP) return fgmres_ss(h, b, B, x, info);
   return fgmres_df(h, b, B, x, info);
 }
 

@@ -144,7 +144,7 @@ KArgs make_kargs(const Handle& h, int B) {
   a.nblk = (int)((h.N + a.chunk - 1) / a.chunk);
   a.Np = (h.N + 63) / 64 * 64;
   a.inv_h2 = 1.0 / (h.p.h * h.p.h);
-  a.pstride = 2 * h.m + 4;
+  a.pstride = partial_stride(h.m);
   return a;
 }
 
@@ -160,6 +160,8 @@ mgh_status finish_solve(Handle& h, int B, mgh_solve_info* info) {
     h.acc.residuals += S.nres;
     h.acc.updates += S.nupd;
     h.acc.update_reads += S.zsum;
+    h.acc.cycle_steps += S.csteps > 0 ? S.csteps : S.iterations;
+    h.acc.gram_reads += S.gsum;
     if (info) {
       info[i].iterations = S.iterations;
       info[i].restarts = S.restarts;

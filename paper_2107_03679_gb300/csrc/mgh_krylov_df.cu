@@ -21,6 +21,7 @@
 // are in flight while the FP32 pipes work on the current one.  Double-float fields (basis
 // vectors, w, the operator diagonal) are pairs of float2 planes (hi, lo) with plane stride Np.
 #include <cmath>
+#include <utility>
 
 #include "mgh_df.cuh"
 #include "mgh_krylov_common.cuh"
@@ -661,6 +662,292 @@ k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, float2
   }
 }
 
+
+// ---------------------------------------------------------------- s-step cycle (MGH_ARNOLDI_SSTEP)
+// One restart cycle of flexible GMRES(m) in s-step form (Chronopoulos & Gear 1989; Hoemmen 2010),
+// with the Krylov basis orthogonalised at the end of the cycle by a Cholesky factor of its Gram
+// matrix:
+//   v_0 = r (double-float), and for k < m:  z_k = M^{-1}(v_k / ||v_k||),  v_{k+1} = A z_k
+//   G = V^H V over v_0 .. v_m (one sweep, double-float sums),  G = R^H R (FP64, equilibrated)
+//   r - A Z y = V (e_0 - [0; y]),  so  ||r - A Z y|| = ||R[:,0] - R[:,1:] y||
+// The small least-squares problem is the GMRES one with the upper-Hessenberg matrix R[:,1:] and
+// right-hand side R_00 e_0; Givens rotations give the residual of every prefix, and the cycle
+// keeps the shortest prefix that meets the tolerance.  In exact arithmetic this is the same
+// iterate as Arnoldi-based FGMRES(m) on the same z_k; the Gram matrix needs the basis to be well
+// enough conditioned for double-float sums, and a Cholesky pivot that vanishes ends the usable
+// basis there.
+
+template <int NV>
+struct GramPairs {
+  static constexpr int NP = NV * (NV + 1) / 2;   // pairs i <= j, row by row
+  static constexpr int PG = (NP + 3) / 4;        // pairs per group of 64 threads (4 groups)
+  __host__ __device__ static constexpr int row(int p) {
+    int i = 0;
+    while (p >= NV - i) { p -= NV - i; ++i; }
+    return i;
+  }
+  __host__ __device__ static constexpr int col(int p) {
+    int i = 0;
+    while (p >= NV - i) { p -= NV - i; ++i; }
+    return i + p;
+  }
+};
+
+template <typename F, int... I>
+__device__ __forceinline__ void unroll_seq(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void unroll(F&& f) {
+  unroll_seq(f, std::make_integer_sequence<int, N>{});
+}
+
+// v_{k+1} = A z_k in double-float (z_k FP32), written to basis slot k + 1, and its partial
+// ||v_{k+1}||^2 (slot 0 of the partial buffer).
+__global__ void __launch_bounds__(kKThreads)
+k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__ DAdf, float2* __restrict__ V,
+            cd* __restrict__ partial, const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (!st[rhs].active) return;
+  const cf* z = Z + ((size_t)rhs * a.m + k) * a.N;
+  float2* vh = V + (((size_t)rhs * (a.m + 1) + k + 1) * 2) * a.Np;
+  float2* vl = vh + a.Np;
+  const float2* dh = DAdf;
+  const float2* dl = DAdf + a.Np;
+  const df ih = df_from_double(a.inv_h2);
+  df nrm = {0.f, 0.f};
+  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
+  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
+#pragma unroll 2
+  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
+    const cf zc = z[q];
+    const cf zw = m > 0 ? z[q - 1] : mk<float>(0.f, 0.f);
+    const cf ze = m < a.nx - 1 ? z[q + 1] : mk<float>(0.f, 0.f);
+    const cf zs = n > 0 ? z[q - a.nx] : mk<float>(0.f, 0.f);
+    const cf zn = n < a.ny - 1 ? z[q + a.nx] : mk<float>(0.f, 0.f);
+    const float2 d0 = dh[q], d1 = dl[q];
+    df sr = {0.f, 0.f}, si = {0.f, 0.f};
+    df_add1(sr, zw.re); df_add1(si, zw.im);
+    df_add1(sr, ze.re); df_add1(si, ze.im);
+    df_add1(sr, zs.re); df_add1(si, zs.im);
+    df_add1(sr, zn.re); df_add1(si, zn.im);
+    cdf w = cdf_zero();
+    df_fma1(w.re, d0.x, d1.x, zc.re);
+    df_fma1(w.re, -d0.y, -d1.y, zc.im);
+    df_fma1(w.im, d0.x, d1.x, zc.im);
+    df_fma1(w.im, d0.y, d1.y, zc.re);
+    df_fma(w.re, -ih.hi, -ih.lo, sr.hi, sr.lo);
+    df_fma(w.im, -ih.hi, -ih.lo, si.hi, si.lo);
+    w.re = df_norm(w.re);
+    w.im = df_norm(w.im);
+    vh[q] = make_float2(w.re.hi, w.im.hi);
+    vl[q] = make_float2(w.re.lo, w.im.lo);
+    cdf_abs2_acc(nrm, w);
+  }
+  df vals[1] = {nrm};
+  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
+  block_reduce_df(vals, 1, [&](int) -> double* { out->im = 0.0; return &out->re; });
+}
+
+// 1 / ||v_{k+1}|| for the next multigrid input.
+__global__ void k_ss_norm(KArgs a, int k, const cd* __restrict__ partial, double* __restrict__ vscale,
+                          const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.x;
+  if (!st[rhs].active || threadIdx.x != 0) return;
+  double n2 = 0.0;
+  for (int b = 0; b < a.nblk; ++b) n2 += partial[((size_t)rhs * a.nblk + b) * a.pstride].re;
+  vscale[(size_t)rhs * (a.m + 1) + k + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+}
+
+// The Gram sums of one tile's points for the pairs of thread group G.
+template <int NV, int G>
+__device__ __forceinline__ void gram_tile(const Pipe& pp, int slot, size_t q0, size_t p1, int l64, cdf* acc) {
+  using PR = GramPairs<NV>;
+  constexpr int P0 = G * PR::PG;
+  constexpr int P1 = P0 + PR::PG < PR::NP ? P0 + PR::PG : PR::NP;
+  if constexpr (P1 > P0) {
+    constexpr int IMIN = PR::row(P0);
+#pragma unroll
+    for (int r = 0; r < kTile / 64; ++r) {
+      const int t = l64 + 64 * r;
+      if (q0 + t >= p1) break;
+      cdf v[NV];
+#pragma unroll
+      for (int i = IMIN; i < NV; ++i) {
+        const float2 hh = pp.plane(slot, 2 * i)[t], ll = pp.plane(slot, 2 * i + 1)[t];
+        v[i].re.hi = hh.x; v[i].im.hi = hh.y; v[i].re.lo = ll.x; v[i].im.lo = ll.y;
+      }
+      unroll<P1 - P0>([&](auto PC) {
+        constexpr int p = P0 + decltype(PC)::value;
+        constexpr int i = PR::row(p), j = PR::col(p);
+        if constexpr (i == j) cdf_abs2_acc(acc[p - P0].re, v[i]);
+        else cdf_dot_acc(acc[p - P0], v[i], v[j]);
+      });
+    }
+  }
+}
+
+// G_ij = v_i^H v_j (i <= j) over v_0 .. v_{NV-1}: one sweep of the basis through the TMA ring;
+// four groups of 64 threads share the pairs, each thread sums 4 points of every tile.
+template <int NV>
+__global__ void __launch_bounds__(kDfThreads)
+k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial, const RhsState* __restrict__ st,
+          int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using PR = GramPairs<NV>;
+  static_assert(kDfThreads == 256, "four groups of 64 threads");
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (!st[rhs].active) return;
+  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  Pipe pp = pipe_begin(smem, S, 2 * NV, p0, p1);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NV; ++i) {
+      pp.src[2 * i] = vplane(V, a, rhs, i, 0);
+      pp.src[2 * i + 1] = vplane(V, a, rhs, i, 1);
+    }
+  }
+  int* fail = reinterpret_cast<int*>(smem + kSmemHeader - 16);
+  pipe_start(pp, fail);
+  const int l64 = threadIdx.x & 63, grp = threadIdx.x >> 6;
+  cdf acc[PR::PG];
+#pragma unroll
+  for (int c = 0; c < PR::PG; ++c) acc[c] = cdf_zero();
+  for (int k = 0; k < pp.ntiles; ++k) {
+    const bool ready = pipe_wait(pp, k, fail);
+    const int slot = k % S;
+    const size_t q0 = p0 + (size_t)k * kTile;
+    if (ready) {
+      switch (grp) {
+        case 0: gram_tile<NV, 0>(pp, slot, q0, p1, l64, acc); break;
+        case 1: gram_tile<NV, 1>(pp, slot, q0, p1, l64, acc); break;
+        case 2: gram_tile<NV, 2>(pp, slot, q0, p1, l64, acc); break;
+        default: gram_tile<NV, 3>(pp, slot, q0, p1, l64, acc); break;
+      }
+    }
+    if (!pipe_release(pp, k, fail, err)) return;
+  }
+  __shared__ float4 sh[kDfThreads / 32][PR::PG];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < PR::PG; ++c) {
+    const df re = warp_sum_df(acc[c].re), im = warp_sum_df(acc[c].im);
+    if (lane == 0) sh[warp][c] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+  __syncthreads();
+  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
+  for (int t = threadIdx.x; t < PR::NP; t += kDfThreads) {
+    const int g = t / PR::PG, c = t - g * PR::PG;
+    const float4 x0 = sh[2 * g][c], x1 = sh[2 * g + 1][c];
+    const df re = df_add(df{x0.x, x0.y}, df{x1.x, x1.y}), im = df_add(df{x0.z, x0.w}, df{x1.z, x1.w});
+    out[t] = mk<double>(df_to_double(re), df_to_double(im));
+  }
+}
+
+// Per right-hand side: the Gram matrix from the block sums, its equilibrated Cholesky factor,
+// the cycle's least-squares problem by Givens rotations, the prefix to keep and its y.
+template <int NV>
+__global__ void k_ss_lsq(KArgs a, const cd* __restrict__ partial, cd* __restrict__ y, RhsState* __restrict__ st,
+                         double tol, int maxit) {
+  using PR = GramPairs<NV>;
+  constexpr int M = NV - 1;
+  __shared__ cd Gs[PR::NP];
+  const int rhs = blockIdx.x;
+  if (!st[rhs].active) return;
+  for (int t = threadIdx.x; t < PR::NP; t += blockDim.x) {
+    cd acc = czero<double>();
+    for (int b = 0; b < a.nblk; ++b) acc = acc + partial[((size_t)rhs * a.nblk + b) * a.pstride + t];
+    Gs[t] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  RhsState& S = st[rhs];
+  auto G = [&](int i, int j) -> cd { return Gs[i * NV - i * (i - 1) / 2 + (j - i)]; };   // i <= j
+  // equilibrated factor: G~ = D G D with D = diag(1 / sqrt(G_ii)), G~ = Rt^H Rt, R = Rt D^{-1}
+  double dsc[NV];
+  cd R[NV][NV];
+  int nv = NV;   // basis vectors whose pivots are usable
+  for (int i = 0; i < NV; ++i) {
+    const double gii = G(i, i).re;
+    if (!(gii > 0.0)) { nv = i; break; }
+    dsc[i] = 1.0 / sqrt(gii);
+  }
+  for (int j = 0; j < nv; ++j) {
+    double s = 1.0;
+    for (int i = 0; i < j; ++i) s -= cabs2(R[i][j]);
+    if (!(s > 1e-12)) {   // v_j (numerically) in the span of v_0 .. v_{j-1}
+      R[j][j] = czero<double>();
+      nv = j + 1;
+      break;
+    }
+    R[j][j] = mk<double>(sqrt(s), 0.0);
+    for (int k = j + 1; k < nv; ++k) {
+      cd t = (dsc[j] * dsc[k]) * G(j, k);
+      for (int i = 0; i < j; ++i) t = t - cconj(R[i][j]) * R[i][k];
+      R[j][k] = (1.0 / R[j][j].re) * t;
+    }
+  }
+  for (int j = 0; j < nv; ++j)
+    for (int i = 0; i <= j; ++i) R[i][j] = (1.0 / dsc[j]) * R[i][j];
+  int kmax = nv - 1;   // usable steps: columns 1 .. kmax of R
+  if (kmax > maxit - S.iterations) kmax = maxit - S.iterations;
+  S.active = 0;
+  S.csteps += M;
+  S.gsum += NV;
+  if (kmax < 1) {   // no usable direction: stop this right-hand side
+    S.done = 1;
+    S.converged = 0;
+    S.jend = 0;
+    return;
+  }
+  // Givens on the (kmax+1) x kmax upper-Hessenberg matrix H[i][c] = R[i][c+1], rhs g = R_00 e_0
+  cd g[NV], H[NV][NV];
+  double cs[NV];
+  cd sn[NV];
+  g[0] = R[0][0];
+  for (int i = 1; i < NV; ++i) g[i] = czero<double>();
+  int jend = kmax;
+  for (int c = 0; c < kmax; ++c) {
+    cd col[NV];
+    for (int i = 0; i <= c + 1; ++i) col[i] = R[i][c + 1];
+    for (int i = 0; i < c; ++i) {
+      const cd t = cs[i] * col[i] + sn[i] * col[i + 1];
+      col[i + 1] = (-1.0 * cconj(sn[i])) * col[i] + cs[i] * col[i + 1];
+      col[i] = t;
+    }
+    const cd aa = col[c], bb = col[c + 1];
+    double cc;
+    cd sv;
+    if (bb.re == 0.0 && bb.im == 0.0) { cc = 1.0; sv = czero<double>(); }
+    else if (aa.re == 0.0 && aa.im == 0.0) { cc = 0.0; sv = mk<double>(1.0, 0.0); }
+    else {
+      const double na = sqrt(cabs2(aa)), rho = sqrt(cabs2(aa) + cabs2(bb));
+      cc = na / rho;
+      sv = (1.0 / (na * rho)) * (aa * cconj(bb));
+    }
+    col[c] = cc * col[c] + sv * col[c + 1];
+    cs[c] = cc;
+    sn[c] = sv;
+    g[c + 1] = (-1.0 * cconj(sv)) * g[c];
+    g[c] = cc * g[c];
+    for (int i = 0; i <= c; ++i) H[i][c] = col[i];
+    if (!(sqrt(cabs2(g[c + 1])) > tol * S.tol_scale * S.bnorm)) { jend = c + 1; break; }
+  }
+  cd* yy = y + (size_t)rhs * a.m;
+  for (int i = jend - 1; i >= 0; --i) {
+    cd t = g[i];
+    for (int k = i + 1; k < jend; ++k) t = t - H[i][k] * yy[k];
+    const cd d = H[i][i];
+    const double den = cabs2(d);
+    yy[i] = den > 0.0 ? t * mk<double>(d.re / den, -d.im / den) : czero<double>();
+  }
+  S.jend = jend;
+  S.iterations += jend;
+  S.nupd += 1;
+  S.zsum += jend;
+}
+
 // ---------------------------------------------------------------- host side
 // Stages of the shared-memory ring for P planes and the dynamic shared memory they need.
 int stages_for(int P) {
@@ -753,7 +1040,12 @@ mgh_status df_xupdate(Handle& h, const KArgs& a, int B) {
 
 }  // namespace
 
-mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
+namespace {
+
+// Restarted flexible GMRES with a double-float iterate: the start, the FP64-verified restarts
+// and the exit are shared; `cycle` runs one restart cycle (its steps and the iterate update).
+template <typename Cycle>
+mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info, Cycle&& cycle) {
   KArgs a = make_kargs(h, B);
   const dim3 grid(a.nblk, B);
   const dim3 pgrid((unsigned)((a.N + 255) / 256), B);
@@ -809,14 +1101,7 @@ mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info)
     bool any = false;
     for (int i = 0; i < B; ++i) any |= (h.st_host[i].done == 0);
     if (!any) break;
-    for (int j = 0; j < a.m; ++j) MGH_TRY(df_arnoldi_step(h, a, j, B));
-    MGH_TRY(df_tail(h, a, B));
-    {
-      ProfScope ps(h, P_REDUCE);
-      k_lsq<<<(B + 63) / 64, 64, 0, h.stream>>>(a, h.H, h.g, h.y, h.st, B);
-      MGH_CHECK_LAUNCH(); h.launches++;
-    }
-    MGH_TRY(df_xupdate(h, a, B));
+    MGH_TRY(cycle(a));
     MGH_TRY(residual_and_start(0));
   }
   {
@@ -827,6 +1112,80 @@ mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info)
   }
   MGH_CUDA(cudaStreamSynchronize(h.stream));
   return finish_solve(h, B, info);
+}
+
+}  // namespace
+
+mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
+  return df_driver(h, b, B, x, info, [&](const KArgs& a) -> mgh_status {
+    for (int j = 0; j < a.m; ++j) MGH_TRY(df_arnoldi_step(h, a, j, B));
+    MGH_TRY(df_tail(h, a, B));
+    {
+      ProfScope ps(h, P_REDUCE);
+      k_lsq<<<(B + 63) / 64, 64, 0, h.stream>>>(a, h.H, h.g, h.y, h.st, B);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    return df_xupdate(h, a, B);
+  });
+}
+
+namespace {
+
+template <int NV>
+mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
+  static bool init = false;
+  if (!init) {
+    MGH_TRY(set_smem(k_ss_gram<NV>));
+    init = true;
+  }
+  const dim3 grid(a.nblk, B);
+  float2* V = reinterpret_cast<float2*>(h.V);
+  for (int k = 0; k < a.m; ++k) {
+    // z_k = M^{-1}(v_k / ||v_k||), reading only the hi plane of v_k
+    const cf* vhi = reinterpret_cast<const cf*>(V + (size_t)k * 2 * a.Np);
+    MGH_TRY(vcycle_f32in(h, vhi, (size_t)(a.m + 1) * 2 * a.Np, h.vscale + k, (size_t)(a.m + 1),
+                         (cf*)h.Z + (size_t)k * a.N, (size_t)a.m * a.N, B, h.st, k));
+    {
+      ProfScope ps(h, P_MATVEC_DOTS);
+      k_ss_matvec<<<grid, kKThreads, 0, h.stream>>>(a, k, (const cf*)h.Z, h.DAdf, V, h.partial, h.st);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    if (k + 1 < a.m) {
+      ProfScope ps(h, P_REDUCE);
+      k_ss_norm<<<B, 32, 0, h.stream>>>(a, k, h.partial, h.vscale, h.st);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+  }
+  {
+    const int P = 2 * NV, S = stages_for(P);
+    ProfScope ps(h, P_UPDATE);
+    k_ss_gram<NV><<<grid, kDfThreads, smem_for(P, S), h.stream>>>(a, S, V, h.partial, h.st, h.dev_err);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  {
+    ProfScope ps(h, P_REDUCE);
+    k_ss_lsq<NV><<<B, 64, 0, h.stream>>>(a, h.partial, h.y, h.st, h.p.tol, h.p.maxit);
+    MGH_CHECK_LAUNCH(); h.launches++;
+  }
+  return df_xupdate(h, a, B);
+}
+
+}  // namespace
+
+mgh_status fgmres_ss(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
+  return df_driver(h, b, B, x, info, [&](const KArgs& a) -> mgh_status {
+    switch (a.m + 1) {
+      case 2: return ss_cycle<2>(h, a, B);
+      case 3: return ss_cycle<3>(h, a, B);
+      case 4: return ss_cycle<4>(h, a, B);
+      case 5: return ss_cycle<5>(h, a, B);
+      case 6: return ss_cycle<6>(h, a, B);
+      case 7: return ss_cycle<7>(h, a, B);
+      case 8: return ss_cycle<8>(h, a, B);
+      case 9: return ss_cycle<9>(h, a, B);
+    }
+    return MGH_INVALID_ARG;
+  });
 }
 
 }  // namespace mgh

@@ -60,3 +60,13 @@ def test_host_only_entry_points(lib):
     with pytest.raises(capi.MGHError):
         capi.mgh_workspace_bytes(bad)
     assert capi.mgh_status_string(capi.MGH_NOT_CONVERGED) == "not converged"
+    # the s-step engine holds its Gram sums in registers: restart 1..8 on the mixed path
+    ss = capi.mgh_default_params()
+    ss.precision, ss.arnoldi, ss.restart = capi.MGH_PREC_MIXED32, capi.MGH_ARNOLDI_SSTEP, 8
+    assert capi.mgh_workspace_bytes(ss) > 0
+    ss.restart = 9
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(ss)
+    ss.arnoldi = 3
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(ss)

@@ -154,6 +154,56 @@ def test_mixed_arnoldi_variants_agree(restart):
         assert abs(a - c) <= max(3, 0.1 * c)
 
 
+@pytest.mark.parametrize("restart", [1, 4, 8])
+def test_sstep_cycles_match_direct_solve_and_arnoldi(restart):
+    """s-step cycles (monomial basis orthogonalised by the Cholesky factor of its Gram matrix)
+    reach the direct solution, with the iteration counts of Arnoldi-based FGMRES(m): in exact
+    arithmetic both minimise the residual over the same space in every cycle."""
+    torch = torch_cuda()
+    w = ragged(precision="mixed32", levels=4, nu1=1, nu2=1, tol=1e-10, restart=restart)
+    p, f, o = oracle_solver(w)
+    th = W.angles(w)
+    b = np.stack([O.rhs(p, f, t) for t in th])
+    out = {}
+    for ar in ("df", "sstep"):
+        s = make_solver(w, B=3, maxit=6000, arnoldi=ar)
+        s.set_contrast(to_t(f, torch))
+        x, infos = s.solve(to_t(b, torch))
+        assert all(i["converged"] for i in infos), (ar, infos)
+        out[ar] = (x.cpu().numpy(), [i["iterations"] for i in infos], [i["rel_residual"] for i in infos])
+    for q in range(3):
+        ref = O.direct_solve(p, o.D, b[q])
+        xs = out["sstep"][0][q]
+        assert rel(xs, ref) < 1e-5
+        true = np.linalg.norm(b[q] - o.apply_A(xs)) / np.linalg.norm(b[q])
+        assert true <= 1e-10 * (1 + 1e-6) and abs(true - out["sstep"][2][q]) <= 1e-3 * 1e-10
+    for a, c in zip(out["sstep"][1], out["df"][1]):
+        assert abs(a - c) <= max(3, 0.1 * c)
+
+
+def test_sstep_zero_rhs_maxit_and_oracle_iterations():
+    """b = 0 gives x = 0 in zero steps; maxit caps the steps even inside a cycle; and the step
+    count to 1e-8 matches the oracle's FGMRES(8) on the same problem."""
+    torch = torch_cuda()
+    w = ragged(precision="mixed32", levels=4, nu1=1, nu2=1, restart=8, tol=1e-8)
+    p, f, o = oracle_solver(w, tol=1e-8, restart=8)
+    s = make_solver(w, B=3, maxit=2, arnoldi="sstep")
+    s.set_contrast(to_t(f, torch))
+    b = np.zeros((3, p.ny, p.nx), dtype=np.complex128)
+    b[1] = O.rhs(p, f, 0.3)
+    x, infos = s.solve(to_t(b, torch), x0=to_t(W.random_field((3, p.ny, p.nx), 1), torch))
+    x = x.cpu().numpy()
+    assert np.all(x[0] == 0) and np.all(x[2] == 0)
+    assert infos[0]["iterations"] == 0 and infos[0]["converged"]
+    assert not infos[1]["converged"] and infos[1]["iterations"] == 2
+    s = make_solver(w, B=1, maxit=6000, arnoldi="sstep")
+    s.set_contrast(to_t(f, torch))
+    x, infos = s.solve(to_t(b[1:2], torch))
+    _, ref = o.solve(b[1])
+    assert infos[0]["converged"] and ref.converged
+    assert abs(infos[0]["iterations"] - ref.iterations) <= max(5, 0.1 * ref.iterations), (infos, ref.iterations)
+
+
 def test_forward_matches_oracle_forward():
     torch = torch_cuda()
     w = ragged(precision="fp64", tol=1e-11)
@@ -281,13 +331,15 @@ def test_autograd_function_matches_finite_differences():
         assert float((g * d).sum()) == pytest.approx(float(fd), rel=1e-6)
 
 
-def test_ellipses576_full_size_residual_property():
+@pytest.mark.parametrize("arnoldi", ["df", "sstep"])
+def test_ellipses576_full_size_residual_property(arnoldi):
     """Full-size batched mixed-precision forward (512^2 + 32 layer, 60 angles, FP32 V-cycle with
-    6 levels, FP64 FGMRES(20), tol 1e-6), the launch configuration the bench times.  The oracle
-    recomputes the true FP64 residual of sampled returned fields."""
+    6 levels, FGMRES(8) with double-float Arnoldi or s-step cycles, tol 1e-6), the launch
+    configuration the bench times.  The oracle recomputes the true FP64 residual of sampled
+    returned fields."""
     torch = torch_cuda()
     w = W.WORKLOADS["ellipses576"]
-    s = make_solver(w, B=w.n_angles, maxit=5000)
+    s = make_solver(w, B=w.n_angles, maxit=5000, arnoldi=arnoldi)
     p = O.Problem.from_workload(w)
     f = W.phantom(w)
     s.set_contrast(to_t(f, torch))
