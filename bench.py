@@ -51,8 +51,9 @@ def parse_args(argv=None):
     ap.add_argument("--nu", type=int, default=None, help="pre- and post-smoothing sweeps (default: the workload's)")
     ap.add_argument("--levels", type=int, default=None, help="multigrid levels (default: the workload's)")
     ap.add_argument("--maxit", type=int, default=20000, help="Arnoldi steps per solve before giving up")
-    ap.add_argument("--arnoldi", choices=["df", "fp64", "sstep"], default="df",
-                    help="mixed precision Arnoldi arithmetic: double-float on FP32 pipes or native FP64")
+    ap.add_argument("--arnoldi", choices=["auto", "df", "fp64", "sstep"], default="auto",
+                    help="mixed-precision Krylov engine: s-step cycles (Gram/Cholesky), double-float Arnoldi, "
+                         "native-FP64 Arnoldi; auto = s-step when the restart length is at most 8")
     ap.add_argument("--autotune", action="store_true",
                     help="pick nu and the restart length with the autotuner (cached) before timing")
     ap.add_argument("--descent", type=int, default=0,
@@ -417,7 +418,7 @@ def gpu_main(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel class (CUDA events over the timed region)
     cs = 16 if precision == "fp64" else 8
     N = solver.N
-    alg = algorithmic_bytes(prof, N, cs, prof["launches"], args.arnoldi if precision == "mixed32" else "fp64")
+    alg = algorithmic_bytes(prof, N, cs, prof["launches"], solver.arnoldi if precision == "mixed32" else "fp64")
     ms_cls = prof["ms"]
     dom = max(ms_cls, key=lambda k: ms_cls[k])
     peak, peak_kind = load_peaks()
@@ -457,7 +458,7 @@ def gpu_main(args, rank, world, local_rank):
         "dtype": "f32+f64" if precision == "mixed32" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
                    "angles_per_gpu": B, "angles_total": B * world, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
-                   "restart": w.restart, "tol": w.tol, "arnoldi": args.arnoldi if precision == "mixed32" else "fp64", "shift": [w.shift_re, w.shift_im],
+                   "restart": w.restart, "tol": w.tol, "arnoldi": solver.arnoldi if precision == "mixed32" else "fp64", "shift": [w.shift_re, w.shift_im],
                    "step": f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient",
                    "solves_per_step": 2 * B, "l2": "inputs larger than L2 (Krylov basis "
                    f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}"},

@@ -643,22 +643,39 @@ k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, float2
   float2* xh = xdf + (size_t)rhs * 2 * a.Np;
   float2* xl = xh + a.Np;
   const size_t p0 = blockIdx.x * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
-  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads) {
-    cdf v = load_df(xh, a.Np, q);
+  // two points per thread and iteration, every load issued before the arithmetic
+  for (size_t q = p0 + threadIdx.x; q < p1; q += 2 * kKThreads) {
+    const size_t q2 = q + kKThreads;
+    const bool two = q2 < p1;
+    cf z1[NV], z2[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      z1[i] = i < je ? Zb[(size_t)i * a.N + q] : mk<float>(0.f, 0.f);
+      z2[i] = (i < je && two) ? Zb[(size_t)i * a.N + q2] : mk<float>(0.f, 0.f);
+    }
+    cdf v[2] = {load_df(xh, a.Np, q), two ? load_df(xh, a.Np, q2) : cdf_zero()};
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       if (i < je) {
-        const cf z = Zb[(size_t)i * a.N + q];
-        df_fma1(v.re, ys[i].re.hi, ys[i].re.lo, z.re);
-        df_fma1(v.re, -ys[i].im.hi, -ys[i].im.lo, z.im);
-        df_fma1(v.im, ys[i].re.hi, ys[i].re.lo, z.im);
-        df_fma1(v.im, ys[i].im.hi, ys[i].im.lo, z.re);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const cf z = u == 0 ? z1[i] : z2[i];
+          df_fma1(v[u].re, ys[i].re.hi, ys[i].re.lo, z.re);
+          df_fma1(v[u].re, -ys[i].im.hi, -ys[i].im.lo, z.im);
+          df_fma1(v[u].im, ys[i].re.hi, ys[i].re.lo, z.im);
+          df_fma1(v[u].im, ys[i].im.hi, ys[i].im.lo, z.re);
+        }
       }
     }
-    v.re = df_norm(v.re);
-    v.im = df_norm(v.im);
-    xh[q] = make_float2(v.re.hi, v.im.hi);
-    xl[q] = make_float2(v.re.lo, v.im.lo);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !two) break;
+      const size_t qq = u == 0 ? q : q2;
+      v[u].re = df_norm(v[u].re);
+      v[u].im = df_norm(v[u].im);
+      xh[qq] = make_float2(v[u].re.hi, v[u].im.hi);
+      xl[qq] = make_float2(v[u].re.lo, v[u].im.lo);
+    }
   }
 }
 
@@ -702,6 +719,17 @@ __device__ __forceinline__ void unroll(F&& f) {
   unroll_seq(f, std::make_integer_sequence<int, N>{});
 }
 
+// a + b + c + d of four floats, exactly as a double-float (three TwoSums)
+__device__ __forceinline__ df sum4(float a, float b, float c, float d) {
+  float s1, t1, s2, t2, s, t3;
+  two_sum(a, b, s1, t1);
+  two_sum(c, d, s2, t2);
+  two_sum(s1, s2, s, t3);
+  df r;
+  two_sum(s, __fadd_rn(t3, __fadd_rn(t1, t2)), r.hi, r.lo);
+  return r;
+}
+
 // v_{k+1} = A z_k in double-float (z_k FP32), written to basis slot k + 1, and its partial
 // ||v_{k+1}||^2 (slot 0 of the partial buffer).
 __global__ void __launch_bounds__(kKThreads)
@@ -715,7 +743,7 @@ k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__
   const float2* dh = DAdf;
   const float2* dl = DAdf + a.Np;
   const df ih = df_from_double(a.inv_h2);
-  df nrm = {0.f, 0.f};
+  float nrm = 0.f;
   const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
   int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
   int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
@@ -728,11 +756,7 @@ k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__
     const cf zs = n > 0 ? z[q - a.nx] : mk<float>(0.f, 0.f);
     const cf zn = n < a.ny - 1 ? z[q + a.nx] : mk<float>(0.f, 0.f);
     const float2 d0 = dh[q], d1 = dl[q];
-    df sr = {0.f, 0.f}, si = {0.f, 0.f};
-    df_add1(sr, zw.re); df_add1(si, zw.im);
-    df_add1(sr, ze.re); df_add1(si, ze.im);
-    df_add1(sr, zs.re); df_add1(si, zs.im);
-    df_add1(sr, zn.re); df_add1(si, zn.im);
+    const df sr = sum4(zw.re, ze.re, zs.re, zn.re), si = sum4(zw.im, ze.im, zs.im, zn.im);
     cdf w = cdf_zero();
     df_fma1(w.re, d0.x, d1.x, zc.re);
     df_fma1(w.re, -d0.y, -d1.y, zc.im);
@@ -744,9 +768,10 @@ k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__
     w.im = df_norm(w.im);
     vh[q] = make_float2(w.re.hi, w.im.hi);
     vl[q] = make_float2(w.re.lo, w.im.lo);
-    cdf_abs2_acc(nrm, w);
+    nrm = fmaf(w.re.hi, w.re.hi, fmaf(w.im.hi, w.im.hi, nrm));
   }
-  df vals[1] = {nrm};
+  // the norm only scales the next multigrid input (the Gram matrix holds the exact one): FP32
+  df vals[1] = {{nrm, 0.f}};
   cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
   block_reduce_df(vals, 1, [&](int) -> double* { out->im = 0.0; return &out->re; });
 }
@@ -769,7 +794,7 @@ __device__ __forceinline__ void gram_tile(const Pipe& pp, int slot, size_t q0, s
   constexpr int P1 = P0 + PR::PG < PR::NP ? P0 + PR::PG : PR::NP;
   if constexpr (P1 > P0) {
     constexpr int IMIN = PR::row(P0);
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < kTile / 64; ++r) {
       const int t = l64 + 64 * r;
       if (q0 + t >= p1) break;
@@ -790,7 +815,9 @@ __device__ __forceinline__ void gram_tile(const Pipe& pp, int slot, size_t q0, s
 }
 
 // G_ij = v_i^H v_j (i <= j) over v_0 .. v_{NV-1}: one sweep of the basis through the TMA ring;
-// four groups of 64 threads share the pairs, each thread sums 4 points of every tile.
+// four groups of 64 threads share the pairs, each thread sums 4 points of every tile.  Group g
+// is warps g and g + 4, which run on the same SM sub-partition, so that each sub-partition's
+// instruction cache holds the code of one group.
 template <int NV>
 __global__ void __launch_bounds__(kDfThreads)
 k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial, const RhsState* __restrict__ st,
@@ -810,7 +837,7 @@ k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial
   }
   int* fail = reinterpret_cast<int*>(smem + kSmemHeader - 16);
   pipe_start(pp, fail);
-  const int l64 = threadIdx.x & 63, grp = threadIdx.x >> 6;
+  const int grp = (threadIdx.x >> 5) & 3, l64 = (threadIdx.x & 31) + 32 * (threadIdx.x >> 7);
   cdf acc[PR::PG];
 #pragma unroll
   for (int c = 0; c < PR::PG; ++c) acc[c] = cdf_zero();
@@ -839,7 +866,7 @@ k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial
   cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
   for (int t = threadIdx.x; t < PR::NP; t += kDfThreads) {
     const int g = t / PR::PG, c = t - g * PR::PG;
-    const float4 x0 = sh[2 * g][c], x1 = sh[2 * g + 1][c];
+    const float4 x0 = sh[g][c], x1 = sh[g + 4][c];
     const df re = df_add(df{x0.x, x0.y}, df{x1.x, x1.y}), im = df_add(df{x0.z, x0.w}, df{x1.z, x1.w});
     out[t] = mk<double>(df_to_double(re), df_to_double(im));
   }

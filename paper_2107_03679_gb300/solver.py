@@ -13,13 +13,23 @@ import torch
 from . import capi
 
 
+def resolve_arnoldi(arnoldi: str, precision: str, restart: int) -> str:
+    """"auto": s-step cycles on the mixed path when the restart length allows them (m <= 8),
+    otherwise the double-float Arnoldi; the FP64 path always runs native FP64 Gram-Schmidt."""
+    if arnoldi != "auto":
+        return arnoldi
+    if precision != "mixed32":
+        return "df"
+    return "sstep" if restart <= 8 else "df"
+
+
 class Solver:
     """Batched MG-preconditioned FGMRES solver for one discretised Helmholtz problem (Sec. IV)."""
 
     def __init__(self, nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: float = 0.15,
                  shift=(1.0, 0.5), levels: int = 4, nu1: int = 1, nu2: int = 1, omega: float = 0.8,
                  restart: int = 20, maxit: int = 5000, tol: float = 1e-6, precision: str = "mixed32",
-                 batch_max: int = 1, arnoldi: str = "df", device: Optional[torch.device] = None, stream=None):
+                 batch_max: int = 1, arnoldi: str = "auto", device: Optional[torch.device] = None, stream=None):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         p = capi.mgh_params()
@@ -30,7 +40,8 @@ class Solver:
         p.restart, p.maxit, p.tol = restart, maxit, tol
         p.precision = capi.PRECISIONS[precision]
         p.batch_max = batch_max
-        p.arnoldi = capi.ARNOLDI[arnoldi]
+        self.arnoldi = resolve_arnoldi(arnoldi, precision, restart)
+        p.arnoldi = capi.ARNOLDI[self.arnoldi]
         self.params = p
         self.precision = precision
         self.nx_int, self.ny_int, self.abl = nx_int, ny_int, abl
