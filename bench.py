@@ -147,22 +147,36 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- algorithmic bytes
-def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str) -> dict:
-    """Minimal DRAM bytes of each kernel class from the engine counters (fields read once,
-    per-grid coefficient arrays counted once per launch).  N = fine points, cs = bytes of one
-    complex number of the multigrid precision; engine = "df", "sstep" or "fp64"."""
+def coarse_fraction(nx: int, ny: int, levels: int) -> float:
+    """Points of the levels 1 .. L-2 (the coarser smoothing levels) per fine point."""
+    tot, cx, cy = 0, nx, ny
+    for _ in range(1, levels - 1):
+        cx, cy = (cx - 1) // 2 + 1, (cy - 1) // 2 + 1
+        tot += cx * cy
+    return tot / (nx * ny)
+
+
+def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, cfrac: float = 0.0) -> dict:
+    """Minimal bytes of each kernel class from the engine counters (fields read once, per-grid
+    coefficient arrays counted once per launch).  N = fine points, cs = bytes of one complex
+    number of the multigrid precision; engine = "df", "sstep" or "fp64"; cfrac = points of the
+    coarser smoothing levels per fine point (their fields fit in L2, so this class is not bound
+    by DRAM alone)."""
     steps = prof["arnoldi_steps"]
     c16 = 16
     if engine == "sstep":
         # s-step cycles: every step of a cycle runs (cycle_steps), one Gram sweep per cycle
         run = prof["cycle_steps"]
         return {
+            # levels 1 .. L-2: pre reads b, writes v and the restricted residual; post reads b, v and
+            # the coarse correction, writes the result
+            "vcycle_coarse": run * N * cfrac * cs * (3.25 + 3.25),
             "vcycle_pre_l0": run * N * (8 + cs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
             "vcycle_post_l0": run * N * (8 + 2 * cs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
-            # v_{k+1} = A z_k: read z_k (FP32), write v_{k+1} (double-float); D_A planes per launch
-            "matvec_dots": run * N * (cs + c16) + launches["matvec_dots"] * c16 * N,
-            # Gram sweep: read the m + 1 basis vectors
-            "gs_update": prof["gram_reads"] * N * c16,
+            # v_{k+1} = A z_k in FP32: read z_k, write v_{k+1}; D_A (FP32) per launch
+            "matvec_dots": run * N * (cs + cs) + launches["matvec_dots"] * cs * N,
+            # Gram sweep: read the m + 1 FP32 basis vectors
+            "gs_update": prof["gram_reads"] * N * cs,
             "true_residual": prof["residuals"] * N * 3 * c16,
             "x_update": prof["updates"] * N * 2 * c16 + prof["update_reads"] * N * cs,
         }
@@ -418,7 +432,8 @@ def gpu_main(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel class (CUDA events over the timed region)
     cs = 16 if precision == "fp64" else 8
     N = solver.N
-    alg = algorithmic_bytes(prof, N, cs, prof["launches"], solver.arnoldi if precision == "mixed32" else "fp64")
+    alg = algorithmic_bytes(prof, N, cs, prof["launches"], solver.arnoldi if precision == "mixed32" else "fp64",
+                            coarse_fraction(w.nx, w.ny, w.levels))
     ms_cls = prof["ms"]
     dom = max(ms_cls, key=lambda k: ms_cls[k])
     peak, peak_kind = load_peaks()

@@ -693,6 +693,15 @@ k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, float2
 // iterate as Arnoldi-based FGMRES(m) on the same z_k; the Gram matrix needs the basis to be well
 // enough conditioned for double-float sums, and a Cholesky pivot that vanishes ends the usable
 // basis there.
+//
+// The basis is stored in FP32 (the hi planes of the basis slots) and v_{k+1} = A z_k is formed
+// in FP32: the cycle only has to find a near-optimal correction, and the relation
+// A Z = V_{1:m+1} then holds to FP32 rounding, which perturbs the residual reduction of a cycle by
+// about eps32 * cond(V) (1e-4 for cond(V) ~ 1e3).  The Gram entries are exact products of the
+// stored floats summed in double-float (FP64-class), so the Cholesky factor is that of the stored
+// basis to working accuracy.  The iterate and the restart residual stay double-float and every
+// accepted iterate is checked by the FP64 true residual, so the attainable accuracy is that of
+// the outer iteration (iterative refinement with an FP32 inner cycle).
 
 template <int NV>
 struct GramPairs {
@@ -730,24 +739,22 @@ __device__ __forceinline__ df sum4(float a, float b, float c, float d) {
   return r;
 }
 
-// v_{k+1} = A z_k in double-float (z_k FP32), written to basis slot k + 1, and its partial
-// ||v_{k+1}||^2 (slot 0 of the partial buffer).
+// v_{k+1} = A z_k in FP32, written to the hi plane of basis slot k + 1, and its partial
+// ||v_{k+1}||^2 (slot 0 of the partial buffer; FP32 sums: the norm only scales the next
+// multigrid input, the Gram matrix holds the exact one).
 __global__ void __launch_bounds__(kKThreads)
-k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__ DAdf, float2* __restrict__ V,
+k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__ D32, float2* __restrict__ V,
             cd* __restrict__ partial, const RhsState* __restrict__ st) {
   const int rhs = blockIdx.y, blk = blockIdx.x;
   if (!st[rhs].active) return;
   const cf* z = Z + ((size_t)rhs * a.m + k) * a.N;
   float2* vh = V + (((size_t)rhs * (a.m + 1) + k + 1) * 2) * a.Np;
-  float2* vl = vh + a.Np;
-  const float2* dh = DAdf;
-  const float2* dl = DAdf + a.Np;
-  const df ih = df_from_double(a.inv_h2);
+  const float ih = (float)a.inv_h2;
   float nrm = 0.f;
   const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
   int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
   int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
-#pragma unroll 2
+#pragma unroll 4
   for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads) {
     while (m >= a.nx) { m -= a.nx; ++n; }
     const cf zc = z[q];
@@ -755,22 +762,13 @@ k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__
     const cf ze = m < a.nx - 1 ? z[q + 1] : mk<float>(0.f, 0.f);
     const cf zs = n > 0 ? z[q - a.nx] : mk<float>(0.f, 0.f);
     const cf zn = n < a.ny - 1 ? z[q + a.nx] : mk<float>(0.f, 0.f);
-    const float2 d0 = dh[q], d1 = dl[q];
-    const df sr = sum4(zw.re, ze.re, zs.re, zn.re), si = sum4(zw.im, ze.im, zs.im, zn.im);
-    cdf w = cdf_zero();
-    df_fma1(w.re, d0.x, d1.x, zc.re);
-    df_fma1(w.re, -d0.y, -d1.y, zc.im);
-    df_fma1(w.im, d0.x, d1.x, zc.im);
-    df_fma1(w.im, d0.y, d1.y, zc.re);
-    df_fma(w.re, -ih.hi, -ih.lo, sr.hi, sr.lo);
-    df_fma(w.im, -ih.hi, -ih.lo, si.hi, si.lo);
-    w.re = df_norm(w.re);
-    w.im = df_norm(w.im);
-    vh[q] = make_float2(w.re.hi, w.im.hi);
-    vl[q] = make_float2(w.re.lo, w.im.lo);
-    nrm = fmaf(w.re.hi, w.re.hi, fmaf(w.im.hi, w.im.hi, nrm));
+    const float2 d = D32[q];
+    const float sr = (zw.re + ze.re) + (zs.re + zn.re), si = (zw.im + ze.im) + (zs.im + zn.im);
+    const float wr = fmaf(d.x, zc.re, fmaf(-d.y, zc.im, -ih * sr));
+    const float wi = fmaf(d.x, zc.im, fmaf(d.y, zc.re, -ih * si));
+    vh[q] = make_float2(wr, wi);
+    nrm = fmaf(wr, wr, fmaf(wi, wi, nrm));
   }
-  // the norm only scales the next multigrid input (the Gram matrix holds the exact one): FP32
   df vals[1] = {{nrm, 0.f}};
   cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
   block_reduce_df(vals, 1, [&](int) -> double* { out->im = 0.0; return &out->re; });
@@ -786,6 +784,17 @@ __global__ void k_ss_norm(KArgs a, int k, const cd* __restrict__ partial, double
   vscale[(size_t)rhs * (a.m + 1) + k + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
 }
 
+// acc += x * y for floats x, y: exact product (FMA TwoProduct) summed by TwoSum into acc.hi, every
+// rounding error gathered in acc.lo.
+__device__ __forceinline__ void df_acc_prod(df& acc, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float e = __fmaf_rn(x, y, -p);
+  float s, t;
+  two_sum(acc.hi, p, s, t);
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+}
+
 // The Gram sums of one tile's points for the pairs of thread group G.
 template <int NV, int G>
 __device__ __forceinline__ void gram_tile(const Pipe& pp, int slot, size_t q0, size_t p1, int l64, cdf* acc) {
@@ -798,23 +807,28 @@ __device__ __forceinline__ void gram_tile(const Pipe& pp, int slot, size_t q0, s
     for (int r = 0; r < kTile / 64; ++r) {
       const int t = l64 + 64 * r;
       if (q0 + t >= p1) break;
-      cdf v[NV];
+      float2 v[NV];
 #pragma unroll
-      for (int i = IMIN; i < NV; ++i) {
-        const float2 hh = pp.plane(slot, 2 * i)[t], ll = pp.plane(slot, 2 * i + 1)[t];
-        v[i].re.hi = hh.x; v[i].im.hi = hh.y; v[i].re.lo = ll.x; v[i].im.lo = ll.y;
-      }
+      for (int i = IMIN; i < NV; ++i) v[i] = pp.plane(slot, i)[t];
       unroll<P1 - P0>([&](auto PC) {
         constexpr int p = P0 + decltype(PC)::value;
         constexpr int i = PR::row(p), j = PR::col(p);
-        if constexpr (i == j) cdf_abs2_acc(acc[p - P0].re, v[i]);
-        else cdf_dot_acc(acc[p - P0], v[i], v[j]);
+        cdf& c = acc[p - P0];
+        if constexpr (i == j) {
+          df_acc_prod(c.re, v[i].x, v[i].x);
+          df_acc_prod(c.re, v[i].y, v[i].y);
+        } else {   // conj(v_i) v_j
+          df_acc_prod(c.re, v[i].x, v[j].x);
+          df_acc_prod(c.re, v[i].y, v[j].y);
+          df_acc_prod(c.im, v[i].x, v[j].y);
+          df_acc_prod(c.im, -v[i].y, v[j].x);
+        }
       });
     }
   }
 }
 
-// G_ij = v_i^H v_j (i <= j) over v_0 .. v_{NV-1}: one sweep of the basis through the TMA ring;
+// G_ij = v_i^H v_j (i <= j) over the stored v_0 .. v_{NV-1}: one sweep of the basis through the TMA ring;
 // four groups of 64 threads share the pairs, each thread sums 4 points of every tile.  Group g
 // is warps g and g + 4, which run on the same SM sub-partition, so that each sub-partition's
 // instruction cache holds the code of one group.
@@ -828,13 +842,9 @@ k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial
   const int rhs = blockIdx.y, blk = blockIdx.x;
   if (!st[rhs].active) return;
   const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
-  Pipe pp = pipe_begin(smem, S, 2 * NV, p0, p1);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < NV; ++i) {
-      pp.src[2 * i] = vplane(V, a, rhs, i, 0);
-      pp.src[2 * i + 1] = vplane(V, a, rhs, i, 1);
-    }
-  }
+  Pipe pp = pipe_begin(smem, S, NV, p0, p1);   // the FP32 (hi) planes of the basis
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NV; ++i) pp.src[i] = vplane(V, a, rhs, i, 0);
   int* fail = reinterpret_cast<int*>(smem + kSmemHeader - 16);
   pipe_start(pp, fail);
   const int grp = (threadIdx.x >> 5) & 3, l64 = (threadIdx.x & 31) + 32 * (threadIdx.x >> 7);
@@ -1174,7 +1184,7 @@ mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
                          (cf*)h.Z + (size_t)k * a.N, (size_t)a.m * a.N, B, h.st, k));
     {
       ProfScope ps(h, P_MATVEC_DOTS);
-      k_ss_matvec<<<grid, kKThreads, 0, h.stream>>>(a, k, (const cf*)h.Z, h.DAdf, V, h.partial, h.st);
+      k_ss_matvec<<<grid, kKThreads, 0, h.stream>>>(a, k, (const cf*)h.Z, h.DAdf, V, h.partial, h.st);   // hi plane
       MGH_CHECK_LAUNCH(); h.launches++;
     }
     if (k + 1 < a.m) {
@@ -1184,7 +1194,7 @@ mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
     }
   }
   {
-    const int P = 2 * NV, S = stages_for(P);
+    const int P = NV, S = stages_for(P);
     ProfScope ps(h, P_UPDATE);
     k_ss_gram<NV><<<grid, kDfThreads, smem_for(P, S), h.stream>>>(a, S, V, h.partial, h.st, h.dev_err);
     MGH_CHECK_LAUNCH(); h.launches++;
