@@ -834,21 +834,38 @@ int persistent_blocks(Handle& h, K kern, size_t smem, int tiles, int threads = k
 // ---------------------------------------------------------------- wavefront level kernels (host side)
 bool a16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// Rows per warp segment: about the longest of 64, 32, 16, 8 that still gives the GPU three waves
-// of warps (longer segments repeat fewer halo rows, shorter ones fill small levels), moved down
-// to an even length whose step count (seg + extra) wastes at most one step of the last unrolled
-// period of P steps.
-int wave_seg(const Handle& h, int ny, int nstrips, int B, int extra, int P) {
-  int seg = 64;
+// Rows per warp segment.  All warps of a launch run the same number of steps K (rows + halo
+// rows, rounded up to the unroll period P), so a launch takes about K times the number of
+// waves of resident warps; the even segment length from 4 to 128 with the least
+// K * ceil(warps / resident) is taken (long segments repeat fewer halo rows, short ones fill
+// the GPU on small levels).
+int wave_seg(const Handle& h, int ny, int nstrips, int B, int extra, int P, long resident) {
   if (h.wave_seg > 0) {
-    seg = (h.wave_seg + 1) & ~1;
-  } else {
-    const long target = 3L * h.num_sms * 16;
-    while (seg > 8 && (long)nstrips * ((ny + seg - 1) / seg) * B < target) seg /= 2;
+    const int seg = (h.wave_seg + 1) & ~1;
+    for (int s = seg; s >= 4; s -= 2)
+      if ((P - (s + extra) % P) % P <= 1) return s;
+    return seg;
   }
-  for (int s = seg; s >= 4; s -= 2)
-    if ((P - (s + extra) % P) % P <= 1) return s;
-  return seg;
+  if (resident < 1) resident = 1;
+  long best = -1;
+  int bs = 4;
+  for (int s = 4; s <= 128; s += 2) {
+    const long K = (s + extra + P - 1) / P * P;
+    const long warps = (long)nstrips * ((ny + s - 1) / s) * B;
+    const long t = K * ((warps + resident - 1) / resident);
+    if (best < 0 || t < best) { best = t; bs = s; }
+    if ((ny + s - 1) / s == 1) break;   // one segment covers the level
+  }
+  return bs;
+}
+
+// Warps of a wavefront kernel resident on the whole GPU (occupancy of the default variant).
+template <typename K>
+long resident_warps(const Handle& h, K kern, int threads, size_t smem) {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, threads, smem) != cudaSuccess || blocks < 1)
+    blocks = 1;
+  return (long)blocks * (threads / 32) * h.num_sms;
 }
 
 bool use_wave(const Handle& h, int l) { return h.vc_wave && h.lev[l].nx >= h.wave_min_nx; }
@@ -993,7 +1010,15 @@ mgh_status launch_pre_wave(Handle& h, int l, const cf* bin, size_t b_stride, con
                            : (h.wave_ring >= 2 ? wave::RingLen<wave::PreW<NU, 1>::P, NU, 2>::S
                                                : wave::RingLen<wave::PreW<NU, 1>::P, NU, 1>::S);
   const int nstrips = (lv.nx + G::XO - 1) / G::XO;
-  const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * G::H - 1, period);
+  static long resident = -1;
+  if (resident < 0) {
+    constexpr int S1 = wave::RingLen<wave::PreW<NU, 1>::P, NU, 1>::S;
+    auto kern = wave::k_pre_wa<NU, 4, 1>;
+    constexpr size_t smem = wave::LaneRingSmem<4, S1>::bytes();
+    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    resident = resident_warps(h, kern, 128, smem);
+  }
+  const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * G::H - 1, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
   if (ring) {
@@ -1024,7 +1049,15 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
                            : (h.wave_ring >= 2 ? wave::RingLen<wave::PostW<NU, 1>::P, NU, 2>::S
                                                : wave::RingLen<wave::PostW<NU, 1>::P, NU, 1>::S);
   const int nstrips = (lv.nx + G::XO - 1) / G::XO;
-  const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * NU, period);
+  static long resident = -1;
+  if (resident < 0) {
+    constexpr int S1 = wave::RingLen<wave::PostW<NU, 1>::P, NU, 1>::S;
+    auto kern = wave::k_post_wa<NU, 4, 1>;
+    constexpr size_t smem = wave::LaneRingSmem<4, S1>::bytes();
+    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    resident = resident_warps(h, kern, 128, smem);
+  }
+  const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * NU, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
   if (ring) {
