@@ -774,6 +774,50 @@ k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__
   block_reduce_df(vals, 1, [&](int) -> double* { out->im = 0.0; return &out->re; });
 }
 
+// The same for rows of even width: two adjacent points per thread and step (the pair never
+// straddles a row), 16-byte loads of z, D and the rows above and below, one 16-byte store.
+__global__ void __launch_bounds__(kKThreads)
+k_ss_matvec2(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__ D32, float2* __restrict__ V,
+             cd* __restrict__ partial, const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (!st[rhs].active) return;
+  const cf* z = Z + ((size_t)rhs * a.m + k) * a.N;
+  float2* vh = V + (((size_t)rhs * (a.m + 1) + k + 1) * 2) * a.Np;
+  const float ih = (float)a.inv_h2;
+  float nrm = 0.f;
+  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;   // both even
+  const float4* z4 = reinterpret_cast<const float4*>(z);
+  const float4* d4 = reinterpret_cast<const float4*>(D32);
+  float4* v4 = reinterpret_cast<float4*>(vh);
+  const size_t half = a.nx / 2;
+  size_t q = p0 + 2 * threadIdx.x;
+  int n = (int)((unsigned)q / (unsigned)a.nx);
+  int m = (int)((unsigned)q - (unsigned)n * (unsigned)a.nx);
+#pragma unroll 2
+  for (; q < p1; q += 2 * kKThreads, m += 2 * kKThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
+    const size_t h = q / 2;
+    const float4 c = z4[h];
+    const float4 up = n > 0 ? z4[h - half] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 dn = n < a.ny - 1 ? z4[h + half] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const cf zl = m > 0 ? z[q - 1] : mk<float>(0.f, 0.f);
+    const cf zr = m + 2 < a.nx ? z[q + 2] : mk<float>(0.f, 0.f);
+    const float4 d = d4[h];
+    // point q: neighbours zl, (c.z, c.w), up.xy, dn.xy; point q+1: (c.x, c.y), zr, up.zw, dn.zw
+    const float s0r = (zl.re + c.z) + (up.x + dn.x), s0i = (zl.im + c.w) + (up.y + dn.y);
+    const float s1r = (c.x + zr.re) + (up.z + dn.z), s1i = (c.y + zr.im) + (up.w + dn.w);
+    const float w0r = fmaf(d.x, c.x, fmaf(-d.y, c.y, -ih * s0r));
+    const float w0i = fmaf(d.x, c.y, fmaf(d.y, c.x, -ih * s0i));
+    const float w1r = fmaf(d.z, c.z, fmaf(-d.w, c.w, -ih * s1r));
+    const float w1i = fmaf(d.z, c.w, fmaf(d.w, c.z, -ih * s1i));
+    v4[h] = make_float4(w0r, w0i, w1r, w1i);
+    nrm = fmaf(w0r, w0r, fmaf(w0i, w0i, fmaf(w1r, w1r, fmaf(w1i, w1i, nrm))));
+  }
+  df vals[1] = {{nrm, 0.f}};
+  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
+  block_reduce_df(vals, 1, [&](int) -> double* { out->im = 0.0; return &out->re; });
+}
+
 // 1 / ||v_{k+1}|| for the next multigrid input.
 __global__ void k_ss_norm(KArgs a, int k, const cd* __restrict__ partial, double* __restrict__ vscale,
                           const RhsState* __restrict__ st) {
@@ -1184,7 +1228,10 @@ mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
                          (cf*)h.Z + (size_t)k * a.N, (size_t)a.m * a.N, B, h.st, k));
     {
       ProfScope ps(h, P_MATVEC_DOTS);
-      k_ss_matvec<<<grid, kKThreads, 0, h.stream>>>(a, k, (const cf*)h.Z, h.DAdf, V, h.partial, h.st);   // hi plane
+      if (a.nx % 2 == 0)
+        k_ss_matvec2<<<grid, kKThreads, 0, h.stream>>>(a, k, (const cf*)h.Z, h.DAdf, V, h.partial, h.st);
+      else
+        k_ss_matvec<<<grid, kKThreads, 0, h.stream>>>(a, k, (const cf*)h.Z, h.DAdf, V, h.partial, h.st);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
     if (k + 1 < a.m) {
