@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--arnoldi", choices=["auto", "df", "fp64", "sstep"], default="auto",
                     help="mixed-precision Krylov engine: s-step cycles (Gram/Cholesky), double-float Arnoldi, "
                          "native-FP64 Arnoldi; auto = s-step when the restart length is at most 8")
+    ap.add_argument("--krylov", choices=["fgmres", "bicgstab"], default="fgmres",
+                    help="outer Krylov method: flexible GMRES (default) or the paper's Bi-CGSTAB (Alg. 3)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick nu and the restart length with the autotuner (cached) before timing")
     ap.add_argument("--descent", type=int, default=0,
@@ -164,6 +166,17 @@ def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, 
     by DRAM alone)."""
     steps = prof["arnoldi_steps"]
     c16 = 16
+    if engine == "bicgstab":
+        # per cycle (two per iteration): A y and its dot (read y 8 + w 16, write 16); per iteration
+        # the p, s and r updates read/write 72 + 96 + 104 B; counters count cycles
+        return {
+            "vcycle_pre_l0": steps * N * (8 + cs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
+            "vcycle_post_l0": steps * N * (8 + 2 * cs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
+            "vcycle_coarse": steps * N * cfrac * cs * (3.25 + 3.25),
+            "matvec_dots": steps * N * (cs + 2 * c16) + launches["matvec_dots"] * c16 * N,
+            "gs_update": steps / 2 * N * (72 + 96 + 104),
+            "true_residual": prof["residuals"] * N * 3 * c16,
+        }
     if engine == "sstep":
         # s-step cycles: every step of a cycle runs (cycle_steps), one Gram sweep per cycle
         run = prof["cycle_steps"]
@@ -329,7 +342,8 @@ def gpu_main(args, rank, world, local_rank):
         tuned, trials = tune(w, torch.from_numpy(f_step).to(dev), torch.from_numpy(th), dev, precision=precision)
         w.nu1 = w.nu2 = tuned["nu"]
         w.restart = tuned["restart"]
-    solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=args.maxit, arnoldi=args.arnoldi)
+    solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=args.maxit, arnoldi=args.arnoldi,
+                                  krylov=args.krylov)
     stream = solver.stream
     d_th = torch.from_numpy(th).to(dev)
     d_rec = torch.from_numpy(rec).to(dev)
@@ -436,8 +450,8 @@ def gpu_main(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel class (CUDA events over the timed region)
     cs = 16 if precision == "fp64" else 8
     N = solver.N
-    alg = algorithmic_bytes(prof, N, cs, prof["launches"], solver.arnoldi if precision == "mixed32" else "fp64",
-                            coarse_fraction(w.nx, w.ny, w.levels))
+    engine = "bicgstab" if args.krylov == "bicgstab" else (solver.arnoldi if precision == "mixed32" else "fp64")
+    alg = algorithmic_bytes(prof, N, cs, prof["launches"], engine, coarse_fraction(w.nx, w.ny, w.levels))
     ms_cls = prof["ms"]
     dom = max(ms_cls, key=lambda k: ms_cls[k])
     peak, peak_kind = load_peaks()
@@ -477,7 +491,7 @@ def gpu_main(args, rank, world, local_rank):
         "dtype": "f32+f64" if precision == "mixed32" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
                    "angles_per_gpu": B, "angles_total": B * world, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
-                   "restart": w.restart, "tol": w.tol, "arnoldi": solver.arnoldi if precision == "mixed32" else "fp64", "shift": [w.shift_re, w.shift_im],
+                   "restart": w.restart, "tol": w.tol, "krylov": args.krylov, "arnoldi": solver.arnoldi if precision == "mixed32" else "fp64", "shift": [w.shift_re, w.shift_im],
                    "step": f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient",
                    "solves_per_step": 2 * B, "l2": "inputs larger than L2 (Krylov basis "
                    f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}"},

@@ -66,6 +66,15 @@ typedef enum {
                                sweep over the basis per cycle instead of two per step */
 } mgh_arnoldi;
 
+typedef enum {
+  MGH_KRYLOV_FGMRES = 0,    /* right-preconditioned flexible GMRES(restart) (the target's method) */
+  MGH_KRYLOV_BICGSTAB = 1   /* right-preconditioned Bi-CGSTAB of Alg. 3 (the paper's method): two
+                               multigrid cycles per iteration, FP64 vectors and inner products, the
+                               cycle in the handle's precision; uses the GMRES workspace, so it needs
+                               restart >= 5; `arnoldi` is ignored; iterations count cycles (2 per
+                               Bi-CGSTAB iteration) */
+} mgh_krylov;
+
 /* Solver parameters.  Lengths are in the same unit as h (grid cells when h = 1). */
 typedef struct {
   int nx_int, ny_int;       /* interior Omega size in grid points */
@@ -84,6 +93,7 @@ typedef struct {
   int precision;            /* mgh_precision */
   int batch_max;            /* largest batch B any later call may use; sizes the workspace */
   int arnoldi;              /* mgh_arnoldi, used when precision is MGH_PREC_MIXED32 */
+  int krylov;               /* mgh_krylov (default MGH_KRYLOV_FGMRES) */
 } mgh_params;
 
 typedef struct {

@@ -17,6 +17,8 @@ MGH_PREC_FP64, MGH_PREC_MIXED32 = 0, 1
 PRECISIONS = {"fp64": MGH_PREC_FP64, "mixed32": MGH_PREC_MIXED32}
 MGH_ARNOLDI_DF, MGH_ARNOLDI_FP64, MGH_ARNOLDI_SSTEP = 0, 1, 2
 ARNOLDI = {"df": MGH_ARNOLDI_DF, "fp64": MGH_ARNOLDI_FP64, "sstep": MGH_ARNOLDI_SSTEP}
+MGH_KRYLOV_FGMRES, MGH_KRYLOV_BICGSTAB = 0, 1
+KRYLOV = {"fgmres": MGH_KRYLOV_FGMRES, "bicgstab": MGH_KRYLOV_BICGSTAB}
 
 
 class mgh_params(ctypes.Structure):
@@ -28,6 +30,7 @@ class mgh_params(ctypes.Structure):
         ("omega", ctypes.c_double),
         ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
         ("precision", ctypes.c_int), ("batch_max", ctypes.c_int), ("arnoldi", ctypes.c_int),
+        ("krylov", ctypes.c_int),
     ]
 
 

@@ -36,8 +36,11 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
     return MGH_INVALID_ARG;
   if (p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_DF && p->restart > kMaxRestartDf)
     return MGH_INVALID_ARG;
-  if (p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_SSTEP && p->restart > kMaxRestartSs)
+  if (p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_SSTEP && p->restart > kMaxRestartSs &&
+      p->krylov == MGH_KRYLOV_FGMRES)
     return MGH_INVALID_ARG;
+  if (p->krylov != MGH_KRYLOV_FGMRES && p->krylov != MGH_KRYLOV_BICGSTAB) return MGH_INVALID_ARG;
+  if (p->krylov == MGH_KRYLOV_BICGSTAB && p->restart < 5) return MGH_INVALID_ARG;
   if (!std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) return MGH_INVALID_ARG;
   const long long nx = p->nx_int + 2LL * p->abl, ny = p->ny_int + 2LL * p->abl;
   if (nx > (1 << 20) || ny > (1 << 20) || nx * ny > (1LL << 31)) return MGH_INVALID_ARG;

@@ -179,5 +179,6 @@ constexpr int kErrTimeout = 1;
 
 // mgh_krylov.cu
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
+mgh_status bicgstab_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
 
 }  // namespace mgh

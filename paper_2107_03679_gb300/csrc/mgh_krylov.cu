@@ -400,6 +400,7 @@ mgh_status fgmres_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) 
 }  // namespace
 
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
+  if (h.p.krylov == MGH_KRYLOV_BICGSTAB) return bicgstab_solve(h, b, B, x, info);
   if (h.fp64) return fgmres_t<double>(h, b, B, x, info);
   if (h.p.arnoldi == MGH_ARNOLDI_FP64) return fgmres_t<float>(h, b, B, x, info);
   if (h.p.arnoldi == MGH_ARNOLDI_SSTEP) return fgmres_ss(h, b, B, x, info);

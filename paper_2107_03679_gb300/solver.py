@@ -29,7 +29,8 @@ class Solver:
     def __init__(self, nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: float = 0.15,
                  shift=(1.0, 0.5), levels: int = 4, nu1: int = 1, nu2: int = 1, omega: float = 0.8,
                  restart: int = 20, maxit: int = 5000, tol: float = 1e-6, precision: str = "mixed32",
-                 batch_max: int = 1, arnoldi: str = "auto", device: Optional[torch.device] = None, stream=None):
+                 batch_max: int = 1, arnoldi: str = "auto", krylov: str = "fgmres",
+                 device: Optional[torch.device] = None, stream=None):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         p = capi.mgh_params()
@@ -42,6 +43,8 @@ class Solver:
         p.batch_max = batch_max
         self.arnoldi = resolve_arnoldi(arnoldi, precision, restart)
         p.arnoldi = capi.ARNOLDI[self.arnoldi]
+        self.krylov = krylov
+        p.krylov = capi.KRYLOV[krylov]
         self.params = p
         self.precision = precision
         self.nx_int, self.ny_int, self.abl = nx_int, ny_int, abl

@@ -70,3 +70,13 @@ def test_host_only_entry_points(lib):
     ss.arnoldi = 3
     with pytest.raises(capi.MGHError):
         capi.mgh_workspace_bytes(ss)
+    # Bi-CGSTAB keeps its six FP64 vectors in the GMRES workspace: restart >= 5
+    bc = capi.mgh_default_params()
+    bc.krylov = capi.MGH_KRYLOV_BICGSTAB
+    assert capi.mgh_workspace_bytes(bc) > 0
+    bc.restart = 4
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(bc)
+    bc.restart, bc.krylov = 8, 2
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(bc)

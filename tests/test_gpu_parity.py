@@ -204,6 +204,46 @@ def test_sstep_zero_rhs_maxit_and_oracle_iterations():
     assert abs(infos[0]["iterations"] - ref.iterations) <= max(5, 0.1 * ref.iterations), (infos, ref.iterations)
 
 
+@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-12, 1e-10), ("mixed32", 1e-10, 1e-5)])
+def test_bicgstab_matches_direct_solve_and_oracle(precision, tol, bound):
+    """Bi-CGSTAB of Alg. 3 (two multigrid cycles per iteration): the direct solution within the
+    path's tolerance, the true residual it reports, and the oracle's step count (FP64 path: same
+    arithmetic up to rounding order; mixed path: FP32 cycle)."""
+    torch = torch_cuda()
+    w = ragged(precision=precision, levels=4, nu1=1, nu2=1, tol=tol, restart=8)
+    s = make_solver(w, B=3, maxit=3000, krylov="bicgstab")
+    p, f, o = oracle_solver(w, tol=tol, krylov="bicgstab")
+    s.set_contrast(to_t(f, torch))
+    th = W.angles(w)
+    b = np.stack([O.rhs(p, f, t) for t in th])
+    x, infos = s.solve(to_t(b, torch))
+    x = x.cpu().numpy()
+    for q in range(len(th)):
+        assert infos[q]["converged"], infos
+        ref = O.direct_solve(p, o.D, b[q])
+        assert rel(x[q], ref) < bound
+        true = np.linalg.norm(b[q] - o.apply_A(x[q])) / np.linalg.norm(b[q])
+        assert true <= tol * (1 + 1e-6)
+        _, info_ref = o.solve(b[q])
+        slack = max(4, 0.05 * info_ref.iterations) if precision == "fp64" else max(8, 0.15 * info_ref.iterations)
+        assert abs(infos[q]["iterations"] - info_ref.iterations) <= slack, (infos[q], info_ref.iterations)
+
+
+def test_bicgstab_zero_rhs_and_maxit():
+    torch = torch_cuda()
+    w = ragged(precision="mixed32", levels=4, nu1=1, nu2=1, restart=8)
+    p, f, o = oracle_solver(w)
+    s = make_solver(w, B=3, maxit=2, krylov="bicgstab")
+    s.set_contrast(to_t(f, torch))
+    b = np.zeros((3, p.ny, p.nx), dtype=np.complex128)
+    b[1] = O.rhs(p, f, 0.3)
+    x, infos = s.solve(to_t(b, torch), x0=to_t(W.random_field((3, p.ny, p.nx), 1), torch))
+    x = x.cpu().numpy()
+    assert np.all(x[0] == 0) and np.all(x[2] == 0)
+    assert infos[0]["iterations"] == 0 and infos[0]["converged"]
+    assert not infos[1]["converged"] and infos[1]["iterations"] == 2
+
+
 def test_forward_matches_oracle_forward():
     torch = torch_cuda()
     w = ragged(precision="fp64", tol=1e-11)
