@@ -107,6 +107,9 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->dev_err); cudaFree(h->xdf); cudaFree(h->bdf);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  if (h->gev_in) cudaEventDestroy(h->gev_in);
+  if (h->gev_out) cudaEventDestroy(h->gev_out);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
   delete[] h->tma;
   delete[] h->tma_in;
   delete h;
@@ -267,6 +270,8 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   if (const char* e = std::getenv("MGH_WAVE_WARPS")) h->wave_warps = std::atoi(e) == 2 ? 2 : 4;
   if (const char* e = std::getenv("MGH_WAVE_RING")) h->wave_ring = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("MGH_WAVE_FILL")) h->wave_lane_ring = std::strcmp(e, "bulk") != 0;
+  // MGH_GRAPHS=0 issues every restart cycle's launches directly instead of replaying a CUDA graph
+  if (const char* e = std::getenv("MGH_GRAPHS")) h->use_graphs = std::strcmp(e, "0") != 0;
   s = build_vcycle_tma(*h);
   if (s != MGH_OK) { free_handle(h); return s; }
   // start from f_d = 0 so that every later call finds a complete operator

@@ -64,6 +64,9 @@ struct Handle {
   int wave_ring = 1;         // shared-memory row ring of the wavefront kernels, in unroll periods
                              // (1 or 2; 0: loads prefetched into registers)
   bool wave_lane_ring = true;  // rings filled per lane by cp.async (else by bulk copies)
+  bool use_graphs = true;    // replay each restart cycle's launches from a captured CUDA graph
+  cudaStream_t gstream = nullptr;  // non-blocking stream the cycle graphs are captured and replayed on
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;  // order gstream after / before `stream`
   size_t csize = 16;         // bytes per complex of the cycle precision
   Level lev[kMaxLevels];
   bool contrast_set = false;

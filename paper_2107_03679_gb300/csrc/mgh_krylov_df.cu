@@ -728,17 +728,6 @@ __device__ __forceinline__ void unroll(F&& f) {
   unroll_seq(f, std::make_integer_sequence<int, N>{});
 }
 
-// a + b + c + d of four floats, exactly as a double-float (three TwoSums)
-__device__ __forceinline__ df sum4(float a, float b, float c, float d) {
-  float s1, t1, s2, t2, s, t3;
-  two_sum(a, b, s1, t1);
-  two_sum(c, d, s2, t2);
-  two_sum(s1, s2, s, t3);
-  df r;
-  two_sum(s, __fadd_rn(t3, __fadd_rn(t1, t2)), r.hi, r.lo);
-  return r;
-}
-
 // v_{k+1} = A z_k in FP32, written to the hi plane of basis slot k + 1, and its partial
 // ||v_{k+1}||^2 (slot 0 of the partial buffer; FP32 sums: the norm only scales the next
 // multigrid input, the Gram matrix holds the exact one).
@@ -1121,6 +1110,16 @@ mgh_status df_xupdate(Handle& h, const KArgs& a, int B) {
 
 }  // namespace
 
+#define MGH_CUDA_RESTORE(call, restore)                                  \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) {                                             \
+      restore;                                                           \
+      ::mgh::set_error(#call, e_, __FILE__, __LINE__);                   \
+      return MGH_CUDA_ERROR;                                             \
+    }                                                                    \
+  } while (0)
+
 namespace {
 
 // Restarted flexible GMRES with a double-float iterate: the start, the FP64-verified restarts
@@ -1172,8 +1171,22 @@ mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info,
     MGH_CHECK_LAUNCH(); h.launches++;
   }
   MGH_TRY(residual_and_start(1));
+  // The body of a restart cycle (its steps, multigrid levels included, and the restart) issues the
+  // same launches every time, all gated by device state, between two host reads of that state: it
+  // is captured once into a CUDA graph and replayed.  The first cycle runs directly (lazy kernel
+  // attributes and occupancy queries happen there), and graphs are not used while launches are
+  // profiled one by one.
+  struct GraphGuard {
+    cudaGraphExec_t exec = nullptr;
+    ~GraphGuard() { if (exec) cudaGraphExecDestroy(exec); }
+  } graph;
+  uint64_t graph_launches = 0;
+  auto body = [&]() -> mgh_status {
+    MGH_TRY(cycle(a));
+    return residual_and_start(0);
+  };
   int err_host = 0;
-  for (;;) {
+  for (int ncycle = 0;; ++ncycle) {
     MGH_CUDA(cudaMemcpyAsync(h.st_host, h.st, sizeof(RhsState) * B, cudaMemcpyDeviceToHost, h.stream));
     MGH_CUDA(cudaMemcpyAsync(&err_host, h.dev_err, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
     MGH_CUDA(cudaStreamSynchronize(h.stream));
@@ -1182,8 +1195,40 @@ mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info,
     bool any = false;
     for (int i = 0; i < B; ++i) any |= (h.st_host[i].done == 0);
     if (!any) break;
-    MGH_TRY(cycle(a));
-    MGH_TRY(residual_and_start(0));
+    if (!h.use_graphs || h.prof || ncycle == 0) {
+      MGH_TRY(body());
+      continue;
+    }
+    // graphs are captured and replayed on the handle's own non-blocking stream (the caller's may
+    // be the legacy default stream, which cannot be captured), ordered after and before it by events
+    if (!h.gstream) {
+      MGH_CUDA(cudaStreamCreateWithFlags(&h.gstream, cudaStreamNonBlocking));
+      MGH_CUDA(cudaEventCreateWithFlags(&h.gev_in, cudaEventDisableTiming));
+      MGH_CUDA(cudaEventCreateWithFlags(&h.gev_out, cudaEventDisableTiming));
+    }
+    if (!graph.exec) {
+      const uint64_t l0 = h.launches;
+      cudaStream_t user = h.stream;
+      h.stream = h.gstream;
+      MGH_CUDA_RESTORE(cudaStreamBeginCapture(h.gstream, cudaStreamCaptureModeRelaxed), h.stream = user);
+      const mgh_status sb = body();
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(h.gstream, &g);
+      h.stream = user;
+      graph_launches = h.launches - l0;
+      h.launches = l0;
+      if (sb != MGH_OK) { if (g) cudaGraphDestroy(g); return sb; }
+      if (ec != cudaSuccess) { if (g) cudaGraphDestroy(g); MGH_CUDA(ec); }
+      const cudaError_t ei = cudaGraphInstantiate(&graph.exec, g, 0);
+      cudaGraphDestroy(g);
+      MGH_CUDA(ei);
+    }
+    MGH_CUDA(cudaEventRecord(h.gev_in, h.stream));
+    MGH_CUDA(cudaStreamWaitEvent(h.gstream, h.gev_in, 0));
+    MGH_CUDA(cudaGraphLaunch(graph.exec, h.gstream));
+    MGH_CUDA(cudaEventRecord(h.gev_out, h.gstream));
+    MGH_CUDA(cudaStreamWaitEvent(h.stream, h.gev_out, 0));
+    h.launches += graph_launches;
   }
   {
     // every RHS leaves with its double-float iterate rounded to FP64
