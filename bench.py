@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--restart", type=int, default=None, help="GMRES restart length (default: the workload's)")
     ap.add_argument("--nu", type=int, default=None, help="pre- and post-smoothing sweeps (default: the workload's)")
     ap.add_argument("--levels", type=int, default=None, help="multigrid levels (default: the workload's)")
+    ap.add_argument("--shift-im", type=float, default=None,
+                    help="imaginary part of the multigrid shift kappa (default: the workload's)")
     ap.add_argument("--maxit", type=int, default=20000, help="Arnoldi steps per solve before giving up")
     ap.add_argument("--arnoldi", choices=["auto", "df", "fp64", "sstep"], default="auto",
                     help="mixed-precision Krylov engine: s-step cycles (Gram/Cholesky), double-float Arnoldi, "
@@ -331,6 +333,8 @@ def gpu_main(args, rank, world, local_rank):
         w.nu1 = w.nu2 = args.nu
     if args.levels:
         w.levels = args.levels
+    if args.shift_im is not None:
+        w.shift_im = args.shift_im
     precision = args.precision or w.precision
     f_gt, f_step, th, rec = make_inputs(w)
     if args.angles:
