@@ -14,7 +14,8 @@
 // runs in FP32 on FP32 copies of p and s written by the update kernels; on the FP64 path it runs
 // in FP64 on p and s directly.  The vectors live in the GMRES workspace: r, r^, p, v, s, t in the
 // first six basis slots (so restart >= 5) and p32, y, s32, z in the first four preconditioned
-// slots.  The host reads the state once per iteration.
+// slots.  The host reads the state once per iteration; the iteration's launches are replayed from
+// a captured CUDA graph after the first one.
 #include "mgh_krylov_common.cuh"
 
 namespace mgh {
@@ -300,13 +301,7 @@ mgh_status bicgstab_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info
     k_zero_if_b_zero<<<grid, kKThreads, 0, h.stream>>>(a, x, h.st);
     MGH_CHECK_LAUNCH(); h.launches++;
   }
-  for (;;) {
-    MGH_CUDA(cudaMemcpyAsync(h.st_host, h.st, sizeof(RhsState) * B, cudaMemcpyDeviceToHost, h.stream));
-    MGH_CUDA(cudaStreamSynchronize(h.stream));
-    MGH_TRY(prof_flush(h));
-    bool any = false;
-    for (int i = 0; i < B; ++i) any |= (h.st_host[i].active != 0);
-    if (!any) break;
+  auto body = [&]() -> mgh_status {
     {
       ProfScope ps(h, P_UPDATE);
       k_bc_p<<<grid, kKThreads, 0, h.stream>>>(a, r, p, v, p32, zs, h.coef, h.st);
@@ -365,6 +360,19 @@ mgh_status bicgstab_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info
       k_bc_decide<<<B, 32, 0, h.stream>>>(a, h.partial, h.st, tol, maxit);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
+    return MGH_OK;
+  };
+  // the iteration is replayed from a captured graph after the first one
+  CycleGraph graph;
+  for (int it = 0;; ++it) {
+    MGH_CUDA(cudaMemcpyAsync(h.st_host, h.st, sizeof(RhsState) * B, cudaMemcpyDeviceToHost, h.stream));
+    MGH_CUDA(cudaStreamSynchronize(h.stream));
+    MGH_TRY(prof_flush(h));
+    bool any = false;
+    for (int i = 0; i < B; ++i) any |= (h.st_host[i].active != 0);
+    if (!any) break;
+    if (!h.use_graphs || h.prof || it == 0) MGH_TRY(body());
+    else MGH_TRY(graph.run(h, body));
   }
   return finish_solve(h, B, info);
 }

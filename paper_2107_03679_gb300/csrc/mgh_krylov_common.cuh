@@ -148,6 +148,55 @@ KArgs make_kargs(const Handle& h, int B) {
   return a;
 }
 
+// A launch sequence that repeats between two host reads of the per-RHS state (a restart cycle,
+// a Bi-CGSTAB iteration), every launch gated by device state, captured once into a CUDA graph and
+// replayed.  Capture and replay happen on the handle's own non-blocking stream (the caller's may
+// be the legacy default stream, which cannot be captured), ordered after and before the caller's
+// stream by events.  The caller runs the first repetition directly, so that lazy kernel attributes
+// and occupancy queries happen outside capture; graphs are off while launches are profiled.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t launches = 0;   // launches of one repetition
+  CycleGraph() = default;
+  CycleGraph(const CycleGraph&) = delete;
+  CycleGraph& operator=(const CycleGraph&) = delete;
+  ~CycleGraph() { if (exec) cudaGraphExecDestroy(exec); }
+
+  template <typename Body>
+  mgh_status run(Handle& h, Body&& body) {
+    if (!h.gstream) {
+      MGH_CUDA(cudaStreamCreateWithFlags(&h.gstream, cudaStreamNonBlocking));
+      MGH_CUDA(cudaEventCreateWithFlags(&h.gev_in, cudaEventDisableTiming));
+      MGH_CUDA(cudaEventCreateWithFlags(&h.gev_out, cudaEventDisableTiming));
+    }
+    if (!exec) {
+      const uint64_t l0 = h.launches;
+      cudaStream_t user = h.stream;
+      h.stream = h.gstream;
+      const cudaError_t eb = cudaStreamBeginCapture(h.gstream, cudaStreamCaptureModeRelaxed);
+      if (eb != cudaSuccess) { h.stream = user; MGH_CUDA(eb); }
+      const mgh_status sb = body();
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(h.gstream, &g);
+      h.stream = user;
+      launches = h.launches - l0;
+      h.launches = l0;
+      if (sb != MGH_OK) { if (g) cudaGraphDestroy(g); return sb; }
+      if (ec != cudaSuccess) { if (g) cudaGraphDestroy(g); MGH_CUDA(ec); }
+      const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      MGH_CUDA(ei);
+    }
+    MGH_CUDA(cudaEventRecord(h.gev_in, h.stream));
+    MGH_CUDA(cudaStreamWaitEvent(h.gstream, h.gev_in, 0));
+    MGH_CUDA(cudaGraphLaunch(exec, h.gstream));
+    MGH_CUDA(cudaEventRecord(h.gev_out, h.gstream));
+    MGH_CUDA(cudaStreamWaitEvent(h.stream, h.gev_out, 0));
+    h.launches += launches;
+    return MGH_OK;
+  }
+};
+
 // Per-RHS results of a finished solve (host mirror already synchronised) and profile counters.
 mgh_status finish_solve(Handle& h, int B, mgh_solve_info* info) {
   bool all_conv = true;

@@ -706,7 +706,9 @@ k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, float2
 template <int NV>
 struct GramPairs {
   static constexpr int NP = NV * (NV + 1) / 2;   // pairs i <= j, row by row
-  static constexpr int PG = (NP + 3) / 4;        // pairs per group of 64 threads (4 groups)
+  static constexpr int PG = (NP + 3) / 4;        // most pairs of one group of 64 threads (4 groups)
+  // group g sums pairs [first(g), first(g + 1)): contiguous shares that differ by at most one
+  __host__ __device__ static constexpr int first(int g) { return (g * NP + 2) / 4; }
   __host__ __device__ static constexpr int row(int p) {
     int i = 0;
     while (p >= NV - i) { p -= NV - i; ++i; }
@@ -832,8 +834,9 @@ __device__ __forceinline__ void df_acc_prod(df& acc, float x, float y) {
 template <int NV, int G>
 __device__ __forceinline__ void gram_tile(const Pipe& pp, int slot, size_t q0, size_t p1, int l64, cdf* acc) {
   using PR = GramPairs<NV>;
-  constexpr int P0 = G * PR::PG;
-  constexpr int P1 = P0 + PR::PG < PR::NP ? P0 + PR::PG : PR::NP;
+  constexpr int P0 = PR::first(G);
+  constexpr int P1 = PR::first(G + 1);
+  static_assert(P1 - P0 <= PR::PG, "group share above its accumulators");
   if constexpr (P1 > P0) {
     constexpr int IMIN = PR::row(P0);
 #pragma unroll 1
@@ -908,7 +911,9 @@ k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial
   __syncthreads();
   cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
   for (int t = threadIdx.x; t < PR::NP; t += kDfThreads) {
-    const int g = t / PR::PG, c = t - g * PR::PG;
+    int g = 0;
+    while (t >= PR::first(g + 1)) ++g;
+    const int c = t - PR::first(g);
     const float4 x0 = sh[g][c], x1 = sh[g + 4][c];
     const df re = df_add(df{x0.x, x0.y}, df{x1.x, x1.y}), im = df_add(df{x0.z, x0.w}, df{x1.z, x1.w});
     out[t] = mk<double>(df_to_double(re), df_to_double(im));
@@ -1110,16 +1115,6 @@ mgh_status df_xupdate(Handle& h, const KArgs& a, int B) {
 
 }  // namespace
 
-#define MGH_CUDA_RESTORE(call, restore)                                  \
-  do {                                                                   \
-    cudaError_t e_ = (call);                                             \
-    if (e_ != cudaSuccess) {                                             \
-      restore;                                                           \
-      ::mgh::set_error(#call, e_, __FILE__, __LINE__);                   \
-      return MGH_CUDA_ERROR;                                             \
-    }                                                                    \
-  } while (0)
-
 namespace {
 
 // Restarted flexible GMRES with a double-float iterate: the start, the FP64-verified restarts
@@ -1171,16 +1166,9 @@ mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info,
     MGH_CHECK_LAUNCH(); h.launches++;
   }
   MGH_TRY(residual_and_start(1));
-  // The body of a restart cycle (its steps, multigrid levels included, and the restart) issues the
-  // same launches every time, all gated by device state, between two host reads of that state: it
-  // is captured once into a CUDA graph and replayed.  The first cycle runs directly (lazy kernel
-  // attributes and occupancy queries happen there), and graphs are not used while launches are
-  // profiled one by one.
-  struct GraphGuard {
-    cudaGraphExec_t exec = nullptr;
-    ~GraphGuard() { if (exec) cudaGraphExecDestroy(exec); }
-  } graph;
-  uint64_t graph_launches = 0;
+  // the body of a restart cycle (its steps with every multigrid level, and the restart) is
+  // replayed from a captured graph after the first cycle
+  CycleGraph graph;
   auto body = [&]() -> mgh_status {
     MGH_TRY(cycle(a));
     return residual_and_start(0);
@@ -1195,40 +1183,8 @@ mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info,
     bool any = false;
     for (int i = 0; i < B; ++i) any |= (h.st_host[i].done == 0);
     if (!any) break;
-    if (!h.use_graphs || h.prof || ncycle == 0) {
-      MGH_TRY(body());
-      continue;
-    }
-    // graphs are captured and replayed on the handle's own non-blocking stream (the caller's may
-    // be the legacy default stream, which cannot be captured), ordered after and before it by events
-    if (!h.gstream) {
-      MGH_CUDA(cudaStreamCreateWithFlags(&h.gstream, cudaStreamNonBlocking));
-      MGH_CUDA(cudaEventCreateWithFlags(&h.gev_in, cudaEventDisableTiming));
-      MGH_CUDA(cudaEventCreateWithFlags(&h.gev_out, cudaEventDisableTiming));
-    }
-    if (!graph.exec) {
-      const uint64_t l0 = h.launches;
-      cudaStream_t user = h.stream;
-      h.stream = h.gstream;
-      MGH_CUDA_RESTORE(cudaStreamBeginCapture(h.gstream, cudaStreamCaptureModeRelaxed), h.stream = user);
-      const mgh_status sb = body();
-      cudaGraph_t g = nullptr;
-      const cudaError_t ec = cudaStreamEndCapture(h.gstream, &g);
-      h.stream = user;
-      graph_launches = h.launches - l0;
-      h.launches = l0;
-      if (sb != MGH_OK) { if (g) cudaGraphDestroy(g); return sb; }
-      if (ec != cudaSuccess) { if (g) cudaGraphDestroy(g); MGH_CUDA(ec); }
-      const cudaError_t ei = cudaGraphInstantiate(&graph.exec, g, 0);
-      cudaGraphDestroy(g);
-      MGH_CUDA(ei);
-    }
-    MGH_CUDA(cudaEventRecord(h.gev_in, h.stream));
-    MGH_CUDA(cudaStreamWaitEvent(h.gstream, h.gev_in, 0));
-    MGH_CUDA(cudaGraphLaunch(graph.exec, h.gstream));
-    MGH_CUDA(cudaEventRecord(h.gev_out, h.gstream));
-    MGH_CUDA(cudaStreamWaitEvent(h.stream, h.gev_out, 0));
-    h.launches += graph_launches;
+    if (!h.use_graphs || h.prof || ncycle == 0) MGH_TRY(body());
+    else MGH_TRY(graph.run(h, body));
   }
   {
     // every RHS leaves with its double-float iterate rounded to FP64
