@@ -504,10 +504,14 @@ __device__ __forceinline__ cdf load_df(const float2* __restrict__ h, size_t Np, 
 }
 
 // r = b - A x in double-float (x, b double-float planes), written as the candidate u_0 in basis
-// slot 0; partial ||r||^2 (slot 0) and ||b||^2 (slot 1).
+// slot 0 (its lo plane only when `write_lo`: the s-step engine reads the FP32 hi plane); partial
+// ||r||^2 (slot 0) and, on the first cycle, ||b||^2 (slot 1, double-float: it sets the acceptance
+// threshold).  ||r||^2 is summed in FP32 per thread (FP64 across threads): it only scales the
+// first basis vector and decides when the FP64 true residual, which decides acceptance, is checked.
 __global__ void __launch_bounds__(kKThreads)
 k_df_residual(KArgs a, const float2* __restrict__ bdf, const float2* __restrict__ xdf, const float2* __restrict__ DAdf,
-              float2* __restrict__ V, cd* __restrict__ partial, const RhsState* __restrict__ st) {
+              float2* __restrict__ V, cd* __restrict__ partial, const RhsState* __restrict__ st, int first,
+              int write_lo) {
   const int rhs = blockIdx.y, blk = blockIdx.x;
   if (st[rhs].done) return;
   const float2* xb = xdf + (size_t)rhs * 2 * a.Np;
@@ -515,23 +519,25 @@ k_df_residual(KArgs a, const float2* __restrict__ bdf, const float2* __restrict_
   float2* rh = V + ((size_t)rhs * (a.m + 1) * 2) * a.Np;
   float2* rl = rh + a.Np;
   const df ih = df_from_double(a.inv_h2);
-  df rn = {0.f, 0.f}, bn = {0.f, 0.f};
+  float rn = 0.f;
+  df bn = {0.f, 0.f};   // ||b||^2 sets the acceptance threshold: double-float, first cycle only
   const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
   int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);
   int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);
   for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads) {
     while (m >= a.nx) { m -= a.nx; ++n; }
-    cdf sum = cdf_zero();
-    if (m > 0) { const cdf v = load_df(xb, a.Np, q - 1); df_fma(sum.re, v.re.hi, v.re.lo, 1.f, 0.f); df_fma(sum.im, v.im.hi, v.im.lo, 1.f, 0.f); }
-    if (m < a.nx - 1) { const cdf v = load_df(xb, a.Np, q + 1); df_fma(sum.re, v.re.hi, v.re.lo, 1.f, 0.f); df_fma(sum.im, v.im.hi, v.im.lo, 1.f, 0.f); }
-    if (n > 0) { const cdf v = load_df(xb, a.Np, q - a.nx); df_fma(sum.re, v.re.hi, v.re.lo, 1.f, 0.f); df_fma(sum.im, v.im.hi, v.im.lo, 1.f, 0.f); }
-    if (n < a.ny - 1) { const cdf v = load_df(xb, a.Np, q + a.nx); df_fma(sum.re, v.re.hi, v.re.lo, 1.f, 0.f); df_fma(sum.im, v.im.hi, v.im.lo, 1.f, 0.f); }
-    sum.re = df_norm(sum.re);
-    sum.im = df_norm(sum.im);
+    const cdf z = cdf_zero();
+    const cdf vw = m > 0 ? load_df(xb, a.Np, q - 1) : z;
+    const cdf ve = m < a.nx - 1 ? load_df(xb, a.Np, q + 1) : z;
+    const cdf vs = n > 0 ? load_df(xb, a.Np, q - a.nx) : z;
+    const cdf vn = n < a.ny - 1 ? load_df(xb, a.Np, q + a.nx) : z;
     const cdf xc = load_df(xb, a.Np, q);
     const cdf D = load_df(DAdf, a.Np, q);
     cdf r = load_df(bb, a.Np, q);
-    cdf_abs2_acc(bn, r);
+    if (first) cdf_abs2_acc(bn, r);
+    cdf sum;
+    sum.re = df_add(df_add(vw.re, ve.re), df_add(vs.re, vn.re));
+    sum.im = df_add(df_add(vw.im, ve.im), df_add(vs.im, vn.im));
     // r = b - D x + (1/h^2) sum
     cdf_sub_mul(r, D, xc);
     df_fma(r.re, ih.hi, ih.lo, sum.re.hi, sum.re.lo);
@@ -539,10 +545,10 @@ k_df_residual(KArgs a, const float2* __restrict__ bdf, const float2* __restrict_
     r.re = df_norm(r.re);
     r.im = df_norm(r.im);
     rh[q] = make_float2(r.re.hi, r.im.hi);
-    rl[q] = make_float2(r.re.lo, r.im.lo);
-    cdf_abs2_acc(rn, r);
+    if (write_lo) rl[q] = make_float2(r.re.lo, r.im.lo);
+    rn = fmaf(r.re.hi, r.re.hi, fmaf(r.im.hi, r.im.hi, rn));
   }
-  cd acc[1] = {mk<double>(df_to_double(rn), 0.0)};
+  cd acc[1] = {mk<double>((double)rn, 0.0)};
   block_reduce_store<1>(acc, 1, df_to_double(bn), 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
 }
 
@@ -1120,7 +1126,7 @@ namespace {
 // Restarted flexible GMRES with a double-float iterate: the start, the FP64-verified restarts
 // and the exit are shared; `cycle` runs one restart cycle (its steps and the iterate update).
 template <typename Cycle>
-mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info, Cycle&& cycle) {
+mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info, bool write_lo, Cycle&& cycle) {
   KArgs a = make_kargs(h, B);
   const dim3 grid(a.nblk, B);
   const dim3 pgrid((unsigned)((a.N + 255) / 256), B);
@@ -1130,7 +1136,8 @@ mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info,
   auto residual_and_start = [&](int first) -> mgh_status {
     {
       ProfScope ps(h, P_RESIDUAL);
-      k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, h.bdf, h.xdf, h.DAdf, V, h.partial, h.st);
+      k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, h.bdf, h.xdf, h.DAdf, V, h.partial, h.st, first,
+                                                      write_lo ? 1 : 0);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
     {
@@ -1199,7 +1206,7 @@ mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info,
 }  // namespace
 
 mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
-  return df_driver(h, b, B, x, info, [&](const KArgs& a) -> mgh_status {
+  return df_driver(h, b, B, x, info, true, [&](const KArgs& a) -> mgh_status {
     for (int j = 0; j < a.m; ++j) MGH_TRY(df_arnoldi_step(h, a, j, B));
     MGH_TRY(df_tail(h, a, B));
     {
@@ -1258,7 +1265,7 @@ mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
 }  // namespace
 
 mgh_status fgmres_ss(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
-  return df_driver(h, b, B, x, info, [&](const KArgs& a) -> mgh_status {
+  return df_driver(h, b, B, x, info, false, [&](const KArgs& a) -> mgh_status {
     switch (a.m + 1) {
       case 2: return ss_cycle<2>(h, a, B);
       case 3: return ss_cycle<3>(h, a, B);
