@@ -802,6 +802,7 @@ k_pre_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__
   const int ci = g0 >> 1;
   const bool own_c = own && g0 >= 0 && ci < nxc;
   const float sc = bscale ? (float)bscale[rhs * scale_stride] : 1.f;
+  const float fw = 0.0625f * sc;   // full-weighting factor 1/16 times the right-hand side's scale
   const cf* __restrict__ bb = bin + rhs * b_stride;
   cf* __restrict__ vo = vpre + rhs * v_stride;
   cf* __restrict__ co = bc + rhs * bc_stride;
@@ -828,25 +829,26 @@ k_pre_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__
       const int k = kb + Kc;
       g.issue(k + PFD, (Kc + PFD) % S, bb, wD, D);   // rows past the end read as zeros
       cp_wait<PFD>();
+      // the cycle is linear: the stages run on b unscaled and the two outputs are scaled by sc
       constexpr int s0 = slot(Kc, 0, R);
       {
-        const C2 sb = scale2(sc, g.get(Kc, 0)), wd = g.get(Kc, 1);
-        v[0][s0].a = wd.a * sb.a;
-        v[0][s0].b = wd.b * sb.b;
+        const C2 b0 = g.get(Kc, 0), wd = g.get(Kc, 1);
+        v[0][s0].a = wd.a * b0.a;
+        v[0][s0].b = wd.b * b0.b;
       }
       unroll<NU - 1>([&](auto SC) {
         constexpr int s = decltype(SC)::value + 2;
         constexpr int so = slot(Kc, s - 1, R);
         constexpr int gs = slot(Kc, s - 1, S);
         v[s - 1][so] = jac_row(v[s - 2][slot(Kc, s, R)], v[s - 2][so], v[s - 2][slot(Kc, s - 2, R)],
-                               scale2(sc, g.get(gs, 0)), g.get(gs, 1), ih, om1);
+                               g.get(gs, 0), g.get(gs, 1), ih, om1);
       });
       {
         constexpr int sr = slot(Kc, NU, R);
         constexpr int gs = slot(Kc, NU, S);
         const int yr = i0 + k - NU;
         const bool okr = yr >= 0 && yr < ny;
-        const C2 sb = scale2(sc, g.get(gs, 0)), dd = g.get(gs, 2);
+        const C2 sb = g.get(gs, 0), dd = g.get(gs, 2);
         const C2& up = v[NU - 1][slot(Kc, NU + 1, R)];
         const C2& mid = v[NU - 1][sr];
         const C2& dn = v[NU - 1][slot(Kc, NU - 1, R)];
@@ -861,13 +863,13 @@ k_pre_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__
         if (k >= 2 * H && yf < ys + rows && yf < ny && own_c) {
           const cf a = hr[slot(Kc, NU + 2, R)], m = hr[slot(Kc, NU + 1, R)], c = hr[slot(Kc, NU, R)];
           co[(size_t)(yf >> 1) * nxc + ci] =
-              mk<float>(0.0625f * (a.re + 2.f * m.re + c.re), 0.0625f * (a.im + 2.f * m.im + c.im));
+              mk<float>(fw * (a.re + 2.f * m.re + c.re), fw * (a.im + 2.f * m.im + c.im));
         }
       }
       {
         const int yv = i0 + k - (NU - 1);
         if (yv >= ys && yv < ys + seg && yv < ny)
-          st2<true>(vo, (ptrdiff_t)yv * nx + g0, own && in0, own && in1, v[NU - 1][slot(Kc, NU - 1, R)]);
+          st2<true>(vo, (ptrdiff_t)yv * nx + g0, own && in0, own && in1, scale2(sc, v[NU - 1][slot(Kc, NU - 1, R)]));
       }
     });
   }

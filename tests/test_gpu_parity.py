@@ -396,6 +396,31 @@ def test_ellipses576_full_size_residual_property(arnoldi):
         assert abs(true - infos[q]["rel_residual"]) <= 1e-3 * w.tol
 
 
+def test_ellipses576_mixed_field_matches_fp64_path():
+    """The bench configuration's field error: two angles of the full-size workload solved by the
+    mixed path (FP32 cycle, s-step cycles) and by the plain FP64 path, both to a true relative
+    residual of 1e-8; the two fields agree to well within the mixed tolerance of 1e-5.  The
+    measured difference is written to gpurun_out/ for the design notes when that folder exists."""
+    torch = torch_cuda()
+    w = W.WORKLOADS["ellipses576"]
+    f = W.phantom(w)
+    th = W.angles(w)[[0, 59]]
+    out = {}
+    for prec in ("mixed32", "fp64"):
+        s = make_solver(w, B=2, maxit=5000, precision=prec, tol=1e-8)
+        s.set_contrast(to_t(f, torch))
+        u, infos = s.forward(to_t(th, torch))
+        assert all(i["converged"] for i in infos), (prec, infos)
+        out[prec] = u.cpu().numpy()
+        s.close()
+    d = max(rel(out["mixed32"][q], out["fp64"][q]) for q in range(2))
+    assert d < 1e-5, d
+    import os
+    if os.path.isdir("gpurun_out"):
+        with open("gpurun_out/mixed_vs_fp64_ellipses576.txt", "w") as fh:
+            fh.write(f"{d:.3e}\n")
+
+
 def test_gradient_twenty_directions_against_central_differences():
     """Differentiation check of the data-term gradient on 20 seeded random directions: the CUDA
     forward/adjoint gradient (FP64, tight tolerance) against central differences of the loss
