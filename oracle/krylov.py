@@ -7,6 +7,10 @@
   when the true residual ||b - A x|| / ||b|| <= tol (the relative stopping rule of Sec. VI);
   the Givens estimate only decides when to leave an Arnoldi cycle early.
 * bicgstab: the paper's preconditioned Bi-CGSTAB, Alg. 3, with the relative stopping rule.
+* sstep_cycle: one restart cycle of FGMRES(m) in s-step form (Chronopoulos & Gear 1989; Hoemmen
+  2010): the monomial basis v_{k+1} = A M^{-1} v_k is orthogonalised at the end of the cycle by
+  the Cholesky factor of its Gram matrix.  In exact arithmetic it returns the iterate of one
+  Arnoldi cycle of fgmres; the CUDA path's default mixed engine is built on this identity.
 
 Iterations are counted as preconditioner applications (Arnoldi steps for GMRES).
 """
@@ -148,3 +152,31 @@ def bicgstab(apply_A: Callable, apply_M: Callable, b: np.ndarray, tol: float, ma
                 info.converged = True
                 break
     return x, info
+
+
+def sstep_cycle(apply_A: Callable, apply_M: Callable, b: np.ndarray, x: np.ndarray, m: int) -> np.ndarray:
+    """One cycle of FGMRES(m) in s-step form from the iterate x; returns the new iterate.
+
+    v_0 = r / ||r||, z_k = M^{-1} v_k, w_k = A z_k, v_{k+1} = w_k / ||w_k||.  With V = [v_0 .. v_m]
+    and V^H V = R^H R (Cholesky, R upper), A z_k = ||w_k|| v_{k+1} and r = ||r|| v_0 give
+    r - A Z y = V (||r|| e_0 - [0; diag(||w||) y]), so ||r - A Z y|| = ||R (...)||: the cycle's
+    least-squares problem has the matrix R[:, 1:] diag(||w||) and the right-hand side ||r|| R[:, 0].
+    """
+    r = b - apply_A(x)
+    beta = _norm(r)
+    V = [r / beta]
+    Z, wn = [], []
+    for k in range(m):
+        Z.append(apply_M(V[k]))
+        w = apply_A(Z[k])
+        wn.append(_norm(w))
+        V.append(w / wn[k])
+    Vm = np.stack([v.reshape(-1) for v in V], axis=1)          # N x (m+1)
+    G = Vm.conj().T @ Vm
+    R = np.linalg.cholesky(G).conj().T                          # G = R^H R
+    H = R[:, 1:] * np.asarray(wn)[None, :]
+    y = np.linalg.lstsq(H, beta * R[:, 0], rcond=None)[0]
+    x_new = x.astype(np.complex128).copy()
+    for k in range(m):
+        x_new = x_new + y[k] * Z[k]
+    return x_new

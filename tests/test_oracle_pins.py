@@ -244,6 +244,25 @@ def test_gmres_matches_direct_solve():
     assert np.linalg.norm(u - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("m", [1, 4, 8])
+def test_sstep_cycle_equals_arnoldi_cycle(m):
+    """One s-step cycle (Gram matrix + Cholesky) returns the iterate of one Arnoldi cycle of
+    FGMRES(m) from the same starting point: both minimise the residual over x + span(Z), with the
+    same z_k because the preconditioner sees the same normalised vectors."""
+    from oracle.krylov import fgmres, sstep_cycle
+    p, f = _small(seed=5)
+    s = O.MGHSolver(p, f, levels=3, nu1=1, nu2=1, restart=m, tol=1e-30)
+    b = O.rhs(p, f, 0.2)
+    x0 = W.random_field((p.ny, p.nx), 3) * 1e-2
+    x_ar, info = fgmres(s.apply_A, s.M, b, 1e-30, m, m, x0)
+    assert info.iterations == m
+    x_ss = sstep_cycle(s.apply_A, s.M, b, x0, m)
+    assert np.linalg.norm(x_ss - x_ar) <= 1e-9 * np.linalg.norm(x_ar)
+    # and the cycle reduced the residual
+    r0 = np.linalg.norm(b - s.apply_A(x0))
+    assert np.linalg.norm(b - s.apply_A(x_ss)) < r0
+
+
 def test_bicgstab_matches_direct_solve():
     p, f = _small(seed=9)
     s = O.MGHSolver(p, f, levels=2, nu1=1, nu2=1, tol=1e-12, krylov="bicgstab", shift=1.0)
