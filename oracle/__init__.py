@@ -24,11 +24,12 @@ from .multigrid import (coarse_size, restrict, prolong, restrict_coefficient, bu
 from .krylov import fgmres, bicgstab, SolveInfo
 from .tomography import (incident_field, rhs, crop, embed, sample, misfit, gradient_from_adjoint,
                          MGHSolver, direct_solve)
+from .inverse import tv, tv_prox, fbs, snr, grad_fwd, grad_adj
 
 __all__ = [
     "Problem", "absorbing_factor", "fine_coefficient", "operator_diagonal", "apply_operator",
     "assemble_operator", "coarse_size", "restrict", "prolong", "restrict_coefficient",
     "build_hierarchy", "jacobi", "mg_cycle", "Preconditioner", "fgmres", "bicgstab", "SolveInfo",
     "incident_field", "rhs", "crop", "embed", "sample", "misfit", "gradient_from_adjoint",
-    "MGHSolver", "direct_solve",
+    "MGHSolver", "direct_solve", "tv", "tv_prox", "fbs", "snr", "grad_fwd", "grad_adj",
 ]

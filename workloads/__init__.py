@@ -223,3 +223,13 @@ def random_field(shape, seed: int) -> np.ndarray:
     """A seeded complex128 test field with independent N(0,1) real and imaginary parts."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def angle_subsets(n_angles: int, subset: int, iters: int, seed: int = 0):
+    """The angle indices of each reconstruction iteration: `subset` of the n_angles drawn without
+    replacement (sorted) from default_rng(seed), one draw per iteration; all angles when subset is
+    0 or at least n_angles."""
+    if subset <= 0 or subset >= n_angles:
+        return [np.arange(n_angles) for _ in range(iters)]
+    rng = np.random.default_rng(seed)
+    return [np.sort(rng.choice(n_angles, subset, replace=False)) for _ in range(iters)]
