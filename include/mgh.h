@@ -195,6 +195,26 @@ mgh_status mgh_misfit(mgh_handle* h, const mgh_cdouble* u, const mgh_cdouble* y,
 mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u_sc,
                         const mgh_cdouble* G, int B, double* grad, mgh_solve_info* info);
 
+/* Backward step of the accelerated forward-backward splitting (Sec. V, Alg. 4): the proximal
+ * operator of the nonnegativity constraint plus isotropic total variation with weight lam,
+ *   out = argmin_{x >= 0} 1/2 ||x - w||^2 + lam TV(x),   w = fbar - gamma d,
+ * TV(x) = sum_ij sqrt((x_ij - x_i+1,j)^2 + (x_ij - x_i,j+1)^2) with differences that are 0 across
+ * the last row / column, computed by `iters` iterations of fast gradient projection on the dual
+ * (Beck & Teboulle 2009; dual step 1/(8 lam), Nesterov momentum, the primal point of the last
+ * dual iterate).  In Alg. 4, lam = gamma tau.
+ *   fbar, d, out   [ny_int][nx_int] doubles (device); d may be NULL (w = fbar); out may alias
+ *                  fbar or d (w is formed in the handle's workspace first)
+ *   gamma          step of the gradient move (finite); lam >= 0 (lam = 0: out = max(w, 0))
+ *   iters          >= 1 dual iterations
+ * Queued on the handle's stream; no synchronisation, no allocation (the workspace of six
+ * interior fields is allocated by mgh_create). */
+mgh_status mgh_tv_prox(mgh_handle* h, const double* fbar, const double* d, double gamma, double lam,
+                       int iters, double* out);
+
+/* Momentum step of Alg. 4: fbar = f + c (f - f_prev), c = (alpha_k - 1) / alpha_k+1 computed by the
+ * caller.  f, f_prev, fbar: [ny_int][nx_int] doubles (device); fbar may alias f or f_prev. */
+mgh_status mgh_fbs_momentum(mgh_handle* h, const double* f, const double* f_prev, double c, double* fbar);
+
 /* Device-time profile of a handle.  Kernel classes (index into ms/launches):
  *   0 level-0 pre-smoothing + residual + restriction   5 second Gram-Schmidt pass
  *   1 level-0 prolongation + correction + smoothing    6 per-RHS reductions and Givens updates

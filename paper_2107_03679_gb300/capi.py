@@ -90,6 +90,8 @@ def _load():
         "mgh_misfit": (S, [P, P, P, I, P, I, P, P, ctypes.POINTER(D)]),
         "mgh_misfit_noalloc": (S, [I, I, P, P, I, P, I, P, P, P, P]),
         "mgh_gradient": (S, [P, P, P, P, I, P, info_p]),
+        "mgh_tv_prox": (S, [P, P, P, D, D, I, P]),
+        "mgh_fbs_momentum": (S, [P, P, P, D, P]),
         "mgh_profile_enable": (S, [P, I]),
         "mgh_profile_read": (S, [P, ctypes.POINTER(mgh_profile)]),
         "mgh_launch_count": (ctypes.c_uint64, [P, I]),
@@ -110,7 +112,7 @@ EXPORTED = [
     "mgh_default_params", "mgh_workspace_bytes", "mgh_create", "mgh_destroy", "mgh_set_contrast",
     "mgh_incident_field", "mgh_rhs", "mgh_apply", "mgh_precondition", "mgh_coarse_solve",
     "mgh_level_shape", "mgh_level_coefficient", "mgh_solve", "mgh_forward", "mgh_crop", "mgh_sample",
-    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_profile_enable", "mgh_profile_read", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
+    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
 ]
 
 
@@ -243,6 +245,14 @@ def mgh_gradient(h, theta, u_sc, G, B, grad, allow_not_converged=True):
     st = _lib.mgh_gradient(h, theta, u_sc, G, B, grad, info)
     _check("mgh_gradient", st, (MGH_OK, MGH_NOT_CONVERGED) if allow_not_converged else (MGH_OK,))
     return _infos_to_list(info)
+
+
+def mgh_tv_prox(h, fbar, d, gamma, lam, iters, out):
+    _check("mgh_tv_prox", _lib.mgh_tv_prox(h, fbar, d, float(gamma), float(lam), int(iters), out))
+
+
+def mgh_fbs_momentum(h, f, f_prev, c, fbar):
+    _check("mgh_fbs_momentum", _lib.mgh_fbs_momentum(h, f, f_prev, float(c), fbar))
 
 
 def mgh_profile_enable(h, enable=True):

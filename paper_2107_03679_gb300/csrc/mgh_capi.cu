@@ -78,6 +78,7 @@ size_t workspace_bytes(const mgh_params& p) {
   t += pad256(16 * B * (m + 1)) + pad256(16 * B * m) + pad256(8 * B * (m + 1)) + pad256(sizeof(RhsState) * B);
   t += pad256(16 * (1216 + B) * partial_stride(m)) + pad256(8 * (B + 1));
   t += pad256(16 * Np) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m) + pad256(4);   // DAdf, hpend, coef, err
+  t += pad256(48 * (size_t)p.nx_int * p.ny_int);                                          // tvbuf
   if (p.precision != MGH_PREC_FP64) t += 2 * pad256(16 * B * Np);                        // xdf, bdf
   return t;
 }
@@ -104,7 +105,7 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->T1); cudaFree(h->T2); cudaFree(h->H); cudaFree(h->hcol); cudaFree(h->h2col); cudaFree(h->cs);
   cudaFree(h->sn); cudaFree(h->g); cudaFree(h->y); cudaFree(h->vscale); cudaFree(h->st); cudaFree(h->partial);
   cudaFree(h->dscratch); cudaFree(h->DAdf); cudaFree(h->hpend); cudaFree(h->coef);
-  cudaFree(h->dev_err); cudaFree(h->xdf); cudaFree(h->bdf);
+  cudaFree(h->dev_err); cudaFree(h->xdf); cudaFree(h->bdf); cudaFree(h->tvbuf);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
@@ -251,6 +252,7 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->hpend, 16 * B * (m + 1));
   ALLOC(h->coef, 16 * B * 2 * m);
   ALLOC(h->dscratch, 8 * (B + 1));
+  ALLOC(h->tvbuf, 48 * (size_t)p->nx_int * p->ny_int);
 #undef ALLOC
   if (cudaMallocHost((void**)&h->st_host, sizeof(RhsState) * B) != cudaSuccess) {
     h->st_host = nullptr;
@@ -380,6 +382,18 @@ mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u
   if (s != MGH_OK && s != MGH_NOT_CONVERGED) return s;
   MGH_TRY(launch_gradient(*h, theta, (const cd*)u_sc, h->T2, B, grad));
   return s;
+}
+
+mgh_status mgh_tv_prox(mgh_handle* h, const double* fbar, const double* d, double gamma, double lam,
+                       int iters, double* out) {
+  if (!h || !fbar || !out || iters < 1 || !(lam >= 0.0) || !std::isfinite(lam) || !std::isfinite(gamma))
+    return MGH_INVALID_ARG;
+  return tv_prox(*h, fbar, d, gamma, lam, iters, out);
+}
+
+mgh_status mgh_fbs_momentum(mgh_handle* h, const double* f, const double* f_prev, double c, double* fbar) {
+  if (!h || !f || !f_prev || !fbar || !std::isfinite(c)) return MGH_INVALID_ARG;
+  return fbs_momentum(*h, f, f_prev, c, fbar);
 }
 
 mgh_status mgh_profile_enable(mgh_handle* h, int enable) {

@@ -110,6 +110,8 @@ struct Handle {
   cd* partial = nullptr;     // [nblk*B][2m+4] block partial sums
   int nblk = 1;              // reduction blocks per right-hand side
   double* dscratch = nullptr;   // small FP64 scratch (loss)
+  double* tvbuf = nullptr;      // [6][ny_int][nx_int] TV proximal operator: w, x, dual momentum point
+                                // (p, q) and last dual iterate (p, q)
   int* dev_err = nullptr;       // device error word written by kernels with bounded waits
 
   uint64_t launches = 0;
@@ -179,6 +181,11 @@ mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info)
 mgh_status fgmres_ss(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
 // device flag set by a kernel whose bounded wait gave up (0 = none)
 constexpr int kErrTimeout = 1;
+
+// mgh_inverse.cu: backward and momentum steps of the reconstruction loop (arguments checked by the caller)
+mgh_status tv_prox(Handle& h, const double* fbar, const double* d, double gamma, double lam, int iters,
+                   double* out);
+mgh_status fbs_momentum(Handle& h, const double* f, const double* f_prev, double c, double* fbar);
 
 // mgh_krylov.cu
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);

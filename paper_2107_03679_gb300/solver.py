@@ -194,6 +194,35 @@ class Solver:
                                   capi._ptr(grad))
         return grad, infos
 
+    def _interior(self, t: torch.Tensor, name: str, exact: bool = False) -> torch.Tensor:
+        """A [ny_int][nx_int] float64 field on this device; `exact` (output buffers) refuses a copy."""
+        if exact and (t.dtype != torch.float64 or t.device != self.device or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float64 tensor on {self.device}")
+        t = self._dev(t, torch.float64)
+        if tuple(t.shape) != (self.ny_int, self.nx_int):
+            raise ValueError(f"{name} must be [{self.ny_int}, {self.nx_int}]")
+        return t
+
+    def tv_prox(self, fbar: torch.Tensor, d: Optional[torch.Tensor], gamma: float, lam: float, iters: int,
+                out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """argmin_{x >= 0} 1/2 ||x - (fbar - gamma d)||^2 + lam TV(x) by `iters` dual FGP iterations
+        (the backward step of Alg. 4, Sec. V); d = None means w = fbar."""
+        fbar = self._interior(fbar, "fbar")
+        d = self._interior(d, "d") if d is not None else None
+        out = torch.empty_like(fbar) if out is None else self._interior(out, "out", exact=True)
+        capi.mgh_tv_prox(self._h, capi._ptr(fbar), capi._ptr(d) if d is not None else None, gamma, lam, iters,
+                         capi._ptr(out))
+        return out
+
+    def fbs_momentum(self, f: torch.Tensor, f_prev: torch.Tensor, c: float,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """fbar = f + c (f - f_prev) (the momentum step of Alg. 4)."""
+        f = self._interior(f, "f")
+        f_prev = self._interior(f_prev, "f_prev")
+        out = torch.empty_like(f) if out is None else self._interior(out, "out", exact=True)
+        capi.mgh_fbs_momentum(self._h, capi._ptr(f), capi._ptr(f_prev), c, capi._ptr(out))
+        return out
+
     def profile_enable(self, enable: bool = True) -> None:
         capi.mgh_profile_enable(self._h, enable)
 

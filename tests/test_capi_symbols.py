@@ -80,3 +80,11 @@ def test_host_only_entry_points(lib):
     bc.restart, bc.krylov = 8, 2
     with pytest.raises(capi.MGHError):
         capi.mgh_workspace_bytes(bc)
+
+
+def test_reconstruction_entry_points_validate_on_the_host(lib):
+    """mgh_tv_prox / mgh_fbs_momentum reject a missing handle or buffer before any launch."""
+    import paper_2107_03679_gb300.capi as capi
+    L = capi._lib
+    assert L.mgh_tv_prox(None, None, None, 1.0, 0.1, 3, None) == capi.MGH_INVALID_ARG
+    assert L.mgh_fbs_momentum(None, None, None, 0.5, None) == capi.MGH_INVALID_ARG
