@@ -634,6 +634,7 @@ def fbs_main(args, rank, world, local_rank):
     gamma = 0.02 / float(g0.abs().max())
     tau = args.tv_lam / gamma
     eta_gt = torch.sqrt(1.0 + d_gt)
+    snr_db(torch.sqrt(1.0 + f0), eta_gt)   # first use of these torch kernels outside the timed loop
     snrs = []
     times = []
     ev = [torch.cuda.Event(enable_timing=True)]
@@ -661,10 +662,10 @@ def fbs_main(args, rank, world, local_rank):
     torch.cuda.synchronize()
     prox_ms = a.elapsed_time(b)
     n_int = w.nx_int * w.ny_int
-    # w = fbar - gamma d (2 reads, 1 write), dual fields zeroed (4 writes), per iteration the primal
-    # point (w, p, q read, x written) and the dual step (x, p, q, p_prev, q_prev read, 4 written),
-    # and the final primal point (4)
-    prox_bytes = 8.0 * n_int * (3 + 4 + args.prox_iters * 13 + 4)
+    # w = fbar - gamma d (2 reads, 1 write), dual fields zeroed (5 writes), per iteration one pass
+    # that reads w, the momentum point (p, q) and the last dual iterate (p, q) and writes the next
+    # momentum point and dual iterate (5 + 4), and the final primal point (w, p, q read, 1 written)
+    prox_bytes = 8.0 * n_int * (3 + 5 + args.prox_iters * 9 + 4)
     its = [sum(i["iterations"] for i in fw + adj) / max(1, len(fw) + len(adj)) for fw, adj in infos]
     if rank == 0:
         print(json.dumps({

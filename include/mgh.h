@@ -206,7 +206,7 @@ mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u
  *                  fbar or d (w is formed in the handle's workspace first)
  *   gamma          step of the gradient move (finite); lam >= 0 (lam = 0: out = max(w, 0))
  *   iters          >= 1 dual iterations
- * Queued on the handle's stream; no synchronisation, no allocation (the workspace of six
+ * Queued on the handle's stream; no synchronisation, no allocation (the workspace of seven
  * interior fields is allocated by mgh_create). */
 mgh_status mgh_tv_prox(mgh_handle* h, const double* fbar, const double* d, double gamma, double lam,
                        int iters, double* out);

@@ -114,13 +114,20 @@ class CoarseSolver:
         return sla.lu_solve(self.lu, b.ravel()).reshape(self.shape)
 
 
+def _sweeps(nu, l: int) -> int:
+    """Sweeps on level l: nu is one count for every level or a sequence indexed by level (the
+    counts need not be equal across levels, Sec. III after Alg. 2)."""
+    return int(nu) if np.isscalar(nu) else int(nu[l])
+
+
 def mg_cycle(hier: List[Level], coarse: CoarseSolver, l: int, b: np.ndarray, v: np.ndarray,
-             nu1: int, nu2: int, omega: float, cycle_type: int = 1) -> np.ndarray:
-    """MGCycle of Alg. 2 (V-cycle for cycle_type=1, W-cycle for 2) on level l."""
+             nu1, nu2, omega: float, cycle_type: int = 1) -> np.ndarray:
+    """MGCycle of Alg. 2 (V-cycle for cycle_type=1, W-cycle for 2) on level l; nu1 / nu2 are
+    counts or per-level sequences."""
     lv = hier[l]
     if l == len(hier) - 1:                       # coarsest level: solve exactly
         return coarse(b)
-    for _ in range(nu1):                         # nu1 pre-relaxations
+    for _ in range(_sweeps(nu1, l)):             # nu1 pre-relaxations
         v = jacobi(lv, b, v, omega)
     r = b - apply_operator(lv.D, v, lv.h)        # residual
     rc = restrict(r)                             # restrict to the coarse problem
@@ -128,7 +135,7 @@ def mg_cycle(hier: List[Level], coarse: CoarseSolver, l: int, b: np.ndarray, v: 
     for _ in range(cycle_type):                  # CycleType recursive calls
         ec = mg_cycle(hier, coarse, l + 1, rc, ec, nu1, nu2, omega, cycle_type)
     v = v + prolong(ec, lv.ny, lv.nx)            # coarse-grid correction
-    for _ in range(nu2):                         # nu2 post-relaxations
+    for _ in range(_sweeps(nu2, l)):             # nu2 post-relaxations
         v = jacobi(lv, b, v, omega)
     return v
 
@@ -136,7 +143,7 @@ def mg_cycle(hier: List[Level], coarse: CoarseSolver, l: int, b: np.ndarray, v: 
 class Preconditioner:
     """K_MG^{-1}: one MG cycle with zero initial guess applied to K_kappa (Alg. 3, steps 9 and 14)."""
 
-    def __init__(self, p: Problem, c_fine: np.ndarray, levels: int, nu1: int, nu2: int,
+    def __init__(self, p: Problem, c_fine: np.ndarray, levels: int, nu1, nu2,
                  omega: float, shift: complex, cycle_type: int = 1):
         self.hier = build_hierarchy(p, c_fine, levels, shift)
         self.coarse = CoarseSolver(self.hier[-1])

@@ -75,7 +75,7 @@ class MGHSolver:
     """The paper's MGH solver on one contrast: operator A, shifted-Laplacian MG preconditioner and
     a Krylov method, plus the forward map and the data-term gradient."""
 
-    def __init__(self, p: Problem, f_d: np.ndarray, levels: int, nu1: int, nu2: int,
+    def __init__(self, p: Problem, f_d: np.ndarray, levels: int, nu1, nu2,
                  omega: float = 0.8, shift: complex = 1.0 + 0.5j, restart: int = 20,
                  tol: float = 1e-6, maxit: int = 5000, cycle_type: int = 1, krylov: str = "gmres"):
         self.p = p

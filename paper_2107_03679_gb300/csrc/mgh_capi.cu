@@ -78,7 +78,7 @@ size_t workspace_bytes(const mgh_params& p) {
   t += pad256(16 * B * (m + 1)) + pad256(16 * B * m) + pad256(8 * B * (m + 1)) + pad256(sizeof(RhsState) * B);
   t += pad256(16 * (1216 + B) * partial_stride(m)) + pad256(8 * (B + 1));
   t += pad256(16 * Np) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m) + pad256(4);   // DAdf, hpend, coef, err
-  t += pad256(48 * (size_t)p.nx_int * p.ny_int);                                          // tvbuf
+  t += pad256(56 * (size_t)p.nx_int * p.ny_int);                                          // tvbuf
   if (p.precision != MGH_PREC_FP64) t += 2 * pad256(16 * B * Np);                        // xdf, bdf
   return t;
 }
@@ -252,7 +252,7 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->hpend, 16 * B * (m + 1));
   ALLOC(h->coef, 16 * B * 2 * m);
   ALLOC(h->dscratch, 8 * (B + 1));
-  ALLOC(h->tvbuf, 48 * (size_t)p->nx_int * p->ny_int);
+  ALLOC(h->tvbuf, 56 * (size_t)p->nx_int * p->ny_int);
 #undef ALLOC
   if (cudaMallocHost((void**)&h->st_host, sizeof(RhsState) * B) != cudaSuccess) {
     h->st_host = nullptr;

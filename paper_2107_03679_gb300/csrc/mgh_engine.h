@@ -110,8 +110,8 @@ struct Handle {
   cd* partial = nullptr;     // [nblk*B][2m+4] block partial sums
   int nblk = 1;              // reduction blocks per right-hand side
   double* dscratch = nullptr;   // small FP64 scratch (loss)
-  double* tvbuf = nullptr;      // [6][ny_int][nx_int] TV proximal operator: w, x, dual momentum point
-                                // (p, q) and last dual iterate (p, q)
+  double* tvbuf = nullptr;      // [7][ny_int][nx_int] TV proximal operator: w, the dual momentum
+                                // point (p twice, q twice: ping-pong) and the last dual iterate (p, q)
   int* dev_err = nullptr;       // device error word written by kernels with bounded waits
 
   uint64_t launches = 0;

@@ -10,6 +10,11 @@
 //   (pn, qn) = (pr, qr) + grad(x) / (8 lam), divided by max(1, |(pn, qn)|)
 //   (pr, qr) = (pn, qn) + c ((pn, qn) - (pp, qq)),  (pp, qq) = (pn, qn),  c = (t - 1) / t'
 // and the result is max(w - lam adj(pp, qq), 0).
+//
+// The fields are small (2 MB each on a 512^2 interior, all six held in L2), so one iteration is
+// one launch: each thread forms x at its point and at the two forward neighbours from the
+// momentum point (read from one buffer of a ping-pong pair, written to the other), so no pass
+// over x is stored between the primal and the dual step.
 #include <cmath>
 
 #include "mgh_engine.h"
@@ -18,6 +23,7 @@ namespace mgh {
 
 namespace {
 
+constexpr int kTx = 32, kTy = 8;   // 2-D blocks over (x, y) of the interior
 constexpr int kInvThreads = 256;
 
 __device__ __forceinline__ double adj_at(const double* __restrict__ p, const double* __restrict__ q, int i, int j,
@@ -31,6 +37,12 @@ __device__ __forceinline__ double adj_at(const double* __restrict__ p, const dou
   return s;
 }
 
+__device__ __forceinline__ double primal_at(const double* __restrict__ w, const double* __restrict__ p,
+                                            const double* __restrict__ q, double lam, int i, int j, int nx, int ny) {
+  const double v = w[(size_t)i * nx + j] - lam * adj_at(p, q, i, j, nx, ny);
+  return v > 0.0 ? v : 0.0;
+}
+
 // w = fbar - gamma d (d may be null)
 __global__ void k_tv_w(const double* __restrict__ fbar, const double* __restrict__ d, double gamma,
                        double* __restrict__ w, size_t n) {
@@ -42,26 +54,28 @@ __global__ void k_tv_w(const double* __restrict__ fbar, const double* __restrict
 // x = max(w - lam adj(p, q), 0)
 __global__ void k_tv_primal(const double* __restrict__ w, const double* __restrict__ p, const double* __restrict__ q,
                             double lam, double* __restrict__ x, int nx, int ny) {
-  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (k >= (size_t)nx * ny) return;
-  const int i = (int)(k / nx), j = (int)(k - (size_t)i * nx);
-  const double v = w[k] - lam * adj_at(p, q, i, j, nx, ny);
-  x[k] = v > 0.0 ? v : 0.0;
+  const int j = blockIdx.x * kTx + threadIdx.x, i = blockIdx.y * kTy + threadIdx.y;
+  if (i >= ny || j >= nx) return;
+  x[(size_t)i * nx + j] = primal_at(w, p, q, lam, i, j, nx, ny);
 }
 
-// dual projected-gradient step from the momentum point and the next momentum point
-__global__ void k_tv_dual(const double* __restrict__ x, double* __restrict__ pr, double* __restrict__ qr,
-                          double* __restrict__ pp, double* __restrict__ qq, double step, double c, int nx, int ny) {
-  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (k >= (size_t)nx * ny) return;
-  const int i = (int)(k / nx), j = (int)(k - (size_t)i * nx);
-  const double gp = i < ny - 1 ? x[k] - x[k + nx] : 0.0;
-  const double gq = j < nx - 1 ? x[k] - x[k + 1] : 0.0;
+// One FGP iteration: the primal point of the momentum point (pr, qr) at (i, j), (i+1, j) and
+// (i, j+1), the projected dual step, the next momentum point into (pr_out, qr_out) and the dual
+// iterate into (pp, qq) (each thread owns its entries of pp, qq).
+__global__ void k_tv_iter(const double* __restrict__ w, const double* __restrict__ pr, const double* __restrict__ qr,
+                          double* __restrict__ pr_out, double* __restrict__ qr_out, double* __restrict__ pp,
+                          double* __restrict__ qq, double lam, double step, double c, int nx, int ny) {
+  const int j = blockIdx.x * kTx + threadIdx.x, i = blockIdx.y * kTy + threadIdx.y;
+  if (i >= ny || j >= nx) return;
+  const size_t k = (size_t)i * nx + j;
+  const double x0 = primal_at(w, pr, qr, lam, i, j, nx, ny);
+  const double gp = i < ny - 1 ? x0 - primal_at(w, pr, qr, lam, i + 1, j, nx, ny) : 0.0;
+  const double gq = j < nx - 1 ? x0 - primal_at(w, pr, qr, lam, i, j + 1, nx, ny) : 0.0;
   double pn = pr[k] + step * gp, qn = qr[k] + step * gq;
   const double nrm = sqrt(pn * pn + qn * qn);
   if (nrm > 1.0) { pn /= nrm; qn /= nrm; }
-  pr[k] = pn + c * (pn - pp[k]);
-  qr[k] = qn + c * (qn - qq[k]);
+  pr_out[k] = pn + c * (pn - pp[k]);
+  qr_out[k] = qn + c * (qn - qq[k]);
   pp[k] = pn;
   qq[k] = qn;
 }
@@ -82,28 +96,33 @@ mgh_status tv_prox(Handle& h, const double* fbar, const double* d, double gamma,
   const int nx = h.p.nx_int, ny = h.p.ny_int;
   const size_t n = (size_t)nx * ny;
   double* w = h.tvbuf;
-  double* x = w + n;
-  double *pr = x + n, *qr = pr + n, *pp = qr + n, *qq = pp + n;
+  double* pr[2] = {w + n, w + 2 * n};
+  double* qr[2] = {w + 3 * n, w + 4 * n};
+  double *pp = w + 5 * n, *qq = w + 6 * n;
+  const dim3 blk(kTx, kTy), grd((unsigned)((nx + kTx - 1) / kTx), (unsigned)((ny + kTy - 1) / kTy));
   ProfScope ps(h, P_OTHER);
   k_tv_w<<<blocks(n), kInvThreads, 0, h.stream>>>(fbar, d, gamma, w, n);
   MGH_CHECK_LAUNCH(); h.launches++;
   if (lam == 0.0) {   // prox of the constraint alone: the clamp
     MGH_CUDA(cudaMemsetAsync(pp, 0, 2 * n * sizeof(double), h.stream));
-    k_tv_primal<<<blocks(n), kInvThreads, 0, h.stream>>>(w, pp, qq, 0.0, out, nx, ny);
+    k_tv_primal<<<grd, blk, 0, h.stream>>>(w, pp, qq, 0.0, out, nx, ny);
     MGH_CHECK_LAUNCH(); h.launches++;
     return MGH_OK;
   }
-  MGH_CUDA(cudaMemsetAsync(pr, 0, 4 * n * sizeof(double), h.stream));
+  // pr[0], qr[0] (the first momentum point) and pp, qq start at 0; pr[1], qr[1] are written first
+  MGH_CUDA(cudaMemsetAsync(pr[0], 0, n * sizeof(double), h.stream));
+  MGH_CUDA(cudaMemsetAsync(qr[0], 0, 3 * n * sizeof(double), h.stream));   // qr[0], qr[1], pp: contiguous
+  MGH_CUDA(cudaMemsetAsync(qq, 0, n * sizeof(double), h.stream));
   double t = 1.0;
   for (int it = 0; it < iters; ++it) {
     const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
-    k_tv_primal<<<blocks(n), kInvThreads, 0, h.stream>>>(w, pr, qr, lam, x, nx, ny);
-    MGH_CHECK_LAUNCH(); h.launches++;
-    k_tv_dual<<<blocks(n), kInvThreads, 0, h.stream>>>(x, pr, qr, pp, qq, 1.0 / (8.0 * lam), (t - 1.0) / tn, nx, ny);
+    const int a = it & 1;
+    k_tv_iter<<<grd, blk, 0, h.stream>>>(w, pr[a], qr[a], pr[a ^ 1], qr[a ^ 1], pp, qq, lam, 1.0 / (8.0 * lam),
+                                         (t - 1.0) / tn, nx, ny);
     MGH_CHECK_LAUNCH(); h.launches++;
     t = tn;
   }
-  k_tv_primal<<<blocks(n), kInvThreads, 0, h.stream>>>(w, pp, qq, lam, out, nx, ny);
+  k_tv_primal<<<grd, blk, 0, h.stream>>>(w, pp, qq, lam, out, nx, ny);
   MGH_CHECK_LAUNCH(); h.launches++;
   return MGH_OK;
 }

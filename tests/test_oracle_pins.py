@@ -336,6 +336,70 @@ def test_vcycle_equals_iteration_matrix_identity(nu):
     assert np.max(np.abs(M_proc - M_ref)) <= 1e-11 * np.max(np.abs(M_ref))
 
 
+def _gamma_cycle_matrix(hier, l, nu1, nu2, omega, gamma):
+    """Textbook identity of the gamma-cycle with per-level sweeps (Trottenberg et al. 2000, Sec.
+    2.4): M_l^{-1} = (I - E_l) K_l^{-1}, E_l = S_l^{nu2_l} (I - P Mg_{l+1} R K_l) S_l^{nu1_l}, where
+    Mg_{l+1} = (I - (I - M_{l+1}^{-1} K_{l+1})^gamma) K_{l+1}^{-1} is gamma cycles of level l + 1
+    from a zero guess; on the coarsest level M^{-1} = K^{-1}.  Built from dense matrices only."""
+    lv = hier[l]
+    n = lv.nx * lv.ny
+    K = O.assemble_operator(lv.D, lv.h).toarray()
+    Kinv = np.linalg.inv(K)
+    if l == len(hier) - 1:
+        return Kinv
+    c = hier[l + 1]
+    nc = c.nx * c.ny
+    Kc = O.assemble_operator(c.D, c.h).toarray()
+    R = np.stack([O.restrict(np.eye(n)[q].reshape(lv.ny, lv.nx)).ravel() for q in range(n)], axis=1)
+    P = np.stack([O.prolong(np.eye(nc)[q].reshape(c.ny, c.nx), lv.ny, lv.nx).ravel() for q in range(nc)], axis=1)
+    S = np.eye(n) - omega * np.diag(1.0 / lv.D.ravel()) @ K
+    Mc = _gamma_cycle_matrix(hier, l + 1, nu1, nu2, omega, gamma)
+    Ec = np.eye(nc) - Mc @ Kc
+    Mg = (np.eye(nc) - np.linalg.matrix_power(Ec, gamma)) @ np.linalg.inv(Kc)
+    E = np.linalg.matrix_power(S, nu2[l]) @ (np.eye(n) - P @ Mg @ R @ K) @ np.linalg.matrix_power(S, nu1[l])
+    return (np.eye(n) - E) @ Kinv
+
+
+@pytest.mark.parametrize("gamma,nu1,nu2", [(2, (1, 1, 1), (1, 1, 1)), (2, (2, 0, 1), (0, 1, 2)),
+                                           (3, (1, 2, 1), (2, 1, 0)), (1, (0, 2, 1), (1, 0, 2))])
+def test_w_cycle_and_per_level_sweeps_equal_iteration_matrix_identity(gamma, nu1, nu2):
+    p = O.Problem(14, 10, 2, h=1.0, k=2 * math.pi / 6.0, beta=0.3)
+    rng = np.random.default_rng(9)
+    f = rng.uniform(0, 0.3, size=(p.ny_int, p.nx_int))
+    c = O.fine_coefficient(p, f)
+    pre = O.Preconditioner(p, c, levels=4, nu1=list(nu1) + [0], nu2=list(nu2) + [0], omega=0.8,
+                           shift=1 + 0.5j, cycle_type=gamma)
+    n = p.nx * p.ny
+    M_proc = _dense(lambda e: pre(e.reshape(p.ny, p.nx)).ravel(), n)
+    M_ref = _gamma_cycle_matrix(pre.hier, 0, list(nu1) + [0], list(nu2) + [0], 0.8, gamma)
+    assert np.max(np.abs(M_proc - M_ref)) <= 1e-10 * np.max(np.abs(M_ref))
+
+
+@pytest.mark.parametrize("gamma,levels", [(1, 4), (2, 4), (2, 5), (3, 4)])
+def test_cycle_type_visits_the_coarsest_level_gamma_to_the_depth(gamma, levels):
+    """Alg. 2 with CycleType = gamma calls the coarsest solve gamma^(L-1) times: every level
+    0..L-2 calls the next one gamma times."""
+    p = O.Problem(30, 30, 2, h=1.0, k=0.9)
+    c = O.fine_coefficient(p, np.full((30, 30), 0.1))
+    pre = O.Preconditioner(p, c, levels=levels, nu1=1, nu2=1, omega=0.8, shift=1 + 0.5j, cycle_type=gamma)
+    calls = []
+    inner = pre.coarse
+    pre.coarse = lambda b: (calls.append(1), inner(b))[1]
+    pre(W.random_field((p.ny, p.nx), 2))
+    assert len(calls) == gamma ** (levels - 1)
+
+
+def test_w_cycle_on_two_levels_is_the_two_grid_cycle():
+    """With an exact coarse solve, repeating it changes nothing: CycleType 2 on two levels is
+    Alg. 1 (the two-grid cycle)."""
+    p = O.Problem(12, 10, 2, h=1.0, k=0.9)
+    c = O.fine_coefficient(p, np.full((10, 12), 0.2))
+    b = W.random_field((p.ny, p.nx), 5)
+    v = O.Preconditioner(p, c, levels=2, nu1=2, nu2=1, omega=0.8, shift=1 + 0.5j, cycle_type=1)(b)
+    w = O.Preconditioner(p, c, levels=2, nu1=2, nu2=1, omega=0.8, shift=1 + 0.5j, cycle_type=2)(b)
+    np.testing.assert_allclose(w, v, rtol=0, atol=1e-13 * np.abs(v).max())
+
+
 def test_two_grid_without_smoothing_is_p_kinv_r():
     """Alg. 1 with nu1 = nu2 = 0 and an exact coarse solve is P K_c^{-1} R."""
     p = O.Problem(10, 10, 2, h=1.0, k=0.9)
