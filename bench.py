@@ -56,6 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--arnoldi", choices=["auto", "df", "fp64", "sstep"], default="auto",
                     help="mixed-precision Krylov engine: s-step cycles (Gram/Cholesky), double-float Arnoldi, "
                          "native-FP64 Arnoldi; auto = s-step when the restart length is at most 8")
+    ap.add_argument("--cycle", choices=["v", "w"], default="v",
+                    help="multigrid cycle of the preconditioner (CycleType of Alg. 2)")
     ap.add_argument("--krylov", choices=["fgmres", "bicgstab"], default="fgmres",
                     help="outer Krylov method: flexible GMRES (default) or the paper's Bi-CGSTAB (Alg. 3)")
     ap.add_argument("--autotune", action="store_true",
@@ -157,12 +159,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- algorithmic bytes
-def coarse_fraction(nx: int, ny: int, levels: int) -> float:
-    """Points of the levels 1 .. L-2 (the coarser smoothing levels) per fine point."""
+def coarse_fraction(nx: int, ny: int, levels: int, gamma: int = 1) -> float:
+    """Points of the levels 1 .. L-2 (the coarser smoothing levels) per fine point, each level
+    counted once per visit in a cycle of CycleType gamma (gamma^(l-1) visits of level l)."""
     tot, cx, cy = 0, nx, ny
-    for _ in range(1, levels - 1):
+    for l in range(1, levels - 1):
         cx, cy = (cx - 1) // 2 + 1, (cy - 1) // 2 + 1
-        tot += cx * cy
+        tot += gamma ** (l - 1) * cx * cy
     return tot / (nx * ny)
 
 
@@ -353,7 +356,7 @@ def gpu_main(args, rank, world, local_rank):
         w.nu1 = w.nu2 = tuned["nu"]
         w.restart = tuned["restart"]
     solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=args.maxit, arnoldi=args.arnoldi,
-                                  krylov=args.krylov)
+                                  krylov=args.krylov, cycle_type=args.cycle)
     stream = solver.stream
     d_th = torch.from_numpy(th).to(dev)
     d_rec = torch.from_numpy(rec).to(dev)
@@ -461,7 +464,7 @@ def gpu_main(args, rank, world, local_rank):
     cs = 16 if precision == "fp64" else 8
     N = solver.N
     engine = "bicgstab" if args.krylov == "bicgstab" else (solver.arnoldi if precision == "mixed32" else "fp64")
-    alg = algorithmic_bytes(prof, N, cs, prof["launches"], engine, coarse_fraction(w.nx, w.ny, w.levels))
+    alg = algorithmic_bytes(prof, N, cs, prof["launches"], engine, coarse_fraction(w.nx, w.ny, w.levels, 2 if args.cycle == "w" else 1))
     ms_cls = prof["ms"]
     # the dominant kernel: the class with the most time among those that are one kernel each (the
     # coarser multigrid levels and the per-RHS reductions are many small kernels)
@@ -523,7 +526,7 @@ def gpu_main(args, rank, world, local_rank):
         "dtype": "f32+f64" if precision == "mixed32" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
                    "angles_per_gpu": B, "angles_total": B * world, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
-                   "restart": w.restart, "tol": w.tol, "krylov": args.krylov, "arnoldi": solver.arnoldi if precision == "mixed32" else "fp64", "shift": [w.shift_re, w.shift_im],
+                   "restart": w.restart, "tol": w.tol, "krylov": args.krylov, "cycle": args.cycle.upper(), "arnoldi": solver.arnoldi if precision == "mixed32" else "fp64", "shift": [w.shift_re, w.shift_im],
                    "step": f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient",
                    "solves_per_step": 2 * B, "l2": "inputs larger than L2 (Krylov basis "
                    f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}"},

@@ -75,6 +75,8 @@ typedef enum {
                                Bi-CGSTAB iteration) */
 } mgh_krylov;
 
+#define MGH_MAX_LEVELS 12
+
 /* Solver parameters.  Lengths are in the same unit as h (grid cells when h = 1). */
 typedef struct {
   int nx_int, ny_int;       /* interior Omega size in grid points */
@@ -94,6 +96,15 @@ typedef struct {
   int batch_max;            /* largest batch B any later call may use; sizes the workspace */
   int arnoldi;              /* mgh_arnoldi, used when precision is MGH_PREC_MIXED32 */
   int krylov;               /* mgh_krylov (default MGH_KRYLOV_FGMRES) */
+  int cycle_type;           /* CycleType of Alg. 2: each level l < levels-1 runs cycle_type cycles of
+                               level l+1 on its restricted residual, from a zero guess: 1 = V-cycle
+                               (0 is read as 1), 2 = W-cycle, 3.  The coarsest solve is exact, so
+                               it runs once per visit of the level above it */
+  int nu_per_level;         /* 0: nu1 / nu2 on every level; 1: level l uses nu1_level[l] and
+                               nu2_level[l] (0..4 each; Sec. III notes that the counts may differ
+                               by level); entries from levels-1 on are ignored */
+  int nu1_level[MGH_MAX_LEVELS];
+  int nu2_level[MGH_MAX_LEVELS];
 } mgh_params;
 
 typedef struct {

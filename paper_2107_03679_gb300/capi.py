@@ -19,6 +19,8 @@ MGH_ARNOLDI_DF, MGH_ARNOLDI_FP64, MGH_ARNOLDI_SSTEP = 0, 1, 2
 ARNOLDI = {"df": MGH_ARNOLDI_DF, "fp64": MGH_ARNOLDI_FP64, "sstep": MGH_ARNOLDI_SSTEP}
 MGH_KRYLOV_FGMRES, MGH_KRYLOV_BICGSTAB = 0, 1
 KRYLOV = {"fgmres": MGH_KRYLOV_FGMRES, "bicgstab": MGH_KRYLOV_BICGSTAB}
+MGH_MAX_LEVELS = 12
+CYCLES = {"v": 1, "w": 2}
 
 
 class mgh_params(ctypes.Structure):
@@ -30,7 +32,8 @@ class mgh_params(ctypes.Structure):
         ("omega", ctypes.c_double),
         ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
         ("precision", ctypes.c_int), ("batch_max", ctypes.c_int), ("arnoldi", ctypes.c_int),
-        ("krylov", ctypes.c_int),
+        ("krylov", ctypes.c_int), ("cycle_type", ctypes.c_int), ("nu_per_level", ctypes.c_int),
+        ("nu1_level", ctypes.c_int * MGH_MAX_LEVELS), ("nu2_level", ctypes.c_int * MGH_MAX_LEVELS),
     ]
 
 

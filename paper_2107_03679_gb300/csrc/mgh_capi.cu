@@ -13,6 +13,7 @@
 
 // The opaque handle of the C ABI is the engine's Handle.
 struct mgh_handle : public mgh::Handle {};
+static_assert(MGH_MAX_LEVELS == mgh::kMaxLevels, "level arrays of mgh_params and the engine differ");
 
 namespace mgh {
 
@@ -40,6 +41,12 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
       p->krylov == MGH_KRYLOV_FGMRES)
     return MGH_INVALID_ARG;
   if (p->krylov != MGH_KRYLOV_FGMRES && p->krylov != MGH_KRYLOV_BICGSTAB) return MGH_INVALID_ARG;
+  if (p->cycle_type < 0 || p->cycle_type > kMaxCycleType) return MGH_INVALID_ARG;
+  if (p->nu_per_level != 0 && p->nu_per_level != 1) return MGH_INVALID_ARG;
+  if (p->nu_per_level)
+    for (int l = 0; l + 1 < p->levels; ++l)
+      if (p->nu1_level[l] < 0 || p->nu1_level[l] > kMaxSweeps || p->nu2_level[l] < 0 || p->nu2_level[l] > kMaxSweeps)
+        return MGH_INVALID_ARG;
   if (p->krylov == MGH_KRYLOV_BICGSTAB && p->restart < 5) return MGH_INVALID_ARG;
   if (!std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) return MGH_INVALID_ARG;
   const long long nx = p->nx_int + 2LL * p->abl, ny = p->ny_int + 2LL * p->abl;
@@ -68,6 +75,7 @@ size_t workspace_bytes(const mgh_params& p) {
     t += pad256(8 * n) + 2 * pad256(cs * n);
     if (l >= 1) t += 2 * pad256(cs * n * B);             // b, vfin
     if (l + 1 < p.levels) t += pad256(cs * n * B);       // vpre
+    if (p.cycle_type >= 2 && l >= 1 && l + 1 < p.levels) t += pad256(cs * n * B);   // wacc
   }
   const size_t nc = (size_t)nxl[p.levels - 1] * nyl[p.levels - 1];
   const size_t W = 3 * (size_t)nxl[p.levels - 1] + 1;
@@ -99,6 +107,7 @@ void free_handle(mgh_handle* h) {
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& lv = h->lev[l];
     cudaFree(lv.c); cudaFree(lv.D); cudaFree(lv.wDinv); cudaFree(lv.b); cudaFree(lv.vpre); cudaFree(lv.vfin);
+    cudaFree(lv.wacc);
   }
   cudaFree(h->f_d); cudaFree(h->DA); cudaFree(h->band); cudaFree(h->piv); cudaFree(h->kinv64); cudaFree(h->kinv64r);
   cudaFree(h->kinv32); cudaFree(h->lu_info); cudaFree(h->V); cudaFree(h->Z); cudaFree(h->W);
@@ -218,6 +227,7 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
     ALLOC(lv.wDinv, cs * n);
     if (l >= 1) { ALLOC(lv.b, cs * n * B); ALLOC(lv.vfin, cs * n * B); }
     if (l + 1 < h->L) ALLOC(lv.vpre, cs * n * B);
+    if (p->cycle_type >= 2 && l >= 1 && l + 1 < h->L) ALLOC(lv.wacc, cs * n * B);
     hl *= 2.0; sc *= 2;
   }
   const Level& cl = h->lev[h->L - 1];

@@ -24,6 +24,7 @@ inline int partial_stride(int m) {
   return a > b ? a : b;
 }
 constexpr int kMaxSweeps = 4;
+constexpr int kMaxCycleType = 3;   // CycleType of Alg. 2 (launches per cycle grow as CycleType^levels)
 constexpr int kMaxCoarse = 4096;   // unknowns on the coarsest level (dense inverse kept on device)
 
 // Device arrays of one multigrid level.  Coefficient and diagonals are shared by every
@@ -37,6 +38,7 @@ struct Level {
   void* b = nullptr;         // right-hand side of this level (levels >= 1)
   void* vpre = nullptr;      // iterate after pre-smoothing
   void* vfin = nullptr;      // iterate after post-smoothing (levels >= 1)
+  void* wacc = nullptr;      // sum of the earlier cycles' corrections (CycleType >= 2, levels 1..L-2)
   size_t n() const { return (size_t)nx * ny; }
 };
 
@@ -128,6 +130,11 @@ struct Handle {
   size_t ev_used = 0;
   mgh_profile acc{};
 };
+
+// Sweeps of level l, the CycleType of Alg. 2 (0 is read as 1).
+inline int nu_pre(const Handle& h, int l) { return h.p.nu_per_level ? h.p.nu1_level[l] : h.p.nu1; }
+inline int nu_post(const Handle& h, int l) { return h.p.nu_per_level ? h.p.nu2_level[l] : h.p.nu2; }
+inline int cycle_gamma(const Handle& h) { return h.p.cycle_type < 1 ? 1 : h.p.cycle_type; }
 
 enum ProfClass { P_PRE0 = 0, P_POST0, P_COARSE, P_MATVEC_DOTS, P_UPDATE, P_REORTH, P_REDUCE, P_RESIDUAL,
                  P_XUPDATE, P_OTHER };

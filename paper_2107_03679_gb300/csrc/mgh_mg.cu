@@ -1,5 +1,6 @@
-// One multigrid cycle (Alg. 2, V-cycle, zero initial guess) on the shifted-Laplacian operator
-// K_kappa for a batch of right-hand sides, in complex FP32 or FP64.
+// One multigrid cycle (Alg. 2, zero initial guess; V-cycle, or CycleType >= 2 such as the W-cycle)
+// on the shifted-Laplacian operator K_kappa for a batch of right-hand sides, in complex FP32 or
+// FP64, with nu1 / nu2 sweeps that may differ by level.
 //
 // Each level other than the coarsest runs two fused, shared-memory tiled kernels:
 //   k_pre   nu1 damped-Jacobi sweeps from v = 0 (eq. dampedJ), the residual r = b - K v and
@@ -14,6 +15,7 @@
 // Points outside the grid hold 0 in every tile buffer: the Sommerfeld closure already sits in D,
 // and the restriction counts out-of-grid fine samples as 0.
 #include <cudaTypedefs.h>
+#include <algorithm>
 #include <new>
 #include <type_traits>
 
@@ -1205,7 +1207,7 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
 template <typename T, typename TIn>
 mgh_status launch_pre(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
                       size_t scale_stride, int B, const RhsState* st, int in_slot = -1) {
-  switch (h.p.nu1) {
+  switch (nu_pre(h, l)) {
     case 0: return launch_pre_nu<T, 0, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st, in_slot);
     case 1: return launch_pre_nu<T, 1, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st, in_slot);
     case 2: return launch_pre_nu<T, 2, TIn>(h, l, bin, b_stride, bscale, scale_stride, B, st, in_slot);
@@ -1219,7 +1221,7 @@ template <typename T, typename TIn, typename TOut>
 mgh_status launch_post(Handle& h, int l, const void* bin, size_t b_stride, const double* bscale,
                        size_t scale_stride, Cx<TOut>* out, size_t out_stride, int B, const RhsState* st,
                        int in_slot = -1) {
-  switch (h.p.nu2) {
+  switch (nu_post(h, l)) {
     case 0: return launch_post_nu<T, 0, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st, in_slot);
     case 1: return launch_post_nu<T, 1, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st, in_slot);
     case 2: return launch_post_nu<T, 2, TIn, TOut>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st, in_slot);
@@ -1229,21 +1231,92 @@ mgh_status launch_post(Handle& h, int l, const void* bin, size_t b_stride, const
   return MGH_INVALID_ARG;
 }
 
+// CycleType >= 2 (Alg. 2): before the next cycle of level l, whose last cycle left its result v in
+// vfin, the right-hand side b becomes the residual b - K v and v joins the sum of the earlier
+// corrections, so that the next cycle (from a zero guess) computes the correction to that sum:
+// a cycle is affine in its initial guess, MG(b, v) = v + MG(b - K v, 0).
+template <typename T>
+__global__ void k_wc_residual(const Cx<T>* __restrict__ D, Cx<T>* __restrict__ b, const Cx<T>* __restrict__ v,
+                              Cx<T>* __restrict__ acc, int first, int nx, int ny, T inv_h2,
+                              const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y;
+  if (st && !st[rhs].active) return;
+  const int n = nx * ny;
+  const size_t off = (size_t)rhs * n;
+  const Cx<T>* vr = v + off;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int i = k / nx, j = k - i * nx;
+    Cx<T> s = czero<T>();
+    if (j > 0) s = s + vr[k - 1];
+    if (j + 1 < nx) s = s + vr[k + 1];
+    if (i > 0) s = s + vr[k - nx];
+    if (i + 1 < ny) s = s + vr[k + nx];
+    const Cx<T> vk = vr[k];
+    const Cx<T> kv = D[k] * vk - inv_h2 * s;
+    b[off + k] = b[off + k] - kv;
+    acc[off + k] = first ? vk : acc[off + k] + vk;
+  }
+}
+
+// vfin += the sum of the earlier corrections, after the last cycle of level l.
+template <typename T>
+__global__ void k_wc_add(Cx<T>* __restrict__ v, const Cx<T>* __restrict__ acc, int n, const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y;
+  if (st && !st[rhs].active) return;
+  const size_t off = (size_t)rhs * n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    v[off + k] = v[off + k] + acc[off + k];
+}
+
+unsigned wc_blocks(int n) { return (unsigned)std::min(4096, (n + kVThreads - 1) / kVThreads); }
+
+template <typename T>
+mgh_status level_cycles(Handle& h, int l, int B, const RhsState* st);
+
+// One cycle of level l >= 1 from a zero guess: right-hand side lev[l].b, result in lev[l].vfin.
+template <typename T>
+mgh_status level_cycle(Handle& h, int l, int B, const RhsState* st) {
+  const Level& lv = h.lev[l];
+  if (l == h.L - 1)   // coarsest: exact solve
+    return launch_coarse_apply(h, lv.b, lv.n(), lv.vfin, lv.n(), B, st, sizeof(T) == 8);
+  MGH_TRY((launch_pre<T, T>(h, l, lv.b, lv.n(), nullptr, 0, B, st)));
+  MGH_TRY(level_cycles<T>(h, l + 1, B, st));
+  return launch_post<T, T, T>(h, l, lv.b, lv.n(), nullptr, 0, (Cx<T>*)lv.vfin, lv.n(), B, st);
+}
+
+// The CycleType cycles that level l - 1 runs on level l (Alg. 2); the coarsest level's exact solve
+// gives the same result every time, so it runs once.
+template <typename T>
+mgh_status level_cycles(Handle& h, int l, int B, const RhsState* st) {
+  MGH_TRY(level_cycle<T>(h, l, B, st));
+  const int gamma = cycle_gamma(h);
+  if (gamma == 1 || l == h.L - 1) return MGH_OK;
+  Level& lv = h.lev[l];
+  const int n = (int)lv.n();
+  const dim3 grid(wc_blocks(n), B);
+  for (int c = 1; c < gamma; ++c) {
+    {
+      ProfScope ps(h, P_COARSE);
+      k_wc_residual<T><<<grid, kVThreads, 0, h.stream>>>((const Cx<T>*)lv.D, (Cx<T>*)lv.b, (const Cx<T>*)lv.vfin,
+                                                         (Cx<T>*)lv.wacc, c == 1, lv.nx, lv.ny,
+                                                         static_cast<T>(1.0 / (lv.h * lv.h)), st);
+      MGH_CHECK_LAUNCH(); h.launches++;
+    }
+    MGH_TRY(level_cycle<T>(h, l, B, st));
+  }
+  ProfScope ps(h, P_COARSE);
+  k_wc_add<T><<<grid, kVThreads, 0, h.stream>>>((Cx<T>*)lv.vfin, (const Cx<T>*)lv.wacc, n, st);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  return MGH_OK;
+}
+
+// One cycle of Alg. 2 from a zero guess on the fine input: pre-smoothing and restriction of level
+// 0, CycleType cycles of level 1 (recursively), prolongation and post-smoothing of level 0.
 template <typename T, typename TIn>
 mgh_status vcycle_t(Handle& h, const void* in, size_t in_stride, const double* in_scale, size_t scale_stride,
                     void* out, size_t out_stride, bool out_fp64, int B, const RhsState* st, int in_slot = -1) {
-  const int L = h.L;
-  // down: level 0 reads the input, coarser levels their restricted right-hand side
   MGH_TRY((launch_pre<T, TIn>(h, 0, in, in_stride, in_scale, scale_stride, B, st, in_slot)));
-  for (int l = 1; l + 1 < L; ++l)
-    MGH_TRY((launch_pre<T, T>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, B, st)));
-  // coarsest: exact solve
-  const Level& cl = h.lev[L - 1];
-  MGH_TRY(launch_coarse_apply(h, cl.b, cl.n(), cl.vfin, cl.n(), B, st, sizeof(T) == 8));
-  // up
-  for (int l = L - 2; l >= 1; --l)
-    MGH_TRY((launch_post<T, T, T>(h, l, h.lev[l].b, h.lev[l].n(), nullptr, 0, (Cx<T>*)h.lev[l].vfin,
-                                  h.lev[l].n(), B, st)));
+  MGH_TRY(level_cycles<T>(h, 1, B, st));
   if (out_fp64)
     return launch_post<T, TIn, double>(h, 0, in, in_stride, in_scale, scale_stride, (cd*)out, out_stride, B, st);
   return launch_post<T, TIn, T>(h, 0, in, in_stride, in_scale, scale_stride, (Cx<T>*)out, out_stride, B, st,
@@ -1317,9 +1390,9 @@ mgh_status build_vcycle_tma(Handle& h) {
   h.tma = new (std::nothrow) LevelTma[kMaxLevels];
   h.tma_in = new (std::nothrow) CUtensorMap[2 * h.m];
   if (!h.tma || !h.tma_in) return MGH_OUT_OF_MEMORY;
-  const BoxDims bp = pre_box(h.p.nu1), bq = post_box(h.p.nu2);
   const uint64_t B = h.Bmax;
   for (int l = 0; l + 1 < h.L; ++l) {
+    const BoxDims bp = pre_box(nu_pre(h, l)), bq = post_box(nu_post(h, l));
     const Level& lv = h.lev[l];
     const Level& cl = h.lev[l + 1];
     LevelTma& t = h.tma[l];
@@ -1338,6 +1411,7 @@ mgh_status build_vcycle_tma(Handle& h) {
     t.post_ok = okp;
   }
   // level-0 inputs: the hi plane of basis slot j of every right-hand side
+  const BoxDims bp = pre_box(nu_pre(h, 0)), bq = post_box(nu_post(h, 0));
   bool ok = (h.nx % 2 == 0);
   const float2* V = reinterpret_cast<const float2*>(h.V);
   const uint64_t rhs_bytes = (uint64_t)(h.m + 1) * 2 * h.Np * 8;

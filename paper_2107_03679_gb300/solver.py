@@ -29,15 +29,30 @@ class Solver:
     def __init__(self, nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: float = 0.15,
                  shift=(1.0, 0.5), levels: int = 4, nu1: int = 1, nu2: int = 1, omega: float = 0.8,
                  restart: int = 20, maxit: int = 5000, tol: float = 1e-6, precision: str = "mixed32",
-                 batch_max: int = 1, arnoldi: str = "auto", krylov: str = "fgmres",
+                 batch_max: int = 1, arnoldi: str = "auto", krylov: str = "fgmres", cycle_type: int = 1,
                  device: Optional[torch.device] = None, stream=None):
+        """nu1 / nu2: sweeps on every level, or a sequence with one count per level (the coarsest's
+        is ignored); cycle_type: CycleType of Alg. 2 (1 = V, 2 = W, 3; or "v" / "w")."""
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         p = capi.mgh_params()
         p.nx_int, p.ny_int, p.abl = nx_int, ny_int, abl
         p.h, p.k, p.beta = h, k, beta
         p.shift_re, p.shift_im = float(shift[0]), float(shift[1])
-        p.levels, p.nu1, p.nu2, p.omega = levels, nu1, nu2, omega
+        p.levels, p.omega = levels, omega
+        if isinstance(nu1, int) and isinstance(nu2, int):
+            p.nu1, p.nu2 = nu1, nu2
+        else:
+            n1 = [nu1] * levels if isinstance(nu1, int) else list(nu1)
+            n2 = [nu2] * levels if isinstance(nu2, int) else list(nu2)
+            if len(n1) < levels - 1 or len(n2) < levels - 1 or max(len(n1), len(n2)) > capi.MGH_MAX_LEVELS:
+                raise ValueError("per-level sweeps need one count per level above the coarsest")
+            p.nu1, p.nu2, p.nu_per_level = n1[0], n2[0], 1
+            for l in range(len(n1)):
+                p.nu1_level[l] = n1[l]
+            for l in range(len(n2)):
+                p.nu2_level[l] = n2[l]
+        p.cycle_type = capi.CYCLES[cycle_type] if isinstance(cycle_type, str) else int(cycle_type)
         p.restart, p.maxit, p.tol = restart, maxit, tol
         p.precision = capi.PRECISIONS[precision]
         p.batch_max = batch_max

@@ -88,3 +88,50 @@ def test_reconstruction_entry_points_validate_on_the_host(lib):
     L = capi._lib
     assert L.mgh_tv_prox(None, None, None, 1.0, 0.1, 3, None) == capi.MGH_INVALID_ARG
     assert L.mgh_fbs_momentum(None, None, None, 0.5, None) == capi.MGH_INVALID_ARG
+
+
+def test_params_layout_matches_the_c_header(tmp_path):
+    """The ctypes mirror of mgh_params has the C struct's size and field offsets (compiled from
+    include/mgh.h with the host C compiler)."""
+    import shutil
+    import subprocess
+    import paper_2107_03679_gb300.capi as capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in capi.mgh_params._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mgh.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(mgh_params));\n'
+                   + "".join(f'  printf("%zu\\n", offsetof(mgh_params, {f}));\n' for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(capi.mgh_params)
+    assert out[1:] == [getattr(capi.mgh_params, f).offset for f in fields]
+
+
+def test_cycle_type_and_per_level_sweeps_validate_on_the_host(lib):
+    import paper_2107_03679_gb300.capi as capi
+    p = capi.mgh_default_params()
+    base = capi.mgh_workspace_bytes(p)
+    p.cycle_type = 2          # the W-cycle keeps one sum of corrections per level 1..L-2
+    assert capi.mgh_workspace_bytes(p) > base
+    p.cycle_type = 4
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(p)
+    p.cycle_type = 1
+    p.nu_per_level = 1
+    for l, (a, b) in enumerate([(2, 1), (1, 0), (0, 3)]):
+        p.nu1_level[l], p.nu2_level[l] = a, b
+    assert capi.mgh_workspace_bytes(p) == base
+    p.nu2_level[1] = 5
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(p)
+    p.nu2_level[1] = 1
+    p.nu1_level[3] = 9        # the coarsest level's entry is ignored
+    assert capi.mgh_workspace_bytes(p) == base
+    p.nu_per_level = 2
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(p)
