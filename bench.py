@@ -689,7 +689,6 @@ def fbs_main(args, rank, world, local_rank):
 def uneven_main(args, rank, world, local_rank):
     """Four grids of different sizes solved together: one solver handle and one CUDA stream per
     grid, driven from one host thread each so that their kernels overlap on the GPU."""
-    import threading as th
     import torch
     import workloads as W
     from paper_2107_03679_gb300 import Solver
@@ -713,23 +712,18 @@ def uneven_main(args, rank, world, local_rank):
         jobs.append(d)
     torch.cuda.synchronize()
 
-    def run_one(d, out):
-        with torch.cuda.stream(d["stream"]):
-            s = d["s"]
-            s.set_contrast(d["f"])
-            _, inf_f = s.forward(d["th"], out=d["u"])
-            _, G, _ = s.misfit(d["u"], d["y"], d["rec"])
-            _, inf_a = s.gradient(d["th"], d["u"], G)
-        out.extend(inf_f + inf_a)
+    from paper_2107_03679_gb300.multi import run_concurrently
+
+    def run_one(i, s):
+        d = jobs[i]
+        s.set_contrast(d["f"])
+        _, inf_f = s.forward(d["th"], out=d["u"])
+        _, G, _ = s.misfit(d["u"], d["y"], d["rec"])
+        _, inf_a = s.gradient(d["th"], d["u"], G)
+        return inf_f + inf_a
 
     def step():
-        outs = [[] for _ in jobs]
-        ts = [th.Thread(target=run_one, args=(d, o)) for d, o in zip(jobs, outs)]
-        for t in ts:
-            t.start()
-        for t in ts:
-            t.join()
-        return outs
+        return run_concurrently([d["s"] for d in jobs], run_one)
 
     for _ in range(args.warmup):
         step()
@@ -759,6 +753,78 @@ def uneven_main(args, rank, world, local_rank):
         d["s"].close()
 
 
+# --------------------------------------------------------------------------- multi-frequency batch
+def multifreq_main(args, rank, world, local_rank):
+    """One contrast at four illumination frequencies (3, 5, 6, 8 GHz scaled so that the highest has
+    the workload's 10 points per wavelength) on the 512^2 + 32 grid, 60 angles each: one handle and
+    stream per frequency, driven concurrently.  A step is the data term and its gradient summed
+    over frequencies (set_contrast, forward, misfit, adjoint, gradient for every frequency and
+    angle).  The same steps are also run one frequency after another for comparison."""
+    import torch
+    import workloads as W
+    from paper_2107_03679_gb300.multi import MultiFrequency
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    base = W.WORKLOADS["ellipses576"]
+    ws = W.multifrequency_workloads(base)
+    precision = args.precision or base.precision
+    f_gt, f_step, th, rec = make_inputs(base)
+    B = len(th) if args.angles is None else args.angles
+    th = th[:B]
+    mf = MultiFrequency.from_workloads(ws, batch_max=B, device=dev, precision=precision, maxit=args.maxit,
+                                       arnoldi=args.arnoldi, cycle_type=args.cycle)
+    d_th = torch.from_numpy(th).to(dev)
+    d_rec = torch.from_numpy(rec).to(dev)
+    mf.set_contrast(torch.from_numpy(f_gt).to(dev))
+    ys = [s.sample(u, d_rec) for u, _ in mf.forward(d_th)]
+    d_f = torch.from_numpy(f_step).to(dev)
+    outs = [s.field(B) for s in mf.solvers]
+
+    def concurrent_step():
+        return mf.data_term_gradient(d_f, d_th, d_rec, ys, outs)
+
+    def sequential_step():
+        res = []
+        for i, s in enumerate(mf.solvers):
+            one = MultiFrequency([s]).data_term_gradient(d_f, d_th, d_rec, ys[i:i + 1], outs[i:i + 1])
+            res.append(one)
+        return res
+
+    for _ in range(args.warmup):
+        concurrent_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        loss, grad, infos = concurrent_step()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sequential_step()
+    torch.cuda.synchronize()
+    sec_seq = time.perf_counter() - t0
+    solves = 2 * B * len(ws) * args.steps
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(solves / sec, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "multifreq576", "grid": f"{base.nx}x{base.ny}", "frequencies_GHz": [3, 5, 6, 8],
+                       "points_per_wavelength": [round(w.ppw, 2) for w in ws], "angles": B,
+                       "precision": precision, "cycle": args.cycle.upper(),
+                       "step": "data term + gradient summed over frequencies (forward + adjoint solves)",
+                       "timing": "host wall clock around all streams"},
+            "sequential_value": round(solves / sec_seq, 3),
+            "per_frequency": [{"ppw": round(w.ppw, 2),
+                               "iterations_mean": round(sum(i["iterations"] for i in fw + ad) / len(fw + ad), 1),
+                               "converged": all(i["converged"] for i in fw + ad)}
+                              for w, (fw, ad) in zip(ws, infos)],
+            "loss": loss}))
+    mf.close()
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.cpu_sample:
@@ -780,6 +846,8 @@ def main(argv=None):
             reference_main(args, rank, world)
         elif args.workload == "uneven":
             uneven_main(args, rank, world, local_rank)
+        elif args.workload == "multifreq576":
+            multifreq_main(args, rank, world, local_rank)
         elif args.descent:
             descent_main(args, rank, world, local_rank)
         elif args.fbs:

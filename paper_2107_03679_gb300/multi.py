@@ -1,0 +1,113 @@
+"""Several solver handles at once on one GPU: grids of different sizes (an uneven batch) or one
+contrast at several illumination frequencies (Sec. VI-C reconstructs from four).
+
+Each handle has its own CUDA stream and is driven from its own host thread (the C calls release
+the GIL), so that the kernels of different handles overlap on the GPU: the coarse levels of one
+handle, which cannot fill the GPU alone, run beside the fine levels of another.  This module only
+orders library calls; all arithmetic is in the CUDA library.
+"""
+from __future__ import annotations
+
+import threading
+from typing import Callable, List, Optional, Sequence
+
+import torch
+
+from .solver import Solver
+
+
+def run_concurrently(solvers: Sequence[Solver], fn: Callable[[int, Solver], object]) -> list:
+    """fn(i, solver) for every solver, each in its own host thread with the solver's stream as the
+    current stream; returns the results in order and re-raises the first exception.  Every solver's
+    stream first waits for the caller's current stream (whose work made the inputs), and on return
+    the caller's current stream waits for every solver's stream."""
+    cur = torch.cuda.current_stream()
+    for s in solvers:
+        s.stream.wait_stream(cur)
+    results: list = [None] * len(solvers)
+    errors: list = [None] * len(solvers)
+
+    def body(i: int, s: Solver):
+        try:
+            with torch.cuda.device(s.device), torch.cuda.stream(s.stream):
+                results[i] = fn(i, s)
+        except BaseException as e:  # re-raised in the caller's thread
+            errors[i] = e
+
+    threads = [threading.Thread(target=body, args=(i, s)) for i, s in enumerate(solvers)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for e in errors:
+        if e is not None:
+            raise e
+    for s in solvers:
+        cur.wait_stream(s.stream)
+    return results
+
+
+class MultiFrequency:
+    """One contrast f_d on one grid, illuminated at several wavenumbers k_1..k_F: one handle per
+    frequency (A and the multigrid hierarchy depend on k), all with the same angles and receivers.
+    The data term is the sum over frequencies of 1/2 sum_q ||S u_sc,q - y_q||^2 and its gradient in
+    f_d the sum of the per-frequency gradients (Prop. 1 for each k)."""
+
+    def __init__(self, solvers: Sequence[Solver]):
+        if not solvers:
+            raise ValueError("at least one frequency")
+        shapes = {(s.nx_int, s.ny_int, s.abl) for s in solvers}
+        if len(shapes) != 1:
+            raise ValueError("every frequency must use the same grid")
+        self.solvers = list(solvers)
+
+    @classmethod
+    def from_workloads(cls, workloads, batch_max: int, device: Optional[torch.device] = None, **kw):
+        """One Solver per workload (see workloads.multifrequency_workloads), each on a new stream."""
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        out = []
+        for w in workloads:
+            stream = torch.cuda.Stream(dev)
+            out.append(Solver.from_workload(w, batch_max=batch_max, device=dev, stream=stream, **kw))
+        return cls(out)
+
+    @property
+    def ks(self) -> List[float]:
+        return [s.k for s in self.solvers]
+
+    def close(self):
+        for s in self.solvers:
+            s.close()
+
+    def set_contrast(self, f_d: torch.Tensor) -> None:
+        run_concurrently(self.solvers, lambda i, s: s.set_contrast(f_d))
+
+    def forward(self, theta: torch.Tensor, outs: Optional[List[torch.Tensor]] = None):
+        """Scattered fields of every frequency: a list of ([B][ny][nx], infos)."""
+        res = run_concurrently(self.solvers, lambda i, s: s.forward(theta, out=None if outs is None else outs[i]))
+        cur = torch.cuda.current_stream()
+        for u, _ in res:       # made on a solver's stream, used on the caller's
+            u.record_stream(cur)
+        return res
+
+    def data_term_gradient(self, f_d: torch.Tensor, theta: torch.Tensor, rec: torch.Tensor, ys: Sequence[torch.Tensor],
+                           outs: Optional[List[torch.Tensor]] = None):
+        """Set the contrast, solve the forward and adjoint problems of every frequency and angle, and
+        return (loss summed over frequencies, gradient summed over frequencies, per-frequency
+        (forward infos, adjoint infos)).  ys[i]: [B][M] measurements of frequency i."""
+
+        def one(i, s):
+            s.set_contrast(f_d)
+            u, inf_f = s.forward(theta, out=None if outs is None else outs[i])
+            _, G, loss = s.misfit(u, ys[i], rec)
+            g, inf_a = s.gradient(theta, u, G)
+            return loss, g, (inf_f, inf_a)
+
+        res = run_concurrently(self.solvers, one)
+        cur = torch.cuda.current_stream()
+        for _, g, _ in res:    # made on a solver's stream, used on the caller's
+            g.record_stream(cur)
+        grad = res[0][1]
+        for _, g, _ in res[1:]:
+            grad = grad + g
+        return sum(r[0] for r in res), grad, [r[2] for r in res]

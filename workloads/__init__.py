@@ -20,7 +20,7 @@ Conventions (shared by both sides):
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field, asdict
+from dataclasses import dataclass, field, asdict, replace
 from typing import List, Optional
 
 import numpy as np
@@ -98,6 +98,14 @@ def uneven_workloads() -> List[Workload]:
     spec = [(256, 90, 5, 51), (384, 60, 5, 52), (768, 40, 6, 53), (2048, 16, 8, 54)]
     return [Workload(f"uneven{n}", n, n, n // 16, 10.0, b, -60.0, 60.0, "ellipses", seed, levels=lv,
                      nu1=2, nu2=2, restart=8, tol=1e-6) for n, b, lv, seed in spec]
+
+
+def multifrequency_workloads(w: Workload, freqs=(3.0, 5.0, 6.0, 8.0)) -> List[Workload]:
+    """One contrast illuminated at several frequencies on w's grid (Sec. VI-C uses 3, 5, 6 and 8
+    GHz): the highest frequency has w's points per wavelength, a lower frequency f proportionally
+    more (ppw * f_max / f); everything else, the phantom and its seed included, is w's."""
+    fmax = max(freqs)
+    return [replace(w, name=f"{w.name}@{f:g}", ppw=w.ppw * fmax / f) for f in freqs]
 
 
 def small_workload(name: str = "small", n_int: int = 40, abl: int = 6, ppw: float = 10.0,
