@@ -777,7 +777,7 @@ def multifreq_main(args, rank, world, local_rank):
     d_th = torch.from_numpy(th).to(dev)
     d_rec = torch.from_numpy(rec).to(dev)
     mf.set_contrast(torch.from_numpy(f_gt).to(dev))
-    ys = [s.sample(u, d_rec) for u, _ in mf.forward(d_th)]
+    ys = [s.sample(u, d_rec) for s, (u, _) in zip(mf.solvers, mf.forward(d_th))]
     d_f = torch.from_numpy(f_step).to(dev)
     outs = [s.field(B) for s in mf.solvers]
 

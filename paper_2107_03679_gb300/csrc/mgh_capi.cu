@@ -284,6 +284,10 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   if (const char* e = std::getenv("MGH_WAVE_FILL")) h->wave_lane_ring = std::strcmp(e, "bulk") != 0;
   // MGH_GRAPHS=0 issues every restart cycle's launches directly instead of replaying a CUDA graph
   if (const char* e = std::getenv("MGH_GRAPHS")) h->use_graphs = std::strcmp(e, "0") != 0;
+  // the coarse levels whose fields fit in one block's shared memory run as one kernel per cycle;
+  // MGH_TAIL=0 keeps every level on the level kernels
+  h->tail_l0 = choose_tail_level(*h);
+  if (const char* e = std::getenv("MGH_TAIL")) if (std::strcmp(e, "0") == 0) h->tail_l0 = 0;
   s = build_vcycle_tma(*h);
   if (s != MGH_OK) { free_handle(h); return s; }
   // start from f_d = 0 so that every later call finds a complete operator

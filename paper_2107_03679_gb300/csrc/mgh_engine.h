@@ -67,6 +67,7 @@ struct Handle {
                              // (1 or 2; 0: loads prefetched into registers)
   bool wave_lane_ring = true;  // rings filled per lane by cp.async (else by bulk copies)
   bool use_graphs = true;    // replay each restart cycle's launches from a captured CUDA graph
+  int tail_l0 = 0;           // first level of the one-kernel coarse tail (0: every level by level kernels)
   cudaStream_t gstream = nullptr;  // non-blocking stream the cycle graphs are captured and replayed on
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;  // order gstream after / before `stream`
   size_t csize = 16;         // bytes per complex of the cycle precision
@@ -188,6 +189,11 @@ mgh_status fgmres_df(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info)
 mgh_status fgmres_ss(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
 // device flag set by a kernel whose bounded wait gave up (0 = none)
 constexpr int kErrTimeout = 1;
+
+// mgh_tail.cu: every cycle of levels tail_l0 .. L-1 in one kernel, one block per right-hand side
+// (input lev[tail_l0].b, output lev[tail_l0].vfin; reps cycles of level tail_l0, the first from 0)
+int choose_tail_level(const Handle& h);
+mgh_status launch_tail(Handle& h, int reps, int B, const RhsState* st, bool fp64);
 
 // mgh_inverse.cu: backward and momentum steps of the reconstruction loop (arguments checked by the caller)
 mgh_status tv_prox(Handle& h, const double* fbar, const double* d, double gamma, double lam, int iters,

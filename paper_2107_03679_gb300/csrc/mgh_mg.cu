@@ -1288,6 +1288,7 @@ mgh_status level_cycle(Handle& h, int l, int B, const RhsState* st) {
 // gives the same result every time, so it runs once.
 template <typename T>
 mgh_status level_cycles(Handle& h, int l, int B, const RhsState* st) {
+  if (h.tail_l0 > 0 && l == h.tail_l0) return launch_tail(h, cycle_gamma(h), B, st, sizeof(T) == 8);
   MGH_TRY(level_cycle<T>(h, l, B, st));
   const int gamma = cycle_gamma(h);
   if (gamma == 1 || l == h.L - 1) return MGH_OK;

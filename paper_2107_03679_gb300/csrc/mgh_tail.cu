@@ -1,0 +1,291 @@
+// The coarse tail of the multigrid cycle in one kernel: one thread block per right-hand side runs
+// every cycle of levels l0 .. L-1 (Alg. 2 with its CycleType recursion: damped-Jacobi smoothing,
+// residual, full-weighting restriction, exact coarsest solve, bilinear prolongation and
+// correction) with all of that right-hand side's fields in shared memory.
+//
+// Below some level a multigrid level is too small to fill the GPU: its kernels run for a few
+// microseconds on a few blocks and the cycle is bound by launch latency (the W-cycle visits level l
+// CycleType^(l-1) times per cycle).  From the first level l0 whose fields fit in a block's shared
+// memory on, each right-hand side is independent and small (a 73 x 73 level holds 43 KB of complex
+// FP32), so a block keeps the right-hand side and iterate of every tail level, plus one scratch
+// field, on chip and synchronises with __syncthreads() between the steps of the cycle.
+//
+// Arithmetic is that of the level kernels: Jacobi v <- (1 - w) v + (w / D)(b + (sum of
+// neighbours)/h^2) (the first sweep from v = 0 is (w / D) b), residual b - (D v - (sum)/h^2), the
+// 1/16 [1 2 1; 2 4 2; 1 2 1] restriction onto coarse point (i, j) at fine (2i, 2j), prolongation by
+// parity with weights 1, 1/2, 1/4, every sample outside a grid read as 0, and the coarsest solve
+// as the product with the dense inverse.  A later cycle of a level starts from that level's last
+// iterate (Alg. 2); the exact coarsest solve gives the same result every time, so it runs once
+// per visit of the level above it.
+#include <algorithm>
+
+#include "mgh_engine.h"
+
+namespace mgh {
+
+namespace {
+
+constexpr int kTailThreads = 1024;
+constexpr size_t kTailSmemMax = 200 * 1024;
+
+template <typename T>
+struct TailLevel {
+  const Cx<T>* D;      // diagonal of K_kappa on this level
+  const Cx<T>* wd;     // omega / D
+  int nx, ny, nu1, nu2;
+  int off_b, off_v;    // element offsets of the right-hand side and iterate in shared memory
+  T inv_h2;
+};
+
+template <typename T>
+struct TailArgs {
+  TailLevel<T> lv[kMaxLevels];  // index 0 = level l0
+  int depth;                    // tail levels, the coarsest included (>= 2)
+  int gamma;                    // CycleType
+  int reps;                     // cycles of level l0 (the level above runs it CycleType times)
+  int off_t;                    // scratch field
+  T om1;                        // 1 - omega
+  const Cx<T>* b_in;            // right-hand sides of level l0, b_in + rhs * stride
+  Cx<T>* v_out;                 // results on level l0, v_out + rhs * stride
+  size_t stride;
+  const Cx<T>* kinv;            // coarsest inverse, row-major [nc][nc]
+  const RhsState* st;
+};
+
+template <typename T>
+__device__ __forceinline__ Cx<T> at(const Cx<T>* f, int x, int y, int nx, int ny) {
+  return (x >= 0 && x < nx && y >= 0 && y < ny) ? f[y * nx + x] : czero<T>();
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> nb_sum(const Cx<T>* v, int x, int y, int nx, int ny) {
+  return at(v, x - 1, y, nx, ny) + at(v, x + 1, y, nx, ny) + at(v, x, y - 1, nx, ny) + at(v, x, y + 1, nx, ny);
+}
+
+// `sweeps` damped-Jacobi sweeps on K v = b, from v = 0 when `zero`; the result is left in v.
+template <typename T>
+__device__ void tail_smooth(Cx<T>* sm, const TailLevel<T>& L, Cx<T>* tmp, int sweeps, bool zero, T om1) {
+  Cx<T>* v = sm + L.off_v;
+  const Cx<T>* b = sm + L.off_b;
+  const int n = L.nx * L.ny;
+  int s = 0;
+  if (zero) {
+    for (int k = threadIdx.x; k < n; k += kTailThreads) v[k] = sweeps > 0 ? L.wd[k] * b[k] : czero<T>();
+    __syncthreads();
+    s = 1;
+  }
+  Cx<T>* src = v;
+  Cx<T>* dst = tmp;
+  for (; s < sweeps; ++s) {
+    for (int k = threadIdx.x; k < n; k += kTailThreads) {
+      const int y = k / L.nx, x = k - y * L.nx;
+      const Cx<T> nb = nb_sum(src, x, y, L.nx, L.ny);
+      const Cx<T> bk = b[k];
+      const Cx<T> t = mk<T>(bk.re + L.inv_h2 * nb.re, bk.im + L.inv_h2 * nb.im);
+      const Cx<T> c = src[k], w = L.wd[k];
+      dst[k] = mk<T>(om1 * c.re + w.re * t.re - w.im * t.im, om1 * c.im + w.re * t.im + w.im * t.re);
+    }
+    __syncthreads();
+    Cx<T>* x = src; src = dst; dst = x;
+  }
+  if (src != v) {
+    for (int k = threadIdx.x; k < n; k += kTailThreads) v[k] = src[k];
+    __syncthreads();
+  }
+}
+
+// r = b - K v into the scratch field, then its full-weighting restriction into the next level's b.
+template <typename T>
+__device__ void tail_restrict(Cx<T>* sm, const TailLevel<T>& L, const TailLevel<T>& C, Cx<T>* r) {
+  const Cx<T>* v = sm + L.off_v;
+  const Cx<T>* b = sm + L.off_b;
+  const int n = L.nx * L.ny;
+  for (int k = threadIdx.x; k < n; k += kTailThreads) {
+    const int y = k / L.nx, x = k - y * L.nx;
+    const Cx<T> s = nb_sum(v, x, y, L.nx, L.ny);
+    const Cx<T> kv = L.D[k] * v[k] - L.inv_h2 * s;
+    r[k] = b[k] - kv;
+  }
+  __syncthreads();
+  Cx<T>* bc = sm + C.off_b;
+  const int nc = C.nx * C.ny;
+  const T q16 = T(1) / T(16);
+  for (int k = threadIdx.x; k < nc; k += kTailThreads) {
+    const int cj = k / C.nx, ci = k - cj * C.nx;
+    const int x = 2 * ci, y = 2 * cj;
+    const Cx<T> e = at(r, x - 1, y, L.nx, L.ny) + at(r, x + 1, y, L.nx, L.ny) + at(r, x, y - 1, L.nx, L.ny) +
+                    at(r, x, y + 1, L.nx, L.ny);
+    const Cx<T> c = at(r, x - 1, y - 1, L.nx, L.ny) + at(r, x + 1, y - 1, L.nx, L.ny) +
+                    at(r, x - 1, y + 1, L.nx, L.ny) + at(r, x + 1, y + 1, L.nx, L.ny);
+    const Cx<T> rc = r[y * L.nx + x];
+    bc[k] = mk<T>(q16 * (T(4) * rc.re + T(2) * e.re + c.re), q16 * (T(4) * rc.im + T(2) * e.im + c.im));
+  }
+  __syncthreads();
+}
+
+// v += P e (bilinear by parity; coarse samples outside the coarse grid read as 0).
+template <typename T>
+__device__ void tail_prolong(Cx<T>* sm, const TailLevel<T>& L, const TailLevel<T>& C) {
+  Cx<T>* v = sm + L.off_v;
+  const Cx<T>* e = sm + C.off_v;
+  const int n = L.nx * L.ny;
+  for (int k = threadIdx.x; k < n; k += kTailThreads) {
+    const int y = k / L.nx, x = k - y * L.nx;
+    const int ia = x >> 1, ja = y >> 1;
+    const bool ox = x & 1, oy = y & 1;
+    Cx<T> p;
+    if (!ox && !oy) {
+      p = at(e, ia, ja, C.nx, C.ny);
+    } else if (ox && !oy) {
+      p = T(0.5) * (at(e, ia, ja, C.nx, C.ny) + at(e, ia + 1, ja, C.nx, C.ny));
+    } else if (!ox && oy) {
+      p = T(0.5) * (at(e, ia, ja, C.nx, C.ny) + at(e, ia, ja + 1, C.nx, C.ny));
+    } else {
+      p = T(0.25) * (at(e, ia, ja, C.nx, C.ny) + at(e, ia + 1, ja, C.nx, C.ny) + at(e, ia, ja + 1, C.nx, C.ny) +
+                     at(e, ia + 1, ja + 1, C.nx, C.ny));
+    }
+    v[k] = v[k] + p;
+  }
+  __syncthreads();
+}
+
+// Coarsest level: v = K^{-1} b, one warp per row of the inverse (read from L2), lanes over columns.
+template <typename T>
+__device__ void tail_coarsest(Cx<T>* sm, const TailLevel<T>& L, const Cx<T>* __restrict__ kinv) {
+  const Cx<T>* b = sm + L.off_b;
+  Cx<T>* v = sm + L.off_v;
+  const int n = L.nx * L.ny;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < n; r += kTailThreads / 32) {
+    const Cx<T>* row = kinv + (size_t)r * n;
+    T ar = 0, ai = 0;
+    for (int c = lane; c < n; c += 32) {
+      const Cx<T> k = row[c], x = b[c];
+      ar = fma(k.re, x.re, fma(-k.im, x.im, ar));
+      ai = fma(k.re, x.im, fma(k.im, x.re, ai));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) v[r] = mk<T>(ar, ai);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailArgs<T> a) {
+  const int rhs = blockIdx.x;
+  if (a.st && !a.st[rhs].active) return;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  Cx<T>* sm = reinterpret_cast<Cx<T>*>(tail_smem);
+  Cx<T>* tmp = sm + a.off_t;
+  const TailLevel<T>& top = a.lv[0];
+  const int n0 = top.nx * top.ny;
+  const Cx<T>* bin = a.b_in + rhs * a.stride;
+  for (int k = threadIdx.x; k < n0; k += kTailThreads) sm[top.off_b + k] = bin[k];
+  __syncthreads();
+
+  const int last = a.depth - 1;
+  int cnt[kMaxLevels];
+  bool zero[kMaxLevels];
+  for (int rep = 0; rep < a.reps; ++rep) {
+    // the state (d, down, cnt, zero) is the same in every thread: all of them take every branch
+    int d = 0;
+    bool down = true;
+    zero[0] = rep == 0;
+    while (true) {
+      if (down) {
+        if (d == last) {                       // exact solve, once per visit of the level above
+          tail_coarsest(sm, a.lv[d], a.kinv);
+          --d;
+          down = false;
+          cnt[d] = a.gamma - 1;
+          continue;
+        }
+        tail_smooth(sm, a.lv[d], tmp, a.lv[d].nu1, zero[d], a.om1);
+        tail_restrict(sm, a.lv[d], a.lv[d + 1], tmp);
+        cnt[d] = 0;
+        zero[d + 1] = true;
+        ++d;
+        continue;
+      }
+      if (++cnt[d] < a.gamma) {                // next cycle of level d + 1 from its last iterate
+        zero[d + 1] = false;
+        ++d;
+        down = true;
+        continue;
+      }
+      tail_prolong(sm, a.lv[d], a.lv[d + 1]);
+      tail_smooth(sm, a.lv[d], tmp, a.lv[d].nu2, false, a.om1);
+      if (d == 0) break;
+      --d;
+    }
+  }
+  Cx<T>* vo = a.v_out + rhs * a.stride;
+  for (int k = threadIdx.x; k < n0; k += kTailThreads) vo[k] = sm[top.off_v + k];
+}
+
+// Shared memory of a tail from level l0: right-hand side and iterate of every tail level and one
+// scratch field of the size of level l0.
+template <typename T>
+size_t tail_smem_bytes(const Handle& h, int l0) {
+  size_t e = h.lev[l0].n();
+  for (int l = l0; l < h.L; ++l) e += 2 * h.lev[l].n();
+  return e * sizeof(Cx<T>);
+}
+
+template <typename T>
+mgh_status launch_tail_t(Handle& h, int reps, int B, const RhsState* st) {
+  const int l0 = h.tail_l0;
+  TailArgs<T> a{};
+  int off = 0;
+  for (int l = l0; l < h.L; ++l) {
+    const Level& lv = h.lev[l];
+    TailLevel<T>& t = a.lv[l - l0];
+    t.D = (const Cx<T>*)lv.D;
+    t.wd = (const Cx<T>*)lv.wDinv;
+    t.nx = lv.nx; t.ny = lv.ny;
+    t.nu1 = nu_pre(h, l); t.nu2 = nu_post(h, l);
+    t.inv_h2 = static_cast<T>(1.0 / (lv.h * lv.h));
+    t.off_b = off; off += (int)lv.n();
+    t.off_v = off; off += (int)lv.n();
+  }
+  a.off_t = off;
+  a.depth = h.L - l0;
+  a.gamma = cycle_gamma(h);
+  a.reps = reps;
+  a.om1 = static_cast<T>(1.0 - h.p.omega);
+  a.b_in = (const Cx<T>*)h.lev[l0].b;
+  a.v_out = (Cx<T>*)h.lev[l0].vfin;
+  a.stride = h.lev[l0].n();
+  a.kinv = sizeof(T) == 8 ? (const Cx<T>*)(const void*)h.kinv64r : (const Cx<T>*)(const void*)h.kinv32;
+  a.st = st;
+  const size_t smem = tail_smem_bytes<T>(h, l0);
+  static bool attr = false;
+  if (!attr) {
+    MGH_CUDA(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax));
+    attr = true;
+  }
+  ProfScope ps(h, P_COARSE);
+  k_tail<T><<<B, kTailThreads, smem, h.stream>>>(a);
+  MGH_CHECK_LAUNCH(); h.launches++;
+  return MGH_OK;
+}
+
+}  // namespace
+
+int choose_tail_level(const Handle& h) {
+  for (int l = 1; l + 2 <= h.L; ++l) {
+    const size_t bytes = h.fp64 ? tail_smem_bytes<double>(h, l) : tail_smem_bytes<float>(h, l);
+    if (bytes <= kTailSmemMax) return l;
+  }
+  return 0;
+}
+
+mgh_status launch_tail(Handle& h, int reps, int B, const RhsState* st, bool fp64) {
+  return fp64 ? launch_tail_t<double>(h, reps, B, st) : launch_tail_t<float>(h, reps, B, st);
+}
+
+}  // namespace mgh

@@ -103,3 +103,25 @@ def test_w_cycle_fp64_step_count_matches_oracle():
         steps[gamma] = infos[0]["iterations"]
     assert ref.converged and abs(steps[2] - ref.iterations) <= 1, (steps, ref.iterations)
     assert steps[2] <= steps[1] + 2
+
+
+@pytest.mark.parametrize("precision,gamma,bound", [("fp64", 1, 1e-13), ("fp64", 2, 1e-13), ("mixed32", 1, 1e-5),
+                                                   ("mixed32", 3, 1e-5)])
+def test_one_kernel_coarse_tail_matches_level_kernels(precision, gamma, bound, monkeypatch):
+    """The coarse tail in one kernel (every level from the first that fits in shared memory) gives
+    the cycle of the level-by-level kernels (MGH_TAIL=0): same FP64 arithmetic to rounding, FP32
+    within the FP32 cycle's bound; on this grid the tail starts at level 1."""
+    torch = torch_cuda()
+    w = ragged(levels=4, precision=precision)
+    p, f, o = oracle_solver(w, nu1=[2, 1, 1, 0], nu2=[1, 2, 1, 0], cycle_type=gamma)
+    b = W.random_field((3, p.ny, p.nx), 15)
+    z = {}
+    for tail in ("1", "0"):
+        monkeypatch.setenv("MGH_TAIL", tail)
+        s = make_solver(w, B=3, nu1=[2, 1, 1], nu2=[1, 2, 1], cycle_type=gamma)
+        s.set_contrast(to_t(f, torch))
+        z[tail] = s.precondition(to_t(b, torch)).cpu().numpy()
+        s.close()
+    for q in range(3):
+        assert rel(z["1"][q], z["0"][q]) < bound
+        assert rel(z["1"][q], o.M(b[q])) < (1e-12 if precision == "fp64" else 1e-5)
