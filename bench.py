@@ -813,6 +813,7 @@ def multifreq_main(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": "multifreq576", "grid": f"{base.nx}x{base.ny}", "frequencies_GHz": [3, 5, 6, 8],
                        "points_per_wavelength": [round(w.ppw, 2) for w in ws], "angles": B,
+                       "sweeps_per_level": [list(s.nu_levels) for s in mf.solvers],
                        "precision": precision, "cycle": args.cycle.upper(),
                        "step": "data term + gradient summed over frequencies (forward + adjoint solves)",
                        "timing": "host wall clock around all streams"},

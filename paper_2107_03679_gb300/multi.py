@@ -14,6 +14,7 @@ from typing import Callable, List, Optional, Sequence
 import torch
 
 from .solver import Solver
+from .sweeps import smoothing_sweeps
 
 
 def run_concurrently(solvers: Sequence[Solver], fn: Callable[[int, Solver], object]) -> list:
@@ -62,13 +63,21 @@ class MultiFrequency:
         self.solvers = list(solvers)
 
     @classmethod
-    def from_workloads(cls, workloads, batch_max: int, device: Optional[torch.device] = None, **kw):
-        """One Solver per workload (see workloads.multifrequency_workloads), each on a new stream."""
+    def from_workloads(cls, workloads, batch_max: int, device: Optional[torch.device] = None,
+                       lfa_sweeps: bool = True, **kw):
+        """One Solver per workload (see workloads.multifrequency_workloads), each on a new stream.
+        With lfa_sweeps, each frequency's per-level sweep counts come from smoothing_sweeps (the
+        same hierarchy meets a different k h on every level at every frequency)."""
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         out = []
         for w in workloads:
             stream = torch.cuda.Stream(dev)
-            out.append(Solver.from_workload(w, batch_max=batch_max, device=dev, stream=stream, **kw))
+            args = dict(kw)
+            if lfa_sweeps:
+                shift = complex(w.shift_re, w.shift_im)
+                args.setdefault("nu1", smoothing_sweeps(w.k, w.h, w.levels, w.nu1, w.omega, shift))
+                args.setdefault("nu2", smoothing_sweeps(w.k, w.h, w.levels, w.nu2, w.omega, shift))
+            out.append(Solver.from_workload(w, batch_max=batch_max, device=dev, stream=stream, **args))
         return cls(out)
 
     @property

@@ -53,6 +53,9 @@ class Solver:
             for l in range(len(n2)):
                 p.nu2_level[l] = n2[l]
         p.cycle_type = capi.CYCLES[cycle_type] if isinstance(cycle_type, str) else int(cycle_type)
+        # (pre, post) sweeps of every level above the coarsest
+        self.nu_levels = [(p.nu1_level[l], p.nu2_level[l]) if p.nu_per_level else (p.nu1, p.nu2)
+                          for l in range(levels - 1)]
         p.restart, p.maxit, p.tol = restart, maxit, tol
         p.precision = capi.PRECISIONS[precision]
         p.batch_max = batch_max
