@@ -33,7 +33,10 @@ struct TailLevel {
   const Cx<T>* D;      // diagonal of K_kappa on this level
   const Cx<T>* wd;     // omega / D
   int nx, ny, nu1, nu2;
-  int off_b, off_v;    // element offsets of the right-hand side and iterate in shared memory
+  int pitch;           // nx + 2: fields carry a border of zeros one point wide
+  int dx, dy;          // a step of kTailThreads points in row-major order: dy rows and dx columns
+  int off_b, off_v;    // element offsets of the right-hand side and iterate (bordered)
+  int off_t;           // scratch field (bordered; on the coarsest level a plain copy of b)
   T inv_h2;
 };
 
@@ -43,7 +46,7 @@ struct TailArgs {
   int depth;                    // tail levels, the coarsest included (>= 2)
   int gamma;                    // CycleType
   int reps;                     // cycles of level l0 (the level above runs it CycleType times)
-  int off_t;                    // scratch field
+  int total;                    // elements of shared memory in use
   T om1;                        // 1 - omega
   const Cx<T>* b_in;            // right-hand sides of level l0, b_in + rhs * stride
   Cx<T>* v_out;                 // results on level l0, v_out + rhs * stride
@@ -52,108 +55,110 @@ struct TailArgs {
   const RhsState* st;
 };
 
-template <typename T>
-__device__ __forceinline__ Cx<T> at(const Cx<T>* f, int x, int y, int nx, int ny) {
-  return (x >= 0 && x < nx && y >= 0 && y < ny) ? f[y * nx + x] : czero<T>();
-}
-
-template <typename T>
-__device__ __forceinline__ Cx<T> nb_sum(const Cx<T>* v, int x, int y, int nx, int ny) {
-  return at(v, x - 1, y, nx, ny) + at(v, x + 1, y, nx, ny) + at(v, x, y - 1, nx, ny) + at(v, x, y + 1, nx, ny);
+// Every interior point of a level once, kTailThreads apart in row-major order: k is the plain
+// index y * nx + x (of the coefficient arrays), i the bordered index (y + 1) * pitch + x + 1.
+// The body runs as body(k, i, x, y).
+template <typename T, typename Body>
+__device__ __forceinline__ void for_points(const TailLevel<T>& L, Body&& body) {
+  const int n = L.nx * L.ny;
+  int y = threadIdx.x / L.nx, x = threadIdx.x - y * L.nx;
+  for (int k = threadIdx.x; k < n; k += kTailThreads) {
+    body(k, k + 2 * y + L.pitch + 1, x, y);
+    x += L.dx;
+    y += L.dy;
+    if (x >= L.nx) { x -= L.nx; ++y; }
+  }
 }
 
 // `sweeps` damped-Jacobi sweeps on K v = b, from v = 0 when `zero`; the result is left in v.
 template <typename T>
-__device__ void tail_smooth(Cx<T>* sm, const TailLevel<T>& L, Cx<T>* tmp, int sweeps, bool zero, T om1) {
+__device__ void tail_smooth(Cx<T>* sm, const TailLevel<T>& L, int sweeps, bool zero, T om1) {
   Cx<T>* v = sm + L.off_v;
   const Cx<T>* b = sm + L.off_b;
-  const int n = L.nx * L.ny;
+  const int P = L.pitch;
   int s = 0;
   if (zero) {
-    for (int k = threadIdx.x; k < n; k += kTailThreads) v[k] = sweeps > 0 ? L.wd[k] * b[k] : czero<T>();
+    for_points(L, [&](int k, int i, int, int) { v[i] = sweeps > 0 ? L.wd[k] * b[i] : czero<T>(); });
     __syncthreads();
     s = 1;
   }
   Cx<T>* src = v;
-  Cx<T>* dst = tmp;
+  Cx<T>* dst = sm + L.off_t;
   for (; s < sweeps; ++s) {
-    for (int k = threadIdx.x; k < n; k += kTailThreads) {
-      const int y = k / L.nx, x = k - y * L.nx;
-      const Cx<T> nb = nb_sum(src, x, y, L.nx, L.ny);
-      const Cx<T> bk = b[k];
+    for_points(L, [&](int k, int i, int, int) {
+      const Cx<T> nb = src[i - 1] + src[i + 1] + src[i - P] + src[i + P];
+      const Cx<T> bk = b[i];
       const Cx<T> t = mk<T>(bk.re + L.inv_h2 * nb.re, bk.im + L.inv_h2 * nb.im);
-      const Cx<T> c = src[k], w = L.wd[k];
-      dst[k] = mk<T>(om1 * c.re + w.re * t.re - w.im * t.im, om1 * c.im + w.re * t.im + w.im * t.re);
-    }
+      const Cx<T> c = src[i], w = L.wd[k];
+      dst[i] = mk<T>(om1 * c.re + w.re * t.re - w.im * t.im, om1 * c.im + w.re * t.im + w.im * t.re);
+    });
     __syncthreads();
     Cx<T>* x = src; src = dst; dst = x;
   }
   if (src != v) {
-    for (int k = threadIdx.x; k < n; k += kTailThreads) v[k] = src[k];
+    for_points(L, [&](int, int i, int, int) { v[i] = src[i]; });
     __syncthreads();
   }
 }
 
 // r = b - K v into the scratch field, then its full-weighting restriction into the next level's b.
 template <typename T>
-__device__ void tail_restrict(Cx<T>* sm, const TailLevel<T>& L, const TailLevel<T>& C, Cx<T>* r) {
+__device__ void tail_restrict(Cx<T>* sm, const TailLevel<T>& L, const TailLevel<T>& C) {
   const Cx<T>* v = sm + L.off_v;
   const Cx<T>* b = sm + L.off_b;
-  const int n = L.nx * L.ny;
-  for (int k = threadIdx.x; k < n; k += kTailThreads) {
-    const int y = k / L.nx, x = k - y * L.nx;
-    const Cx<T> s = nb_sum(v, x, y, L.nx, L.ny);
-    const Cx<T> kv = L.D[k] * v[k] - L.inv_h2 * s;
-    r[k] = b[k] - kv;
-  }
+  Cx<T>* r = sm + L.off_t;
+  const int P = L.pitch;
+  for_points(L, [&](int k, int i, int, int) {
+    const Cx<T> s = v[i - 1] + v[i + 1] + v[i - P] + v[i + P];
+    const Cx<T> kv = L.D[k] * v[i] - L.inv_h2 * s;
+    r[i] = b[i] - kv;
+  });
   __syncthreads();
   Cx<T>* bc = sm + C.off_b;
-  const int nc = C.nx * C.ny;
   const T q16 = T(1) / T(16);
-  for (int k = threadIdx.x; k < nc; k += kTailThreads) {
-    const int cj = k / C.nx, ci = k - cj * C.nx;
-    const int x = 2 * ci, y = 2 * cj;
-    const Cx<T> e = at(r, x - 1, y, L.nx, L.ny) + at(r, x + 1, y, L.nx, L.ny) + at(r, x, y - 1, L.nx, L.ny) +
-                    at(r, x, y + 1, L.nx, L.ny);
-    const Cx<T> c = at(r, x - 1, y - 1, L.nx, L.ny) + at(r, x + 1, y - 1, L.nx, L.ny) +
-                    at(r, x - 1, y + 1, L.nx, L.ny) + at(r, x + 1, y + 1, L.nx, L.ny);
-    const Cx<T> rc = r[y * L.nx + x];
-    bc[k] = mk<T>(q16 * (T(4) * rc.re + T(2) * e.re + c.re), q16 * (T(4) * rc.im + T(2) * e.im + c.im));
-  }
+  for_points(C, [&](int, int ic, int ci, int cj) {
+    const int i = (2 * cj + 1) * P + 2 * ci + 1;   // fine point (2 ci, 2 cj)
+    const Cx<T> e = r[i - 1] + r[i + 1] + r[i - P] + r[i + P];
+    const Cx<T> c = r[i - P - 1] + r[i - P + 1] + r[i + P - 1] + r[i + P + 1];
+    const Cx<T> rc = r[i];
+    bc[ic] = mk<T>(q16 * (T(4) * rc.re + T(2) * e.re + c.re), q16 * (T(4) * rc.im + T(2) * e.im + c.im));
+  });
   __syncthreads();
 }
 
-// v += P e (bilinear by parity; coarse samples outside the coarse grid read as 0).
+// v += P e (bilinear by parity; the zero border supplies coarse samples outside the coarse grid).
 template <typename T>
 __device__ void tail_prolong(Cx<T>* sm, const TailLevel<T>& L, const TailLevel<T>& C) {
   Cx<T>* v = sm + L.off_v;
   const Cx<T>* e = sm + C.off_v;
-  const int n = L.nx * L.ny;
-  for (int k = threadIdx.x; k < n; k += kTailThreads) {
-    const int y = k / L.nx, x = k - y * L.nx;
-    const int ia = x >> 1, ja = y >> 1;
+  const int PC = C.pitch;
+  for_points(L, [&](int, int i, int x, int y) {
+    const int ic = ((y >> 1) + 1) * PC + (x >> 1) + 1;
     const bool ox = x & 1, oy = y & 1;
     Cx<T> p;
     if (!ox && !oy) {
-      p = at(e, ia, ja, C.nx, C.ny);
+      p = e[ic];
     } else if (ox && !oy) {
-      p = T(0.5) * (at(e, ia, ja, C.nx, C.ny) + at(e, ia + 1, ja, C.nx, C.ny));
+      p = T(0.5) * (e[ic] + e[ic + 1]);
     } else if (!ox && oy) {
-      p = T(0.5) * (at(e, ia, ja, C.nx, C.ny) + at(e, ia, ja + 1, C.nx, C.ny));
+      p = T(0.5) * (e[ic] + e[ic + PC]);
     } else {
-      p = T(0.25) * (at(e, ia, ja, C.nx, C.ny) + at(e, ia + 1, ja, C.nx, C.ny) + at(e, ia, ja + 1, C.nx, C.ny) +
-                     at(e, ia + 1, ja + 1, C.nx, C.ny));
+      p = T(0.25) * (e[ic] + e[ic + 1] + e[ic + PC] + e[ic + PC + 1]);
     }
-    v[k] = v[k] + p;
-  }
+    v[i] = v[i] + p;
+  });
   __syncthreads();
 }
 
-// Coarsest level: v = K^{-1} b, one warp per row of the inverse (read from L2), lanes over columns.
+// Coarsest level: v = K^{-1} b, one warp per row of the inverse (read from L2), lanes over columns;
+// b is first copied without its border into the level's scratch field.
 template <typename T>
 __device__ void tail_coarsest(Cx<T>* sm, const TailLevel<T>& L, const Cx<T>* __restrict__ kinv) {
-  const Cx<T>* b = sm + L.off_b;
+  const Cx<T>* bb = sm + L.off_b;
+  Cx<T>* b = sm + L.off_t;
   Cx<T>* v = sm + L.off_v;
+  for_points(L, [&](int k, int i, int, int) { b[k] = bb[i]; });
+  __syncthreads();
   const int n = L.nx * L.ny;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int r = warp; r < n; r += kTailThreads / 32) {
@@ -169,7 +174,10 @@ __device__ void tail_coarsest(Cx<T>* sm, const TailLevel<T>& L, const Cx<T>* __r
       ar += __shfl_xor_sync(0xffffffffu, ar, o);
       ai += __shfl_xor_sync(0xffffffffu, ai, o);
     }
-    if (lane == 0) v[r] = mk<T>(ar, ai);
+    if (lane == 0) {
+      const int ry = r / L.nx, rx = r - ry * L.nx;
+      v[(ry + 1) * L.pitch + rx + 1] = mk<T>(ar, ai);
+    }
   }
   __syncthreads();
 }
@@ -180,11 +188,15 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailArgs<T> a) {
   if (a.st && !a.st[rhs].active) return;
   extern __shared__ __align__(16) unsigned char tail_smem[];
   Cx<T>* sm = reinterpret_cast<Cx<T>*>(tail_smem);
-  Cx<T>* tmp = sm + a.off_t;
+  // zero everything once: the borders are never written afterwards
+  for (int k = threadIdx.x; k < a.total; k += kTailThreads) sm[k] = czero<T>();
+  __syncthreads();
   const TailLevel<T>& top = a.lv[0];
-  const int n0 = top.nx * top.ny;
   const Cx<T>* bin = a.b_in + rhs * a.stride;
-  for (int k = threadIdx.x; k < n0; k += kTailThreads) sm[top.off_b + k] = bin[k];
+  {
+    Cx<T>* b0 = sm + top.off_b;
+    for_points(top, [&](int k, int i, int, int) { b0[i] = bin[k]; });
+  }
   __syncthreads();
 
   const int last = a.depth - 1;
@@ -204,8 +216,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailArgs<T> a) {
           cnt[d] = a.gamma - 1;
           continue;
         }
-        tail_smooth(sm, a.lv[d], tmp, a.lv[d].nu1, zero[d], a.om1);
-        tail_restrict(sm, a.lv[d], a.lv[d + 1], tmp);
+        tail_smooth(sm, a.lv[d], a.lv[d].nu1, zero[d], a.om1);
+        tail_restrict(sm, a.lv[d], a.lv[d + 1]);
         cnt[d] = 0;
         zero[d + 1] = true;
         ++d;
@@ -218,41 +230,54 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailArgs<T> a) {
         continue;
       }
       tail_prolong(sm, a.lv[d], a.lv[d + 1]);
-      tail_smooth(sm, a.lv[d], tmp, a.lv[d].nu2, false, a.om1);
+      tail_smooth(sm, a.lv[d], a.lv[d].nu2, false, a.om1);
       if (d == 0) break;
       --d;
     }
   }
   Cx<T>* vo = a.v_out + rhs * a.stride;
-  for (int k = threadIdx.x; k < n0; k += kTailThreads) vo[k] = sm[top.off_v + k];
+  const Cx<T>* v0 = sm + top.off_v;
+  for_points(top, [&](int k, int i, int, int) { vo[k] = v0[i]; });
 }
 
-// Shared memory of a tail from level l0: right-hand side and iterate of every tail level and one
-// scratch field of the size of level l0.
+// Shared-memory layout of a tail from level l0 (element offsets per level; returns the total):
+// bordered right-hand side, iterate and scratch field on every level above the coarsest; on the
+// coarsest, bordered right-hand side and iterate and a plain copy of the right-hand side.
+template <typename T>
+int tail_layout(const Handle& h, int l0, TailLevel<T>* lv) {
+  int off = 0;
+  for (int l = l0; l < h.L; ++l) {
+    const Level& L = h.lev[l];
+    const int ps = (L.nx + 2) * (L.ny + 2);
+    TailLevel<T> t{};
+    t.nx = L.nx; t.ny = L.ny; t.pitch = L.nx + 2;
+    t.dx = kTailThreads % L.nx; t.dy = kTailThreads / L.nx;
+    t.off_b = off; off += ps;
+    t.off_v = off; off += ps;
+    t.off_t = off; off += l + 1 < h.L ? ps : (int)L.n();
+    if (lv) lv[l - l0] = t;
+  }
+  return off;
+}
+
 template <typename T>
 size_t tail_smem_bytes(const Handle& h, int l0) {
-  size_t e = h.lev[l0].n();
-  for (int l = l0; l < h.L; ++l) e += 2 * h.lev[l].n();
-  return e * sizeof(Cx<T>);
+  return (size_t)tail_layout<T>(h, l0, nullptr) * sizeof(Cx<T>);
 }
 
 template <typename T>
 mgh_status launch_tail_t(Handle& h, int reps, int B, const RhsState* st) {
   const int l0 = h.tail_l0;
   TailArgs<T> a{};
-  int off = 0;
+  a.total = tail_layout<T>(h, l0, a.lv);
   for (int l = l0; l < h.L; ++l) {
     const Level& lv = h.lev[l];
     TailLevel<T>& t = a.lv[l - l0];
     t.D = (const Cx<T>*)lv.D;
     t.wd = (const Cx<T>*)lv.wDinv;
-    t.nx = lv.nx; t.ny = lv.ny;
     t.nu1 = nu_pre(h, l); t.nu2 = nu_post(h, l);
     t.inv_h2 = static_cast<T>(1.0 / (lv.h * lv.h));
-    t.off_b = off; off += (int)lv.n();
-    t.off_v = off; off += (int)lv.n();
   }
-  a.off_t = off;
   a.depth = h.L - l0;
   a.gamma = cycle_gamma(h);
   a.reps = reps;
@@ -262,7 +287,7 @@ mgh_status launch_tail_t(Handle& h, int reps, int B, const RhsState* st) {
   a.stride = h.lev[l0].n();
   a.kinv = sizeof(T) == 8 ? (const Cx<T>*)(const void*)h.kinv64r : (const Cx<T>*)(const void*)h.kinv32;
   a.st = st;
-  const size_t smem = tail_smem_bytes<T>(h, l0);
+  const size_t smem = (size_t)a.total * sizeof(Cx<T>);
   static bool attr = false;
   if (!attr) {
     MGH_CUDA(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax));
