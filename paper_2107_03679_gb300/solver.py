@@ -6,6 +6,7 @@ layout of mgh_cdouble), shaped [B, ny, nx] on the extended grid.
 """
 from __future__ import annotations
 
+import numbers
 from typing import List, Optional, Sequence
 
 import torch
@@ -23,6 +24,40 @@ def resolve_arnoldi(arnoldi: str, precision: str, restart: int) -> str:
     return "sstep" if restart <= 8 else "df"
 
 
+def make_params(nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: float = 0.15, shift=(1.0, 0.5),
+                levels: int = 4, nu1=1, nu2=1, omega: float = 0.8, restart: int = 20, maxit: int = 5000,
+                tol: float = 1e-6, precision: str = "mixed32", batch_max: int = 1, arnoldi: str = "auto",
+                krylov: str = "fgmres", cycle_type=1):
+    """The mgh_params of a solver (host only) and the resolved Arnoldi engine.  nu1 / nu2: one
+    count for every level, or one per level above the coarsest (per-level fields of mgh_params)."""
+    p = capi.mgh_params()
+    p.nx_int, p.ny_int, p.abl = nx_int, ny_int, abl
+    p.h, p.k, p.beta = h, k, beta
+    p.shift_re, p.shift_im = float(shift[0]), float(shift[1])
+    p.levels, p.omega = levels, omega
+    scalar = lambda v: isinstance(v, numbers.Integral)
+    if scalar(nu1) and scalar(nu2):
+        p.nu1, p.nu2 = int(nu1), int(nu2)
+    else:
+        n1 = [int(nu1)] * levels if scalar(nu1) else [int(v) for v in nu1]
+        n2 = [int(nu2)] * levels if scalar(nu2) else [int(v) for v in nu2]
+        if len(n1) < levels - 1 or len(n2) < levels - 1 or max(len(n1), len(n2)) > capi.MGH_MAX_LEVELS:
+            raise ValueError("per-level sweeps need one count per level above the coarsest")
+        p.nu1, p.nu2, p.nu_per_level = n1[0], n2[0], 1
+        for l, v in enumerate(n1):
+            p.nu1_level[l] = v
+        for l, v in enumerate(n2):
+            p.nu2_level[l] = v
+    p.cycle_type = capi.CYCLES[cycle_type] if isinstance(cycle_type, str) else int(cycle_type)
+    p.restart, p.maxit, p.tol = restart, maxit, tol
+    p.precision = capi.PRECISIONS[precision]
+    p.batch_max = batch_max
+    resolved = resolve_arnoldi(arnoldi, precision, restart)
+    p.arnoldi = capi.ARNOLDI[resolved]
+    p.krylov = capi.KRYLOV[krylov]
+    return p, resolved
+
+
 class Solver:
     """Batched MG-preconditioned FGMRES solver for one discretised Helmholtz problem (Sec. IV)."""
 
@@ -35,34 +70,12 @@ class Solver:
         is ignored); cycle_type: CycleType of Alg. 2 (1 = V, 2 = W, 3; or "v" / "w")."""
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        p = capi.mgh_params()
-        p.nx_int, p.ny_int, p.abl = nx_int, ny_int, abl
-        p.h, p.k, p.beta = h, k, beta
-        p.shift_re, p.shift_im = float(shift[0]), float(shift[1])
-        p.levels, p.omega = levels, omega
-        if isinstance(nu1, int) and isinstance(nu2, int):
-            p.nu1, p.nu2 = nu1, nu2
-        else:
-            n1 = [nu1] * levels if isinstance(nu1, int) else list(nu1)
-            n2 = [nu2] * levels if isinstance(nu2, int) else list(nu2)
-            if len(n1) < levels - 1 or len(n2) < levels - 1 or max(len(n1), len(n2)) > capi.MGH_MAX_LEVELS:
-                raise ValueError("per-level sweeps need one count per level above the coarsest")
-            p.nu1, p.nu2, p.nu_per_level = n1[0], n2[0], 1
-            for l in range(len(n1)):
-                p.nu1_level[l] = n1[l]
-            for l in range(len(n2)):
-                p.nu2_level[l] = n2[l]
-        p.cycle_type = capi.CYCLES[cycle_type] if isinstance(cycle_type, str) else int(cycle_type)
+        p, self.arnoldi = make_params(nx_int, ny_int, abl, h, k, beta, shift, levels, nu1, nu2, omega, restart, maxit,
+                                      tol, precision, batch_max, arnoldi, krylov, cycle_type)
         # (pre, post) sweeps of every level above the coarsest
         self.nu_levels = [(p.nu1_level[l], p.nu2_level[l]) if p.nu_per_level else (p.nu1, p.nu2)
                           for l in range(levels - 1)]
-        p.restart, p.maxit, p.tol = restart, maxit, tol
-        p.precision = capi.PRECISIONS[precision]
-        p.batch_max = batch_max
-        self.arnoldi = resolve_arnoldi(arnoldi, precision, restart)
-        p.arnoldi = capi.ARNOLDI[self.arnoldi]
         self.krylov = krylov
-        p.krylov = capi.KRYLOV[krylov]
         self.params = p
         self.precision = precision
         self.nx_int, self.ny_int, self.abl = nx_int, ny_int, abl

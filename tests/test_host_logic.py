@@ -1,0 +1,99 @@
+"""Host-side logic of the package, on the CPU: solver parameters (cycle type, per-level sweeps)
+validated by the library's own host check, and the order of calls and the buffers of the FBS
+driver (Alg. 4), run against a fake solver whose steps are the oracle's."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+import paper_2107_03679_gb300.capi as capi
+from paper_2107_03679_gb300.solver import make_params
+from paper_2107_03679_gb300.reconstruct import fbs
+
+
+def test_make_params_uniform_and_per_level_sweeps():
+    p, arnoldi = make_params(128, 128, 16, 1.0, 2 * math.pi / 10, levels=4, nu1=2, nu2=1, restart=8)
+    assert arnoldi == "sstep" and p.nu_per_level == 0 and (p.nu1, p.nu2) == (2, 1)
+    assert capi.mgh_workspace_bytes(p) > 0
+    p, _ = make_params(128, 128, 16, 1.0, 2 * math.pi / 10, levels=4, nu1=np.array([2, 1, 0]),
+                       nu2=[0, 1, 2], cycle_type="w", precision="fp64")
+    assert p.nu_per_level == 1 and list(p.nu1_level)[:3] == [2, 1, 0] and list(p.nu2_level)[:3] == [0, 1, 2]
+    assert p.cycle_type == 2 and p.precision == capi.MGH_PREC_FP64
+    assert capi.mgh_workspace_bytes(p) > 0
+    with pytest.raises(ValueError):
+        make_params(128, 128, 16, 1.0, 0.6, levels=4, nu1=[2, 1], nu2=2)
+    bad, _ = make_params(128, 128, 16, 1.0, 0.6, levels=4, nu1=[2, 5, 1], nu2=2)
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(bad)
+
+
+class FakeSolver:
+    """The calls fbs() makes, on CPU tensors: per angle q the data term 1/2 ||f - C_q||^2 (C_q is
+    the real part of y[q]), the TV prox of the oracle and the momentum step written out."""
+
+    def __init__(self, shape):
+        self.device = torch.device("cpu")
+        self.shape = shape
+        self.f = None
+        self.calls = []
+
+    def set_contrast(self, f):
+        self.f = f.clone()
+        self.calls.append("set_contrast")
+
+    def field(self, B):
+        return torch.zeros((B, 1), dtype=torch.complex128)
+
+    def forward(self, th, out=None):
+        self.calls.append("forward")
+        return out, [dict(iterations=1, converged=True)] * th.numel()
+
+    def misfit(self, u, y, rec):
+        self.calls.append("misfit")
+        self.C = [y[q].real.reshape(self.shape) for q in range(y.shape[0])]
+        loss = sum(0.5 * float(torch.sum((self.f - c) ** 2)) for c in self.C)
+        return None, None, loss
+
+    def gradient(self, th, u, G):
+        self.calls.append("gradient")
+        return sum(self.f - c for c in self.C), [dict(iterations=1, converged=True)] * th.numel()
+
+    def tv_prox(self, fbar, d, gamma, lam, iters, out=None):
+        self.calls.append("tv_prox")
+        out[:] = torch.from_numpy(O.tv_prox((fbar - gamma * d).numpy(), lam, iters))
+        return out
+
+    def fbs_momentum(self, f, f_prev, c, out=None):
+        self.calls.append("fbs_momentum")
+        out[:] = f + c * (f - f_prev)
+        return out
+
+
+def test_fbs_driver_follows_the_oracle_recursion():
+    shape = (7, 9)
+    rng = np.random.default_rng(3)
+    C = rng.uniform(-0.2, 0.6, size=(5,) + shape)
+    y = torch.from_numpy(C.reshape(5, -1).astype(np.complex128))
+    subsets = W.angle_subsets(5, 2, 6, seed=8)
+    gamma, tau, iters = 0.3, 0.05, 30
+    ref_losses = []
+
+    def grad_fn(f, idx):
+        ref_losses.append(sum(0.5 * float(np.sum((f - C[q]) ** 2)) for q in idx))
+        return sum(f - C[q] for q in idx)
+
+    ref = O.fbs(grad_fn, np.zeros(shape), subsets, gamma, tau, prox_iters=iters)
+    s = FakeSolver(shape)
+    seen = []
+    f, losses, infos = fbs(s, torch.arange(5, dtype=torch.float64), torch.zeros(1, dtype=torch.int64), y,
+                           torch.zeros(shape, dtype=torch.float64), subsets, gamma, tau, prox_iters=iters,
+                           callback=lambda it, fk, loss: seen.append(fk.clone()))
+    np.testing.assert_allclose(f.numpy(), ref, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(losses, ref_losses, rtol=1e-14)
+    assert len(infos) == len(subsets) and len(seen) == len(subsets)
+    assert torch.equal(seen[-1], f)
+    assert s.calls[:6] == ["set_contrast", "forward", "misfit", "gradient", "tv_prox", "fbs_momentum"]
+    assert float(f.min()) >= 0.0
