@@ -113,3 +113,11 @@ namespace mgh { void set_error(const char* what, cudaError_t e, const char* file
     mgh_status s_ = (expr);                                              \
     if (s_ != MGH_OK) return s_;                                         \
   } while (0)
+// A one-time set-up step (kernel attributes) run once per process, also when several host threads
+// drive handles at the same time: a function-local static is initialised exactly once (C++11), and
+// every call returns the step's status.  The arguments are the statements of the step.
+#define MGH_ONCE(...)                                                                      \
+  do {                                                                                     \
+    static const mgh_status once_ = [&]() -> mgh_status { __VA_ARGS__ return MGH_OK; }(); \
+    if (once_ != MGH_OK) return once_;                                                    \
+  } while (0)

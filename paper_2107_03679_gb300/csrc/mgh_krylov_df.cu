@@ -1047,12 +1047,7 @@ mgh_status set_smem(K kern) {
 
 template <int NV>
 mgh_status df_step_nv(Handle& h, const KArgs& a, int j, int B) {
-  static bool init = false;
-  if (!init) {
-    MGH_TRY(set_smem(k_df_pass1<NV>));
-    MGH_TRY(set_smem(k_df_pass2<NV>));
-    init = true;
-  }
+  MGH_ONCE(MGH_TRY(set_smem(k_df_pass1<NV>)); MGH_TRY(set_smem(k_df_pass2<NV>)););
   const dim3 grid(a.nblk, B);
   float2* V = reinterpret_cast<float2*>(h.V);
   float2* W = reinterpret_cast<float2*>(h.W);
@@ -1222,11 +1217,7 @@ namespace {
 
 template <int NV>
 mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
-  static bool init = false;
-  if (!init) {
-    MGH_TRY(set_smem(k_ss_gram<NV>));
-    init = true;
-  }
+  MGH_ONCE(MGH_TRY(set_smem(k_ss_gram<NV>)););
   const dim3 grid(a.nblk, B);
   float2* V = reinterpret_cast<float2*>(h.V);
   for (int k = 0; k < a.m; ++k) {

@@ -903,11 +903,7 @@ mgh_status pre_ring_go(Handle& h, int l, const cf* bin, size_t b_stride, const d
   auto kern = wave::k_pre_wt<NU, NW, MS>;
   constexpr int S = wave::RingLen<wave::PreW<NU, 1>::P, NU, MS>::S;
   constexpr size_t smem = wave::RingSmem<NW, S>::bytes();
-  static bool attr = false;
-  if (!attr) {
-    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)););
   const dim3 grid((nwarps + NW - 1) / NW, 1, B);
   kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.D, (const cf*)lv.wDinv,
                                           (cf*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx,
@@ -925,11 +921,7 @@ mgh_status post_ring_go(Handle& h, int l, const cf* bin, size_t b_stride, const 
   auto kern = wave::k_post_wt<NU, NW, MS>;
   constexpr int S = wave::RingLen<wave::PostW<NU, 1>::P, NU, MS>::S;
   constexpr size_t smem = wave::RingSmem<NW, S>::bytes();
-  static bool attr = false;
-  if (!attr) {
-    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)););
   const dim3 grid((nwarps + NW - 1) / NW, 1, B);
   kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.wDinv,
                                           (const cf*)lv.vpre, lv.n(), (const cf*)cl.vfin, cl.n(), cl.nx, cl.ny, out,
@@ -946,11 +938,7 @@ mgh_status pre_lane_go(Handle& h, int l, const cf* bin, size_t b_stride, const d
   auto kern = wave::k_pre_wa<NU, NW, MS>;
   constexpr int S = wave::RingLen<wave::PreW<NU, 1>::P, NU, MS>::S;
   constexpr size_t smem = wave::LaneRingSmem<NW, S>::bytes();
-  static bool attr = false;
-  if (!attr) {
-    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)););
   const dim3 grid((nwarps + NW - 1) / NW, 1, B);
   kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.D, (const cf*)lv.wDinv,
                                           (cf*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx,
@@ -968,11 +956,7 @@ mgh_status post_lane_go(Handle& h, int l, const cf* bin, size_t b_stride, const 
   auto kern = wave::k_post_wa<NU, NW, MS>;
   constexpr int S = wave::RingLen<wave::PostW<NU, 1>::P, NU, MS>::S;
   constexpr size_t smem = wave::LaneRingSmem<NW, S>::bytes();
-  static bool attr = false;
-  if (!attr) {
-    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)););
   const dim3 grid((nwarps + NW - 1) / NW, 1, B);
   kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.wDinv,
                                           (const cf*)lv.vpre, lv.n(), (const cf*)cl.vfin, cl.n(), cl.nx, cl.ny, out,
@@ -1012,14 +996,11 @@ mgh_status launch_pre_wave(Handle& h, int l, const cf* bin, size_t b_stride, con
                            : (h.wave_ring >= 2 ? wave::RingLen<wave::PreW<NU, 1>::P, NU, 2>::S
                                                : wave::RingLen<wave::PreW<NU, 1>::P, NU, 1>::S);
   const int nstrips = (lv.nx + G::XO - 1) / G::XO;
-  static long resident = -1;
-  if (resident < 0) {
-    constexpr int S1 = wave::RingLen<wave::PreW<NU, 1>::P, NU, 1>::S;
-    auto kern = wave::k_pre_wa<NU, 4, 1>;
-    constexpr size_t smem = wave::LaneRingSmem<4, S1>::bytes();
-    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    resident = resident_warps(h, kern, 128, smem);
-  }
+  constexpr int S1 = wave::RingLen<wave::PreW<NU, 1>::P, NU, 1>::S;
+  constexpr size_t smem1 = wave::LaneRingSmem<4, S1>::bytes();
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(wave::k_pre_wa<NU, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem1)););
+  static const long resident = resident_warps(h, wave::k_pre_wa<NU, 4, 1>, 128, smem1);
   const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * G::H - 1, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
@@ -1051,14 +1032,11 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
                            : (h.wave_ring >= 2 ? wave::RingLen<wave::PostW<NU, 1>::P, NU, 2>::S
                                                : wave::RingLen<wave::PostW<NU, 1>::P, NU, 1>::S);
   const int nstrips = (lv.nx + G::XO - 1) / G::XO;
-  static long resident = -1;
-  if (resident < 0) {
-    constexpr int S1 = wave::RingLen<wave::PostW<NU, 1>::P, NU, 1>::S;
-    auto kern = wave::k_post_wa<NU, 4, 1>;
-    constexpr size_t smem = wave::LaneRingSmem<4, S1>::bytes();
-    MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    resident = resident_warps(h, kern, 128, smem);
-  }
+  constexpr int S1 = wave::RingLen<wave::PostW<NU, 1>::P, NU, 1>::S;
+  constexpr size_t smem1 = wave::LaneRingSmem<4, S1>::bytes();
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(wave::k_post_wa<NU, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem1)););
+  static const long resident = resident_warps(h, wave::k_post_wa<NU, 4, 1>, 128, smem1);
   const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * NU, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
@@ -1092,11 +1070,7 @@ mgh_status launch_pre_nu(Handle& h, int l, const void* bin, size_t b_stride, con
     if (tma) {
       using G = PreGeom<NU, 64, 16>;
       auto kern = k_pre_t<NU, 64, 16, kVcThreadsTma>;
-      static bool attr = false;
-      if (!attr) {
-        MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem()));
-        attr = true;
-      }
+      MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem())););
       TileWalk tw;
       tw.ntx = (lv.nx + 63) / 64; tw.nty = (lv.ny + 15) / 16; tw.per_rhs = tw.ntx * tw.nty; tw.total = tw.per_rhs * B;
       tw.st = st;
@@ -1156,11 +1130,7 @@ mgh_status launch_post_nu(Handle& h, int l, const void* bin, size_t b_stride, co
     if (tma) {
       using G = PostGeom<NU, 64, 16>;
       auto kern = k_post_t<NU, 64, 16, kVcThreadsTma>;
-      static bool attr = false;
-      if (!attr) {
-        MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem()));
-        attr = true;
-      }
+      MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem())););
       TileWalk tw;
       tw.ntx = (lv.nx + 63) / 64; tw.nty = (lv.ny + 15) / 16; tw.per_rhs = tw.ntx * tw.nty; tw.total = tw.per_rhs * B;
       tw.st = st;
@@ -1342,16 +1312,14 @@ mgh_status vcycle_f32in(Handle& h, const cf* in, size_t in_stride, const double*
 namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return nullptr;
+  }();
   return fn;
 }
 

@@ -288,11 +288,7 @@ mgh_status launch_tail_t(Handle& h, int reps, int B, const RhsState* st) {
   a.kinv = sizeof(T) == 8 ? (const Cx<T>*)(const void*)h.kinv64r : (const Cx<T>*)(const void*)h.kinv32;
   a.st = st;
   const size_t smem = (size_t)a.total * sizeof(Cx<T>);
-  static bool attr = false;
-  if (!attr) {
-    MGH_CUDA(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax));
-    attr = true;
-  }
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax)););
   ProfScope ps(h, P_COARSE);
   k_tail<T><<<B, kTailThreads, smem, h.stream>>>(a);
   MGH_CHECK_LAUNCH(); h.launches++;
