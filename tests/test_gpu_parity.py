@@ -400,7 +400,8 @@ def test_ellipses576_mixed_field_matches_fp64_path():
     """The bench configuration's field error: two angles of the full-size workload solved by the
     mixed path (FP32 cycle, s-step cycles) and by the plain FP64 path, both to a true relative
     residual of 1e-8; the two fields agree to well within the mixed tolerance of 1e-5.  The
-    measured difference is written to gpurun_out/ for the design notes when that folder exists."""
+    measured difference is written to $MGH_TEST_REPORT_DIR/mixed_vs_fp64_ellipses576.txt when that
+    variable names a directory."""
     torch = torch_cuda()
     w = W.WORKLOADS["ellipses576"]
     f = W.phantom(w)
@@ -416,8 +417,9 @@ def test_ellipses576_mixed_field_matches_fp64_path():
     d = max(rel(out["mixed32"][q], out["fp64"][q]) for q in range(2))
     assert d < 1e-5, d
     import os
-    if os.path.isdir("gpurun_out"):
-        with open("gpurun_out/mixed_vs_fp64_ellipses576.txt", "w") as fh:
+    report = os.environ.get("MGH_TEST_REPORT_DIR")
+    if report and os.path.isdir(report):
+        with open(os.path.join(report, "mixed_vs_fp64_ellipses576.txt"), "w") as fh:
             fh.write(f"{d:.3e}\n")
 
 
