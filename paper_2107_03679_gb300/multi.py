@@ -21,16 +21,22 @@ def run_concurrently(solvers: Sequence[Solver], fn: Callable[[int, Solver], obje
     """fn(i, solver) for every solver, each in its own host thread with the solver's stream as the
     current stream; returns the results in order and re-raises the first exception.  Every solver's
     stream first waits for the caller's current stream (whose work made the inputs), and on return
-    the caller's current stream waits for every solver's stream."""
-    cur = torch.cuda.current_stream()
-    for s in solvers:
-        s.stream.wait_stream(cur)
+    the caller's current stream waits for every solver's stream.  Objects without a CUDA stream
+    (stream None) are run in threads with no stream ordering."""
+    cuda = all(getattr(s, "stream", None) is not None for s in solvers)
+    if cuda:
+        cur = torch.cuda.current_stream()
+        for s in solvers:
+            s.stream.wait_stream(cur)
     results: list = [None] * len(solvers)
     errors: list = [None] * len(solvers)
 
-    def body(i: int, s: Solver):
+    def body(i: int, s):
         try:
-            with torch.cuda.device(s.device), torch.cuda.stream(s.stream):
+            if cuda:
+                with torch.cuda.device(s.device), torch.cuda.stream(s.stream):
+                    results[i] = fn(i, s)
+            else:
                 results[i] = fn(i, s)
         except BaseException as e:  # re-raised in the caller's thread
             errors[i] = e
@@ -43,8 +49,9 @@ def run_concurrently(solvers: Sequence[Solver], fn: Callable[[int, Solver], obje
     for e in errors:
         if e is not None:
             raise e
-    for s in solvers:
-        cur.wait_stream(s.stream)
+    if cuda:
+        for s in solvers:
+            cur.wait_stream(s.stream)
     return results
 
 

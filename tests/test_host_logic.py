@@ -1,6 +1,8 @@
 """Host-side logic of the package, on the CPU: solver parameters (cycle type, per-level sweeps)
-validated by the library's own host check, and the order of calls and the buffers of the FBS
-driver (Alg. 4), run against a fake solver whose steps are the oracle's."""
+validated by the library's own host check; the order of calls and the buffers of the FBS driver
+(Alg. 4), run against a fake solver whose steps are the oracle's; the threads of the concurrent
+multi-handle driver (results in order, the first exception re-raised); the multi-frequency
+workloads."""
 import math
 
 import numpy as np
@@ -97,3 +99,42 @@ def test_fbs_driver_follows_the_oracle_recursion():
     assert torch.equal(seen[-1], f)
     assert s.calls[:6] == ["set_contrast", "forward", "misfit", "gradient", "tv_prox", "fbs_momentum"]
     assert float(f.min()) >= 0.0
+
+
+def test_run_concurrently_orders_results_and_reraises():
+    import threading
+    from paper_2107_03679_gb300.multi import run_concurrently
+
+    class Job:
+        stream = None
+
+        def __init__(self, k):
+            self.k = k
+
+    seen = set()
+    barrier = threading.Barrier(4, timeout=10)
+
+    def fn(i, job):
+        barrier.wait()            # all four run at the same time, each in its own thread
+        seen.add(threading.get_ident())
+        return job.k * 10 + i
+
+    assert run_concurrently([Job(k) for k in range(4)], fn) == [0, 11, 22, 33]
+    assert len(seen) == 4
+
+    def bad(i, job):
+        if i == 2:
+            raise RuntimeError("frequency 2 failed")
+        return i
+
+    with pytest.raises(RuntimeError, match="frequency 2"):
+        run_concurrently([Job(k) for k in range(3)], bad)
+
+
+def test_multifrequency_workloads_scale_points_per_wavelength():
+    base = W.WORKLOADS["ellipses576"]
+    ws = W.multifrequency_workloads(base)
+    assert [round(w.ppw, 3) for w in ws] == [26.667, 16.0, 13.333, 10.0]
+    assert all(w.nx == base.nx and w.seed == base.seed and w.n_angles == base.n_angles for w in ws)
+    assert np.array_equal(W.phantom(ws[0]), W.phantom(base))
+    assert ws[-1].k == pytest.approx(base.k) and ws[0].k == pytest.approx(base.k * 3 / 8)
