@@ -7,7 +7,7 @@ layout of mgh_cdouble), shaped [B, ny, nx] on the extended grid.
 from __future__ import annotations
 
 import numbers
-from typing import List, Optional, Sequence
+from typing import Optional
 
 import torch
 

@@ -7,7 +7,6 @@ tiles are 64 or 32 wide and 16 high) and ragged batches.  Tolerances:
   * solves: both sides solved to a tight residual, fields within 1e-10 (FP64 path) and 1e-5
     (mixed path), per the reading that two converged solutions differ by at most cond(A)*tol.
 """
-import math
 
 import numpy as np
 import pytest

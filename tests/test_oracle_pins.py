@@ -9,7 +9,6 @@ import math
 
 import numpy as np
 import pytest
-import scipy.sparse.linalg as spla
 import scipy.special as ssp
 
 import oracle as O

@@ -7,7 +7,6 @@ a row, the second with a smaller batch and different data, must both agree with 
 stale scratch entry from the first call cannot leak into the second.  This file is collected
 last on purpose.
 """
-import ctypes
 
 import numpy as np
 import pytest
