@@ -493,3 +493,24 @@ def test_point_source_is_outgoing():
     err_in = np.linalg.norm(u[ring] - g_in) / np.linalg.norm(g_in)
     assert err_out < 0.1
     assert err_in > 1.0
+
+
+def test_flexible_gmres_tolerates_fp16_rounded_preconditioned_vectors():
+    """Flexible GMRES builds x from the stored preconditioned vectors z_j and their products A z_j,
+    so rounding z_j (as FP16 storage would) changes the preconditioner, not the result: FGMRES(8)
+    with the MG cycle's output rounded to half precision reaches the direct solution to the same
+    tolerance in the same number of steps (within 2 %) as with the exact cycle."""
+    w = W.Workload("r", 70, 53, 9, 8.0, 1, 0, 0, "ellipses", 11, levels=4, nu1=2, nu2=2, restart=8, tol=1e-10)
+    p = O.Problem.from_workload(w)
+    f = W.phantom(w)
+    s = O.MGHSolver(p, f, 4, 2, 2, 0.8, 1 + 0.5j, 8, 1e-10, maxit=3000)
+    b = O.rhs(p, f, 0.3)
+    ref = O.direct_solve(p, s.D, b)
+    half = lambda z: z.real.astype(np.float16).astype(np.float64) + 1j * z.imag.astype(np.float16).astype(np.float64)
+    x0, i0 = O.fgmres(s.apply_A, s.M, b, 1e-10, 8, 3000)
+    x1, i1 = O.fgmres(s.apply_A, lambda r: half(s.M(r)), b, 1e-10, 8, 3000)
+    assert i0.converged and i1.converged
+    assert abs(i1.iterations - i0.iterations) <= 0.02 * i0.iterations + 1
+    for x in (x0, x1):
+        assert np.linalg.norm(b - s.apply_A(x)) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-9)
+        assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
