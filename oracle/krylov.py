@@ -154,8 +154,12 @@ def bicgstab(apply_A: Callable, apply_M: Callable, b: np.ndarray, tol: float, ma
     return x, info
 
 
-def sstep_cycle(apply_A: Callable, apply_M: Callable, b: np.ndarray, x: np.ndarray, m: int) -> np.ndarray:
+def sstep_cycle(apply_A: Callable, apply_M: Callable, b: np.ndarray, x: np.ndarray, m: int,
+                gram: Callable = None) -> np.ndarray:
     """One cycle of FGMRES(m) in s-step form from the iterate x; returns the new iterate.
+
+    gram(Vm) returns the Gram matrix Vm^H Vm of the N x (m+1) basis; the default forms it in FP64.
+    A caller may pass a rounded evaluation to study how much accuracy the cycle needs in it.
 
     v_0 = r / ||r||, z_k = M^{-1} v_k, w_k = A z_k, v_{k+1} = w_k / ||w_k||.  With V = [v_0 .. v_m]
     and V^H V = R^H R (Cholesky, R upper), A z_k = ||w_k|| v_{k+1} and r = ||r|| v_0 give
@@ -172,7 +176,7 @@ def sstep_cycle(apply_A: Callable, apply_M: Callable, b: np.ndarray, x: np.ndarr
         wn.append(_norm(w))
         V.append(w / wn[k])
     Vm = np.stack([v.reshape(-1) for v in V], axis=1)          # N x (m+1)
-    G = Vm.conj().T @ Vm
+    G = Vm.conj().T @ Vm if gram is None else gram(Vm)
     R = np.linalg.cholesky(G).conj().T                          # G = R^H R
     H = R[:, 1:] * np.asarray(wn)[None, :]
     y = np.linalg.lstsq(H, beta * R[:, 0], rcond=None)[0]

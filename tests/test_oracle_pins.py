@@ -262,6 +262,65 @@ def test_sstep_cycle_equals_arnoldi_cycle(m):
     assert np.linalg.norm(b - s.apply_A(x_ss)) < r0
 
 
+def _gram_fp32_runs(Vm, run=32, lanes=64):
+    """The Gram matrix as the CUDA s-step sweep forms it: the basis stored in FP32, every product
+    of a pair rounded to FP32 and summed in FP32 in runs of `run` products per lane (a lane takes
+    every `lanes`-th point), the run sums added exactly (here in FP64)."""
+    V = Vm.astype(np.complex64)
+    N, nv = V.shape
+    per = run * lanes
+    pad = (-N) % per
+    G = np.zeros((nv, nv), dtype=np.complex128)
+    for i in range(nv):
+        for j in range(i, nv):
+            P = np.conj(V[:, i]) * V[:, j]
+            P = np.concatenate([P, np.zeros(pad, np.complex64)]).reshape(-1, run, lanes)
+            s = P[:, 0, :].copy()
+            for t in range(1, run):
+                s = (s + P[:, t, :]).astype(np.complex64)
+            G[i, j] = s.astype(np.complex128).sum()
+            G[j, i] = np.conj(G[i, j])
+    return G
+
+
+def test_sstep_cycles_need_only_fp32_gram_sums():
+    """The reading behind the CUDA Gram sweep's FP32 running sums: s-step FGMRES(8) cycles whose
+    Gram matrix is that of the FP32-rounded basis summed in FP32 runs of 32 products take the same
+    steps to 1e-8 as cycles with the exact FP64 Gram matrix, and reach the same residual.  The
+    rounded Gram stays within the recursive-summation bound (run + 1) u32 sum_p |v_i[p]| |v_j[p]|
+    of the Gram of the rounded basis, so its error is a normwise perturbation of size
+    FP32 storage of the basis already makes."""
+    from oracle.krylov import sstep_cycle
+    w = W.Workload("sstep96", 96, 96, 12, 10.0, 1, 0.0, 0.0, "ellipses", 2, levels=4, nu1=2, nu2=2, restart=8)
+    p = O.Problem.from_workload(w)
+    f = W.phantom(w)
+    s = O.MGHSolver(p, f, levels=4, nu1=2, nu2=2, restart=8, tol=1e-8)
+    b = O.rhs(p, f, 0.3)
+    nb = np.linalg.norm(b)
+    out = {}
+    for name, gram in (("fp64", None), ("fp32_runs", _gram_fp32_runs)):
+        x = np.zeros_like(b)
+        steps = 0
+        while np.linalg.norm(b - s.apply_A(x)) > 1e-8 * nb and steps < 2000:
+            x = sstep_cycle(s.apply_A, s.M, b, x, 8, gram=gram)
+            steps += 8
+        out[name] = (steps, np.linalg.norm(b - s.apply_A(x)) / nb)
+    assert out["fp64"][0] < 2000 and out["fp32_runs"][0] == out["fp64"][0], out
+    assert out["fp32_runs"][1] <= 1e-8 and abs(out["fp32_runs"][1] - out["fp64"][1]) <= 1e-2 * out["fp64"][1]
+    # the error model on a basis of this problem (the V-cycle's monomial basis of one cycle)
+    r = b.copy()
+    Vs = [r / np.linalg.norm(r)]
+    for _ in range(8):
+        wv = s.apply_A(s.M(Vs[-1]))
+        Vs.append(wv / np.linalg.norm(wv))
+    Vm = np.stack([v.ravel() for v in Vs], axis=1)
+    V32 = Vm.astype(np.complex64).astype(np.complex128)
+    G_ref = V32.conj().T @ V32
+    bound = 33 * np.finfo(np.float32).eps * (np.abs(V32).T @ np.abs(V32)) * 2
+    err = np.abs(_gram_fp32_runs(Vm) - G_ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
 def test_bicgstab_matches_direct_solve():
     p, f = _small(seed=9)
     s = O.MGHSolver(p, f, levels=2, nu1=1, nu2=1, tol=1e-12, krylov="bicgstab", shift=1.0)
