@@ -27,6 +27,9 @@
  *   - Errors are reported by the return code only; nothing is thrown across the ABI.  On
  *     MGH_INVALID_ARG nothing was launched.  On MGH_CUDA_ERROR the handle should be destroyed.
  *   - A handle is not thread-safe: one host thread at a time per handle.
+ *   - A handle belongs to the CUDA device that was current when mgh_create ran; every later call
+ *     on it must be made with that device current (MGH_INVALID_ARG otherwise).  Handles on
+ *     different devices may be used by one process.
  */
 #ifndef MGH_H
 #define MGH_H
@@ -46,13 +49,19 @@ typedef enum {
   MGH_NOT_CONVERGED = 2,    /* maxit reached for at least one right-hand side; best iterate kept */
   MGH_CUDA_ERROR = 3,       /* a CUDA call failed; the message is in mgh_last_error() */
   MGH_OUT_OF_MEMORY = 4,    /* device allocation failed at create */
-  MGH_TIMEOUT = 5,          /* reserved: a device-side wait gave up */
+  MGH_TIMEOUT = 5,          /* a kernel's bounded device-side wait (an mbarrier of a bulk-copy ring)
+                               gave up and set the handle's device error word; the solve stops at
+                               the next restart and the handle stays usable */
   MGH_NOT_SUPPORTED = 6     /* option not built into this library */
 } mgh_status;
 
 typedef enum {
   MGH_PREC_FP64 = 0,        /* everything in complex FP64 (the plain form) */
-  MGH_PREC_MIXED32 = 1      /* multigrid cycle in complex FP32, FP64 outer Krylov and residuals */
+  MGH_PREC_MIXED32 = 1      /* multigrid cycle in complex FP32 storage and arithmetic; the iterate,
+                               right-hand side and restart residual in double-float (FP64-class),
+                               every accepted iterate checked by the native-FP64 true residual; the
+                               Krylov basis per `arnoldi` (double-float, native FP64, or FP32 for
+                               the s-step cycles) */
 } mgh_precision;
 
 typedef enum {
@@ -60,10 +69,11 @@ typedef enum {
                                double-float (pairs of FP32, ~48-bit significand) on the FP32 pipes */
   MGH_ARNOLDI_FP64 = 1,     /* native FP64 Gram-Schmidt (always used when precision is FP64) */
   MGH_ARNOLDI_SSTEP = 2     /* mixed precision, restart <= 8: each cycle builds the monomial basis
-                               v_{k+1} = A M^{-1} v_k (double-float), orthogonalises it at once by a
-                               Cholesky factor of its Gram matrix (double-float sums, FP64 factor),
-                               and solves the cycle's least-squares problem on that factor; one
-                               sweep over the basis per cycle instead of two per step */
+                               v_{k+1} = A M^{-1} v_k, stored and formed in FP32, orthogonalises it
+                               at once by a Cholesky factor of its Gram matrix (FP32 running sums
+                               of 32 products promoted to double-float, FP64 factor), and solves
+                               the cycle's least-squares problem on that factor; one sweep over
+                               the basis per cycle instead of two per step */
 } mgh_arnoldi;
 
 typedef enum {
@@ -85,7 +95,8 @@ typedef struct {
   double k;                 /* background wavenumber k = k0 * eta_b */
   double beta;              /* layer strength: alpha = 1 + j*beta*(d/L)^2, d = distance to Omega in cells */
   double shift_re, shift_im;/* kappa of K_kappa (Sec. IV-B); (1, 0) is the unshifted operator */
-  int levels;               /* multigrid levels including the finest, >= 1 (Alg. 2) */
+  int levels;               /* multigrid levels including the finest, 2..12 (Alg. 2); the coarsest
+                               level may hold at most 8192 unknowns (its dense inverse is kept) */
   int nu1, nu2;             /* pre- and post-relaxation sweeps, 0..4 (Alg. 2) */
   double omega;             /* damped-Jacobi weight omega_S in (0, 1] (eq. dampedJ) */
   int restart;              /* GMRES restart length m, 1..32 (1..20 with MGH_ARNOLDI_DF, 1..8 with
@@ -269,11 +280,21 @@ mgh_status mgh_profile_read(mgh_handle* h, mgh_profile* out);
  *   loss_dev     device double receiving 1/2 sum_q ||S u_q - y_q||^2
  *   cuda_stream  cudaStream_t the work is queued on (NULL = legacy default stream)
  * The first call on a device looks up the static array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the array: calls that
+ * make that first call before any stream capture (a first call made while cuda_stream is being
+ * captured returns MGH_INVALID_ARG and changes nothing).  All calls share the array: calls that
  * overlap on the GPU (different streams, no ordering between them) race on it. */
 mgh_status mgh_misfit_noalloc(int nx, int ny, const mgh_cdouble* u, const mgh_cdouble* y, int B,
                               const int64_t* rec, int M, mgh_cdouble* r, mgh_cdouble* G,
                               double* loss_dev, void* cuda_stream);
+
+/* Test hook for the failure path of the bounded device-side waits (the paper has no counterpart).
+ * The next mgh_solve / mgh_forward / mgh_gradient solve of this handle starts with the handle's
+ * device error word set, exactly as a kernel whose bounded mbarrier wait gave up would leave it;
+ * that solve returns MGH_TIMEOUT without running a cycle, and later calls work normally.  This
+ * lets a test check the error-word -> MGH_TIMEOUT path without making any wait run out.  Only
+ * handles whose solver polls the word: precision MGH_PREC_MIXED32, krylov MGH_KRYLOV_FGMRES,
+ * arnoldi MGH_ARNOLDI_DF or MGH_ARNOLDI_SSTEP (MGH_NOT_SUPPORTED otherwise). */
+mgh_status mgh_debug_inject_timeout(mgh_handle* h);
 
 /* Kernel launches issued by this handle since creation (or since the last reset). */
 uint64_t mgh_launch_count(const mgh_handle* h, int reset);

@@ -97,6 +97,7 @@ def _load():
         "mgh_fbs_momentum": (S, [P, P, P, D, P]),
         "mgh_profile_enable": (S, [P, I]),
         "mgh_profile_read": (S, [P, ctypes.POINTER(mgh_profile)]),
+        "mgh_debug_inject_timeout": (S, [P]),
         "mgh_launch_count": (ctypes.c_uint64, [P, I]),
         "mgh_status_string": (ctypes.c_char_p, [S]),
         "mgh_last_error": (ctypes.c_char_p, []),
@@ -115,7 +116,7 @@ EXPORTED = [
     "mgh_default_params", "mgh_workspace_bytes", "mgh_create", "mgh_destroy", "mgh_set_contrast",
     "mgh_incident_field", "mgh_rhs", "mgh_apply", "mgh_precondition", "mgh_coarse_solve",
     "mgh_level_shape", "mgh_level_coefficient", "mgh_solve", "mgh_forward", "mgh_crop", "mgh_sample",
-    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
+    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_debug_inject_timeout", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
 ]
 
 
@@ -270,6 +271,10 @@ def mgh_profile_read(h) -> dict:
                 arnoldi_steps=int(p.arnoldi_steps), basis_reads=int(p.basis_reads),
                 reorth_reads=int(p.reorth_reads), residuals=int(p.residuals), updates=int(p.updates),
                 update_reads=int(p.update_reads), cycle_steps=int(p.cycle_steps), gram_reads=int(p.gram_reads))
+
+
+def mgh_debug_inject_timeout(h) -> None:
+    _check("mgh_debug_inject_timeout", _lib.mgh_debug_inject_timeout(h))
 
 
 def mgh_launch_count(h, reset=False) -> int:

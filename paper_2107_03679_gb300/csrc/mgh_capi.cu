@@ -125,7 +125,14 @@ void free_handle(mgh_handle* h) {
   delete h;
 }
 
-bool batch_ok(const Handle* h, int B) { return h && B >= 1 && B <= h->Bmax; }
+// The handle exists and its device is the current one (kernels and streams belong to it).
+bool handle_ok(const Handle* h) {
+  if (!h) return false;
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == h->device;
+}
+
+bool batch_ok(const Handle* h, int B) { return handle_ok(h) && B >= 1 && B <= h->Bmax; }
 
 }  // namespace
 
@@ -202,8 +209,10 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   h->stream = (cudaStream_t)cuda_stream;
   {
     int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_error("cudaGetDevice", e, __FILE__, __LINE__); delete h; return MGH_CUDA_ERROR; }
+    h->device = dev;
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (h->num_sms < 1) h->num_sms = 1;
   }
   h->nx = nxl[0]; h->ny = nyl[0]; h->N = (size_t)h->nx * h->ny;
@@ -306,7 +315,7 @@ void mgh_destroy(mgh_handle* h) {
 }
 
 mgh_status mgh_set_contrast(mgh_handle* h, const double* f_d) {
-  if (!h || !f_d) return MGH_INVALID_ARG;
+  if (!handle_ok(h) || !f_d) return MGH_INVALID_ARG;
   return setup_contrast(*h, f_d);
 }
 
@@ -344,7 +353,7 @@ mgh_status mgh_level_shape(const mgh_handle* h, int level, int* nx, int* ny, dou
 }
 
 mgh_status mgh_level_coefficient(mgh_handle* h, int level, double* c) {
-  if (!h || !c || level < 0 || level >= h->L) return MGH_INVALID_ARG;
+  if (!handle_ok(h) || !c || level < 0 || level >= h->L) return MGH_INVALID_ARG;
   MGH_CUDA(cudaMemcpyAsync(c, h->lev[level].c, 8 * h->lev[level].n(), cudaMemcpyDeviceToDevice, h->stream));
   return MGH_OK;
 }
@@ -400,18 +409,18 @@ mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u
 
 mgh_status mgh_tv_prox(mgh_handle* h, const double* fbar, const double* d, double gamma, double lam,
                        int iters, double* out) {
-  if (!h || !fbar || !out || iters < 1 || !(lam >= 0.0) || !std::isfinite(lam) || !std::isfinite(gamma))
+  if (!handle_ok(h) || !fbar || !out || iters < 1 || !(lam >= 0.0) || !std::isfinite(lam) || !std::isfinite(gamma))
     return MGH_INVALID_ARG;
   return tv_prox(*h, fbar, d, gamma, lam, iters, out);
 }
 
 mgh_status mgh_fbs_momentum(mgh_handle* h, const double* f, const double* f_prev, double c, double* fbar) {
-  if (!h || !f || !f_prev || !fbar || !std::isfinite(c)) return MGH_INVALID_ARG;
+  if (!handle_ok(h) || !f || !f_prev || !fbar || !std::isfinite(c)) return MGH_INVALID_ARG;
   return fbs_momentum(*h, f, f_prev, c, fbar);
 }
 
 mgh_status mgh_profile_enable(mgh_handle* h, int enable) {
-  if (!h) return MGH_INVALID_ARG;
+  if (!handle_ok(h)) return MGH_INVALID_ARG;
   MGH_CUDA(cudaStreamSynchronize(h->stream));
   MGH_TRY(prof_flush(*h));
   h->acc = mgh_profile{};
@@ -420,10 +429,17 @@ mgh_status mgh_profile_enable(mgh_handle* h, int enable) {
 }
 
 mgh_status mgh_profile_read(mgh_handle* h, mgh_profile* out) {
-  if (!h || !out) return MGH_INVALID_ARG;
+  if (!handle_ok(h) || !out) return MGH_INVALID_ARG;
   MGH_CUDA(cudaStreamSynchronize(h->stream));
   MGH_TRY(prof_flush(*h));
   *out = h->acc;
+  return MGH_OK;
+}
+
+mgh_status mgh_debug_inject_timeout(mgh_handle* h) {
+  if (!handle_ok(h)) return MGH_INVALID_ARG;
+  if (h->fp64 || h->p.krylov != MGH_KRYLOV_FGMRES || h->p.arnoldi == MGH_ARNOLDI_FP64) return MGH_NOT_SUPPORTED;
+  h->inject_timeout = true;
   return MGH_OK;
 }
 

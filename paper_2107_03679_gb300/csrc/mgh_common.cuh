@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 
@@ -113,11 +114,22 @@ namespace mgh { void set_error(const char* what, cudaError_t e, const char* file
     mgh_status s_ = (expr);                                              \
     if (s_ != MGH_OK) return s_;                                         \
   } while (0)
-// A one-time set-up step (kernel attributes) run once per process, also when several host threads
-// drive handles at the same time: a function-local static is initialised exactly once (C++11), and
-// every call returns the step's status.  The arguments are the statements of the step.
-#define MGH_ONCE(...)                                                                      \
-  do {                                                                                     \
-    static const mgh_status once_ = [&]() -> mgh_status { __VA_ARGS__ return MGH_OK; }(); \
-    if (once_ != MGH_OK) return once_;                                                    \
+// A one-time set-up step (kernel attributes) run once per device: cudaFuncSetAttribute applies to
+// the device that is current when it is called, so every device a process drives handles on needs
+// its own call.  One bit per device (devices 0..63; others run the step on every call) records a
+// step that succeeded; a step that failed is tried again by the next call.  Host threads that reach
+// the step together on one device may each run it: the steps are idempotent attribute settings.
+// The arguments are the statements of the step.
+#define MGH_ONCE(...)                                                                          \
+  do {                                                                                         \
+    static std::atomic<unsigned long long> once_done_{0ull};                                   \
+    int once_dev_ = -1;                                                                        \
+    MGH_CUDA(cudaGetDevice(&once_dev_));                                                       \
+    const unsigned long long once_bit_ =                                                       \
+        (once_dev_ >= 0 && once_dev_ < 64) ? (1ull << once_dev_) : 0ull;                       \
+    if (once_bit_ == 0ull || !(once_done_.load(std::memory_order_acquire) & once_bit_)) {      \
+      const mgh_status once_s_ = [&]() -> mgh_status { __VA_ARGS__ return MGH_OK; }();        \
+      if (once_s_ != MGH_OK) return once_s_;                                                   \
+      once_done_.fetch_or(once_bit_, std::memory_order_acq_rel);                               \
+    }                                                                                          \
   } while (0)

@@ -25,7 +25,7 @@ inline int partial_stride(int m) {
 }
 constexpr int kMaxSweeps = 4;
 constexpr int kMaxCycleType = 3;   // CycleType of Alg. 2 (launches per cycle grow as CycleType^levels)
-constexpr int kMaxCoarse = 4096;   // unknowns on the coarsest level (dense inverse kept on device)
+constexpr int kMaxCoarse = 8192;   // unknowns on the coarsest level (dense inverse kept on device: 1 GB in FP64)
 
 // Device arrays of one multigrid level.  Coefficient and diagonals are shared by every
 // right-hand side; the field buffers hold batch_max right-hand sides.
@@ -52,7 +52,9 @@ struct LevelTma {
 struct Handle {
   mgh_params p{};
   cudaStream_t stream = nullptr;
+  int device = -1;           // CUDA device current at mgh_create; every later call must run with it current
   int num_sms = 1;           // multiprocessors of the handle's device
+  bool inject_timeout = false;  // test hook: the next double-float solve starts with the error word set
   int nx = 0, ny = 0;
   size_t N = 0;              // points of the extended grid
   size_t Np = 0;             // plane stride of double-float fields: N rounded up to 64 points

@@ -866,8 +866,21 @@ template <typename K>
 long resident_warps(const Handle& h, K kern, int threads, size_t smem) {
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, threads, smem) != cudaSuccess || blocks < 1)
-    blocks = 1;
+    return -1;
   return (long)blocks * (threads / 32) * h.num_sms;
+}
+
+// resident_warps cached per device (the figure depends on the device's SM count and limits); a
+// failed occupancy query is not cached and counts as one block per SM.
+template <typename K>
+long resident_cached(std::atomic<long>* cache, const Handle& h, K kern, int threads, size_t smem) {
+  const bool slot = h.device >= 0 && h.device < 64;
+  long v = slot ? cache[h.device].load(std::memory_order_acquire) : 0;
+  if (v > 0) return v;
+  v = resident_warps(h, kern, threads, smem);
+  if (v <= 0) return (long)(threads / 32) * h.num_sms;
+  if (slot) cache[h.device].store(v, std::memory_order_release);
+  return v;
 }
 
 bool use_wave(const Handle& h, int l) { return h.vc_wave && h.lev[l].nx >= h.wave_min_nx; }
@@ -1000,7 +1013,8 @@ mgh_status launch_pre_wave(Handle& h, int l, const cf* bin, size_t b_stride, con
   constexpr size_t smem1 = wave::LaneRingSmem<4, S1>::bytes();
   MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(wave::k_pre_wa<NU, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem1)););
-  static const long resident = resident_warps(h, wave::k_pre_wa<NU, 4, 1>, 128, smem1);
+  static std::atomic<long> resident_by_dev[64];
+  const long resident = resident_cached(resident_by_dev, h, wave::k_pre_wa<NU, 4, 1>, 128, smem1);
   const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * G::H - 1, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
@@ -1036,7 +1050,8 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
   constexpr size_t smem1 = wave::LaneRingSmem<4, S1>::bytes();
   MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(wave::k_post_wa<NU, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem1)););
-  static const long resident = resident_warps(h, wave::k_post_wa<NU, 4, 1>, 128, smem1);
+  static std::atomic<long> resident_by_dev[64];
+  const long resident = resident_cached(resident_by_dev, h, wave::k_post_wa<NU, 4, 1>, 128, smem1);
   const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * NU, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);

@@ -17,13 +17,18 @@ static __device__ __align__(256) double g_misfit_scratch[kNoallocMaxBatch];
 std::mutex g_mutex;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device, resolved once per device.
-mgh_status scratch_address(double** out) {
+// Device address of the scratch array on the current device, resolved once per device.  The
+// look-up is not a stream operation: while `s` is being captured into a graph it is refused
+// (MGH_INVALID_ARG, nothing changed) instead of being run inside the caller's capture.
+mgh_status scratch_address(double** out, cudaStream_t s) {
   int dev = 0;
   MGH_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return MGH_NOT_SUPPORTED;
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_scratch_addr[dev]) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MGH_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return MGH_INVALID_ARG;
     void* p = nullptr;
     MGH_CUDA(cudaGetSymbolAddress(&p, g_misfit_scratch));
     g_scratch_addr[dev] = static_cast<double*>(p);
@@ -71,9 +76,9 @@ extern "C" mgh_status mgh_misfit_noalloc(int nx, int ny, const mgh_cdouble* u, c
                                          double* loss_dev, void* cuda_stream) {
   if (nx < 1 || ny < 1 || !u || !y || !rec || !loss_dev || M < 1 || B < 1) return MGH_INVALID_ARG;
   if (B > kNoallocMaxBatch) return MGH_INVALID_ARG;
-  double* part = nullptr;
-  MGH_TRY(scratch_address(&part));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  double* part = nullptr;
+  MGH_TRY(scratch_address(&part, s));
   const size_t N = (size_t)nx * ny;
   if (G) MGH_CUDA(cudaMemsetAsync(G, 0, sizeof(cd) * N * B, s));
   k_misfit_scratch<<<B, 256, 0, s>>>(reinterpret_cast<const cd*>(u), reinterpret_cast<const cd*>(y), N, rec, M,

@@ -55,8 +55,12 @@ def test_host_only_entry_points(lib):
     bad.levels = 1
     with pytest.raises(capi.MGHError):
         capi.mgh_workspace_bytes(bad)
+    ok = capi.mgh_default_params()
+    ok.levels = 2           # coarsest 80x80 = 6400 unknowns: within the 8192 of the dense inverse
+    assert capi.mgh_workspace_bytes(ok) > 16 * 6400 * 6400
     bad = capi.mgh_default_params()
-    bad.levels = 2          # coarsest 80x80 = 6400 unknowns > dense-inverse limit
+    bad.nx_int = bad.ny_int = 200
+    bad.levels = 2          # coarsest 116x116 = 13456 unknowns > dense-inverse limit
     with pytest.raises(capi.MGHError):
         capi.mgh_workspace_bytes(bad)
     assert capi.mgh_status_string(capi.MGH_NOT_CONVERGED) == "not converged"
@@ -88,6 +92,7 @@ def test_reconstruction_entry_points_validate_on_the_host(lib):
     L = capi._lib
     assert L.mgh_tv_prox(None, None, None, 1.0, 0.1, 3, None) == capi.MGH_INVALID_ARG
     assert L.mgh_fbs_momentum(None, None, None, 0.5, None) == capi.MGH_INVALID_ARG
+    assert L.mgh_debug_inject_timeout(None) == capi.MGH_INVALID_ARG
 
 
 def test_params_layout_matches_the_c_header(tmp_path):
