@@ -73,6 +73,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-steps", type=int, default=60, help=argparse.SUPPRESS)
+    ap.add_argument("--sample-angle", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the plain-FP64 run of the same step (speed-up at the same accuracy)")
     return ap.parse_args(argv)
 
 
@@ -240,7 +243,7 @@ def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, 
 # --------------------------------------------------------------------------- CPU oracle sample
 def cpu_sample_main(args):
     """Run in a subprocess with one BLAS thread: time `sample_steps` FGMRES steps of the FP64
-    oracle on angle 0 of the workload and print seconds per Arnoldi step."""
+    oracle on one angle of the workload (--sample-angle) and print seconds per Arnoldi step."""
     import numpy as np
     import oracle as O
     import workloads as W
@@ -251,7 +254,7 @@ def cpu_sample_main(args):
     s = O.MGHSolver(p, f_step, w.levels, w.nu1, w.nu2, w.omega, complex(w.shift_re, w.shift_im), w.restart,
                     w.tol, maxit=args.sample_steps)
     t_setup = time.perf_counter() - t0
-    b = O.rhs(p, f_step, float(th[0]))
+    b = O.rhs(p, f_step, float(th[args.sample_angle % len(th)]))
     t0 = time.perf_counter()
     _, info = s.solve(b)
     t = time.perf_counter() - t0
@@ -270,28 +273,66 @@ def oracle_iterations_per_solve(workload: str):
     return 0.5 * (e["forward_iterations"] + e["adjoint_iterations"])
 
 
-def run_cpu_sample(workload: str, sample_steps: int):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_cpu_samples(workload: str, sample_steps: int, workers: int):
+    """`workers` concurrent oracle processes (one BLAS thread each), worker i on angle i: each
+    times `sample_steps` FGMRES steps of its own solve.  Returns the per-worker records and the
+    host wall clock around all of them."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
-                        "--sample-steps", str(sample_steps)], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError(f"cpu sample failed: {r.stderr[-2000:]}")
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    t0 = time.perf_counter()
+    procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
+                               "--sample-steps", str(sample_steps), "--sample-angle", str(i)],
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for i in range(workers)]
+    out = []
+    for pr in procs:
+        so, se = pr.communicate(timeout=900)
+        if pr.returncode != 0:
+            raise RuntimeError(f"cpu sample failed: {se[-2000:]}")
+        out.append(json.loads(so.strip().splitlines()[-1]))
+    return out, time.perf_counter() - t0
+
+
+def cpu_rate(samples, its: float) -> float:
+    """Aggregate oracle solves/s: every worker's Arnoldi steps per second of its own solve,
+    summed over workers, divided by the oracle's steps per solve."""
+    return sum(s["steps"] / s["solve_s"] for s in samples) / its
 
 
 def cpu_baseline_record(workload: str, sample_steps: int):
     its = oracle_iterations_per_solve(workload)
-    smp = run_cpu_sample(workload, sample_steps)
     if its is None:
         return None
-    value = 1.0 / (smp["sec_per_step"] * its)
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 numpy oracle, 1 thread: {smp['steps']} FGMRES steps of angle 0 "
-                       f"({smp['solve_s']:.1f} s, {smp['sec_per_step'] * 1e3:.0f} ms/step), scaled by the oracle's own "
-                       f"{its:.0f} steps per solve (forward/adjoint mean, {os.path.relpath(ITER_FIXTURE, ROOT)})")}
+    cores = host_cores()
+    multi, wall = run_cpu_samples(workload, sample_steps, cores)
+    one, _ = run_cpu_samples(workload, max(sample_steps // 2, 1), 1)
+    return {"value": cpu_rate(multi, its), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(), "single_core_value": cpu_rate(one, its),
+            "sample": (f"FP64 numpy oracle, one process per host core ({cores} x 1 BLAS thread), process i on "
+                       f"angle i: {sample_steps} FGMRES steps each ({wall:.1f} s wall for all), steps/s summed and "
+                       f"divided by the oracle's own {its:.0f} steps per solve (forward/adjoint mean, "
+                       f"{os.path.relpath(ITER_FIXTURE, ROOT)}); single_core_value: the same with one process")}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -304,23 +345,26 @@ def reference_main(args, rank, world):
     if its is None:
         print(json.dumps({"impl": "reference", "unavailable": f"no oracle iteration fixture for {args.workload}"}))
         return
-    sample_steps = 40
+    sample_steps = 16
+    cores = host_cores()
     for _ in range(args.warmup):
-        run_cpu_sample(args.workload, sample_steps)
-    times = []
+        run_cpu_samples(args.workload, sample_steps, cores)
+    rates, walls = [], []
     for _ in range(args.steps):
-        smp = run_cpu_sample(args.workload, sample_steps)
-        times.append(smp["sec_per_step"])
-    sec = sum(times) / len(times)
-    value = 1.0 / (sec * its)
-    sample = (f"FP64 numpy oracle, 1 thread: {sample_steps} FGMRES steps of angle 0 per step, "
-              f"scaled by {its:.0f} oracle steps per solve")
+        smp, wall = run_cpu_samples(args.workload, sample_steps, cores)
+        rates.append(cpu_rate(smp, its))
+        walls.append(wall)
+    value = sum(rates) / len(rates)
+    sample = (f"FP64 numpy oracle, one process per host core ({cores} x 1 BLAS thread), process i on angle i: "
+              f"{sample_steps} FGMRES steps each per step, steps/s summed and divided by {its:.0f} oracle steps "
+              f"per solve")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * sample_steps * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny}", "angles": w.n_angles},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -456,6 +500,49 @@ def gpu_main(args, rank, world, local_rank):
         e2e = {"value": world * solves_rank / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # ---- the plain FP64 form of the same step at the same accuracy (FP64 cycle, native-FP64 Arnoldi,
+    # the same acceptance test): one warm-up and at most two timed steps, CUDA events on its stream
+    fp64 = None
+    if not args.no_fp64_compare and precision == "mixed32" and args.krylov == "fgmres":
+        s64 = Solver.from_workload(w, batch_max=B, precision="fp64", device=dev, maxit=args.maxit,
+                                   cycle_type=args.cycle)
+        u64 = s64.field(B)
+
+        def step64():
+            s64.set_contrast(d_f)
+            _, a_ = s64.forward(d_th, out=u64)
+            _, G_, _ = s64.misfit(u64, d_y, d_rec)
+            _, b_ = s64.gradient(d_th, u64, G_)
+            return a_ + b_
+
+        step64()
+        k64 = min(args.steps, 2)
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(s64.stream)
+        inf64 = []
+        for _ in range(k64):
+            inf64 += step64()
+        f1.record(s64.stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms64 = f0.elapsed_time(f1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms64], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms64 = float(t.item())
+        v64 = world * 2 * B * k64 / (ms64 / 1e3)
+        fp64 = {"value": round(v64, 3), "unit": UNIT, "steps": k64, "warmup": 1,
+                "ms_per_step": round(ms64 / k64, 2), "speedup_of_mixed": round(value / v64, 2),
+                "converged": all(i["converged"] for i in inf64),
+                "worst_rel_residual": max(i["rel_residual"] for i in inf64),
+                "iterations_mean": round(sum(i["iterations"] for i in inf64) / len(inf64), 1),
+                "what": "plain FP64 form of the same step: FP64 multigrid cycle, native-FP64 Arnoldi FGMRES, "
+                        "same restart, levels, sweeps and FP64 acceptance test"}
+        s64.close()
+
     if rank != 0:
         return
 
@@ -481,35 +568,31 @@ def gpu_main(args, rank, world, local_rank):
         kernels[k] = e
     vc_bytes = alg["vcycle_pre_l0"] + alg["vcycle_post_l0"]
     vc_ms = ms_cls["vcycle_pre_l0"] + ms_cls["vcycle_post_l0"]
-    if dom == "gs_update" and engine == "sstep":
-        # the s-step Gram sweep is bound by the FP32 pipes: 40 FP32 operations per complex pair and
-        # point (exact products summed in double-float), 20 per diagonal pair; peak = 152 SMs x 128
-        # FP32 lanes x 2.07 GHz (one operation per lane and clock)
-        nv = w.restart + 1
-        ops_pt = 40 * (nv * (nv - 1) // 2) + 20 * nv
-        ops = ops_pt * N * prof["gram_reads"] / nv
-        alu_peak = 152 * 128 * 2.07e9 / 1e9
-        achieved = ops / (ms_cls[dom] / 1e3) / 1e9
-        n_l = max(prof["launches"][dom], 1)
-        # DRAM bytes of one launch from the ncu capture of profiles/gram_sstep_ellipses576.md (24
-        # angles: 573.4 MB read + 4.2 MB written), scaled by the right-hand sides of this launch
-        traffic = round(577.6e6 * B / 24) if (w.nx == 576 and w.restart == 8 and w.levels == 6) else None
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 1), "peak": round(alu_peak, 1),
-                "unit": "Gop/s (FP32)", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
-                "bytes_per_launch": round(alg[dom] / n_l), "hbm_GBps": round(alg[dom] / (ms_cls[dom] / 1e3) / 1e9, 1),
-                "hbm_peak": peak}
-    elif dom in alg:
+    n_l = max(prof["launches"][dom], 1)
+    if dom in alg:
+        # every class is reported against its algorithmic bytes (fields read or written once per
+        # launch) and the measured copy bandwidth
         achieved = alg[dom] / (ms_cls[dom] / 1e3) / 1e9
-        n_l = max(prof["launches"][dom], 1)
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
                 "bytes_per_launch": round(alg[dom] / n_l)}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
                 "traffic": None, "peak_kind": peak_kind}
+    if dom == "gs_update" and engine == "sstep":
+        # the method's arithmetic of the Gram sweep: 45 complex multiply-adds (8 flops each) per point and
+        # cycle for m = 8, against the measured FP32 FMA rate (69.7 TFLOP/s on this GPU)
+        nv = w.restart + 1
+        flops = 8 * (nv * (nv + 1) // 2) * N * prof["gram_reads"] / nv
+        roof["method_tflops"] = round(flops / (ms_cls[dom] / 1e3) / 1e12, 2)
     roof["vcycle_fine_GBps"] = round(vc_bytes / (vc_ms / 1e3) / 1e9, 1) if vc_ms > 0 else None
     roof["vcycle_fine_frac"] = round(vc_bytes / (vc_ms / 1e3) / 1e9 / peak, 4) if vc_ms > 0 else None
+    vt_bytes = vc_bytes + alg.get("vcycle_coarse", 0.0)
+    vt_ms = vc_ms + ms_cls.get("vcycle_coarse", 0.0)
+    roof["vcycle_total_GBps"] = round(vt_bytes / (vt_ms / 1e3) / 1e9, 1) if vt_ms > 0 else None
+    roof["vcycle_total_frac"] = round(vt_bytes / (vt_ms / 1e3) / 1e9 / peak, 4) if vt_ms > 0 else None
+    step_bytes = sum(alg.values())
+    roof["step_algorithmic_GBps"] = round(step_bytes / (sum(ms_cls.values()) / 1e3) / 1e9, 1)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -534,6 +617,7 @@ def gpu_main(args, rank, world, local_rank):
         "iterations": {"mean": round(sum(its) / len(its), 1), "min": min(its), "max": max(its)},
         "converged": conv, "worst_rel_residual": worst,
         "gpu_launches": int(launches),
+        "fp64_same_accuracy": fp64,
         "autotuned": tuned,
         "clocks": clk,
         "e2e": e2e,
