@@ -57,11 +57,20 @@ typedef enum {
 
 typedef enum {
   MGH_PREC_FP64 = 0,        /* everything in complex FP64 (the plain form) */
-  MGH_PREC_MIXED32 = 1      /* multigrid cycle in complex FP32 storage and arithmetic; the iterate,
+  MGH_PREC_MIXED32 = 1,     /* multigrid cycle in complex FP32 storage and arithmetic; the iterate,
                                right-hand side and restart residual in double-float (FP64-class),
                                every accepted iterate checked by the native-FP64 true residual; the
                                Krylov basis per `arnoldi` (double-float, native FP64, or FP32 for
                                the s-step cycles) */
+  MGH_PREC_MIXED16 = 2      /* MGH_PREC_MIXED32 with FP16 storage on the fine level: the level-0
+                               iterate between pre- and post-smoothing and the preconditioned
+                               vectors Z are stored as complex FP16 (arithmetic stays FP32; the
+                               level-0 cycle input is scaled by a power of two near sqrt(N)/16 so
+                               that the stored values sit well inside FP16's normal range).  Needs
+                               arnoldi = MGH_ARNOLDI_SSTEP, krylov = MGH_KRYLOV_FGMRES, an even
+                               extended-grid width and at least one sweep before and after the
+                               level-0 correction (MGH_NOT_SUPPORTED otherwise).  mgh_precondition
+                               applies the FP32 cycle; FP16 storage is used inside solves */
 } mgh_precision;
 
 typedef enum {

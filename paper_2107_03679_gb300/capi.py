@@ -13,8 +13,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmgh.so")
 
 MGH_OK, MGH_INVALID_ARG, MGH_NOT_CONVERGED, MGH_CUDA_ERROR, MGH_OUT_OF_MEMORY, MGH_TIMEOUT, MGH_NOT_SUPPORTED = range(7)
-MGH_PREC_FP64, MGH_PREC_MIXED32 = 0, 1
-PRECISIONS = {"fp64": MGH_PREC_FP64, "mixed32": MGH_PREC_MIXED32}
+MGH_PREC_FP64, MGH_PREC_MIXED32, MGH_PREC_MIXED16 = 0, 1, 2
+PRECISIONS = {"fp64": MGH_PREC_FP64, "mixed32": MGH_PREC_MIXED32, "mixed16": MGH_PREC_MIXED16}
 MGH_ARNOLDI_DF, MGH_ARNOLDI_FP64, MGH_ARNOLDI_SSTEP = 0, 1, 2
 ARNOLDI = {"df": MGH_ARNOLDI_DF, "fp64": MGH_ARNOLDI_FP64, "sstep": MGH_ARNOLDI_SSTEP}
 MGH_KRYLOV_FGMRES, MGH_KRYLOV_BICGSTAB = 0, 1

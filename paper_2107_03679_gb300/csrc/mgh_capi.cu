@@ -31,13 +31,14 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
   if (p->nu1 < 0 || p->nu1 > kMaxSweeps || p->nu2 < 0 || p->nu2 > kMaxSweeps) return MGH_INVALID_ARG;
   if (!(p->omega > 0.0 && p->omega <= 1.0)) return MGH_INVALID_ARG;
   if (p->restart < 1 || p->restart > kMaxRestart || p->maxit < 1 || !(p->tol > 0.0)) return MGH_INVALID_ARG;
-  if (p->precision != MGH_PREC_FP64 && p->precision != MGH_PREC_MIXED32) return MGH_INVALID_ARG;
+  if (p->precision != MGH_PREC_FP64 && p->precision != MGH_PREC_MIXED32 && p->precision != MGH_PREC_MIXED16)
+    return MGH_INVALID_ARG;
   if (p->batch_max < 1 || p->batch_max > 65535) return MGH_INVALID_ARG;
   if (p->arnoldi != MGH_ARNOLDI_DF && p->arnoldi != MGH_ARNOLDI_FP64 && p->arnoldi != MGH_ARNOLDI_SSTEP)
     return MGH_INVALID_ARG;
-  if (p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_DF && p->restart > kMaxRestartDf)
+  if (p->precision != MGH_PREC_FP64 && p->arnoldi == MGH_ARNOLDI_DF && p->restart > kMaxRestartDf)
     return MGH_INVALID_ARG;
-  if (p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_SSTEP && p->restart > kMaxRestartSs &&
+  if (p->precision != MGH_PREC_FP64 && p->arnoldi == MGH_ARNOLDI_SSTEP && p->restart > kMaxRestartSs &&
       p->krylov == MGH_KRYLOV_FGMRES)
     return MGH_INVALID_ARG;
   if (p->krylov != MGH_KRYLOV_FGMRES && p->krylov != MGH_KRYLOV_BICGSTAB) return MGH_INVALID_ARG;
@@ -50,6 +51,14 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
   if (p->krylov == MGH_KRYLOV_BICGSTAB && p->restart < 5) return MGH_INVALID_ARG;
   if (!std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) return MGH_INVALID_ARG;
   const long long nx = p->nx_int + 2LL * p->abl, ny = p->ny_int + 2LL * p->abl;
+  if (p->precision == MGH_PREC_MIXED16) {
+    // FP16 storage is built into the s-step FGMRES engine and the level-0 wavefront kernels
+    // (lane rings of 8-byte FP16 pairs: even rows; both level-0 stages need a sweep)
+    const int n1 = p->nu_per_level ? p->nu1_level[0] : p->nu1, n2 = p->nu_per_level ? p->nu2_level[0] : p->nu2;
+    if (p->krylov != MGH_KRYLOV_FGMRES || p->arnoldi != MGH_ARNOLDI_SSTEP || p->restart > kMaxRestartSs ||
+        nx % 2 != 0 || n1 < 1 || n2 < 1)
+      return MGH_NOT_SUPPORTED;
+  }
   if (nx > (1 << 20) || ny > (1 << 20) || nx * ny > (1LL << 31)) return MGH_INVALID_ARG;
   int cx = (int)nx, cy = (int)ny;
   for (int l = 0; l < p->levels; ++l) {
@@ -219,6 +228,11 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   h->Np = (h->N + 63) / 64 * 64;
   h->L = p->levels;
   h->fp64 = p->precision == MGH_PREC_FP64;
+  h->half = p->precision == MGH_PREC_MIXED16;
+  if (h->half) {   // scale sqrt(N)/16 rounded to a power of two: FP16 values near 1/16 in RMS
+    const double t = std::sqrt((double)nxl[0] * nyl[0]) / 16.0;
+    h->zmul = (float)std::ldexp(1.0, std::max(0, (int)std::lround(std::log2(std::max(t, 1.0)))));
+  }
   h->csize = h->fp64 ? 16 : 8;
   h->m = p->restart;
   h->Bmax = p->batch_max;
@@ -291,6 +305,12 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   if (const char* e = std::getenv("MGH_WAVE_WARPS")) h->wave_warps = std::atoi(e) == 2 ? 2 : 4;
   if (const char* e = std::getenv("MGH_WAVE_RING")) h->wave_ring = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("MGH_WAVE_FILL")) h->wave_lane_ring = std::strcmp(e, "bulk") != 0;
+  if (h->half) {   // the FP16 level-0 kernels exist only as lane-ring wavefront kernels
+    h->vc_wave = true;
+    h->wave_min_nx = 0;
+    h->wave_ring = 1;
+    h->wave_lane_ring = true;
+  }
   // MGH_GRAPHS=0 issues every restart cycle's launches directly instead of replaying a CUDA graph
   if (const char* e = std::getenv("MGH_GRAPHS")) h->use_graphs = std::strcmp(e, "0") != 0;
   // the coarse levels whose fields fit in one block's shared memory run as one kernel per cycle;

@@ -60,6 +60,9 @@ struct Handle {
   size_t Np = 0;             // plane stride of double-float fields: N rounded up to 64 points
   int L = 0;                 // levels
   bool fp64 = true;          // cycle precision: double (true) or float (false)
+  bool half = false;         // MGH_PREC_MIXED16: level-0 v_pre and the preconditioned vectors Z in FP16
+  float zmul = 1.f;          // power-of-two scale of the level-0 cycle input when `half` (keeps the
+                             // FP16 values near 1/16 in RMS: sqrt(N)/16, rounded to a power of two)
   bool vc_wave = true;       // FP32 levels: wavefront kernels (else shared-memory tiles)
   int wave_seg = 0;          // rows per warp segment of the wavefront kernels (0: automatic)
   int wave_min_nx = 0;       // levels narrower than this use the tiled kernels

@@ -20,6 +20,8 @@
 // filled by bulk copies (TMA, cp.async.bulk) that complete on mbarriers, so loads of later tiles
 // are in flight while the FP32 pipes work on the current one.  Double-float fields (basis
 // vectors, w, the operator diagonal) are pairs of float2 planes (hi, lo) with plane stride Np.
+#include <cuda_fp16.h>
+
 #include <cmath>
 #include <utility>
 
@@ -634,10 +636,18 @@ __global__ void k_verify_decide(KArgs a, const cd* __restrict__ partial, double*
   for (int i = 1; i <= a.m; ++i) gg[i] = czero<double>();
 }
 
-// x += sum_{i < jend} y_i z_i, all in double-float (x planes, z FP32, y split to double-float).
-template <int NV>
+// The preconditioned vector z_i at point q from its storage (complex FP32, or complex FP16 under
+// MGH_PREC_MIXED16).
+__device__ __forceinline__ cf zload(const cf* Z, size_t i) { return Z[i]; }
+__device__ __forceinline__ cf zload(const __half2* Z, size_t i) {
+  const float2 f = __half22float2(Z[i]);
+  return mk<float>(f.x, f.y);
+}
+
+// x += sum_{i < jend} y_i z_i, all in double-float (x planes, z FP32 or FP16, y split to double-float).
+template <int NV, typename ZT = cf>
 __global__ void __launch_bounds__(kKThreads)
-k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, float2* __restrict__ xdf,
+k_df_xupdate(KArgs a, const ZT* __restrict__ Z, const cd* __restrict__ y, float2* __restrict__ xdf,
              const RhsState* __restrict__ st) {
   const int rhs = blockIdx.y;
   if (st[rhs].done || st[rhs].jend == 0) return;
@@ -645,7 +655,7 @@ k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, float2
   __shared__ cdf ys[NV];
   if (threadIdx.x < NV && (int)threadIdx.x < je) ys[threadIdx.x] = cdf_from(y[(size_t)rhs * a.m + threadIdx.x]);
   __syncthreads();
-  const cf* Zb = Z + (size_t)rhs * a.m * a.N;
+  const ZT* Zb = Z + (size_t)rhs * a.m * a.N;
   float2* xh = xdf + (size_t)rhs * 2 * a.Np;
   float2* xl = xh + a.Np;
   const size_t p0 = blockIdx.x * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
@@ -656,8 +666,8 @@ k_df_xupdate(KArgs a, const cf* __restrict__ Z, const cd* __restrict__ y, float2
     cf z1[NV], z2[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      z1[i] = i < je ? Zb[(size_t)i * a.N + q] : mk<float>(0.f, 0.f);
-      z2[i] = (i < je && two) ? Zb[(size_t)i * a.N + q2] : mk<float>(0.f, 0.f);
+      z1[i] = i < je ? zload(Zb, (size_t)i * a.N + q) : mk<float>(0.f, 0.f);
+      z2[i] = (i < je && two) ? zload(Zb, (size_t)i * a.N + q2) : mk<float>(0.f, 0.f);
     }
     cdf v[2] = {load_df(xh, a.Np, q), two ? load_df(xh, a.Np, q2) : cdf_zero()};
 #pragma unroll
@@ -774,22 +784,32 @@ k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__
   block_reduce_df(vals, 1, [&](int) -> double* { out->im = 0.0; return &out->re; });
 }
 
+// Two adjacent points of z (q even) as (re0, im0, re1, im1): one 16-byte load of FP32 storage or
+// one 8-byte load of FP16 storage.
+__device__ __forceinline__ float4 zpair(const cf* z, size_t q) { return reinterpret_cast<const float4*>(z)[q / 2]; }
+__device__ __forceinline__ float4 zpair(const __half2* z, size_t q) {
+  const uint2 u = reinterpret_cast<const uint2*>(z)[q / 2];
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
 // The same for rows of even width: two adjacent points per thread and step (the pair never
-// straddles a row), 16-byte loads of z, D and the rows above and below, one 16-byte store.
+// straddles a row), 16-byte loads of z (8-byte for FP16 storage), D and the rows above and below,
+// one 16-byte store.
+template <typename ZT = cf>
 __global__ void __launch_bounds__(kKThreads)
-k_ss_matvec2(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__ D32, float2* __restrict__ V,
+k_ss_matvec2(KArgs a, int k, const ZT* __restrict__ Z, const float2* __restrict__ D32, float2* __restrict__ V,
              cd* __restrict__ partial, const RhsState* __restrict__ st) {
   const int rhs = blockIdx.y, blk = blockIdx.x;
   if (!st[rhs].active) return;
-  const cf* z = Z + ((size_t)rhs * a.m + k) * a.N;
+  const ZT* z = Z + ((size_t)rhs * a.m + k) * a.N;
   float2* vh = V + (((size_t)rhs * (a.m + 1) + k + 1) * 2) * a.Np;
   const float ih = (float)a.inv_h2;
   float nrm = 0.f;
   const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;   // both even
-  const float4* z4 = reinterpret_cast<const float4*>(z);
   const float4* d4 = reinterpret_cast<const float4*>(D32);
   float4* v4 = reinterpret_cast<float4*>(vh);
-  const size_t half = a.nx / 2;
   size_t q = p0 + 2 * threadIdx.x;
   int n = (int)((unsigned)q / (unsigned)a.nx);
   int m = (int)((unsigned)q - (unsigned)n * (unsigned)a.nx);
@@ -797,11 +817,11 @@ k_ss_matvec2(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict_
   for (; q < p1; q += 2 * kKThreads, m += 2 * kKThreads) {
     while (m >= a.nx) { m -= a.nx; ++n; }
     const size_t h = q / 2;
-    const float4 c = z4[h];
-    const float4 up = n > 0 ? z4[h - half] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 dn = n < a.ny - 1 ? z4[h + half] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const cf zl = m > 0 ? z[q - 1] : mk<float>(0.f, 0.f);
-    const cf zr = m + 2 < a.nx ? z[q + 2] : mk<float>(0.f, 0.f);
+    const float4 c = zpair(z, q);
+    const float4 up = n > 0 ? zpair(z, q - a.nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 dn = n < a.ny - 1 ? zpair(z, q + a.nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const cf zl = m > 0 ? zload(z, q - 1) : mk<float>(0.f, 0.f);
+    const cf zr = m + 2 < a.nx ? zload(z, q + 2) : mk<float>(0.f, 0.f);
     const float4 d = d4[h];
     // point q: neighbours zl, (c.z, c.w), up.xy, dn.xy; point q+1: (c.x, c.y), zr, up.zw, dn.zw
     const float s0r = (zl.re + c.z) + (up.x + dn.x), s0i = (zl.im + c.w) + (up.y + dn.y);
@@ -1112,6 +1132,13 @@ mgh_status df_xupdate(Handle& h, const KArgs& a, int B) {
   ProfScope ps(h, P_XUPDATE);
   const int m = a.m;
   float2* x = h.xdf;
+  if (h.half) {   // FP16 preconditioned vectors (s-step engine, m <= 8)
+    const __half2* Zh = reinterpret_cast<const __half2*>(h.Z);
+    if (m <= 4) k_df_xupdate<4, __half2><<<grid, kKThreads, 0, h.stream>>>(a, Zh, h.y, x, h.st);
+    else k_df_xupdate<8, __half2><<<grid, kKThreads, 0, h.stream>>>(a, Zh, h.y, x, h.st);
+    MGH_CHECK_LAUNCH(); h.launches++;
+    return MGH_OK;
+  }
   if (m <= 4) k_df_xupdate<4><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
   else if (m <= 8) k_df_xupdate<8><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
   else if (m <= 12) k_df_xupdate<12><<<grid, kKThreads, 0, h.stream>>>(a, (const cf*)h.Z, h.y, x, h.st);
@@ -1234,11 +1261,19 @@ mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
   for (int k = 0; k < a.m; ++k) {
     // z_k = M^{-1}(v_k / ||v_k||), reading only the hi plane of v_k
     const cf* vhi = reinterpret_cast<const cf*>(V + (size_t)k * 2 * a.Np);
-    MGH_TRY(vcycle_f32in(h, vhi, (size_t)(a.m + 1) * 2 * a.Np, h.vscale + k, (size_t)(a.m + 1),
-                         (cf*)h.Z + (size_t)k * a.N, (size_t)a.m * a.N, B, h.st, k));
+    // slot k of Z: complex FP32, or complex FP16 (half the bytes per slot) under MGH_PREC_MIXED16,
+    // where it holds zmul * M^{-1}(v_k / ||v_k||): any fixed scale of z_k leaves the cycle's
+    // iterate unchanged, since v_{k+1} = A z_k is formed from the stored z_k
+    __half2* zh = reinterpret_cast<__half2*>(h.Z) + (size_t)k * a.N;
+    cf* zk = h.half ? reinterpret_cast<cf*>(zh) : (cf*)h.Z + (size_t)k * a.N;
+    MGH_TRY(vcycle_f32in(h, vhi, (size_t)(a.m + 1) * 2 * a.Np, h.vscale + k, (size_t)(a.m + 1), zk,
+                         (size_t)a.m * a.N, B, h.st, k));
     {
       ProfScope ps(h, P_MATVEC_DOTS);
-      if (a.nx % 2 == 0)
+      if (h.half)
+        k_ss_matvec2<__half2><<<grid, kKThreads, 0, h.stream>>>(a, k, reinterpret_cast<const __half2*>(h.Z), h.DAdf,
+                                                                V, h.partial, h.st);
+      else if (a.nx % 2 == 0)
         k_ss_matvec2<<<grid, kKThreads, 0, h.stream>>>(a, k, (const cf*)h.Z, h.DAdf, V, h.partial, h.st);
       else
         k_ss_matvec<<<grid, kKThreads, 0, h.stream>>>(a, k, (const cf*)h.Z, h.DAdf, V, h.partial, h.st);

@@ -835,6 +835,7 @@ int persistent_blocks(Handle& h, K kern, size_t smem, int tiles, int threads = k
 
 // ---------------------------------------------------------------- wavefront level kernels (host side)
 bool a16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+bool a8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
 
 // Rows per warp segment.  All warps of a launch run the same number of steps K (rows + halo
 // rows, rounded up to the unroll period P), so a launch takes about K times the number of
@@ -943,38 +944,44 @@ mgh_status post_ring_go(Handle& h, int l, const cf* bin, size_t b_stride, const 
   return MGH_OK;
 }
 
-template <int NU, int NW, int MS>
+// VT / OT: storage of the level's v_pre and of the result; FP16 only on level 0 of an
+// MGH_PREC_MIXED16 handle, whose cycle input is scaled by h.zmul (an exact power of two).
+template <int NU, int NW, int MS, typename VT = cf>
 mgh_status pre_lane_go(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale, size_t scale_stride,
                        int B, const RhsState* st, int nstrips, int nwarps, int seg) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
-  auto kern = wave::k_pre_wa<NU, NW, MS>;
+  auto kern = wave::k_pre_wa<NU, NW, MS, VT>;
   constexpr int S = wave::RingLen<wave::PreW<NU, 1>::P, NU, MS>::S;
   constexpr size_t smem = wave::LaneRingSmem<NW, S>::bytes();
   MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)););
   const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  const float smul = std::is_same<VT, cf>::value ? 1.f : h.zmul;
   kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.D, (const cf*)lv.wDinv,
-                                          (cf*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx,
+                                          (VT*)lv.vpre, lv.n(), (cf*)cl.b, cl.n(), lv.nx, lv.ny, cl.nx,
                                           (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega), nstrips, nwarps,
-                                          seg, st);
+                                          seg, st, smul);
   return MGH_OK;
 }
 
-template <int NU, int NW, int MS>
+template <int NU, int NW, int MS, typename VT = cf>
 mgh_status post_lane_go(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale,
                         size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st, int nstrips,
                         int nwarps, int seg) {
   const Level& lv = h.lev[l];
   const Level& cl = h.lev[l + 1];
-  auto kern = wave::k_post_wa<NU, NW, MS>;
+  auto kern = wave::k_post_wa<NU, NW, MS, VT, VT>;
   constexpr int S = wave::RingLen<wave::PostW<NU, 1>::P, NU, MS>::S;
   constexpr size_t smem = wave::LaneRingSmem<NW, S>::bytes();
   MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)););
   const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  const float smul = std::is_same<VT, cf>::value ? 1.f : h.zmul;
+  // an FP16 result goes to the FP16 slot whose address the caller passed as `out`
   kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.wDinv,
-                                          (const cf*)lv.vpre, lv.n(), (const cf*)cl.vfin, cl.n(), cl.nx, cl.ny, out,
-                                          out_stride, lv.nx, lv.ny, (float)(1.0 / (lv.h * lv.h)),
-                                          (float)(1.0 - h.p.omega), nstrips, nwarps, seg, st);
+                                          (const VT*)lv.vpre, lv.n(), (const cf*)cl.vfin, cl.n(), cl.nx, cl.ny,
+                                          reinterpret_cast<VT*>(out), out_stride, lv.nx, lv.ny,
+                                          (float)(1.0 / (lv.h * lv.h)), (float)(1.0 - h.p.omega), nstrips, nwarps,
+                                          seg, st, smul);
   return MGH_OK;
 }
 
@@ -1002,8 +1009,9 @@ mgh_status launch_pre_wave(Handle& h, int l, const cf* bin, size_t b_stride, con
                            size_t scale_stride, int B, const RhsState* st) {
   const Level& lv = h.lev[l];
   using G = wave::PreW<NU, 2>;   // period of the PF = 2 variant (a multiple of the PF = 1 one)
+  const bool hv = l == 0 && h.half;   // v_pre in FP16: 8-byte pairs
   const bool v4 = lv.nx % 2 == 0 && b_stride % 2 == 0 && lv.n() % 2 == 0 && a16(bin) && a16(lv.D) &&
-                  a16(lv.wDinv) && a16(lv.vpre);
+                  a16(lv.wDinv) && (hv ? a8(lv.vpre) : a16(lv.vpre));
   const bool ring = v4 && h.wave_ring > 0;
   const int period = !ring ? G::P
                            : (h.wave_ring >= 2 ? wave::RingLen<wave::PreW<NU, 1>::P, NU, 2>::S
@@ -1018,6 +1026,12 @@ mgh_status launch_pre_wave(Handle& h, int l, const cf* bin, size_t b_stride, con
   const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * G::H - 1, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
+  if (l == 0 && h.half) {   // FP16 storage: lane rings, 4 warps, one unroll period (checked at create)
+    if (!ring) return MGH_NOT_SUPPORTED;
+    MGH_TRY((pre_lane_go<NU, 4, 1, __half2>(h, l, bin, b_stride, bscale, scale_stride, B, st, nstrips, nwarps, seg)));
+    MGH_CHECK_LAUNCH(); h.launches++;
+    return MGH_OK;
+  }
   if (ring) {
     if (h.wave_lane_ring)
       MGH_TRY(MGH_RING_DISPATCH(pre_lane_go, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,
@@ -1039,8 +1053,9 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
                             size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st) {
   const Level& lv = h.lev[l];
   using G = wave::PostW<NU, 2>;
+  const bool hv = l == 0 && h.half;   // v_pre and the result in FP16: 8-byte pairs
   const bool v4 = lv.nx % 2 == 0 && b_stride % 2 == 0 && out_stride % 2 == 0 && lv.n() % 2 == 0 && a16(bin) &&
-                  a16(out) && a16(lv.wDinv) && a16(lv.vpre);
+                  (hv ? a8(out) && a8(lv.vpre) : a16(out) && a16(lv.vpre)) && a16(lv.wDinv);
   const bool ring = v4 && h.wave_ring > 0;
   const int period = !ring ? G::P
                            : (h.wave_ring >= 2 ? wave::RingLen<wave::PostW<NU, 1>::P, NU, 2>::S
@@ -1055,6 +1070,13 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
   const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * NU, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
+  if (l == 0 && h.half) {
+    if (!ring) return MGH_NOT_SUPPORTED;
+    MGH_TRY((post_lane_go<NU, 4, 1, __half2>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st,
+                                             nstrips, nwarps, seg)));
+    MGH_CHECK_LAUNCH(); h.launches++;
+    return MGH_OK;
+  }
   if (ring) {
     if (h.wave_lane_ring)
       MGH_TRY(MGH_RING_DISPATCH(post_lane_go, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,

@@ -20,7 +20,10 @@
 // masked before it is restricted.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <cstddef>
+#include <type_traits>
 #include <utility>
 
 #include "mgh_common.cuh"
@@ -80,6 +83,29 @@ __device__ __forceinline__ void st2(cf* __restrict__ p, ptrdiff_t off, bool ok0,
     if (ok0) p[off] = v.a;
     if (ok1) p[off + 1] = v.b;
   }
+}
+
+// Complex FP16 storage (MGH_PREC_MIXED16): one __half2 per point, x = re, y = im.  Arithmetic
+// stays FP32; values are rounded to nearest on store.
+__device__ __forceinline__ __half2 to_h2(cf v) { return __floats2half2_rn(v.re, v.im); }
+__device__ __forceinline__ cf from_h2(__half2 v) {
+  const float2 f = __half22float2(v);
+  return mk<float>(f.x, f.y);
+}
+
+// The lane's two points (8 bytes, g0 even so the pair is 8-byte aligned) as FP16.
+__device__ __forceinline__ void st2h(__half2* __restrict__ p, ptrdiff_t off, bool ok0, const C2& v) {
+  if (ok0) {
+    __half2 h[2] = {to_h2(v.a), to_h2(v.b)};
+    *reinterpret_cast<uint2*>(p + off) = *reinterpret_cast<const uint2*>(h);
+  }
+}
+
+// Store of the lane's two points in the storage type VT (cf or __half2).
+template <typename VT>
+__device__ __forceinline__ void st2v(VT* __restrict__ p, ptrdiff_t off, bool ok0, bool ok1, const C2& v) {
+  if constexpr (std::is_same<VT, __half2>::value) st2h(p, off, ok0, v);
+  else st2<true>(p, off, ok0, ok1, v);
 }
 
 // Damped Jacobi at one point: (1 - omega) c + (omega/D) (sb + (l + r + u + d) / h^2).
@@ -731,6 +757,9 @@ struct LaneRingSmem {
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src, uint32_t n) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
 }
+__device__ __forceinline__ void cp8(uint32_t dst, const void* src, uint32_t n) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -743,19 +772,34 @@ struct LaneRing {
   int i0, ny, nx, g0;
   bool in0;
 
-  // row r into slot s: the lane's columns of the three arrays, then one commit group
-  __device__ __forceinline__ void issue(int r, int s, const cf* a0, const cf* a1, const cf* a2) const {
+  // row r into slot s: the lane's columns of the three arrays, then one commit group; array 0 may
+  // be stored in FP16 (8 bytes for the lane's two points, in the first half of its 16-byte cell)
+  template <typename A0>
+  __device__ __forceinline__ void issue(int r, int s, const A0* a0, const cf* a1, const cf* a2) const {
     const int y = i0 + r;
     const bool ok = in0 && y >= 0 && y < ny;
     const size_t off = ok ? (size_t)y * nx + g0 : 0;
-    const uint32_t n = ok ? 16u : 0u;
     const uint32_t d = base + (uint32_t)(s * 3) * 512u;
-    cp16(d, a0 + off, n);
-    cp16(d + 512u, a1 + off, n);
-    cp16(d + 1024u, a2 + off, n);
+    if constexpr (std::is_same<A0, __half2>::value) cp8(d, a0 + off, ok ? 8u : 0u);
+    else cp16(d, a0 + off, ok ? 16u : 0u);
+    cp16(d + 512u, a1 + off, ok ? 16u : 0u);
+    cp16(d + 1024u, a2 + off, ok ? 16u : 0u);
     cp_commit();
   }
   __device__ __forceinline__ C2 get(int s, int a) const { return lds2(mine + (s * 3 + a) * 64); }
+  // array 0 of slot s stored as FP16
+  __device__ __forceinline__ C2 get_h(int s) const {
+    const uint2 u = *reinterpret_cast<const uint2*>(mine + (s * 3) * 64);
+    C2 r;
+    r.a = from_h2(*reinterpret_cast<const __half2*>(&u.x));
+    r.b = from_h2(*reinterpret_cast<const __half2*>(&u.y));
+    return r;
+  }
+  template <typename A0>
+  __device__ __forceinline__ C2 get0(int s) const {
+    if constexpr (std::is_same<A0, __half2>::value) return get_h(s);
+    else return get(s, 0);
+  }
 };
 
 template <int NW, int S>
@@ -778,12 +822,15 @@ __device__ __forceinline__ LaneRing lane_ring_begin(unsigned char* smem, int nx,
   return g;
 }
 
-template <int NU, int NW, int MS>
+// VT: storage of v_pre (cf, or __half2 for FP16 storage).  smul multiplies the right-hand side's
+// scale: the cycle is linear, so every output (v_pre, the restricted residual and, through the
+// coarser levels and the post kernel, z) is smul times the cycle of the scaled input.
+template <int NU, int NW, int MS, typename VT = cf>
 __global__ void __launch_bounds__(32 * NW)
 k_pre_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
-         const cf* __restrict__ D, const cf* __restrict__ wD, cf* __restrict__ vpre, size_t v_stride,
+         const cf* __restrict__ D, const cf* __restrict__ wD, VT* __restrict__ vpre, size_t v_stride,
          cf* __restrict__ bc, size_t bc_stride, int nx, int ny, int nxc, float ih, float om1, int nstrips,
-         int nwarps, int seg, const RhsState* __restrict__ st) {
+         int nwarps, int seg, const RhsState* __restrict__ st, float smul) {
   static_assert(NU >= 1, "the wavefront pre kernel starts with one pointwise sweep");
   using G = PreW<NU, 1>;
   constexpr int H = G::H, HX = G::HX, XO = G::XO, R = G::R;
@@ -801,10 +848,10 @@ k_pre_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__
   const bool own = lane >= HX / 2 && lane < HX / 2 + XO / 2;
   const int ci = g0 >> 1;
   const bool own_c = own && g0 >= 0 && ci < nxc;
-  const float sc = bscale ? (float)bscale[rhs * scale_stride] : 1.f;
+  const float sc = smul * (bscale ? (float)bscale[rhs * scale_stride] : 1.f);
   const float fw = 0.0625f * sc;   // full-weighting factor 1/16 times the right-hand side's scale
   const cf* __restrict__ bb = bin + rhs * b_stride;
-  cf* __restrict__ vo = vpre + rhs * v_stride;
+  VT* __restrict__ vo = vpre + rhs * v_stride;
   cf* __restrict__ co = bc + rhs * bc_stride;
   const int i0 = ys - H;
   int rows = ny - ys < seg ? ny - ys : seg;
@@ -869,19 +916,21 @@ k_pre_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__
       {
         const int yv = i0 + k - (NU - 1);
         if (yv >= ys && yv < ys + seg && yv < ny)
-          st2<true>(vo, (ptrdiff_t)yv * nx + g0, own && in0, own && in1, scale2(sc, v[NU - 1][slot(Kc, NU - 1, R)]));
+          st2v<VT>(vo, (ptrdiff_t)yv * nx + g0, own && in0, own && in1, scale2(sc, v[NU - 1][slot(Kc, NU - 1, R)]));
       }
     });
   }
   cp_wait<0>();   // the copies of rows past the end
 }
 
-template <int NU, int NW, int MS>
+// VT: storage of v_pre, OT: storage of the result (cf, or __half2 for FP16 storage); smul as in
+// k_pre_wa (the same factor must reach both kernels of a cycle).
+template <int NU, int NW, int MS, typename VT = cf, typename OT = cf>
 __global__ void __launch_bounds__(32 * NW)
 k_post_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
-          const cf* __restrict__ wD, const cf* __restrict__ vpre, size_t v_stride, const cf* __restrict__ ec,
-          size_t ec_stride, int nxc, int nyc, cf* __restrict__ out, size_t out_stride, int nx, int ny, float ih,
-          float om1, int nstrips, int nwarps, int seg, const RhsState* __restrict__ st) {
+          const cf* __restrict__ wD, const VT* __restrict__ vpre, size_t v_stride, const cf* __restrict__ ec,
+          size_t ec_stride, int nxc, int nyc, OT* __restrict__ out, size_t out_stride, int nx, int ny, float ih,
+          float om1, int nstrips, int nwarps, int seg, const RhsState* __restrict__ st, float smul) {
   static_assert(NU >= 1, "the wavefront post kernel ends with a sweep");
   using G = PostW<NU, 1>;
   constexpr int HX = G::HX, XO = G::XO, R = G::R;
@@ -899,11 +948,11 @@ k_post_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict_
   const bool own = lane >= HX / 2 && lane < HX / 2 + XO / 2;
   const int ci = g0 >> 1;
   const bool okc0 = ci >= 0 && ci < nxc, okc1 = ci + 1 >= 0 && ci + 1 < nxc;
-  const float sc = bscale ? (float)bscale[rhs * scale_stride] : 1.f;
+  const float sc = smul * (bscale ? (float)bscale[rhs * scale_stride] : 1.f);
   const cf* __restrict__ bb = bin + rhs * b_stride;
-  const cf* __restrict__ vp = vpre + rhs * v_stride;
+  const VT* __restrict__ vp = vpre + rhs * v_stride;
   const cf* __restrict__ eb = ec + rhs * ec_stride;
-  cf* __restrict__ o = out + rhs * out_stride;
+  OT* __restrict__ o = out + rhs * out_stride;
   const int i0 = ys - NU;
   const int rows = ny - ys < seg ? ny - ys : seg;
   const int K = (rows + 2 * NU + S - 1) / S * S;
@@ -953,7 +1002,7 @@ k_post_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict_
       const bool oky = y >= 0 && y < ny;
       constexpr int s0 = slot(Kc, 0, R);
       {
-        const C2 vpk = g.get(Kc, 0);
+        const C2 vpk = g.template get0<VT>(Kc);
         v[0][s0].a = sel(oky && in0, vpk.a + pe.a);
         v[0][s0].b = sel(oky && in1, vpk.b + pe.b);
       }
@@ -970,7 +1019,7 @@ k_post_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict_
         const C2 vn = jac_row(v[NU - 1][slot(Kc, NU + 1, R)], v[NU - 1][so], v[NU - 1][slot(Kc, NU - 1, R)],
                               scale2(sc, g.get(gs, 1)), g.get(gs, 2), ih, om1);
         const int yv = y - NU;
-        if (yv >= ys && yv < ys + seg && yv < ny) st2<true>(o, (ptrdiff_t)yv * nx + g0, own && in0, own && in1, vn);
+        if (yv >= ys && yv < ys + seg && yv < ny) st2v<OT>(o, (ptrdiff_t)yv * nx + g0, own && in0, own && in1, vn);
       }
     });
   }

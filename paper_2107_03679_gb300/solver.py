@@ -16,9 +16,12 @@ from . import capi
 
 def resolve_arnoldi(arnoldi: str, precision: str, restart: int) -> str:
     """"auto": s-step cycles on the mixed path when the restart length allows them (m <= 8),
-    otherwise the double-float Arnoldi; the FP64 path always runs native FP64 Gram-Schmidt."""
+    otherwise the double-float Arnoldi; FP16 storage (mixed16) runs only with s-step cycles; the
+    FP64 path always runs native FP64 Gram-Schmidt."""
     if arnoldi != "auto":
         return arnoldi
+    if precision == "mixed16":
+        return "sstep"
     if precision != "mixed32":
         return "df"
     return "sstep" if restart <= 8 else "df"

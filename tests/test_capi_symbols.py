@@ -84,6 +84,22 @@ def test_host_only_entry_points(lib):
     bc.restart, bc.krylov = 8, 2
     with pytest.raises(capi.MGHError):
         capi.mgh_workspace_bytes(bc)
+    # FP16 storage (MGH_PREC_MIXED16): s-step FGMRES, even width, a sweep on each side of level 0
+    hs = capi.mgh_default_params()
+    hs.precision, hs.arnoldi, hs.restart = capi.MGH_PREC_MIXED16, capi.MGH_ARNOLDI_SSTEP, 8
+    assert capi.mgh_workspace_bytes(hs) > 0
+    for field, value in (("arnoldi", capi.MGH_ARNOLDI_DF), ("krylov", capi.MGH_KRYLOV_BICGSTAB), ("nx_int", 129),
+                         ("nu2", 0)):
+        bad = capi.mgh_default_params()
+        bad.precision, bad.arnoldi, bad.restart = capi.MGH_PREC_MIXED16, capi.MGH_ARNOLDI_SSTEP, 8
+        setattr(bad, field, value)
+        with pytest.raises(capi.MGHError) as e:
+            capi.mgh_workspace_bytes(bad)
+        assert e.value.status == capi.MGH_NOT_SUPPORTED, field
+    bad = capi.mgh_default_params()
+    bad.precision = 3
+    with pytest.raises(capi.MGHError):
+        capi.mgh_workspace_bytes(bad)
 
 
 def test_reconstruction_entry_points_validate_on_the_host(lib):
