@@ -43,7 +43,11 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mgh", "reference"], default="mgh")
     ap.add_argument("--workload", default="ellipses576")
-    ap.add_argument("--precision", choices=["mixed32", "fp64"], default=None)
+    ap.add_argument("--precision", choices=["mixed32", "mixed16", "fp64"], default=None,
+                    help="mixed16: FP16 storage of the level-0 iterate and the preconditioned vectors")
+    ap.add_argument("--split", type=int, default=1,
+                    help="split the angles over this many handles on concurrent streams (coarse levels of one "
+                         "part overlap the fine levels of another)")
     ap.add_argument("--angles", type=int, default=None,
                     help="use only the first N illumination angles (smaller case for profiling)")
     ap.add_argument("--restart", type=int, default=None, help="GMRES restart length (default: the workload's)")
@@ -76,6 +80,8 @@ def parse_args(argv=None):
     ap.add_argument("--sample-angle", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain-FP64 run of the same step (speed-up at the same accuracy)")
+    ap.add_argument("--no-fp16-compare", action="store_true",
+                    help="skip the run of the same step with FP16 storage on the fine level (mixed16)")
     return ap.parse_args(argv)
 
 
@@ -171,12 +177,15 @@ def coarse_fraction(nx: int, ny: int, levels: int, gamma: int = 1) -> float:
     return tot / (nx * ny)
 
 
-def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, cfrac: float = 0.0) -> dict:
+def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, cfrac: float = 0.0,
+                      zs: int = None) -> dict:
     """Minimal bytes of each kernel class from the engine counters (fields read once, per-grid
     coefficient arrays counted once per launch).  N = fine points, cs = bytes of one complex
-    number of the multigrid precision; engine = "df", "sstep" or "fp64"; cfrac = points of the
-    coarser smoothing levels per fine point (their fields fit in L2, so this class is not bound
-    by DRAM alone)."""
+    number of the multigrid precision, zs = bytes of one stored level-0 iterate / preconditioned
+    vector entry (cs, or 4 with FP16 storage); engine = "df", "sstep" or "fp64"; cfrac = points of
+    the coarser smoothing levels per fine point (their fields fit in L2, so this class is not
+    bound by DRAM alone)."""
+    zs = cs if zs is None else zs
     steps = prof["arnoldi_steps"]
     c16 = 16
     if engine == "bicgstab":
@@ -197,14 +206,14 @@ def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, 
             # levels 1 .. L-2: pre reads b, writes v and the restricted residual; post reads b, v and
             # the coarse correction, writes the result
             "vcycle_coarse": run * N * cfrac * cs * (3.25 + 3.25),
-            "vcycle_pre_l0": run * N * (8 + cs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
-            "vcycle_post_l0": run * N * (8 + 2 * cs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
+            "vcycle_pre_l0": run * N * (8 + zs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
+            "vcycle_post_l0": run * N * (8 + 2 * zs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
             # v_{k+1} = A z_k in FP32: read z_k, write v_{k+1}; D_A (FP32) per launch
-            "matvec_dots": run * N * (cs + cs) + launches["matvec_dots"] * cs * N,
+            "matvec_dots": run * N * (zs + cs) + launches["matvec_dots"] * cs * N,
             # Gram sweep: read the m + 1 FP32 basis vectors
             "gs_update": prof["gram_reads"] * N * cs,
             "true_residual": prof["residuals"] * N * 3 * c16,
-            "x_update": prof["updates"] * N * 2 * c16 + prof["update_reads"] * N * cs,
+            "x_update": prof["updates"] * N * 2 * c16 + prof["update_reads"] * N * zs,
         }
     if engine == "df":
         # double-float Arnoldi (mixed path): the V-cycle reads the 8-byte hi plane of u_j
@@ -411,8 +420,26 @@ def gpu_main(args, rank, world, local_rank):
     d_y = solver.sample(u_gt, d_rec)
     del u_gt
     u = solver.field(B)
+    runner = solver          # what the timed steps drive: one handle, or the angles split over several
+    if args.split > 1:
+        from paper_2107_03679_gb300.multi import SplitBatch
+        solver.close()
+        runner = SplitBatch.from_workload(w, batch_max=B, parts=args.split, precision=precision, device=dev,
+                                          maxit=args.maxit, arnoldi=args.arnoldi, krylov=args.krylov,
+                                          cycle_type=args.cycle)
+        solver = runner.solvers[0]
+        stream = torch.cuda.current_stream(dev)
+        u_crop = torch.empty((B, w.ny_int, w.nx_int), dtype=torch.complex128, device=dev)
+
+    def sample_all(uu):
+        if args.split == 1:
+            return solver.sample(uu, d_rec)
+        return torch.cat([s.sample(uu[a:b], d_rec) for s, (a, b) in zip(runner.solvers, runner.ranges(B))])
 
     def step(f_dev, y_dev):
+        if args.split > 1:   # every stage below, per part, parts on concurrent streams
+            loss, g, inf_f, inf_a = runner.data_term_gradient(f_dev, d_th, d_rec, y_dev, u, crop_out=u_crop)
+            return g, loss, inf_f, inf_a, u_crop
         solver.set_contrast(f_dev)                               # contrast, hierarchy, coarsest inverse
         _, inf_f = solver.forward(d_th, out=u)                   # right-hand sides + forward solves
         u_int = solver.crop(u)                                   # truncation to the interior
@@ -434,7 +461,7 @@ def gpu_main(args, rank, world, local_rank):
     # ---- device-timed region: inputs resident in HBM
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0] or 0)
                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local_rank)
-    l0 = solver.launch_count()
+    l0 = runner.launch_count()
     barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -448,14 +475,14 @@ def gpu_main(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    launches = solver.launch_count() - l0
+    launches = runner.launch_count() - l0
     # ---- kernel classes: the same K steps once more, every launch bracketed by CUDA events on
     # the solver's stream (kept out of the timed region above, whose time they would inflate)
-    solver.profile_enable(True)
+    runner.profile_enable(True)
     for _ in range(args.steps):
         step(d_f, d_y)
-    prof = solver.profile_read()
-    solver.profile_enable(False)
+    prof = runner.profile_read()
+    runner.profile_enable(False)
     ms = ev0.elapsed_time(ev1)
     ms_max = ms
     if world > 1:
@@ -487,7 +514,7 @@ def gpu_main(args, rank, world, local_rank):
             y_dev = h_y.to(dev, non_blocking=True)
             g, loss, _, _, _ = step(f_dev, y_dev)
             h_g.copy_(g, non_blocking=True)
-            h_s.copy_(solver.sample(u, d_rec), non_blocking=True)
+            h_s.copy_(sample_all(u), non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -503,7 +530,7 @@ def gpu_main(args, rank, world, local_rank):
     # ---- the plain FP64 form of the same step at the same accuracy (FP64 cycle, native-FP64 Arnoldi,
     # the same acceptance test): one warm-up and at most two timed steps, CUDA events on its stream
     fp64 = None
-    if not args.no_fp64_compare and precision == "mixed32" and args.krylov == "fgmres":
+    if not args.no_fp64_compare and precision != "fp64" and args.krylov == "fgmres":
         s64 = Solver.from_workload(w, batch_max=B, precision="fp64", device=dev, maxit=args.maxit,
                                    cycle_type=args.cycle)
         u64 = s64.field(B)
@@ -543,14 +570,57 @@ def gpu_main(args, rank, world, local_rank):
                         "same restart, levels, sweeps and FP64 acceptance test"}
         s64.close()
 
+    # ---- the same step with FP16 storage of the level-0 iterate and the preconditioned vectors
+    # (MGH_PREC_MIXED16): one warm-up and at most three timed steps
+    fp16 = None
+    if not args.no_fp16_compare and precision == "mixed32" and args.krylov == "fgmres" and solver.arnoldi == "sstep":
+        s16 = Solver.from_workload(w, batch_max=B, precision="mixed16", device=dev, maxit=args.maxit,
+                                   cycle_type=args.cycle)
+        u16 = s16.field(B)
+
+        def step16():
+            s16.set_contrast(d_f)
+            _, a_ = s16.forward(d_th, out=u16)
+            _, G_, _ = s16.misfit(u16, d_y, d_rec)
+            _, b_ = s16.gradient(d_th, u16, G_)
+            return a_ + b_
+
+        step16()
+        k16 = min(args.steps, 3)
+        barrier()
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(s16.stream)
+        inf16 = []
+        for _ in range(k16):
+            inf16 += step16()
+        h1.record(s16.stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms16 = h0.elapsed_time(h1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms16], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms16 = float(t.item())
+        fp16 = {"value": round(world * 2 * B * k16 / (ms16 / 1e3), 3), "unit": UNIT, "steps": k16, "warmup": 1,
+                "ms_per_step": round(ms16 / k16, 2), "converged": all(i["converged"] for i in inf16),
+                "worst_rel_residual": max(i["rel_residual"] for i in inf16),
+                "iterations_mean": round(sum(i["iterations"] for i in inf16) / len(inf16), 1),
+                "what": "the same step with the level-0 iterate and the preconditioned vectors stored in FP16 "
+                        "(MGH_PREC_MIXED16), FP32 arithmetic"}
+        s16.close()
+
     if rank != 0:
         return
 
     # ---- roofline of the dominant kernel class (CUDA events over the timed region)
     cs = 16 if precision == "fp64" else 8
     N = solver.N
-    engine = "bicgstab" if args.krylov == "bicgstab" else (solver.arnoldi if precision == "mixed32" else "fp64")
-    alg = algorithmic_bytes(prof, N, cs, prof["launches"], engine, coarse_fraction(w.nx, w.ny, w.levels, 2 if args.cycle == "w" else 1))
+    engine = "bicgstab" if args.krylov == "bicgstab" else (solver.arnoldi if precision != "fp64" else "fp64")
+    alg = algorithmic_bytes(prof, N, cs, prof["launches"], engine,
+                            coarse_fraction(w.nx, w.ny, w.levels, 2 if args.cycle == "w" else 1),
+                            zs=4 if precision == "mixed16" else cs)
     ms_cls = prof["ms"]
     # the dominant kernel: the class with the most time among those that are one kernel each (the
     # coarser multigrid levels and the per-RHS reductions are many small kernels)
@@ -605,19 +675,22 @@ def gpu_main(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if precision == "mixed32" else "f64", "data": "synthetic",
+        "dtype": {"mixed32": "f32+f64", "mixed16": "f16-stored f32+f64"}.get(precision, "f64"), "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
                    "angles_per_gpu": B, "angles_total": B * world, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
-                   "restart": w.restart, "tol": w.tol, "krylov": args.krylov, "cycle": args.cycle.upper(), "arnoldi": solver.arnoldi if precision == "mixed32" else "fp64", "shift": [w.shift_re, w.shift_im],
+                   "restart": w.restart, "tol": w.tol, "krylov": args.krylov, "cycle": args.cycle.upper(), "arnoldi": solver.arnoldi if precision != "fp64" else "fp64", "shift": [w.shift_re, w.shift_im],
                    "step": f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient",
                    "solves_per_step": 2 * B, "l2": "inputs larger than L2 (Krylov basis "
-                   f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}"},
+                   f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}",
+                   "split": (f"{B} angles as {args.split} handles of about {-(-B // args.split)} on concurrent streams"
+                             if args.split > 1 else None)},
         "roofline": roof,
         "kernels": kernels,
         "iterations": {"mean": round(sum(its) / len(its), 1), "min": min(its), "max": max(its)},
         "converged": conv, "worst_rel_residual": worst,
         "gpu_launches": int(launches),
         "fp64_same_accuracy": fp64,
+        "fp16_storage": fp16,
         "autotuned": tuned,
         "clocks": clk,
         "e2e": e2e,
@@ -823,7 +896,7 @@ def uneven_main(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": round(solves / sec, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed32" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"mixed32": "f32+f64", "mixed16": "f16-stored f32+f64"}.get(precision, "f64"),
         "data": "synthetic",
         "config": {"workload": "uneven", "grids": [f"{d['w'].nx}x{d['w'].ny}:{d['th'].numel()}" for d in jobs],
                    "precision": precision, "timing": "host wall clock around all streams"},
@@ -892,7 +965,7 @@ def multifreq_main(args, rank, world, local_rank):
         print(json.dumps({
             "metric": METRIC, "value": round(solves / sec, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed32" else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"mixed32": "f32+f64", "mixed16": "f16-stored f32+f64"}.get(precision, "f64"),
             "data": "synthetic",
             "config": {"workload": "multifreq576", "grid": f"{base.nx}x{base.ny}", "frequencies_GHz": [3, 5, 6, 8],
                        "points_per_wavelength": [round(w.ppw, 2) for w in ws], "angles": B,

@@ -127,3 +127,92 @@ class MultiFrequency:
         for _, g, _ in res[1:]:
             grad = grad + g
         return sum(r[0] for r in res), grad, [r[2] for r in res]
+
+
+class SplitBatch:
+    """One contrast at one frequency with the batch of illumination angles split over several
+    handles of the same configuration, each with its own CUDA stream and host thread.  The angles
+    are independent problems, so the results are those of one handle over all angles; what changes
+    is the schedule: while one part runs the coarse levels of its multigrid cycle (short kernels
+    that cannot fill the GPU), another part's fine-level kernels run beside them.  The data term
+    and its gradient are sums over the parts (Prop. 1 sums over illuminations)."""
+
+    def __init__(self, solvers: Sequence[Solver]):
+        if not solvers:
+            raise ValueError("at least one part")
+        self.solvers = list(solvers)
+
+    @classmethod
+    def from_workload(cls, w, batch_max: int, parts: int = 2, device: Optional[torch.device] = None, **kw):
+        """`parts` handles of w's configuration, each for at most ceil(batch_max / parts) angles and
+        on a new stream."""
+        if parts < 1 or parts > batch_max:
+            raise ValueError("parts must be in [1, batch_max]")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        per = -(-batch_max // parts)
+        return cls([Solver.from_workload(w, batch_max=per, device=dev, stream=torch.cuda.Stream(dev), **kw)
+                    for _ in range(parts)])
+
+    @property
+    def arnoldi(self) -> str:
+        return self.solvers[0].arnoldi
+
+    def close(self):
+        for s in self.solvers:
+            s.close()
+
+    def launch_count(self) -> int:
+        return sum(s.launch_count() for s in self.solvers)
+
+    def ranges(self, n: int):
+        """[start, stop) of every part's share of n angles (sizes differ by at most one)."""
+        from .distributed import shard
+        return [shard(n, i, len(self.solvers)) for i in range(len(self.solvers))]
+
+    def data_term_gradient(self, f_d: torch.Tensor, theta: torch.Tensor, rec: torch.Tensor, y: torch.Tensor,
+                           u_out: torch.Tensor, crop_out: Optional[torch.Tensor] = None):
+        """Set the contrast, solve every angle's forward problem into u_out ([B][ny][nx]; cropped to
+        the interior into crop_out when given), form the receiver misfit against y ([B][M]) and solve
+        the adjoint problems; returns (loss, gradient in f_d, forward infos, adjoint infos), each over
+        all B angles in order."""
+        rs = self.ranges(theta.numel())
+
+        def one(i, s):
+            a, b = rs[i]
+            s.set_contrast(f_d)
+            u, inf_f = s.forward(theta[a:b], out=u_out[a:b])
+            if crop_out is not None:
+                crop_out[a:b].copy_(s.crop(u))
+            _, G, loss = s.misfit(u, y[a:b], rec)
+            g, inf_a = s.gradient(theta[a:b], u, G)
+            return loss, g, inf_f, inf_a
+
+        res = run_concurrently(self.solvers, one)
+        if res[0][1].is_cuda:
+            cur = torch.cuda.current_stream()
+            for _, g, _, _ in res:   # made on a part's stream, used on the caller's
+                g.record_stream(cur)
+        grad = res[0][1]
+        for _, g, _, _ in res[1:]:
+            grad = grad + g
+        return (sum(r[0] for r in res), grad, [i for r in res for i in r[2]], [i for r in res for i in r[3]])
+
+    def profile_enable(self, enable: bool = True) -> None:
+        for s in self.solvers:
+            s.profile_enable(enable)
+
+    def profile_read(self) -> dict:
+        """The parts' profiles summed (class times add up across concurrent streams)."""
+        out = None
+        for s in self.solvers:
+            p = s.profile_read()
+            if out is None:
+                out = {k: (dict(v) if isinstance(v, dict) else v) for k, v in p.items()}
+                continue
+            for k, v in p.items():
+                if isinstance(v, dict):
+                    for c, x in v.items():
+                        out[k][c] = out[k].get(c, 0) + x
+                else:
+                    out[k] = out[k] + v
+        return out

@@ -138,3 +138,66 @@ def test_multifrequency_workloads_scale_points_per_wavelength():
     assert all(w.nx == base.nx and w.seed == base.seed and w.n_angles == base.n_angles for w in ws)
     assert np.array_equal(W.phantom(ws[0]), W.phantom(base))
     assert ws[-1].k == pytest.approx(base.k) and ws[0].k == pytest.approx(base.k * 3 / 8)
+
+
+class _OracleStandIn:
+    """CPU stand-in for a Solver handle (the calls SplitBatch makes), backed by the FP64 oracle."""
+
+    stream = None
+
+    def __init__(self, p, levels=2):
+        self.p, self.levels, self.s = p, levels, None
+
+    def set_contrast(self, f_d):
+        self.s = O.MGHSolver(self.p, f_d.numpy(), levels=self.levels, nu1=1, nu2=1, tol=1e-12)
+
+    def forward(self, theta, out=None):
+        u, infos = self.s.forward(theta.numpy())
+        out.copy_(torch.from_numpy(u))
+        return out, infos
+
+    def crop(self, u):
+        return torch.from_numpy(O.crop(self.p, u.numpy()))
+
+    def misfit(self, u, y, rec):
+        r, loss = O.misfit(O.sample(u.numpy(), rec.numpy()), y.numpy())
+        G = np.zeros((u.shape[0], self.p.ny * self.p.nx), dtype=np.complex128)
+        G[:, rec.numpy()] = r
+        return torch.from_numpy(r), torch.from_numpy(G.reshape(u.shape)), loss
+
+    def gradient(self, theta, u, G):
+        g = np.zeros((self.p.ny_int, self.p.nx_int))
+        infos = []
+        for q, th in enumerate(theta.numpy()):
+            z, info = self.s.solve(np.conj(G[q].numpy()))
+            infos.append(info)
+            g += O.gradient_from_adjoint(self.p, z[None], (u[q].numpy() + O.incident_field(self.p, float(th)))[None])
+        return torch.from_numpy(g), infos
+
+
+def test_split_batch_equals_one_handle_over_all_angles():
+    """SplitBatch: 5 angles over 2 parts (3 + 2), each part solving its share in its own thread;
+    loss, gradient, fields, cropped fields and infos equal one solver's over all angles."""
+    from paper_2107_03679_gb300.multi import SplitBatch
+    w = W.Workload("split", 12, 12, 3, 6.0, 5, -40.0, 40.0, "gt_ellipse", 4, levels=2, nu1=1, nu2=1,
+                   precision="fp64")
+    p = O.Problem.from_workload(w)
+    f_gt = W.phantom(w)
+    th = W.angles(w)
+    rec = W.receivers(w, f_gt)
+    gt = O.MGHSolver(p, f_gt, levels=2, nu1=1, nu2=1, tol=1e-12)
+    y = O.sample(gt.forward(th)[0], rec)
+    f = 0.5 * f_gt
+    sb = SplitBatch([_OracleStandIn(p), _OracleStandIn(p)])
+    assert sb.ranges(5) == [(0, 3), (3, 5)]
+    u = torch.zeros((5, p.ny, p.nx), dtype=torch.complex128)
+    uc = torch.zeros((5, p.ny_int, p.nx_int), dtype=torch.complex128)
+    loss, g, inf_f, inf_a = sb.data_term_gradient(torch.from_numpy(f), torch.from_numpy(th), torch.from_numpy(rec),
+                                                  torch.from_numpy(y), u, crop_out=uc)
+    ref = O.MGHSolver(p, f, levels=2, nu1=1, nu2=1, tol=1e-12)
+    loss_ref, g_ref, u_ref = ref.gradient(th, rec, y)
+    assert loss == pytest.approx(loss_ref, rel=1e-12)
+    np.testing.assert_allclose(g.numpy(), g_ref, rtol=1e-10, atol=1e-14 * np.abs(g_ref).max())
+    np.testing.assert_allclose(u.numpy(), u_ref, rtol=0, atol=1e-12 * np.abs(u_ref).max())
+    np.testing.assert_array_equal(uc.numpy(), O.crop(p, u.numpy()))
+    assert len(inf_f) == 5 and len(inf_a) == 5
