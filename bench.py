@@ -61,10 +61,12 @@ def parse_args(argv=None):
                          "native-FP64 Arnoldi; auto = s-step when the restart length is at most 8")
     ap.add_argument("--cycle", choices=["v", "w"], default="v",
                     help="multigrid cycle of the preconditioner (CycleType of Alg. 2)")
-    ap.add_argument("--krylov", choices=["fgmres", "bicgstab"], default="fgmres",
-                    help="outer Krylov method: flexible GMRES (default) or the paper's Bi-CGSTAB (Alg. 3)")
-    ap.add_argument("--autotune", action="store_true",
-                    help="pick nu and the restart length with the autotuner (cached) before timing")
+    ap.add_argument("--krylov", choices=["fgmres", "bicgstab"], default=None,
+                    help="outer Krylov method: flexible GMRES or the paper's Bi-CGSTAB (Alg. 3); default: the "
+                         "workload's")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (nu, restart length and level-kernel launch shapes, chosen by timing "
+                         "before the timed region and cached)")
     ap.add_argument("--descent", type=int, default=0,
                     help="instead of the throughput line: N projected gradient-descent steps from f = 0")
     ap.add_argument("--fbs", type=int, default=0,
@@ -396,15 +398,19 @@ def gpu_main(args, rank, world, local_rank):
         w.levels = args.levels
     if args.shift_im is not None:
         w.shift_im = args.shift_im
+    if args.krylov is None:
+        args.krylov = getattr(w, "krylov", "fgmres")
     precision = args.precision or w.precision
     f_gt, f_step, th, rec = make_inputs(w)
     if args.angles:
         th = th[:args.angles]
     B = len(th)
     tuned = None
-    if args.autotune:
+    autotune = not args.no_autotune and args.krylov == "fgmres" and args.nu is None and args.restart is None
+    if autotune:
         from paper_2107_03679_gb300.autotune import tune
-        tuned, trials = tune(w, torch.from_numpy(f_step).to(dev), torch.from_numpy(th), dev, precision=precision)
+        tuned, _ = tune(w, torch.from_numpy(f_step).to(dev), torch.from_numpy(th), dev, precision=precision,
+                        restarts=(5, 8), arnoldi=args.arnoldi, cycle_type=args.cycle)
         w.nu1 = w.nu2 = tuned["nu"]
         w.restart = tuned["restart"]
     solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=args.maxit, arnoldi=args.arnoldi,
@@ -430,6 +436,16 @@ def gpu_main(args, rank, world, local_rank):
         solver = runner.solvers[0]
         stream = torch.cuda.current_stream(dev)
         u_crop = torch.empty((B, w.ny_int, w.nx_int), dtype=torch.complex128, device=dev)
+
+    if autotune:   # launch shapes of the level kernels, tuned on each handle's own batch
+        from paper_2107_03679_gb300.autotune import tune_shapes
+        handles = runner.solvers if args.split > 1 else [solver]
+        nb = -(-B // args.split) if args.split > 1 else B
+        shape, _ = tune_shapes(w, d_f, d_th[:nb], dev, precision=precision, arnoldi=args.arnoldi,
+                               krylov=args.krylov, cycle_type=args.cycle)
+        for hnd in handles:
+            hnd.set_kernel_shape(**{k: shape[k] for k in ("wave_seg", "wave_warps", "wave_ring", "tail_level")})
+        tuned = dict(tuned or {}, shape=shape)
 
     def sample_all(uu):
         if args.split == 1:

@@ -296,6 +296,28 @@ mgh_status mgh_misfit_noalloc(int nx, int ny, const mgh_cdouble* u, const mgh_cd
                               const int64_t* rec, int M, mgh_cdouble* r, mgh_cdouble* G,
                               double* loss_dev, void* cuda_stream);
 
+/* Launch shapes of the FP32 multigrid level kernels (the paper has no counterpart: these are
+ * choices of this implementation, for the autotuner).  They change only speed, never results. */
+typedef struct {
+  int wave_seg[MGH_MAX_LEVELS]; /* rows per warp segment of level l's wavefront kernels (rounded to
+                               an even count the kernel's unroll period allows); 0 = the built-in
+                               waves x steps model picks it for the level and batch */
+  int wave_warps;           /* warps per block of the wavefront kernels: 2 or 4 */
+  int wave_ring;            /* shared-memory row ring of the wavefront kernels in unroll periods:
+                               1 or 2 */
+  int tail_level;           /* first level of the one-kernel coarse tail; 0 = no tail (every level
+                               by level kernels); -1 = the automatic choice (the finest level whose
+                               fields fit one block's shared memory); a level whose fields do not
+                               fit returns MGH_INVALID_ARG */
+} mgh_kernel_shape;
+
+/* Current launch shapes of a handle (tail_level reports the level in use, 0 if none). */
+mgh_status mgh_get_kernel_shape(const mgh_handle* h, mgh_kernel_shape* out);
+
+/* Set the launch shapes for later calls; synchronises the handle's stream first.  MGH_PREC_MIXED16
+ * handles need wave_warps = 4 and wave_ring = 1 (MGH_NOT_SUPPORTED otherwise). */
+mgh_status mgh_set_kernel_shape(mgh_handle* h, const mgh_kernel_shape* s);
+
 /* Test hook for the failure path of the bounded device-side waits (the paper has no counterpart).
  * The next mgh_solve / mgh_forward / mgh_gradient solve of this handle starts with the handle's
  * device error word set, exactly as a kernel whose bounded mbarrier wait gave up would leave it;

@@ -1,11 +1,18 @@
 """Autotuner for the solver's free parameters on a given problem.
 
-The sweep counts nu1 = nu2 of the multigrid cycle and the GMRES restart length trade per-step cost
-against the number of steps, and the best pair depends on the grid, the wavenumber and the
-contrast.  The tuner times complete forward solves of a spread-out sample of the illumination
-angles for every candidate pair (CUDA events on the solver's stream), picks the pair with the
-least time per solve, and caches it in a JSON file keyed by grid, batch, precision and level
-count.  All computation runs in the CUDA library; this module only drives and times it.
+Two stages, both cached in a JSON file keyed by grid, batch, precision, level count and k h:
+
+* Method parameters.  The sweep counts nu1 = nu2 of the multigrid cycle and the GMRES restart
+  length trade per-step cost against the number of steps, and the best pair depends on the grid,
+  the wavenumber and the contrast.  Every candidate pair is timed on complete forward solves of a
+  spread-out sample of the illumination angles (CUDA events on the solver's stream); the pair with
+  the least time per solve wins.
+* Launch shapes of the FP32 level kernels (mgh_set_kernel_shape): the wavefront segment length,
+  warps per block and ring depth, and the first level of the one-kernel coarse tail.  They do not
+  change results, only speed, so each candidate is timed on a fixed number of Arnoldi steps of the
+  full batch (the launch configuration that will run), one axis at a time from the built-in choice.
+
+All computation runs in the CUDA library; this module only drives and times it.
 """
 from __future__ import annotations
 
@@ -21,8 +28,8 @@ CACHE = os.environ.get("MGH_AUTOTUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "mgh_autotune.json"))
 
 
-def _key(nx: int, ny: int, B: int, precision: str, levels: int, k: float) -> str:
-    return f"{nx}x{ny}:B{B}:{precision}:L{levels}:kh{k:.6f}"
+def _key(nx: int, ny: int, B: int, precision: str, levels: int, k: float, what: str = "") -> str:
+    return f"{nx}x{ny}:B{B}:{precision}:L{levels}:kh{k:.6f}" + (f":{what}" if what else "")
 
 
 def _load() -> Dict[str, dict]:
@@ -43,7 +50,7 @@ def _store(data: Dict[str, dict]) -> None:
 
 def tune(w, f_d: torch.Tensor, theta: torch.Tensor, device: torch.device, precision: Optional[str] = None,
          sample: int = 8, nus: Iterable[int] = (1, 2, 3), restarts: Iterable[int] = (5, 8, 12),
-         use_cache: bool = True) -> Tuple[dict, list]:
+         use_cache: bool = True, **solver_kw) -> Tuple[dict, list]:
     """Best (nu, restart) for workload geometry `w` with contrast f_d and angles theta.
 
     Returns (choice, trials); choice = {"nu": .., "restart": .., "ms_per_solve": ..}."""
@@ -58,8 +65,11 @@ def tune(w, f_d: torch.Tensor, theta: torch.Tensor, device: torch.device, precis
     trials = []
     for nu in nus:
         for m in restarts:
-            s = Solver.from_workload(w, batch_max=th.numel(), precision=precision, device=device, nu1=nu, nu2=nu,
-                                     restart=m, maxit=20000)
+            try:
+                s = Solver.from_workload(w, batch_max=th.numel(), precision=precision, device=device, nu1=nu,
+                                         nu2=nu, restart=m, maxit=20000, **solver_kw)
+            except Exception:          # a pair this precision or engine does not support
+                continue
             s.set_contrast(f_d)
             s.forward(th)                      # warm-up (kernel attributes, clocks)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -80,3 +90,74 @@ def tune(w, f_d: torch.Tensor, theta: torch.Tensor, device: torch.device, precis
         cache[key] = choice
         _store(cache)
     return choice, trials
+
+
+def _time_steps(solver: Solver, theta: torch.Tensor, reps: int = 2) -> float:
+    """Milliseconds per Arnoldi step of the whole batch: forward solves capped at the handle's maxit
+    (every right-hand side runs the same number of steps), best of `reps` after one warm-up."""
+    solver.forward(theta)
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(solver.stream)
+        _, infos = solver.forward(theta)
+        e1.record(solver.stream)
+        torch.cuda.synchronize(solver.device)
+        steps = max(1, max(i["iterations"] for i in infos))
+        ms = e0.elapsed_time(e1) / steps
+        best = ms if best is None else min(best, ms)
+    return best
+
+
+def tune_shapes(w, f_d: torch.Tensor, theta: torch.Tensor, device: torch.device, precision: Optional[str] = None,
+                steps: int = 48, use_cache: bool = True, **solver_kw) -> Tuple[dict, list]:
+    """Launch shapes of the level kernels for workload w's full batch theta, one axis at a time:
+    wavefront segment length (0 = the built-in model), warps per block, ring depth, first tail level.
+    Each candidate is timed on `steps` Arnoldi steps of forward solves (maxit = steps).  Returns
+    (shape, trials); shape also holds the time per step of the built-in choice and of the winner."""
+    precision = precision or w.precision
+    B = theta.numel()
+    key = _key(w.nx, w.ny, B, precision, w.levels, w.k * w.h, "shape")
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return cache[key], []
+    s = Solver.from_workload(w, batch_max=B, precision=precision, device=device, maxit=steps, **solver_kw)
+    s.set_contrast(f_d)
+    th = theta.to(device)
+    base = s.kernel_shape()
+    auto_tail = base["tail_level"]
+    best, best_ms = dict(base), _time_steps(s, th)
+    trials = [dict(best, ms_per_step=best_ms)]
+    # levels run by the level kernels: 0 .. tail-1 (all but the coarsest without a tail)
+    top = auto_tail if auto_tail > 0 else w.levels - 1
+
+    def with_seg(shape, l, v):
+        segs = list(shape["wave_seg"])
+        segs[l] = v
+        return dict(shape, wave_seg=segs)
+
+    axes = [(f"wave_seg[{l}]", [(lambda sh, v=v, l=l: with_seg(sh, l, v)) for v in (8, 16, 32, 64, 128)])
+            for l in range(top)]
+    axes += [("wave_warps", [(lambda sh, v=v: dict(sh, wave_warps=v)) for v in (2, 4)]),
+             ("wave_ring", [(lambda sh, v=v: dict(sh, wave_ring=v)) for v in (1, 2)]),
+             ("tail_level", [(lambda sh, v=v: dict(sh, tail_level=v)) for v in (0, auto_tail, auto_tail + 1)])]
+    for _, moves in axes:
+        for move in moves:
+            cand = move(best)
+            if cand == best:
+                continue
+            try:
+                s.set_kernel_shape(**cand)
+            except Exception:          # not available for this handle (e.g. FP16 storage, tail too big)
+                continue
+            ms = _time_steps(s, th)
+            trials.append(dict(cand, ms_per_step=ms))
+            if ms < best_ms * 0.99:    # keep a change only for a clear gain
+                best, best_ms = cand, ms
+        s.set_kernel_shape(**best)
+    s.close()
+    shape = dict(best, ms_per_step=best_ms, builtin_ms_per_step=trials[0]["ms_per_step"], steps_timed=steps)
+    if use_cache:
+        cache[key] = shape
+        _store(cache)
+    return shape, trials

@@ -55,6 +55,11 @@ class mgh_profile(ctypes.Structure):
                 ("cycle_steps", ctypes.c_uint64), ("gram_reads", ctypes.c_uint64)]
 
 
+class mgh_kernel_shape(ctypes.Structure):
+    _fields_ = [("wave_seg", ctypes.c_int * MGH_MAX_LEVELS), ("wave_warps", ctypes.c_int), ("wave_ring", ctypes.c_int),
+                ("tail_level", ctypes.c_int)]
+
+
 class MGHError(RuntimeError):
     def __init__(self, fn: str, status: int):
         msg = _lib.mgh_status_string(status).decode()
@@ -98,6 +103,8 @@ def _load():
         "mgh_profile_enable": (S, [P, I]),
         "mgh_profile_read": (S, [P, ctypes.POINTER(mgh_profile)]),
         "mgh_debug_inject_timeout": (S, [P]),
+        "mgh_get_kernel_shape": (S, [P, ctypes.POINTER(mgh_kernel_shape)]),
+        "mgh_set_kernel_shape": (S, [P, ctypes.POINTER(mgh_kernel_shape)]),
         "mgh_launch_count": (ctypes.c_uint64, [P, I]),
         "mgh_status_string": (ctypes.c_char_p, [S]),
         "mgh_last_error": (ctypes.c_char_p, []),
@@ -116,7 +123,7 @@ EXPORTED = [
     "mgh_default_params", "mgh_workspace_bytes", "mgh_create", "mgh_destroy", "mgh_set_contrast",
     "mgh_incident_field", "mgh_rhs", "mgh_apply", "mgh_precondition", "mgh_coarse_solve",
     "mgh_level_shape", "mgh_level_coefficient", "mgh_solve", "mgh_forward", "mgh_crop", "mgh_sample",
-    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_debug_inject_timeout", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
+    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_get_kernel_shape", "mgh_set_kernel_shape", "mgh_debug_inject_timeout", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
 ]
 
 
@@ -271,6 +278,22 @@ def mgh_profile_read(h) -> dict:
                 arnoldi_steps=int(p.arnoldi_steps), basis_reads=int(p.basis_reads),
                 reorth_reads=int(p.reorth_reads), residuals=int(p.residuals), updates=int(p.updates),
                 update_reads=int(p.update_reads), cycle_steps=int(p.cycle_steps), gram_reads=int(p.gram_reads))
+
+
+def mgh_get_kernel_shape(h) -> dict:
+    """wave_seg: list of MGH_MAX_LEVELS per-level segment lengths (0 = the built-in model)."""
+    out = mgh_kernel_shape()
+    _check("mgh_get_kernel_shape", _lib.mgh_get_kernel_shape(h, ctypes.byref(out)))
+    return {"wave_seg": list(out.wave_seg), "wave_warps": out.wave_warps, "wave_ring": out.wave_ring,
+            "tail_level": out.tail_level}
+
+
+def mgh_set_kernel_shape(h, wave_seg=0, wave_warps: int = 4, wave_ring: int = 1, tail_level: int = -1) -> None:
+    """wave_seg: one length for every level, or a sequence of per-level lengths (0 = model)."""
+    segs = [int(wave_seg)] * MGH_MAX_LEVELS if isinstance(wave_seg, int) else list(wave_seg)
+    segs = (segs + [0] * MGH_MAX_LEVELS)[:MGH_MAX_LEVELS]
+    s = mgh_kernel_shape((ctypes.c_int * MGH_MAX_LEVELS)(*segs), wave_warps, wave_ring, tail_level)
+    _check("mgh_set_kernel_shape", _lib.mgh_set_kernel_shape(h, ctypes.byref(s)))
 
 
 def mgh_debug_inject_timeout(h) -> None:

@@ -456,6 +456,32 @@ mgh_status mgh_profile_read(mgh_handle* h, mgh_profile* out) {
   return MGH_OK;
 }
 
+mgh_status mgh_get_kernel_shape(const mgh_handle* h, mgh_kernel_shape* out) {
+  if (!h || !out) return MGH_INVALID_ARG;
+  for (int l = 0; l < kMaxLevels; ++l) out->wave_seg[l] = h->wave_seg_level[l];
+  out->wave_warps = h->wave_warps;
+  out->wave_ring = h->wave_ring;
+  out->tail_level = h->tail_l0;
+  return MGH_OK;
+}
+
+mgh_status mgh_set_kernel_shape(mgh_handle* h, const mgh_kernel_shape* s) {
+  if (!handle_ok(h) || !s) return MGH_INVALID_ARG;
+  for (int l = 0; l < kMaxLevels; ++l)
+    if (s->wave_seg[l] < 0 || s->wave_seg[l] > 4096) return MGH_INVALID_ARG;
+  if (s->wave_warps != 2 && s->wave_warps != 4) return MGH_INVALID_ARG;
+  if (s->wave_ring != 1 && s->wave_ring != 2) return MGH_INVALID_ARG;
+  if (s->tail_level < -1 || s->tail_level > h->L - 2) return MGH_INVALID_ARG;
+  if (s->tail_level > 0 && !tail_level_fits(*h, s->tail_level)) return MGH_INVALID_ARG;
+  if (h->half && (s->wave_warps != 4 || s->wave_ring != 1)) return MGH_NOT_SUPPORTED;
+  MGH_CUDA(cudaStreamSynchronize(h->stream));   // launches already queued keep their shapes
+  for (int l = 0; l < kMaxLevels; ++l) h->wave_seg_level[l] = s->wave_seg[l];
+  h->wave_warps = s->wave_warps;
+  h->wave_ring = s->wave_ring;
+  h->tail_l0 = s->tail_level < 0 ? choose_tail_level(*h) : s->tail_level;
+  return MGH_OK;
+}
+
 mgh_status mgh_debug_inject_timeout(mgh_handle* h) {
   if (!handle_ok(h)) return MGH_INVALID_ARG;
   if (h->fp64 || h->p.krylov != MGH_KRYLOV_FGMRES || h->p.arnoldi == MGH_ARNOLDI_FP64) return MGH_NOT_SUPPORTED;

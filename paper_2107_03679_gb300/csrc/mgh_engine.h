@@ -65,6 +65,7 @@ struct Handle {
                              // FP16 values near 1/16 in RMS: sqrt(N)/16, rounded to a power of two)
   bool vc_wave = true;       // FP32 levels: wavefront kernels (else shared-memory tiles)
   int wave_seg = 0;          // rows per warp segment of the wavefront kernels (0: automatic)
+  int wave_seg_level[kMaxLevels] = {};  // per-level override of wave_seg (0: wave_seg's rule)
   int wave_min_nx = 0;       // levels narrower than this use the tiled kernels
   int wave_pf = 1;           // rows of loads in flight per warp (1 or 2; 16-byte path only)
   int wave_warps = 4;        // warps per block of the wavefront kernels (2 or 4)
@@ -198,6 +199,7 @@ constexpr int kErrTimeout = 1;
 // mgh_tail.cu: every cycle of levels tail_l0 .. L-1 in one kernel, one block per right-hand side
 // (input lev[tail_l0].b, output lev[tail_l0].vfin; reps cycles of level tail_l0, the first from 0)
 int choose_tail_level(const Handle& h);
+bool tail_level_fits(const Handle& h, int l);   // level l's tail fields fit one block's shared memory
 mgh_status launch_tail(Handle& h, int reps, int B, const RhsState* st, bool fp64);
 
 // mgh_inverse.cu: backward and momentum steps of the reconstruction loop (arguments checked by the caller)

@@ -644,6 +644,16 @@ __device__ __forceinline__ cf zload(const __half2* Z, size_t i) {
   return mk<float>(f.x, f.y);
 }
 
+// Two adjacent points of z (q even) as (re0, im0, re1, im1): one 16-byte load of FP32 storage or
+// one 8-byte load of FP16 storage.
+__device__ __forceinline__ float4 zpair(const cf* z, size_t q) { return reinterpret_cast<const float4*>(z)[q / 2]; }
+__device__ __forceinline__ float4 zpair(const __half2* z, size_t q) {
+  const uint2 u = reinterpret_cast<const uint2*>(z)[q / 2];
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
 // x += sum_{i < jend} y_i z_i, all in double-float (x planes, z FP32 or FP16, y split to double-float).
 template <int NV, typename ZT = cf>
 __global__ void __launch_bounds__(kKThreads)
@@ -692,6 +702,54 @@ k_df_xupdate(KArgs a, const ZT* __restrict__ Z, const cd* __restrict__ y, float2
       xh[qq] = make_float2(v[u].re.hi, v[u].im.hi);
       xl[qq] = make_float2(v[u].re.lo, v[u].im.lo);
     }
+  }
+}
+
+// The same for FP16 z (MGH_PREC_MIXED16, even N): two adjacent points per thread and step, one
+// 8-byte load per z_i and 16-byte loads and stores of the x planes, so that a thread keeps as many
+// bytes in flight as the FP32 variant does.
+template <int NV>
+__global__ void __launch_bounds__(kKThreads)
+k_df_xupdate_h2(KArgs a, const __half2* __restrict__ Z, const cd* __restrict__ y, float2* __restrict__ xdf,
+                const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.y;
+  if (st[rhs].done || st[rhs].jend == 0) return;
+  const int je = st[rhs].jend;
+  __shared__ cdf ys[NV];
+  if (threadIdx.x < NV && (int)threadIdx.x < je) ys[threadIdx.x] = cdf_from(y[(size_t)rhs * a.m + threadIdx.x]);
+  __syncthreads();
+  const __half2* Zb = Z + (size_t)rhs * a.m * a.N;
+  float4* xh = reinterpret_cast<float4*>(xdf + (size_t)rhs * 2 * a.Np);
+  float4* xl = reinterpret_cast<float4*>(xdf + (size_t)rhs * 2 * a.Np + a.Np);
+  const size_t p0 = blockIdx.x * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;   // both even
+  for (size_t q = p0 + 2 * threadIdx.x; q < p1; q += 2 * kKThreads) {
+    float4 z[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) z[i] = i < je ? zpair(Zb + (size_t)i * a.N, q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 h = xh[q / 2], l = xl[q / 2];
+    cdf v[2];
+    v[0].re = df{h.x, l.x}; v[0].im = df{h.y, l.y};
+    v[1].re = df{h.z, l.z}; v[1].im = df{h.w, l.w};
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (i < je) {
+        const cf zz[2] = {mk<float>(z[i].x, z[i].y), mk<float>(z[i].z, z[i].w)};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          df_fma1(v[u].re, ys[i].re.hi, ys[i].re.lo, zz[u].re);
+          df_fma1(v[u].re, -ys[i].im.hi, -ys[i].im.lo, zz[u].im);
+          df_fma1(v[u].im, ys[i].re.hi, ys[i].re.lo, zz[u].im);
+          df_fma1(v[u].im, ys[i].im.hi, ys[i].im.lo, zz[u].re);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      v[u].re = df_norm(v[u].re);
+      v[u].im = df_norm(v[u].im);
+    }
+    xh[q / 2] = make_float4(v[0].re.hi, v[0].im.hi, v[1].re.hi, v[1].im.hi);
+    xl[q / 2] = make_float4(v[0].re.lo, v[0].im.lo, v[1].re.lo, v[1].im.lo);
   }
 }
 
@@ -782,16 +840,6 @@ k_ss_matvec(KArgs a, int k, const cf* __restrict__ Z, const float2* __restrict__
   df vals[1] = {{nrm, 0.f}};
   cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
   block_reduce_df(vals, 1, [&](int) -> double* { out->im = 0.0; return &out->re; });
-}
-
-// Two adjacent points of z (q even) as (re0, im0, re1, im1): one 16-byte load of FP32 storage or
-// one 8-byte load of FP16 storage.
-__device__ __forceinline__ float4 zpair(const cf* z, size_t q) { return reinterpret_cast<const float4*>(z)[q / 2]; }
-__device__ __forceinline__ float4 zpair(const __half2* z, size_t q) {
-  const uint2 u = reinterpret_cast<const uint2*>(z)[q / 2];
-  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
-  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
-  return make_float4(a.x, a.y, b.x, b.y);
 }
 
 // The same for rows of even width: two adjacent points per thread and step (the pair never
@@ -1134,8 +1182,8 @@ mgh_status df_xupdate(Handle& h, const KArgs& a, int B) {
   float2* x = h.xdf;
   if (h.half) {   // FP16 preconditioned vectors (s-step engine, m <= 8)
     const __half2* Zh = reinterpret_cast<const __half2*>(h.Z);
-    if (m <= 4) k_df_xupdate<4, __half2><<<grid, kKThreads, 0, h.stream>>>(a, Zh, h.y, x, h.st);
-    else k_df_xupdate<8, __half2><<<grid, kKThreads, 0, h.stream>>>(a, Zh, h.y, x, h.st);
+    if (m <= 4) k_df_xupdate_h2<4><<<grid, kKThreads, 0, h.stream>>>(a, Zh, h.y, x, h.st);
+    else k_df_xupdate_h2<8><<<grid, kKThreads, 0, h.stream>>>(a, Zh, h.y, x, h.st);
     MGH_CHECK_LAUNCH(); h.launches++;
     return MGH_OK;
   }

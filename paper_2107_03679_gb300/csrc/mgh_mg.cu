@@ -842,9 +842,10 @@ bool a8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
 // waves of resident warps; the even segment length from 4 to 128 with the least
 // K * ceil(warps / resident) is taken (long segments repeat fewer halo rows, short ones fill
 // the GPU on small levels).
-int wave_seg(const Handle& h, int ny, int nstrips, int B, int extra, int P, long resident) {
-  if (h.wave_seg > 0) {
-    const int seg = (h.wave_seg + 1) & ~1;
+int wave_seg(const Handle& h, int l, int ny, int nstrips, int B, int extra, int P, long resident) {
+  const int fixed = h.wave_seg_level[l] > 0 ? h.wave_seg_level[l] : h.wave_seg;
+  if (fixed > 0) {
+    const int seg = (fixed + 1) & ~1;
     for (int s = seg; s >= 4; s -= 2)
       if ((P - (s + extra) % P) % P <= 1) return s;
     return seg;
@@ -1023,7 +1024,7 @@ mgh_status launch_pre_wave(Handle& h, int l, const cf* bin, size_t b_stride, con
                                          (int)smem1)););
   static std::atomic<long> resident_by_dev[64];
   const long resident = resident_cached(resident_by_dev, h, wave::k_pre_wa<NU, 4, 1>, 128, smem1);
-  const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * G::H - 1, period, resident);
+  const int seg = wave_seg(h, l, lv.ny, nstrips, B, 2 * G::H - 1, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_PRE0 : P_COARSE);
   if (l == 0 && h.half) {   // FP16 storage: lane rings, 4 warps, one unroll period (checked at create)
@@ -1067,7 +1068,7 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
                                          (int)smem1)););
   static std::atomic<long> resident_by_dev[64];
   const long resident = resident_cached(resident_by_dev, h, wave::k_post_wa<NU, 4, 1>, 128, smem1);
-  const int seg = wave_seg(h, lv.ny, nstrips, B, 2 * NU, period, resident);
+  const int seg = wave_seg(h, l, lv.ny, nstrips, B, 2 * NU, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);
   if (l == 0 && h.half) {

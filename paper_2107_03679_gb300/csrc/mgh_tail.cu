@@ -297,6 +297,12 @@ mgh_status launch_tail_t(Handle& h, int reps, int B, const RhsState* st) {
 
 }  // namespace
 
+bool tail_level_fits(const Handle& h, int l) {
+  if (l < 1 || l + 2 > h.L) return false;
+  const size_t bytes = h.fp64 ? tail_smem_bytes<double>(h, l) : tail_smem_bytes<float>(h, l);
+  return bytes <= kTailSmemMax;
+}
+
 int choose_tail_level(const Handle& h) {
   for (int l = 1; l + 2 <= h.L; ++l) {
     const size_t bytes = h.fp64 ? tail_smem_bytes<double>(h, l) : tail_smem_bytes<float>(h, l);

@@ -95,7 +95,7 @@ class Solver:
         args = dict(nx_int=w.nx_int, ny_int=w.ny_int, abl=w.abl, h=w.h, k=w.k, beta=w.beta,
                     shift=(w.shift_re, w.shift_im), levels=w.levels, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
                     restart=w.restart, tol=w.tol, precision=precision or w.precision,
-                    batch_max=batch_max or w.n_angles)
+                    batch_max=batch_max or w.n_angles, krylov=getattr(w, "krylov", "fgmres"))
         args.update(kw)
         return cls(**args)
 
@@ -265,6 +265,17 @@ class Solver:
 
     def launch_count(self, reset: bool = False) -> int:
         return capi.mgh_launch_count(self._h, reset)
+
+    def kernel_shape(self) -> dict:
+        """Launch shapes of the FP32 level kernels (wave_seg, wave_warps, wave_ring, tail_level)."""
+        return capi.mgh_get_kernel_shape(self._h)
+
+    def set_kernel_shape(self, **shape) -> None:
+        """Change launch shapes (speed only; see mgh_set_kernel_shape); unnamed fields keep their
+        current values."""
+        cur = self.kernel_shape()
+        cur.update(shape)
+        capi.mgh_set_kernel_shape(self._h, **cur)
 
 
 class ScatteredField(torch.autograd.Function):

@@ -50,6 +50,7 @@ class Workload:
     tol: float = 1e-6
     precision: str = "mixed32"  # "fp64" | "mixed32" | "mixed16"
     h: float = 1.0
+    krylov: str = "fgmres"      # outer method: "fgmres" | "bicgstab" (Alg. 3)
     extra: dict = field(default_factory=dict)
 
     @property
