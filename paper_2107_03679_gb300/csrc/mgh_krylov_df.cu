@@ -135,6 +135,26 @@ __device__ __forceinline__ bool pipe_release(const Pipe& pp, int k, const int* f
   return true;
 }
 
+// The same after all threads finished with tiles k and k + 1 (one barrier for both): refill their
+// slots with tiles k + S and k + 1 + S.
+__device__ __forceinline__ bool pipe_release2(const Pipe& pp, int k, const int* fail, int* err) {
+  __syncthreads();
+  if (*fail) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, kErrTimeout);
+      for (int kk = k; kk < k + pp.S && kk < pp.ntiles; ++kk)
+        mbar_wait(&pp.bar[kk % pp.S], (uint32_t)((kk / pp.S) & 1), kWaitLimitNs);
+    }
+    __syncthreads();
+    return false;
+  }
+  if (threadIdx.x == 0) {
+    if (k + pp.S < pp.ntiles) pp.issue(k + pp.S);
+    if (k + 1 + pp.S < pp.ntiles) pp.issue(k + 1 + pp.S);
+  }
+  return true;
+}
+
 __device__ __forceinline__ const float2* vplane(const float2* V, const KArgs& a, int rhs, int i, int h) {
   return V + (((size_t)rhs * (a.m + 1) + i) * 2 + h) * a.Np;
 }
@@ -960,20 +980,24 @@ k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial
     acc[c] = cdf_zero();
     run[c] = make_float2(0.f, 0.f);
   }
-  for (int k = 0; k < pp.ntiles; ++k) {
-    const bool ready = pipe_wait(pp, k, fail);
-    const int slot = k % S;
-    const size_t q0 = p0 + (size_t)k * kTile;
+  // two tiles per barrier: wait for k and k + 1, sum both, release both
+  for (int k = 0; k < pp.ntiles; k += 2) {
+    const bool two = k + 1 < pp.ntiles;
+    const bool ready = pipe_wait(pp, k, fail) && (!two || pipe_wait(pp, k + 1, fail));
     if (ready) {
-      switch (grp) {
-        case 0: gram_tile<NV, 0>(pp, slot, q0, p1, l64, run); break;
-        case 1: gram_tile<NV, 1>(pp, slot, q0, p1, l64, run); break;
-        case 2: gram_tile<NV, 2>(pp, slot, q0, p1, l64, run); break;
-        default: gram_tile<NV, 3>(pp, slot, q0, p1, l64, run); break;
+      for (int u = 0; u < (two ? 2 : 1); ++u) {
+        const int slot = (k + u) % S;
+        const size_t q0 = p0 + (size_t)(k + u) * kTile;
+        switch (grp) {
+          case 0: gram_tile<NV, 0>(pp, slot, q0, p1, l64, run); break;
+          case 1: gram_tile<NV, 1>(pp, slot, q0, p1, l64, run); break;
+          case 2: gram_tile<NV, 2>(pp, slot, q0, p1, l64, run); break;
+          default: gram_tile<NV, 3>(pp, slot, q0, p1, l64, run); break;
+        }
       }
     }
-    if (!pipe_release(pp, k, fail, err)) return;
-    if ((k + 1) % kGramRunTiles == 0 || k + 1 == pp.ntiles) {
+    if (!pipe_release2(pp, k, fail, err)) return;
+    if ((k + 2) % kGramRunTiles == 0 || k + 2 >= pp.ntiles) {
 #pragma unroll
       for (int c = 0; c < PR::PG; ++c) {
         df_add1(acc[c].re, run[c].x);

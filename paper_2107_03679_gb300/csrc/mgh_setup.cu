@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mgh_diag.cuh"
 #include "mgh_engine.h"
 
 namespace mgh {
@@ -20,37 +21,6 @@ constexpr int kThreads = 256;
 inline unsigned blocks_for(size_t n, int threads = kThreads) {
   size_t b = (n + threads - 1) / threads;
   return (unsigned)(b > 0 ? b : 1);
-}
-
-// Squared distance in fine cells from fine position (s*i, s*j) to Omega's index box.
-__device__ __forceinline__ double layer_d2(int i, int j, int s, int x0, int x1, int y0, int y1) {
-  const int fx = s * i, fy = s * j;
-  const int dx = fx < x0 ? x0 - fx : (fx > x1 ? fx - x1 : 0);
-  const int dy = fy < y0 ? y0 - fy : (fy > y1 ? fy - y1 : 0);
-  return (double)dx * dx + (double)dy * dy;
-}
-
-struct DiagArgs {
-  int nx, ny, scale;
-  int x0, x1, y0, y1;     // Omega index box on the fine grid (inclusive)
-  double inv_L2;          // 1 / abl^2 (0 without a layer)
-  double beta, k, h;
-  double kap_re, kap_im;
-  double omega;
-};
-
-// D = 4/h^2 - kappa * alpha * c - nmiss * (1 + j h k)/h^2, alpha = 1 + j beta d^2/L^2.
-__device__ __forceinline__ cd level_diag(const DiagArgs& a, int i, int j, double c) {
-  const double t = a.beta * layer_d2(i, j, a.scale, a.x0, a.x1, a.y0, a.y1) * a.inv_L2;
-  // kappa * alpha = (kr + j ki)(1 + j t)
-  const double ka_re = a.kap_re - a.kap_im * t;
-  const double ka_im = a.kap_im + a.kap_re * t;
-  const int nmiss = (i == 0) + (i == a.nx - 1) + (j == 0) + (j == a.ny - 1);
-  const double ih2 = 1.0 / (a.h * a.h);
-  cd d;
-  d.re = 4.0 * ih2 - ka_re * c - nmiss * ih2;
-  d.im = -ka_im * c - nmiss * a.k / a.h;
-  return d;
 }
 
 __global__ void k_fine_coef(const double* __restrict__ f_d, double* __restrict__ c, int nx, int ny,
@@ -84,7 +54,7 @@ __global__ void k_restrict_coef(const double* __restrict__ cf_, double* __restri
 }
 
 template <typename T>
-__global__ void k_level_diag(const double* __restrict__ c, DiagArgs a, Cx<T>* __restrict__ D,
+__global__ void k_level_diag(const double* __restrict__ c, DiagArgs<double> a, Cx<T>* __restrict__ D,
                              Cx<T>* __restrict__ wDinv) {
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (q >= (size_t)a.nx * a.ny) return;
@@ -409,13 +379,13 @@ mgh_status setup_contrast(Handle& h, const double* f_d) {
     k_restrict_coef<<<blocks_for(b.n()), kThreads, 0, s>>>(a.c, b.c, a.nx, a.ny, b.nx, b.ny, k2);
     MGH_CHECK_LAUNCH(); h.launches++;
   }
-  DiagArgs da;
+  DiagArgs<double> da;
   da.x0 = p.abl; da.x1 = p.abl + p.nx_int - 1;
   da.y0 = p.abl; da.y1 = p.abl + p.ny_int - 1;
   da.inv_L2 = p.abl > 0 ? 1.0 / ((double)p.abl * p.abl) : 0.0;
-  da.beta = p.beta; da.k = p.k; da.omega = p.omega;
+  da.beta = p.beta; da.omega = p.omega;
   // fine operator A (unshifted)
-  da.nx = h.nx; da.ny = h.ny; da.scale = 1; da.h = p.h; da.kap_re = 1.0; da.kap_im = 0.0;
+  da.nx = h.nx; da.ny = h.ny; da.scale = 1; diag_set_spacing(da, p.h, p.k); da.kap_re = 1.0; da.kap_im = 0.0;
   k_level_diag<double><<<blocks_for(h.N), kThreads, 0, s>>>(h.lev[0].c, da, h.DA, nullptr);
   MGH_CHECK_LAUNCH(); h.launches++;
   k_split_df<<<blocks_for(h.N), kThreads, 0, s>>>(h.DA, h.DAdf, h.DAdf + h.Np, h.N);
@@ -424,7 +394,7 @@ mgh_status setup_contrast(Handle& h, const double* f_d) {
   da.kap_re = p.shift_re; da.kap_im = p.shift_im;
   for (int l = 0; l < h.L; ++l) {
     Level& lv = h.lev[l];
-    da.nx = lv.nx; da.ny = lv.ny; da.scale = lv.scale; da.h = lv.h;
+    da.nx = lv.nx; da.ny = lv.ny; da.scale = lv.scale; diag_set_spacing(da, lv.h, p.k);
     if (h.fp64)
       k_level_diag<double><<<blocks_for(lv.n()), kThreads, 0, s>>>(lv.c, da, (cd*)lv.D, (cd*)lv.wDinv);
     else
@@ -434,7 +404,7 @@ mgh_status setup_contrast(Handle& h, const double* f_d) {
   // coarsest: FP64 diagonal (recomputed in FP64 whatever the cycle precision), banded LU, inverse
   const Level& cl = h.lev[h.L - 1];
   const int n = h.nc, kl = cl.nx, ku = cl.nx, W = 2 * kl + ku + 1;
-  da.nx = cl.nx; da.ny = cl.ny; da.scale = cl.scale; da.h = cl.h;
+  da.nx = cl.nx; da.ny = cl.ny; da.scale = cl.scale; diag_set_spacing(da, cl.h, p.k);
   cd* Dc = h.kinv64;  // borrow the inverse buffer (n*n >= n) for the FP64 diagonal
   k_level_diag<double><<<blocks_for(cl.n()), kThreads, 0, s>>>(cl.c, da, Dc, nullptr);
   MGH_CHECK_LAUNCH(); h.launches++;

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 def _w():
     # 136 x 118: three wavefront strips, a ragged last one; levels 136, 68, 34, 17: the tail starts at level 1 or 2
-    return W.Workload("shape", 120, 102, 8, 8.0, 3, -40.0, 40.0, "ellipses", 5, levels=4, nu1=2, nu2=2,
+    return W.Workload("shape", 120, 102, 8, 8.0, 3, -40.0, 40.0, "ellipses", 5, levels=4, nu1=1, nu2=1,
                       restart=8, precision="mixed32", tol=1e-10)
 
 
