@@ -421,10 +421,15 @@ def gpu_main(args, rank, world, local_rank):
     d_fgt = torch.from_numpy(f_gt).to(dev)
     d_f = torch.from_numpy(f_step).to(dev)
     # synthetic measurements: receiver samples of the ground-truth phantom's fields
-    solver.set_contrast(d_fgt)
-    u_gt, _ = solver.forward(d_th)
-    d_y = solver.sample(u_gt, d_rec)
-    del u_gt
+    forward_only = bool(w.extra.get("forward_only"))
+    if forward_only:        # a forward problem: no data term, no end-to-end data path
+        args.no_e2e = True
+        d_y = None
+    else:
+        solver.set_contrast(d_fgt)
+        u_gt, _ = solver.forward(d_th)
+        d_y = solver.sample(u_gt, d_rec)
+        del u_gt
     u = solver.field(B)
     runner = solver          # what the timed steps drive: one handle, or the angles split over several
     if args.split > 1:
@@ -453,6 +458,10 @@ def gpu_main(args, rank, world, local_rank):
         return torch.cat([s.sample(uu[a:b], d_rec) for s, (a, b) in zip(runner.solvers, runner.ranges(B))])
 
     def step(f_dev, y_dev):
+        if forward_only:      # a forward problem (no data term): contrast, right-hand sides, solves, crop
+            solver.set_contrast(f_dev)
+            _, inf_f = solver.forward(d_th, out=u)
+            return None, 0.0, inf_f, [], solver.crop(u)
         if args.split > 1:   # every stage below, per part, parts on concurrent streams
             loss, g, inf_f, inf_a = runner.data_term_gradient(f_dev, d_th, d_rec, y_dev, u, crop_out=u_crop)
             return g, loss, inf_f, inf_a, u_crop
@@ -506,7 +515,7 @@ def gpu_main(args, rank, world, local_rank):
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
-    solves_rank = 2 * B * args.steps
+    solves_rank = (1 if forward_only else 2) * B * args.steps
     value = world * solves_rank / (ms_max / 1e3)
     conv = all(i["converged"] for i in timed_infos)
     worst = max(i["rel_residual"] for i in timed_infos)
@@ -695,8 +704,9 @@ def gpu_main(args, rank, world, local_rank):
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
                    "angles_per_gpu": B, "angles_total": B * world, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
                    "restart": w.restart, "tol": w.tol, "krylov": args.krylov, "cycle": args.cycle.upper(), "arnoldi": solver.arnoldi if precision != "fp64" else "fp64", "shift": [w.shift_re, w.shift_im],
-                   "step": f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient",
-                   "solves_per_step": 2 * B, "l2": "inputs larger than L2 (Krylov basis "
+                   "step": (f"set_contrast + {B} forward solves + crop" if forward_only else
+                            f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient"),
+                   "solves_per_step": (1 if forward_only else 2) * B, "l2": "inputs larger than L2 (Krylov basis "
                    f"{B * (w.restart + 1) * N * 16 / 1e9:.1f} GB per GPU)", "parallelism": f"replicas x{world}",
                    "split": (f"{B} angles as {args.split} handles of about {-(-B // args.split)} on concurrent streams"
                              if args.split > 1 else None)},
@@ -860,69 +870,84 @@ def fbs_main(args, rank, world, local_rank):
 # --------------------------------------------------------------------------- uneven batch
 def uneven_main(args, rank, world, local_rank):
     """Four grids of different sizes solved together: one solver handle and one CUDA stream per
-    grid, driven from one host thread each so that their kernels overlap on the GPU."""
+    grid, driven from one host thread each so that their kernels overlap on the GPU (multi.UnevenBatch);
+    a step is set_contrast + forward + misfit + adjoint + gradient on every grid.  Timed with CUDA
+    events on the caller's stream, which every grid's stream joins; the same step is then timed on
+    the plain FP64 path."""
     import torch
     import workloads as W
-    from paper_2107_03679_gb300 import Solver
+    from paper_2107_03679_gb300.multi import UnevenBatch
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     precision = args.precision or "mixed32"
-    jobs = []
-    for w in W.uneven_workloads():
-        stream = torch.cuda.Stream(dev)
+    ws = W.uneven_workloads()
+    data = []
+    for w in ws:
         f_gt, f_step, thetas, rec = make_inputs(w)
-        with torch.cuda.stream(stream):
-            s = Solver.from_workload(w, batch_max=len(thetas), precision=precision, device=dev, maxit=50000,
-                                     stream=stream, arnoldi=args.arnoldi)
-            d = dict(w=w, s=s, stream=stream, th=torch.from_numpy(thetas).to(dev), rec=torch.from_numpy(rec).to(dev),
-                     f=torch.from_numpy(f_step).to(dev))
-            s.set_contrast(torch.from_numpy(f_gt).to(dev))
-            u, _ = s.forward(d["th"])
-            d["y"] = s.sample(u, d["rec"])
-            d["u"] = u
-        jobs.append(d)
-    torch.cuda.synchronize()
+        data.append(dict(f_gt=torch.from_numpy(f_gt).to(dev), f=torch.from_numpy(f_step).to(dev),
+                         th=torch.from_numpy(thetas).to(dev), rec=torch.from_numpy(rec).to(dev)))
 
-    from paper_2107_03679_gb300.multi import run_concurrently
+    def measure(prec, steps, warmup):
+        ub = UnevenBatch.from_workloads(ws, device=dev, precision=prec, maxit=50000, arnoldi=args.arnoldi)
+        res = ub.forward([d["f_gt"] for d in data], [d["th"] for d in data])
+        ys = [ub.solvers[i].sample(u, data[i]["rec"]) for i, (u, _) in enumerate(res)]
+        outs = [s.field(d["th"].numel()) for s, d in zip(ub.solvers, data)]
 
-    def run_one(i, s):
-        d = jobs[i]
-        s.set_contrast(d["f"])
-        _, inf_f = s.forward(d["th"], out=d["u"])
-        _, G, _ = s.misfit(d["u"], d["y"], d["rec"])
-        _, inf_a = s.gradient(d["th"], d["u"], G)
-        return inf_f + inf_a
+        def step():
+            return ub.data_term_gradient([d["f"] for d in data], [d["th"] for d in data], [d["rec"] for d in data],
+                                         ys, outs)
 
-    def step():
-        return run_concurrently([d["s"] for d in jobs], run_one)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        cur = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ub.launch_count()
+        e0.record(cur)
+        per = None
+        for _ in range(steps):
+            per = step()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = ub.launch_count() - l0
+        ub.close()
+        return ms, per, launches
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    per = None
-    for _ in range(args.steps):
-        per = step()
-    torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    solves = sum(2 * d["th"].numel() for d in jobs) * args.steps
+    ms, per, launches = measure(precision, args.steps, args.warmup)
+    solves = sum(2 * d["th"].numel() for d in data) * args.steps
+    fp64 = None
+    if not args.no_fp64_compare and precision != "fp64":
+        k64 = min(args.steps, 1)
+        ms64, per64, _ = measure("fp64", k64, 1)
+        v64 = sum(2 * d["th"].numel() for d in data) * k64 / (ms64 / 1e3)
+        fp64 = {"value": round(v64, 3), "unit": UNIT, "steps": k64, "warmup": 1, "ms_per_step": round(ms64 / k64, 1),
+                "speedup_of_mixed": round(solves / (ms / 1e3) / v64, 2),
+                "per_grid_iterations_mean": [round(sum(i["iterations"] for i in fw + ad) / len(fw + ad), 1)
+                                             for _, _, fw, ad in per64],
+                "converged": all(i["converged"] for _, _, fw, ad in per64 for i in fw + ad)}
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": round(solves / sec, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"mixed32": "f32+f64", "mixed16": "f16-stored f32+f64"}.get(precision, "f64"),
+        "metric": METRIC, "value": round(solves / (ms / 1e3), 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed32" else precision,
         "data": "synthetic",
-        "config": {"workload": "uneven", "grids": [f"{d['w'].nx}x{d['w'].ny}:{d['th'].numel()}" for d in jobs],
-                   "precision": precision, "timing": "host wall clock around all streams"},
-        "per_grid": [{"grid": f"{d['w'].nx}x{d['w'].ny}", "angles": d["th"].numel(),
-                      "iterations_mean": round(sum(i["iterations"] for i in o) / len(o), 1),
-                      "converged": all(i["converged"] for i in o)} for d, o in zip(jobs, per)],
+        "config": {"workload": "uneven", "grids": [f"{w.nx}x{w.ny}:{d['th'].numel()}" for w, d in zip(ws, data)],
+                   "levels": [w.levels for w in ws], "precision": precision,
+                   "step": "set_contrast + forward + misfit + adjoint + gradient on every grid",
+                   "schedule": "one handle, stream and host thread per grid; each replays its restart cycles "
+                               "from captured CUDA graphs",
+                   "timing": "CUDA events on the caller's stream, which every grid's stream joins"},
+        "gpu_launches": int(launches),
+        "per_grid": [{"grid": f"{w.nx}x{w.ny}", "angles": d["th"].numel(),
+                      "iterations_mean": round(sum(i["iterations"] for i in fw + ad) / len(fw + ad), 1),
+                      "converged": all(i["converged"] for i in fw + ad)}
+                     for w, d, (_, _, fw, ad) in zip(ws, data, per)],
+        "fp64_same_accuracy": fp64,
     }
     print(json.dumps(line))
-    for d in jobs:
-        d["s"].close()
 
 
 # --------------------------------------------------------------------------- multi-frequency batch

@@ -216,3 +216,61 @@ class SplitBatch:
                 else:
                     out[k] = out[k] + v
         return out
+
+
+class UnevenBatch:
+    """Grids of different sizes solved together (an uneven batch): one handle per grid, each with
+    its own contrast, angles, stream and host thread, so that the kernels of all grids overlap on
+    the GPU (each handle replays its own restart cycles from captured graphs).  The grids are
+    independent problems; this class only orders library calls."""
+
+    def __init__(self, solvers: Sequence[Solver]):
+        if not solvers:
+            raise ValueError("at least one grid")
+        self.solvers = list(solvers)
+
+    @classmethod
+    def from_workloads(cls, workloads, device: Optional[torch.device] = None, precision: Optional[str] = None,
+                       **kw):
+        """One handle per workload (batch = its angle count), each on a new stream."""
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        return cls([Solver.from_workload(w, batch_max=w.n_angles, device=dev, stream=torch.cuda.Stream(dev),
+                                         precision=precision or w.precision, **kw) for w in workloads])
+
+    def close(self):
+        for s in self.solvers:
+            s.close()
+
+    def launch_count(self) -> int:
+        return sum(s.launch_count() for s in self.solvers)
+
+    def forward(self, contrasts: Sequence[torch.Tensor], thetas: Sequence[torch.Tensor],
+                outs: Optional[Sequence[torch.Tensor]] = None):
+        """Set every grid's contrast and solve its forward problems: a list of (u, infos)."""
+        def one(i, s):
+            s.set_contrast(contrasts[i])
+            return s.forward(thetas[i], out=None if outs is None else outs[i])
+
+        res = run_concurrently(self.solvers, one)
+        cur = torch.cuda.current_stream()
+        for u, _ in res:       # made on a grid's stream, used on the caller's
+            u.record_stream(cur)
+        return res
+
+    def data_term_gradient(self, contrasts: Sequence[torch.Tensor], thetas: Sequence[torch.Tensor],
+                           recs: Sequence[torch.Tensor], ys: Sequence[torch.Tensor],
+                           outs: Sequence[torch.Tensor]):
+        """Per grid: set the contrast, forward solves into outs[i], misfit against ys[i], adjoint
+        solves and the gradient; a list of (loss, gradient, forward infos, adjoint infos)."""
+        def one(i, s):
+            s.set_contrast(contrasts[i])
+            u, inf_f = s.forward(thetas[i], out=outs[i])
+            _, G, loss = s.misfit(u, ys[i], recs[i])
+            g, inf_a = s.gradient(thetas[i], u, G)
+            return loss, g, inf_f, inf_a
+
+        res = run_concurrently(self.solvers, one)
+        cur = torch.cuda.current_stream()
+        for _, g, _, _ in res:
+            g.record_stream(cur)
+        return res
