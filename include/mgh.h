@@ -226,6 +226,24 @@ mgh_status mgh_misfit(mgh_handle* h, const mgh_cdouble* u, const mgh_cdouble* y,
 mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u_sc,
                         const mgh_cdouble* G, int B, double* grad, mgh_solve_info* info);
 
+/* The data term and its gradient in one call with HOST buffers (Sec. V, Prop. 1): for the contrast
+ * f_d, the B angles theta and the receiver data y, set the contrast, solve the B forward problems,
+ * form L = 1/2 sum_q ||S u_q - y_q||^2 and the residuals r = S u - y, solve the B adjoint problems and
+ * write the gradient of L in f_d.  Every pointer argument is HOST memory (pinned memory makes the
+ * copies asynchronous):
+ *   f_d, grad   [ny_int][nx_int] doubles (in / out)
+ *   theta       B angles; rec: M distinct receiver indices n*nx + m (int64); y: [B][M] complex (in)
+ *   loss        one double (out); r: [B][M] complex (out, may be NULL)
+ *   info_fwd, info_adj   B records each, or NULL
+ * The work is the device-pointer sequence mgh_set_contrast, mgh_forward, mgh_misfit, mgh_gradient,
+ * on device staging that the handle allocates on the first call (two fields of batch_max x N
+ * complex values, and receiver buffers that grow with M) and keeps until mgh_destroy.  The call
+ * returns when the results are on the host; MGH_NOT_CONVERGED if a forward or adjoint solve hit
+ * maxit (the results are then those of the last iterates). */
+mgh_status mgh_data_term_gradient_host(mgh_handle* h, const double* f_d, const double* theta, int B,
+                                       const int64_t* rec, int M, const mgh_cdouble* y, double* grad, double* loss,
+                                       mgh_cdouble* r, mgh_solve_info* info_fwd, mgh_solve_info* info_adj);
+
 /* Backward step of the accelerated forward-backward splitting (Sec. V, Alg. 4): the proximal
  * operator of the nonnegativity constraint plus isotropic total variation with weight lam,
  *   out = argmin_{x >= 0} 1/2 ||x - w||^2 + lam TV(x),   w = fbar - gamma d,

@@ -10,7 +10,8 @@ Two stages, both cached in a JSON file keyed by grid, batch, precision, level co
 * Launch shapes of the FP32 level kernels (mgh_set_kernel_shape): the wavefront segment length,
   warps per block and ring depth, and the first level of the one-kernel coarse tail.  They do not
   change results, only speed, so each candidate is timed on a fixed number of Arnoldi steps of the
-  full batch (the launch configuration that will run), one axis at a time from the built-in choice.
+  full batch (the launch configuration that will run), one axis at a time from the built-in choice,
+  keeping a change only when it gains more than 2 %.
 
 All computation runs in the CUDA library; this module only drives and times it.
 """
@@ -92,7 +93,7 @@ def tune(w, f_d: torch.Tensor, theta: torch.Tensor, device: torch.device, precis
     return choice, trials
 
 
-def _time_steps(solver: Solver, theta: torch.Tensor, reps: int = 2) -> float:
+def _time_steps(solver: Solver, theta: torch.Tensor, reps: int = 3) -> float:
     """Milliseconds per Arnoldi step of the whole batch: forward solves capped at the handle's maxit
     (every right-hand side runs the same number of steps), best of `reps` after one warm-up."""
     solver.forward(theta)
@@ -152,7 +153,7 @@ def tune_shapes(w, f_d: torch.Tensor, theta: torch.Tensor, device: torch.device,
                 continue
             ms = _time_steps(s, th)
             trials.append(dict(cand, ms_per_step=ms))
-            if ms < best_ms * 0.99:    # keep a change only for a clear gain
+            if ms < best_ms * 0.98:    # keep a change only for a clear gain (timing noise is ~1 %)
                 best, best_ms = cand, ms
         s.set_kernel_shape(**best)
     s.close()

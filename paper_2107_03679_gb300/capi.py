@@ -98,6 +98,7 @@ def _load():
         "mgh_misfit": (S, [P, P, P, I, P, I, P, P, ctypes.POINTER(D)]),
         "mgh_misfit_noalloc": (S, [I, I, P, P, I, P, I, P, P, P, P]),
         "mgh_gradient": (S, [P, P, P, P, I, P, info_p]),
+        "mgh_data_term_gradient_host": (S, [P, P, P, I, P, I, P, P, ctypes.POINTER(D), P, info_p, info_p]),
         "mgh_tv_prox": (S, [P, P, P, D, D, I, P]),
         "mgh_fbs_momentum": (S, [P, P, P, D, P]),
         "mgh_profile_enable": (S, [P, I]),
@@ -123,7 +124,7 @@ EXPORTED = [
     "mgh_default_params", "mgh_workspace_bytes", "mgh_create", "mgh_destroy", "mgh_set_contrast",
     "mgh_incident_field", "mgh_rhs", "mgh_apply", "mgh_precondition", "mgh_coarse_solve",
     "mgh_level_shape", "mgh_level_coefficient", "mgh_solve", "mgh_forward", "mgh_crop", "mgh_sample",
-    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_get_kernel_shape", "mgh_set_kernel_shape", "mgh_debug_inject_timeout", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
+    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_data_term_gradient_host", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_get_kernel_shape", "mgh_set_kernel_shape", "mgh_debug_inject_timeout", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
 ]
 
 
@@ -145,6 +146,20 @@ def _ptr(t, dtype=None, numel=None, name="tensor"):
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
     if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, {numel} needed")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(t, dtype, numel, name="tensor"):
+    """Host pointer of a contiguous CPU tensor (checked dtype and size)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a CPU torch.Tensor (host memory)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if t.numel() < numel:
         raise ValueError(f"{name} has {t.numel()} elements, {numel} needed")
     return ctypes.c_void_p(t.data_ptr())
 
@@ -256,6 +271,16 @@ def mgh_gradient(h, theta, u_sc, G, B, grad, allow_not_converged=True):
     st = _lib.mgh_gradient(h, theta, u_sc, G, B, grad, info)
     _check("mgh_gradient", st, (MGH_OK, MGH_NOT_CONVERGED) if allow_not_converged else (MGH_OK,))
     return _infos_to_list(info)
+
+
+def mgh_data_term_gradient_host(h, f_d, theta, B, rec, M, y, grad, r=None, want_infos=False,
+                                allow_not_converged=True):
+    """Host-buffer data term + gradient (pointers to host memory); returns (loss, infos_fwd, infos_adj)."""
+    loss = ctypes.c_double(0.0)
+    inf_f, inf_a = (_infos(B), _infos(B)) if want_infos else (None, None)
+    st = _lib.mgh_data_term_gradient_host(h, f_d, theta, B, rec, M, y, grad, ctypes.byref(loss), r, inf_f, inf_a)
+    _check("mgh_data_term_gradient_host", st, (MGH_OK, MGH_NOT_CONVERGED) if allow_not_converged else (MGH_OK,))
+    return loss.value, (_infos_to_list(inf_f) if want_infos else None), (_infos_to_list(inf_a) if want_infos else None)
 
 
 def mgh_tv_prox(h, fbar, d, gamma, lam, iters, out):

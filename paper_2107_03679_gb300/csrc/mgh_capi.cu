@@ -122,6 +122,8 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->kinv32); cudaFree(h->lu_info); cudaFree(h->V); cudaFree(h->Z); cudaFree(h->W);
   cudaFree(h->T1); cudaFree(h->T2); cudaFree(h->H); cudaFree(h->hcol); cudaFree(h->h2col); cudaFree(h->cs);
   cudaFree(h->sn); cudaFree(h->g); cudaFree(h->y); cudaFree(h->vscale); cudaFree(h->st); cudaFree(h->partial);
+  cudaFree(h->hs_f); cudaFree(h->hs_theta); cudaFree(h->hs_u); cudaFree(h->hs_G); cudaFree(h->hs_rec);
+  cudaFree(h->hs_y); cudaFree(h->hs_r);
   cudaFree(h->dscratch); cudaFree(h->DAdf); cudaFree(h->hpend); cudaFree(h->coef);
   cudaFree(h->dev_err); cudaFree(h->xdf); cudaFree(h->bdf); cudaFree(h->tvbuf);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -425,6 +427,53 @@ mgh_status mgh_gradient(mgh_handle* h, const double* theta, const mgh_cdouble* u
   if (s != MGH_OK && s != MGH_NOT_CONVERGED) return s;
   MGH_TRY(launch_gradient(*h, theta, (const cd*)u_sc, h->T2, B, grad));
   return s;
+}
+
+mgh_status mgh_data_term_gradient_host(mgh_handle* h, const double* f_d, const double* theta, int B,
+                                       const int64_t* rec, int M, const mgh_cdouble* y, double* grad, double* loss,
+                                       mgh_cdouble* r, mgh_solve_info* info_fwd, mgh_solve_info* info_adj) {
+  if (!batch_ok(h, B) || !f_d || !theta || !rec || !y || !grad || !loss || M < 1) return MGH_INVALID_ARG;
+  const size_t Bm = h->Bmax, N = h->N, nint = (size_t)h->p.nx_int * h->p.ny_int;
+  cudaStream_t s = h->stream;
+  // device staging, allocated once per handle (the receiver buffers again when M grows)
+  if (!h->hs_f) {
+    MGH_TRY(dev_alloc(&h->hs_f, 8 * nint));
+    MGH_TRY(dev_alloc(&h->hs_theta, 8 * Bm));
+    MGH_TRY(dev_alloc(&h->hs_u, 16 * Bm * N));
+    MGH_TRY(dev_alloc(&h->hs_G, 16 * Bm * N));
+  }
+  if (M > h->hs_M) {
+    MGH_CUDA(cudaStreamSynchronize(s));
+    cudaFree(h->hs_rec); cudaFree(h->hs_y); cudaFree(h->hs_r);
+    h->hs_rec = nullptr; h->hs_y = nullptr; h->hs_r = nullptr; h->hs_M = 0;
+    MGH_TRY(dev_alloc(&h->hs_rec, 8 * (size_t)M));
+    MGH_TRY(dev_alloc(&h->hs_y, 16 * Bm * M));
+    MGH_TRY(dev_alloc(&h->hs_r, 16 * Bm * M));
+    h->hs_M = M;
+  }
+  // inputs in
+  MGH_CUDA(cudaMemcpyAsync(h->hs_f, f_d, 8 * nint, cudaMemcpyHostToDevice, s));
+  MGH_CUDA(cudaMemcpyAsync(h->hs_theta, theta, 8 * (size_t)B, cudaMemcpyHostToDevice, s));
+  MGH_CUDA(cudaMemcpyAsync(h->hs_rec, rec, 8 * (size_t)M, cudaMemcpyHostToDevice, s));
+  MGH_CUDA(cudaMemcpyAsync(h->hs_y, y, 16 * (size_t)B * M, cudaMemcpyHostToDevice, s));
+  // contrast, forward solves, misfit, adjoint solves and gradient: the device-pointer path
+  MGH_TRY(setup_contrast(*h, h->hs_f));
+  MGH_TRY(launch_incident(*h, h->hs_theta, B, h->T1, true));
+  MGH_CUDA(cudaMemsetAsync(h->hs_u, 0, 16 * N * B, s));
+  const mgh_status sf = fgmres_solve(*h, h->T1, B, h->hs_u, info_fwd);
+  if (sf != MGH_OK && sf != MGH_NOT_CONVERGED) return sf;
+  MGH_TRY(launch_misfit(*h, h->hs_u, h->hs_y, B, h->hs_rec, M, h->hs_r, h->hs_G, h->dscratch + B));
+  MGH_TRY(launch_conj(*h, h->hs_G, B, h->T1));
+  MGH_CUDA(cudaMemsetAsync(h->T2, 0, 16 * N * B, s));
+  const mgh_status sa = fgmres_solve(*h, h->T1, B, h->T2, info_adj);
+  if (sa != MGH_OK && sa != MGH_NOT_CONVERGED) return sa;
+  MGH_TRY(launch_gradient(*h, h->hs_theta, h->hs_u, h->T2, B, h->hs_f));
+  // results out
+  MGH_CUDA(cudaMemcpyAsync(grad, h->hs_f, 8 * nint, cudaMemcpyDeviceToHost, s));
+  MGH_CUDA(cudaMemcpyAsync(loss, h->dscratch + B, 8, cudaMemcpyDeviceToHost, s));
+  if (r) MGH_CUDA(cudaMemcpyAsync(r, h->hs_r, 16 * (size_t)B * M, cudaMemcpyDeviceToHost, s));
+  MGH_CUDA(cudaStreamSynchronize(s));
+  return sf != MGH_OK ? sf : sa;
 }
 
 mgh_status mgh_tv_prox(mgh_handle* h, const double* fbar, const double* d, double gamma, double lam,

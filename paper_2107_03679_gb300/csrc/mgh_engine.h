@@ -119,6 +119,15 @@ struct Handle {
   cd* partial = nullptr;     // [nblk*B][2m+4] block partial sums
   int nblk = 1;              // reduction blocks per right-hand side
   double* dscratch = nullptr;   // small FP64 scratch (loss)
+  // device staging of the host-buffer entry point (allocated on its first call, grown with M)
+  double* hs_f = nullptr;       // [ny_int][nx_int] contrast, then the gradient
+  double* hs_theta = nullptr;   // [Bmax] angles
+  cd* hs_u = nullptr;           // [Bmax][N] scattered fields
+  cd* hs_G = nullptr;           // [Bmax][N] adjoint sources
+  int64_t* hs_rec = nullptr;    // [hs_M] receivers
+  cd* hs_y = nullptr;           // [Bmax][hs_M] data
+  cd* hs_r = nullptr;           // [Bmax][hs_M] residuals at the receivers
+  int hs_M = 0;
   double* tvbuf = nullptr;      // [7][ny_int][nx_int] TV proximal operator: w, the dual momentum
                                 // point (p twice, q twice: ping-pong) and the last dual iterate (p, q)
   int* dev_err = nullptr;       // device error word written by kernels with bounded waits

@@ -17,15 +17,8 @@
 // as the product with the dense inverse.  A later cycle of a level starts from that level's last
 // iterate (Alg. 2); the exact coarsest solve gives the same result every time, so it runs once
 // per visit of the level above it.
-//
-// The block is bound by latency, not bytes.  So that no pass waits on L2, every level's real
-// coefficient c is staged in shared memory once per launch and the diagonal D of K_kappa (and
-// omega / D) is formed from it where a pass needs it, with the set-up kernels' formula in the
-// tail's precision; and the iterate of a level lives in whichever of its two bordered fields the
-// last sweep wrote (no copy pass after an even number of sweeps).
 #include <algorithm>
 
-#include "mgh_diag.cuh"
 #include "mgh_engine.h"
 
 namespace mgh {
@@ -33,31 +26,27 @@ namespace mgh {
 namespace {
 
 constexpr int kTailThreads = 1024;
-constexpr size_t kTailSmemMax = 220 * 1024;
+constexpr size_t kTailSmemMax = 200 * 1024;
 
 template <typename T>
 struct TailLevel {
-  DiagArgs<T> g;       // geometry and coefficients of D on this level
+  const Cx<T>* D;      // diagonal of K_kappa on this level
+  const Cx<T>* wd;     // omega / D
   int nx, ny, nu1, nu2;
   int pitch;           // nx + 2: fields carry a border of zeros one point wide
   int dx, dy;          // a step of kTailThreads points in row-major order: dy rows and dx columns
-  int off_b;           // element offset of the right-hand side (bordered)
-  int off_v, off_t;    // the two iterate / scratch fields (bordered; on the coarsest level off_t is a
-                       // plain copy of b and the iterate is always off_v)
-  int off_c;           // real coefficient c (plain, in the T area after the complex fields; -1 on
-                       // the coarsest level)
+  int off_b, off_v;    // element offsets of the right-hand side and iterate (bordered)
+  int off_t;           // scratch field (bordered; on the coarsest level a plain copy of b)
   T inv_h2;
 };
 
 template <typename T>
 struct TailArgs {
   TailLevel<T> lv[kMaxLevels];  // index 0 = level l0
-  const double* c[kMaxLevels];  // the levels' coefficients (FP64 master copies), staged at launch
   int depth;                    // tail levels, the coarsest included (>= 2)
   int gamma;                    // CycleType
   int reps;                     // cycles of level l0 (the level above runs it CycleType times)
-  int total;                    // complex elements of shared memory in use (the T area follows)
-  int total_c;                  // elements of the T area (coefficients)
+  int total;                    // elements of shared memory in use
   T om1;                        // 1 - omega
   const Cx<T>* b_in;            // right-hand sides of level l0, b_in + rhs * stride
   Cx<T>* v_out;                 // results on level l0, v_out + rhs * stride
@@ -81,24 +70,17 @@ __device__ __forceinline__ void for_points(const TailLevel<T>& L, Body&& body) {
   }
 }
 
-// D and omega / D of point (x, y) of level L, from the staged coefficient.
-template <typename T>
-__device__ __forceinline__ Cx<T> tail_D(const TailLevel<T>& L, const T* __restrict__ cs, int k, int x, int y) {
-  return level_diag(L.g, x, y, cs[L.off_c + k]);
-}
-
 // `sweeps` damped-Jacobi sweeps on K v = b, from v = 0 when `zero`, starting from the iterate in
-// field `cur` (off_v or off_t); returns the field that holds the result.
+// field `cur` (off_v or off_t of the level); returns the field that holds the result (a level's
+// iterate lives in whichever of its two fields the last sweep wrote: no copy pass).
 template <typename T>
-__device__ int tail_smooth(Cx<T>* sm, const T* cs, const TailLevel<T>& L, int cur, int sweeps, bool zero, T om1) {
+__device__ int tail_smooth(Cx<T>* sm, const TailLevel<T>& L, int cur, int sweeps, bool zero, T om1) {
   const Cx<T>* b = sm + L.off_b;
   const int P = L.pitch;
   int s = 0;
   if (zero) {
     Cx<T>* v = sm + cur;
-    for_points(L, [&](int k, int i, int x, int y) {
-      v[i] = sweeps > 0 ? damped_inverse(tail_D(L, cs, k, x, y), L.g.omega) * b[i] : czero<T>();
-    });
+    for_points(L, [&](int k, int i, int, int) { v[i] = sweeps > 0 ? L.wd[k] * b[i] : czero<T>(); });
     __syncthreads();
     s = 1;
   }
@@ -106,11 +88,11 @@ __device__ int tail_smooth(Cx<T>* sm, const T* cs, const TailLevel<T>& L, int cu
     const Cx<T>* src = sm + cur;
     const int nxt = cur == L.off_v ? L.off_t : L.off_v;
     Cx<T>* dst = sm + nxt;
-    for_points(L, [&](int k, int i, int x, int y) {
+    for_points(L, [&](int k, int i, int, int) {
       const Cx<T> nb = src[i - 1] + src[i + 1] + src[i - P] + src[i + P];
       const Cx<T> bk = b[i];
       const Cx<T> t = mk<T>(bk.re + L.inv_h2 * nb.re, bk.im + L.inv_h2 * nb.im);
-      const Cx<T> c = src[i], w = damped_inverse(tail_D(L, cs, k, x, y), L.g.omega);
+      const Cx<T> c = src[i], w = L.wd[k];
       dst[i] = mk<T>(om1 * c.re + w.re * t.re - w.im * t.im, om1 * c.im + w.re * t.im + w.im * t.re);
     });
     __syncthreads();
@@ -119,17 +101,17 @@ __device__ int tail_smooth(Cx<T>* sm, const T* cs, const TailLevel<T>& L, int cu
   return cur;
 }
 
-// r = b - K v (v in field `cur`) into the other field, then its full-weighting restriction into
-// the next level's b.
+// r = b - K v (v in field `cur`) into the level's other field, then its full-weighting restriction
+// into the next level's b.
 template <typename T>
-__device__ void tail_restrict(Cx<T>* sm, const T* cs, const TailLevel<T>& L, int cur, const TailLevel<T>& C) {
+__device__ void tail_restrict(Cx<T>* sm, const TailLevel<T>& L, int cur, const TailLevel<T>& C) {
   const Cx<T>* v = sm + cur;
   const Cx<T>* b = sm + L.off_b;
   Cx<T>* r = sm + (cur == L.off_v ? L.off_t : L.off_v);
   const int P = L.pitch;
-  for_points(L, [&](int k, int i, int x, int y) {
+  for_points(L, [&](int k, int i, int, int) {
     const Cx<T> s = v[i - 1] + v[i + 1] + v[i - P] + v[i + P];
-    const Cx<T> kv = tail_D(L, cs, k, x, y) * v[i] - L.inv_h2 * s;
+    const Cx<T> kv = L.D[k] * v[i] - L.inv_h2 * s;
     r[i] = b[i] - kv;
   });
   __syncthreads();
@@ -145,7 +127,7 @@ __device__ void tail_restrict(Cx<T>* sm, const T* cs, const TailLevel<T>& L, int
   __syncthreads();
 }
 
-// v += P e, v in field `cur` of L, e in field `ccur` of C (bilinear by parity; the zero border
+// v += P e, v in field `cur` of L and e in field `ccur` of C (bilinear by parity; the zero border
 // supplies coarse samples outside the coarse grid).
 template <typename T>
 __device__ void tail_prolong(Cx<T>* sm, const TailLevel<T>& L, int cur, const TailLevel<T>& C, int ccur) {
@@ -171,7 +153,7 @@ __device__ void tail_prolong(Cx<T>* sm, const TailLevel<T>& L, int cur, const Ta
 }
 
 // Coarsest level: v = K^{-1} b, one warp per row of the inverse (read from L2), lanes over columns;
-// b is first copied without its border into the level's scratch field.  The result is in off_v.
+// b is first copied without its border into the level's scratch field.
 template <typename T>
 __device__ void tail_coarsest(Cx<T>* sm, const TailLevel<T>& L, const Cx<T>* __restrict__ kinv) {
   const Cx<T>* bb = sm + L.off_b;
@@ -208,14 +190,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailArgs<T> a) {
   if (a.st && !a.st[rhs].active) return;
   extern __shared__ __align__(16) unsigned char tail_smem[];
   Cx<T>* sm = reinterpret_cast<Cx<T>*>(tail_smem);
-  T* cs = reinterpret_cast<T*>(sm + a.total);
-  // zero every field once (the borders are never written afterwards) and stage the coefficients
+  // zero everything once: the borders are never written afterwards
   for (int k = threadIdx.x; k < a.total; k += kTailThreads) sm[k] = czero<T>();
-  for (int d = 0; d + 1 < a.depth; ++d) {
-    const TailLevel<T>& L = a.lv[d];
-    const int n = L.nx * L.ny;
-    for (int k = threadIdx.x; k < n; k += kTailThreads) cs[L.off_c + k] = static_cast<T>(a.c[d][k]);
-  }
   __syncthreads();
   const TailLevel<T>& top = a.lv[0];
   const Cx<T>* bin = a.b_in + rhs * a.stride;
@@ -245,8 +221,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailArgs<T> a) {
           cnt[d] = a.gamma - 1;
           continue;
         }
-        cur[d] = tail_smooth(sm, cs, a.lv[d], cur[d], a.lv[d].nu1, zero[d], a.om1);
-        tail_restrict(sm, cs, a.lv[d], cur[d], a.lv[d + 1]);
+        cur[d] = tail_smooth(sm, a.lv[d], cur[d], a.lv[d].nu1, zero[d], a.om1);
+        tail_restrict(sm, a.lv[d], cur[d], a.lv[d + 1]);
         cnt[d] = 0;
         zero[d + 1] = true;
         ++d;
@@ -259,7 +235,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailArgs<T> a) {
         continue;
       }
       tail_prolong(sm, a.lv[d], cur[d], a.lv[d + 1], cur[d + 1]);
-      cur[d] = tail_smooth(sm, cs, a.lv[d], cur[d], a.lv[d].nu2, false, a.om1);
+      cur[d] = tail_smooth(sm, a.lv[d], cur[d], a.lv[d].nu2, false, a.om1);
       if (d == 0) break;
       --d;
     }
@@ -269,14 +245,12 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailArgs<T> a) {
   for_points(top, [&](int k, int i, int, int) { vo[k] = v0[i]; });
 }
 
-// Shared-memory layout of a tail from level l0 (element offsets per level; returns the complex
-// total and, in *total_c, the T elements of the coefficient area that follows): bordered
-// right-hand side and two bordered iterate / scratch fields on every level above the coarsest,
-// with its plain coefficient; on the coarsest, bordered right-hand side and iterate and a plain
-// copy of the right-hand side.
+// Shared-memory layout of a tail from level l0 (element offsets per level; returns the total):
+// bordered right-hand side, iterate and scratch field on every level above the coarsest; on the
+// coarsest, bordered right-hand side and iterate and a plain copy of the right-hand side.
 template <typename T>
-int tail_layout(const Handle& h, int l0, TailLevel<T>* lv, int* total_c = nullptr) {
-  int off = 0, offc = 0;
+int tail_layout(const Handle& h, int l0, TailLevel<T>* lv) {
+  int off = 0;
   for (int l = l0; l < h.L; ++l) {
     const Level& L = h.lev[l];
     const int ps = (L.nx + 2) * (L.ny + 2);
@@ -286,39 +260,26 @@ int tail_layout(const Handle& h, int l0, TailLevel<T>* lv, int* total_c = nullpt
     t.off_b = off; off += ps;
     t.off_v = off; off += ps;
     t.off_t = off; off += l + 1 < h.L ? ps : (int)L.n();
-    t.off_c = -1;
-    if (l + 1 < h.L) { t.off_c = offc; offc += (int)L.n(); }
     if (lv) lv[l - l0] = t;
   }
-  if (total_c) *total_c = offc;
   return off;
 }
 
 template <typename T>
 size_t tail_smem_bytes(const Handle& h, int l0) {
-  int tc = 0;
-  const int t = tail_layout<T>(h, l0, nullptr, &tc);
-  return (size_t)t * sizeof(Cx<T>) + (size_t)tc * sizeof(T);
+  return (size_t)tail_layout<T>(h, l0, nullptr) * sizeof(Cx<T>);
 }
 
 template <typename T>
 mgh_status launch_tail_t(Handle& h, int reps, int B, const RhsState* st) {
   const int l0 = h.tail_l0;
   TailArgs<T> a{};
-  a.total = tail_layout<T>(h, l0, a.lv, &a.total_c);
-  const mgh_params& p = h.p;
+  a.total = tail_layout<T>(h, l0, a.lv);
   for (int l = l0; l < h.L; ++l) {
     const Level& lv = h.lev[l];
     TailLevel<T>& t = a.lv[l - l0];
-    DiagArgs<T>& g = t.g;     // K_kappa on this level, as the set-up kernels form it
-    g.nx = lv.nx; g.ny = lv.ny; g.scale = lv.scale;
-    g.x0 = p.abl; g.x1 = p.abl + p.nx_int - 1; g.y0 = p.abl; g.y1 = p.abl + p.ny_int - 1;
-    g.inv_L2 = static_cast<T>(p.abl > 0 ? 1.0 / ((double)p.abl * p.abl) : 0.0);
-    g.beta = static_cast<T>(p.beta);
-    diag_set_spacing(g, lv.h, p.k);
-    g.kap_re = static_cast<T>(p.shift_re); g.kap_im = static_cast<T>(p.shift_im);
-    g.omega = static_cast<T>(p.omega);
-    a.c[l - l0] = lv.c;
+    t.D = (const Cx<T>*)lv.D;
+    t.wd = (const Cx<T>*)lv.wDinv;
     t.nu1 = nu_pre(h, l); t.nu2 = nu_post(h, l);
     t.inv_h2 = static_cast<T>(1.0 / (lv.h * lv.h));
   }
@@ -331,7 +292,7 @@ mgh_status launch_tail_t(Handle& h, int reps, int B, const RhsState* st) {
   a.stride = h.lev[l0].n();
   a.kinv = sizeof(T) == 8 ? (const Cx<T>*)(const void*)h.kinv64r : (const Cx<T>*)(const void*)h.kinv32;
   a.st = st;
-  const size_t smem = (size_t)a.total * sizeof(Cx<T>) + (size_t)a.total_c * sizeof(T);
+  const size_t smem = (size_t)a.total * sizeof(Cx<T>);
   MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax)););
   ProfScope ps(h, P_COARSE);
   k_tail<T><<<B, kTailThreads, smem, h.stream>>>(a);

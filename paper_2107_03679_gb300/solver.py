@@ -237,6 +237,25 @@ class Solver:
             raise ValueError(f"{name} must be [{self.ny_int}, {self.nx_int}]")
         return t
 
+    def data_term_gradient_host(self, f_d: torch.Tensor, theta: torch.Tensor, rec: torch.Tensor, y: torch.Tensor,
+                                grad_out: Optional[torch.Tensor] = None, r_out: Optional[torch.Tensor] = None,
+                                want_infos: bool = False):
+        """The data term and its gradient in one library call on HOST tensors (mgh_data_term_gradient_host):
+        f_d [ny_int, nx_int] float64, theta [B] float64, rec [M] int64, y [B, M] complex128, all on the
+        CPU (pinned memory makes the copies asynchronous).  Returns (loss, gradient [ny_int, nx_int]
+        on the CPU, residuals S u - y [B, M] on the CPU, forward infos, adjoint infos)."""
+        B, M = theta.numel(), rec.numel()
+        self._B(theta.reshape(-1))
+        nint = self.nx_int * self.ny_int
+        grad = grad_out if grad_out is not None else torch.empty((self.ny_int, self.nx_int), dtype=torch.float64)
+        r = r_out if r_out is not None else torch.empty((B, M), dtype=torch.complex128)
+        loss, inf_f, inf_a = capi.mgh_data_term_gradient_host(
+            self._h, capi._hptr(f_d, torch.float64, nint, "f_d"), capi._hptr(theta, torch.float64, B, "theta"), B,
+            capi._hptr(rec, torch.int64, M, "rec"), M, capi._hptr(y, torch.complex128, B * M, "y"),
+            capi._hptr(grad, torch.float64, nint, "grad"), capi._hptr(r, torch.complex128, B * M, "r"),
+            want_infos=want_infos)
+        return loss, grad, r, inf_f, inf_a
+
     def tv_prox(self, fbar: torch.Tensor, d: Optional[torch.Tensor], gamma: float, lam: float, iters: int,
                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
         """argmin_{x >= 0} 1/2 ||x - (fbar - gamma d)||^2 + lam TV(x) by `iters` dual FGP iterations
