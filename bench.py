@@ -100,6 +100,24 @@ def make_inputs(w):
     return f_gt, f_step, th, rec
 
 
+# DRAM bytes of one launch of a kernel class, from ncu captures of 24-angle launches of the current
+# kernels on the 576^2 workload (6 levels, nu = 2, restart 8, FP32 cycle): (bytes of the capture,
+# bytes read once per launch whatever the batch); see profiles/vcycle_post_l0_ellipses576.md and
+# profiles/gram_sstep_ellipses576.md.  Traffic grows with the right-hand sides (independent sweeps).
+NCU_TRAFFIC_24 = {"vcycle_post_l0": (215.5e6, 2.65e6), "gs_update": (577.4e6, 0.0)}
+
+
+def captured_traffic(cls: str, w, precision: str, B: int, shape=None):
+    """Scaled capture for this launch, or None when no capture matches (another workload, or launch
+    shapes other than the captured built-in ones: 4 warps per block, ring of one period)."""
+    if (w.nx, w.levels, w.nu1, w.nu2, w.restart, precision) != (576, 6, 2, 2, 8, "mixed32") or cls not in NCU_TRAFFIC_24:
+        return None
+    if shape and (shape.get("wave_warps", 4) != 4 or shape.get("wave_ring", 1) != 1 or any(shape.get("wave_seg", []))):
+        return None
+    cap, once = NCU_TRAFFIC_24[cls]
+    return round((cap - once) * B / 24 + once)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -701,8 +719,8 @@ def gpu_main(args, rank, world, local_rank):
         # launch) and the measured copy bandwidth
         achieved = alg[dom] / (ms_cls[dom] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_launch": round(alg[dom] / n_l)}
+                "frac": round(achieved / peak, 4), "traffic": captured_traffic(dom, w, precision, B, (tuned or {}).get("shape")),
+                "peak_kind": peak_kind, "bytes_per_launch": round(alg[dom] / n_l)}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
                 "traffic": None, "peak_kind": peak_kind}
