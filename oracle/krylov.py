@@ -11,6 +11,9 @@
   2010): the monomial basis v_{k+1} = A M^{-1} v_k is orthogonalised at the end of the cycle by
   the Cholesky factor of its Gram matrix.  In exact arithmetic it returns the iterate of one
   Arnoldi cycle of fgmres; the CUDA path's default mixed engine is built on this identity.
+* fgmres_dr: flexible GMRES with deflated restarting (Morgan 2002; Giraud et al. 2010), which
+  keeps k harmonic Ritz vectors across restarts: the method for problems on which ordinary
+  restarts stagnate (the strong-scattering workload).
 
 Iterations are counted as preconditioner applications (Arnoldi steps for GMRES).
 """
@@ -184,3 +187,99 @@ def sstep_cycle(apply_A: Callable, apply_M: Callable, b: np.ndarray, x: np.ndarr
     for k in range(m):
         x_new = x_new + y[k] * Z[k]
     return x_new
+
+
+def harmonic_ritz(Hbar: np.ndarray, k: int) -> np.ndarray:
+    """The k harmonic Ritz vectors of smallest harmonic Ritz value modulus of an (m+1) x m
+    Arnoldi matrix Hbar: the eigenvectors g of H_m + |h_{m+1,m}|^2 f e_m^T with H_m^H f = e_m
+    (Morgan 2002), i.e. the solutions of Hbar^H Hbar g = theta H_m^H g.  Returns m x k."""
+    m = Hbar.shape[1]
+    Hm = Hbar[:m, :]
+    em = np.zeros(m)
+    em[-1] = 1.0
+    f = np.linalg.solve(Hm.conj().T, em)
+    T = Hm + abs(Hbar[m, m - 1]) ** 2 * np.outer(f, em)
+    theta, G = np.linalg.eig(T)
+    idx = np.argsort(np.abs(theta))[:k]
+    return G[:, idx]
+
+
+def deflated_restart(V: np.ndarray, Z: np.ndarray, H: np.ndarray, c: np.ndarray, k: int):
+    """The state a deflated restart carries into the next cycle, from the cycle's V (n x (m+1)),
+    Z (n x m), Hbar ((m+1) x m) with A Z = V Hbar, and the residual coefficients c (r = V c):
+    P = [[G_k; 0], c] orthonormalised (G_k the k harmonic Ritz vectors), V P, Z P_k, P^H Hbar P_k
+    and P^H c.  Returns (V_new n x (k+1), Z_new n x k, H_new (k+1) x k, g_new k+1)."""
+    m = H.shape[1]
+    P = np.zeros((m + 1, k + 1), dtype=np.complex128)
+    if k > 0:
+        P[:m, :k] = harmonic_ritz(H, k)
+    P[:, k] = c
+    Q, _ = np.linalg.qr(P)
+    return V @ Q, Z @ Q[:m, :k], Q.conj().T @ H @ Q[:m, :k], Q.conj().T @ c
+
+
+def fgmres_dr(apply_A: Callable, apply_M: Callable, b: np.ndarray, tol: float, m: int, k: int,
+              maxit: int, x0: np.ndarray = None):
+    """Right-preconditioned flexible GMRES(m) with deflated restarting (GMRES-DR of Morgan 2002 in
+    the flexible form of Giraud, Gratton, Pinel & Vasseur 2010); returns (x, SolveInfo).
+
+    A cycle runs Arnoldi from column j0 to m - 1 (classical Gram-Schmidt with a second pass) on
+    z_j = M^{-1} v_j, keeping A Z = V Hbar, and takes the least-squares correction x += Z y.  The
+    next cycle keeps the k harmonic Ritz vectors of smallest modulus: with P = [[g_1 .. g_k; 0], c]
+    orthonormalised (c = g - Hbar y, the coefficients of the residual in V), V <- V P, Z <- Z P_k,
+    Hbar <- P^H Hbar P_k and g <- P^H c, so that the relation A Z = V Hbar and r = V g carry over
+    and Arnoldi continues at column k.  With k = 0 it is FGMRES(m) with ordinary restarts.  The
+    iterate is accepted on the true residual ||b - A x|| <= tol ||b||, checked after every cycle;
+    steps count preconditioner applications."""
+    info = SolveInfo()
+    x = np.zeros_like(b) if x0 is None else x0.astype(np.complex128).copy()
+    bnorm = _norm(b)
+    if bnorm == 0.0:
+        info.converged, info.rel_residual = True, 0.0
+        return np.zeros_like(b), info
+    shape, n = b.shape, b.size
+    r = (b - apply_A(x)).ravel()
+    beta = np.linalg.norm(r)
+    info.rel_residual = beta / bnorm
+    if info.rel_residual <= tol:
+        info.converged = True
+        return x, info
+    V = np.zeros((n, m + 1), dtype=np.complex128)
+    Z = np.zeros((n, m), dtype=np.complex128)
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    g = np.zeros(m + 1, dtype=np.complex128)
+    V[:, 0] = r / beta
+    g[0] = beta
+    j0 = 0
+    while True:
+        for j in range(j0, m):
+            Z[:, j] = apply_M(V[:, j].reshape(shape)).ravel()
+            w = apply_A(Z[:, j].reshape(shape)).ravel()
+            for _ in range(2):
+                h = V[:, :j + 1].conj().T @ w
+                w = w - V[:, :j + 1] @ h
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            V[:, j + 1] = w / H[j + 1, j]
+            info.iterations += 1
+        y = np.linalg.lstsq(H, g, rcond=None)[0]
+        x = x + (Z @ y).reshape(shape)
+        c = g - H @ y
+        info.restarts += 1
+        info.rel_residual = _norm(b - apply_A(x)) / bnorm
+        info.history.append(info.rel_residual)
+        if info.rel_residual <= tol:
+            info.converged = True
+            return x, info
+        if info.iterations >= maxit:
+            return x, info
+        V_new, Z_new, H_new, g_new = deflated_restart(V, Z, H, c, k)
+        V[:] = 0
+        Z[:] = 0
+        H[:] = 0
+        g[:] = 0
+        V[:, :k + 1] = V_new
+        Z[:, :k] = Z_new
+        H[:k + 1, :k] = H_new
+        g[:k + 1] = g_new
+        j0 = k
