@@ -125,6 +125,15 @@ typedef struct {
                                by level); entries from levels-1 on are ignored */
   int nu1_level[MGH_MAX_LEVELS];
   int nu2_level[MGH_MAX_LEVELS];
+  int deflate;              /* FGMRES with deflated restarting (GMRES-DR, Morgan 2002; flexible form of
+                               Giraud et al. 2010): k harmonic Ritz vectors of smallest modulus kept
+                               across restarts, 0 = plain restarts (default), 1..min(restart-1, 16)
+                               otherwise.  A cycle that ran its `restart` steps without converging
+                               keeps V Q1 and Z P_k (P_k the harmonic Ritz vectors, Hbar P_k = Q1 R)
+                               and continues Arnoldi at column k from the true residual
+                               orthogonalised against them.  Needs krylov MGH_KRYLOV_FGMRES with the
+                               native-FP64 Arnoldi: precision MGH_PREC_FP64, or MGH_PREC_MIXED32 with
+                               arnoldi MGH_ARNOLDI_FP64 (MGH_NOT_SUPPORTED otherwise) */
 } mgh_params;
 
 typedef struct {
@@ -344,6 +353,20 @@ mgh_status mgh_set_kernel_shape(mgh_handle* h, const mgh_kernel_shape* s);
  * handles whose solver polls the word: precision MGH_PREC_MIXED32, krylov MGH_KRYLOV_FGMRES,
  * arnoldi MGH_ARNOLDI_DF or MGH_ARNOLDI_SSTEP (MGH_NOT_SUPPORTED otherwise). */
 mgh_status mgh_debug_inject_timeout(mgh_handle* h);
+
+/* Host-side restart data of one deflated restart, exposed for tests (no device work; the solver
+ * calls the same routine).  Inputs: Hbar, the (m+1) x m Arnoldi matrix of a cycle (row-major,
+ * A Z = V Hbar), and c (m+1), the coefficients of the cycle's residual in V.  With g_1..g_k the
+ * harmonic Ritz vectors of smallest harmonic Ritz value modulus -- eigenvectors of
+ * H_m + |h_{m+1,m}|^2 f e_m^T with H_m^H f = e_m (Morgan 2002) -- and P = [[g_1..g_k; 0], c]
+ * orthonormalised, the restart keeps V [C; 0] and Z C with C = P_k W (m x k, row-major), W a
+ * k x k unitary chosen so that Hh = blockdiag(W, 1)^H P^H Hbar P_k W ((k+1) x k, row-major) is
+ * upper Hessenberg; R (k x k, row-major, upper triangular), cs (k, real) and sn (k) are the Givens
+ * QR of Hh (rotation i on rows i, i+1: [[cs_i, sn_i], [-conj(sn_i), cs_i]]).  2 <= m <= 32,
+ * 1 <= k < m; all pointers host memory owned by the caller.  MGH_NOT_CONVERGED when the eigenvalue
+ * iteration fails or a vector vanishes (the solver then restarts plainly). */
+mgh_status mgh_debug_deflate(int m, int k, const mgh_cdouble* Hbar, const mgh_cdouble* c, mgh_cdouble* C,
+                             mgh_cdouble* Hh, mgh_cdouble* R, double* cs, mgh_cdouble* sn);
 
 /* Kernel launches issued by this handle since creation (or since the last reset). */
 uint64_t mgh_launch_count(const mgh_handle* h, int reset);

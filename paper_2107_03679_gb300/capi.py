@@ -34,6 +34,7 @@ class mgh_params(ctypes.Structure):
         ("precision", ctypes.c_int), ("batch_max", ctypes.c_int), ("arnoldi", ctypes.c_int),
         ("krylov", ctypes.c_int), ("cycle_type", ctypes.c_int), ("nu_per_level", ctypes.c_int),
         ("nu1_level", ctypes.c_int * MGH_MAX_LEVELS), ("nu2_level", ctypes.c_int * MGH_MAX_LEVELS),
+        ("deflate", ctypes.c_int),
     ]
 
 
@@ -104,6 +105,7 @@ def _load():
         "mgh_profile_enable": (S, [P, I]),
         "mgh_profile_read": (S, [P, ctypes.POINTER(mgh_profile)]),
         "mgh_debug_inject_timeout": (S, [P]),
+        "mgh_debug_deflate": (S, [I, I, P, P, P, P, P, P, P]),
         "mgh_get_kernel_shape": (S, [P, ctypes.POINTER(mgh_kernel_shape)]),
         "mgh_set_kernel_shape": (S, [P, ctypes.POINTER(mgh_kernel_shape)]),
         "mgh_launch_count": (ctypes.c_uint64, [P, I]),
@@ -124,7 +126,8 @@ EXPORTED = [
     "mgh_default_params", "mgh_workspace_bytes", "mgh_create", "mgh_destroy", "mgh_set_contrast",
     "mgh_incident_field", "mgh_rhs", "mgh_apply", "mgh_precondition", "mgh_coarse_solve",
     "mgh_level_shape", "mgh_level_coefficient", "mgh_solve", "mgh_forward", "mgh_crop", "mgh_sample",
-    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_data_term_gradient_host", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_get_kernel_shape", "mgh_set_kernel_shape", "mgh_debug_inject_timeout", "mgh_launch_count", "mgh_status_string", "mgh_last_error",
+    "mgh_scatter", "mgh_misfit", "mgh_misfit_noalloc", "mgh_gradient", "mgh_data_term_gradient_host", "mgh_tv_prox", "mgh_fbs_momentum", "mgh_profile_enable", "mgh_profile_read", "mgh_get_kernel_shape", "mgh_set_kernel_shape", "mgh_debug_inject_timeout", "mgh_debug_deflate", "mgh_launch_count", "mgh_status_string",
+    "mgh_last_error",
 ]
 
 
@@ -323,6 +326,27 @@ def mgh_set_kernel_shape(h, wave_seg=0, wave_warps: int = 4, wave_ring: int = 1,
 
 def mgh_debug_inject_timeout(h) -> None:
     _check("mgh_debug_inject_timeout", _lib.mgh_debug_inject_timeout(h))
+
+
+def mgh_debug_deflate(Hbar, c, k):
+    """Restart data of one deflated restart from an (m+1) x m Arnoldi matrix and the residual
+    coefficients c (host numpy arrays): returns (C m x k, Hh (k+1) x k, R k x k, cs k, sn k), the
+    solver's host routine (see mgh_debug_deflate in include/mgh.h)."""
+    import numpy as np
+    Hb = np.ascontiguousarray(Hbar, dtype=np.complex128)
+    cc = np.ascontiguousarray(c, dtype=np.complex128)
+    m = Hb.shape[1]
+    if Hb.shape != (m + 1, m) or cc.shape != (m + 1,):
+        raise ValueError("Hbar must be (m+1) x m and c of length m+1")
+    C = np.zeros((m, k), np.complex128)
+    Hh = np.zeros((k + 1, k), np.complex128)
+    R = np.zeros((k, k), np.complex128)
+    cs = np.zeros(k, np.float64)
+    sn = np.zeros(k, np.complex128)
+    _check("mgh_debug_deflate", _lib.mgh_debug_deflate(m, k, Hb.ctypes.data, cc.ctypes.data, C.ctypes.data,
+                                                       Hh.ctypes.data, R.ctypes.data, cs.ctypes.data,
+                                                       sn.ctypes.data))
+    return C, Hh, R, cs, sn
 
 
 def mgh_launch_count(h, reset=False) -> int:

@@ -59,6 +59,12 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
         nx % 2 != 0 || n1 < 1 || n2 < 1)
       return MGH_NOT_SUPPORTED;
   }
+  if (p->deflate < 0 || p->deflate > kMaxDeflate || (p->deflate > 0 && p->deflate >= p->restart))
+    return MGH_INVALID_ARG;
+  if (p->deflate > 0 && (p->krylov != MGH_KRYLOV_FGMRES ||
+                         (p->precision != MGH_PREC_FP64 &&
+                          !(p->precision == MGH_PREC_MIXED32 && p->arnoldi == MGH_ARNOLDI_FP64))))
+    return MGH_NOT_SUPPORTED;
   if (nx > (1 << 20) || ny > (1 << 20) || nx * ny > (1LL << 31)) return MGH_INVALID_ARG;
   int cx = (int)nx, cy = (int)ny;
   for (int l = 0; l < p->levels; ++l) {
@@ -70,6 +76,10 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
 }
 
 size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Complex words of one right-hand side's deflated-restart data: C m x k, Hh (k+1) x k, R k x k,
+// the k Givens cosines (real parts) and sines.
+size_t dr_words(int m, int k) { return (size_t)m * k + (size_t)(k + 1) * k + (size_t)k * k + 2 * (size_t)k; }
 
 // Bytes of every device allocation of a handle, in allocation order.
 size_t workspace_bytes(const mgh_params& p) {
@@ -97,6 +107,9 @@ size_t workspace_bytes(const mgh_params& p) {
   t += pad256(16 * Np) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m) + pad256(4);   // DAdf, hpend, coef, err
   t += pad256(56 * (size_t)p.nx_int * p.ny_int);                                          // tvbuf
   if (p.precision != MGH_PREC_FP64) t += 2 * pad256(16 * B * Np);                        // xdf, bdf
+  if (p.deflate > 0)                                                                       // Hraw, drbuf, dr_mode
+    t += pad256(16 * B * m * (m + 1)) + pad256(16 * B * dr_words(p.restart, p.deflate)) + pad256(4 * B) +
+         pad256(16 * B * (m + 1));
   return t;
 }
 
@@ -126,7 +139,13 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->hs_y); cudaFree(h->hs_r);
   cudaFree(h->dscratch); cudaFree(h->DAdf); cudaFree(h->hpend); cudaFree(h->coef);
   cudaFree(h->dev_err); cudaFree(h->xdf); cudaFree(h->bdf); cudaFree(h->tvbuf);
+  cudaFree(h->Hraw); cudaFree(h->drbuf); cudaFree(h->dr_mode); cudaFree(h->g0);
   if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->dr_hraw_host) cudaFreeHost(h->dr_hraw_host);
+  if (h->dr_host) cudaFreeHost(h->dr_host);
+  if (h->dr_mode_host) cudaFreeHost(h->dr_mode_host);
+  if (h->dr_g0_host) cudaFreeHost(h->dr_g0_host);
+  if (h->dr_y_host) cudaFreeHost(h->dr_y_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
   if (h->gev_out) cudaEventDestroy(h->gev_out);
@@ -288,11 +307,29 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->coef, 16 * B * 2 * m);
   ALLOC(h->dscratch, 8 * (B + 1));
   ALLOC(h->tvbuf, 56 * (size_t)p->nx_int * p->ny_int);
+  if (p->deflate > 0) {
+    ALLOC(h->Hraw, 16 * B * m * (m + 1));
+    ALLOC(h->drbuf, 16 * B * dr_words(p->restart, p->deflate));
+    ALLOC(h->dr_mode, 4 * B);
+    ALLOC(h->g0, 16 * B * (m + 1));
+  }
 #undef ALLOC
   if (cudaMallocHost((void**)&h->st_host, sizeof(RhsState) * B) != cudaSuccess) {
     h->st_host = nullptr;
     free_handle(h);
     return MGH_OUT_OF_MEMORY;
+  }
+  if (p->deflate > 0) {
+    bool ok = true;
+    if (cudaMallocHost((void**)&h->dr_hraw_host, 16 * B * m * (m + 1)) != cudaSuccess) { h->dr_hraw_host = nullptr; ok = false; }
+    if (ok && cudaMallocHost((void**)&h->dr_host, 16 * B * dr_words(p->restart, p->deflate)) != cudaSuccess) {
+      h->dr_host = nullptr;
+      ok = false;
+    }
+    if (ok && cudaMallocHost((void**)&h->dr_mode_host, 4 * B) != cudaSuccess) { h->dr_mode_host = nullptr; ok = false; }
+    if (ok && cudaMallocHost((void**)&h->dr_g0_host, 16 * B * (m + 1)) != cudaSuccess) { h->dr_g0_host = nullptr; ok = false; }
+    if (ok && cudaMallocHost((void**)&h->dr_y_host, 16 * B * m) != cudaSuccess) { h->dr_y_host = nullptr; ok = false; }
+    if (!ok) { free_handle(h); return MGH_OUT_OF_MEMORY; }
   }
   // level-kernel selection (environment): MGH_VCYCLE=tile picks the shared-memory tile kernels
   // for the FP32 levels; MGH_WAVE_SEG sets the rows per warp of the wavefront kernels,

@@ -87,6 +87,8 @@ struct RhsState {
   double inv_nu;     // 1 / ||u_j - Q_j s|| of the current step (mixed path)
   double hjj_re, hjj_im;  // <q_j, w> of the current step (mixed path)
   double tol_scale;  // mixed path: factor on tol for the double-float residual (tightened if the FP64 check fails)
+  int jstart;        // first Arnoldi column of the current cycle (k after a deflated restart)
+  int deflate;       // 1: the cycle ended full length and restarts deflated (residual kept apart from V)
 };
 
 }  // namespace mgh

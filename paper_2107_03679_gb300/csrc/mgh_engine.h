@@ -4,6 +4,7 @@
 #include <cuda.h>            // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <cstddef>
+#include <complex>
 #include <cstdint>
 #include <vector>
 
@@ -16,6 +17,7 @@ constexpr int kMaxLevels = 12;
 constexpr int kMaxRestart = 32;
 constexpr int kMaxRestartDf = 20;  // restart limit of the double-float Arnoldi (register budget)
 constexpr int kMaxRestartSs = 8;   // restart limit of the s-step engine (Gram sums held in registers)
+constexpr int kMaxDeflate = 16;    // harmonic Ritz vectors kept by a deflated restart
 
 // Complex slots per block in the partial-sum buffer: two Gram-Schmidt regions of m + 2, or the
 // (m + 1)(m + 2) / 2 entries of an s-step Gram matrix.
@@ -128,6 +130,16 @@ struct Handle {
   cd* hs_y = nullptr;           // [Bmax][hs_M] data
   cd* hs_r = nullptr;           // [Bmax][hs_M] residuals at the receivers
   int hs_M = 0;
+  // deflated restarting (p.deflate = k > 0): raw Arnoldi columns and the host's restart data
+  cd* Hraw = nullptr;           // [Bmax][m][m+1] Hessenberg columns before the Givens rotations
+  cd* drbuf = nullptr;          // [Bmax][dr_stride(m, k)] C, Hh, R, cs, sn of each right-hand side
+  cd* g0 = nullptr;             // [Bmax][m+1] right-hand side of the cycle's least-squares problem
+  int* dr_mode = nullptr;       // [Bmax] 0 none, 1 deflated restart, 2 plain restart from W
+  cd* dr_hraw_host = nullptr;   // pinned host copies of Hraw, g0, y, drbuf and dr_mode
+  cd* dr_g0_host = nullptr;
+  cd* dr_y_host = nullptr;
+  cd* dr_host = nullptr;
+  int* dr_mode_host = nullptr;
   double* tvbuf = nullptr;      // [7][ny_int][nx_int] TV proximal operator: w, the dual momentum
                                 // point (p twice, q twice: ping-pong) and the last dual iterate (p, q)
   int* dev_err = nullptr;       // device error word written by kernels with bounded waits
@@ -215,6 +227,13 @@ mgh_status launch_tail(Handle& h, int reps, int B, const RhsState* st, bool fp64
 mgh_status tv_prox(Handle& h, const double* fbar, const double* d, double gamma, double lam, int iters,
                    double* out);
 mgh_status fbs_momentum(Handle& h, const double* f, const double* f_prev, double c, double* fbar);
+
+// mgh_deflate.cu: restart data of one right-hand side for a deflated restart (row-major arrays:
+// Hbar (m+1) x m and c (m+1) in; C m x k, Hh (k+1) x k, R k x k, cs k, sn k out); false when it
+// cannot be formed
+bool deflate_restart(int m, int k, const std::complex<double>* Hbar, const std::complex<double>* c,
+                     std::complex<double>* C, std::complex<double>* Hh, std::complex<double>* R, double* cs,
+                     std::complex<double>* sn);
 
 // mgh_krylov.cu
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);

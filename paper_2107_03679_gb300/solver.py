@@ -14,25 +14,29 @@ import torch
 from . import capi
 
 
-def resolve_arnoldi(arnoldi: str, precision: str, restart: int) -> str:
+def resolve_arnoldi(arnoldi: str, precision: str, restart: int, deflate: int = 0) -> str:
     """"auto": s-step cycles on the mixed path when the restart length allows them (m <= 8),
-    otherwise the double-float Arnoldi; FP16 storage (mixed16) runs only with s-step cycles; the
-    FP64 path always runs native FP64 Gram-Schmidt."""
+    otherwise the double-float Arnoldi; FP16 storage (mixed16) runs only with s-step cycles;
+    deflated restarting runs on the native FP64 Gram-Schmidt; the FP64 path always runs native
+    FP64 Gram-Schmidt."""
     if arnoldi != "auto":
         return arnoldi
     if precision == "mixed16":
         return "sstep"
     if precision != "mixed32":
         return "df"
+    if deflate > 0:
+        return "fp64"
     return "sstep" if restart <= 8 else "df"
 
 
 def make_params(nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: float = 0.15, shift=(1.0, 0.5),
                 levels: int = 4, nu1=1, nu2=1, omega: float = 0.8, restart: int = 20, maxit: int = 5000,
                 tol: float = 1e-6, precision: str = "mixed32", batch_max: int = 1, arnoldi: str = "auto",
-                krylov: str = "fgmres", cycle_type=1):
+                krylov: str = "fgmres", cycle_type=1, deflate: int = 0):
     """The mgh_params of a solver (host only) and the resolved Arnoldi engine.  nu1 / nu2: one
-    count for every level, or one per level above the coarsest (per-level fields of mgh_params)."""
+    count for every level, or one per level above the coarsest (per-level fields of mgh_params);
+    deflate: harmonic Ritz vectors kept across FGMRES restarts (0 = plain restarts)."""
     p = capi.mgh_params()
     p.nx_int, p.ny_int, p.abl = nx_int, ny_int, abl
     p.h, p.k, p.beta = h, k, beta
@@ -55,9 +59,10 @@ def make_params(nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: fl
     p.restart, p.maxit, p.tol = restart, maxit, tol
     p.precision = capi.PRECISIONS[precision]
     p.batch_max = batch_max
-    resolved = resolve_arnoldi(arnoldi, precision, restart)
+    resolved = resolve_arnoldi(arnoldi, precision, restart, deflate)
     p.arnoldi = capi.ARNOLDI[resolved]
     p.krylov = capi.KRYLOV[krylov]
+    p.deflate = int(deflate)
     return p, resolved
 
 
@@ -68,13 +73,14 @@ class Solver:
                  shift=(1.0, 0.5), levels: int = 4, nu1: int = 1, nu2: int = 1, omega: float = 0.8,
                  restart: int = 20, maxit: int = 5000, tol: float = 1e-6, precision: str = "mixed32",
                  batch_max: int = 1, arnoldi: str = "auto", krylov: str = "fgmres", cycle_type: int = 1,
-                 device: Optional[torch.device] = None, stream=None):
+                 device: Optional[torch.device] = None, stream=None, deflate: int = 0):
         """nu1 / nu2: sweeps on every level, or a sequence with one count per level (the coarsest's
-        is ignored); cycle_type: CycleType of Alg. 2 (1 = V, 2 = W, 3; or "v" / "w")."""
+        is ignored); cycle_type: CycleType of Alg. 2 (1 = V, 2 = W, 3; or "v" / "w"); deflate:
+        harmonic Ritz vectors kept across FGMRES restarts (GMRES-DR; 0 = plain restarts)."""
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         p, self.arnoldi = make_params(nx_int, ny_int, abl, h, k, beta, shift, levels, nu1, nu2, omega, restart, maxit,
-                                      tol, precision, batch_max, arnoldi, krylov, cycle_type)
+                                      tol, precision, batch_max, arnoldi, krylov, cycle_type, deflate)
         # (pre, post) sweeps of every level above the coarsest
         self.nu_levels = [(p.nu1_level[l], p.nu2_level[l]) if p.nu_per_level else (p.nu1, p.nu2)
                           for l in range(levels - 1)]
@@ -95,7 +101,8 @@ class Solver:
         args = dict(nx_int=w.nx_int, ny_int=w.ny_int, abl=w.abl, h=w.h, k=w.k, beta=w.beta,
                     shift=(w.shift_re, w.shift_im), levels=w.levels, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
                     restart=w.restart, tol=w.tol, precision=precision or w.precision,
-                    batch_max=batch_max or w.n_angles, krylov=getattr(w, "krylov", "fgmres"))
+                    batch_max=batch_max or w.n_angles, krylov=getattr(w, "krylov", "fgmres"),
+                    deflate=getattr(w, "deflate", 0))
         args.update(kw)
         return cls(**args)
 
