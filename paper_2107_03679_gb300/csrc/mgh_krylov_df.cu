@@ -909,11 +909,13 @@ k_ss_matvec2(KArgs a, int k, const ZT* __restrict__ Z, const float2* __restrict_
 // 1 / ||v_{k+1}|| for the next multigrid input.
 __global__ void k_ss_norm(KArgs a, int k, const cd* __restrict__ partial, double* __restrict__ vscale,
                           const RhsState* __restrict__ st) {
+  // one warp per right-hand side: lanes load the block sums in parallel, a butterfly adds them
   const int rhs = blockIdx.x;
-  if (!st[rhs].active || threadIdx.x != 0) return;
+  if (!st[rhs].active) return;
   double n2 = 0.0;
-  for (int b = 0; b < a.nblk; ++b) n2 += partial[((size_t)rhs * a.nblk + b) * a.pstride].re;
-  vscale[(size_t)rhs * (a.m + 1) + k + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+  for (int b = threadIdx.x; b < a.nblk; b += 32) n2 += partial[((size_t)rhs * a.nblk + b) * a.pstride].re;
+  n2 = warp_sum(n2);
+  if (threadIdx.x == 0) vscale[(size_t)rhs * (a.m + 1) + k + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
 }
 
 // The Gram sums of one tile's points for the pairs of thread group G, accumulated by FP32 FMAs
@@ -1026,99 +1028,131 @@ k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial
 }
 
 // Per right-hand side: the Gram matrix from the block sums, its equilibrated Cholesky factor,
-// the cycle's least-squares problem by Givens rotations, the prefix to keep and its y.
+// the cycle's least-squares problem by Givens rotations, the prefix to keep and its y.  One warp
+// per right-hand side (launched with 32 threads): the Gram entries are summed by lanes, row j of
+// the factor is formed with lane k computing entry (j, k), and lane c carries column c of the
+// least-squares matrix through the rotations; every entry is formed with the same operations in
+// the same order as by a single thread.
 template <int NV>
-__global__ void k_ss_lsq(KArgs a, const cd* __restrict__ partial, cd* __restrict__ y, RhsState* __restrict__ st,
-                         double tol, int maxit) {
+__global__ void __launch_bounds__(32) k_ss_lsq(KArgs a, const cd* __restrict__ partial, cd* __restrict__ y,
+                                               RhsState* __restrict__ st, double tol, int maxit) {
   using PR = GramPairs<NV>;
   constexpr int M = NV - 1;
+  static_assert(NV <= 32, "one lane per column");
   __shared__ cd Gs[PR::NP];
+  __shared__ cd R[NV][NV];
+  __shared__ cd Hs[NV][NV];
+  __shared__ double dsc[NV];
   const int rhs = blockIdx.x;
   if (!st[rhs].active) return;
-  for (int t = threadIdx.x; t < PR::NP; t += blockDim.x) {
+  const int lane = threadIdx.x;
+  for (int t = lane; t < PR::NP; t += 32) {
     cd acc = czero<double>();
     for (int b = 0; b < a.nblk; ++b) acc = acc + partial[((size_t)rhs * a.nblk + b) * a.pstride + t];
     Gs[t] = acc;
   }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+  __syncwarp();
   RhsState& S = st[rhs];
   auto G = [&](int i, int j) -> cd { return Gs[i * NV - i * (i - 1) / 2 + (j - i)]; };   // i <= j
   // equilibrated factor: G~ = D G D with D = diag(1 / sqrt(G_ii)), G~ = Rt^H Rt, R = Rt D^{-1}
-  double dsc[NV];
-  cd R[NV][NV];
-  int nv = NV;   // basis vectors whose pivots are usable
-  for (int i = 0; i < NV; ++i) {
-    const double gii = G(i, i).re;
-    if (!(gii > 0.0)) { nv = i; break; }
-    dsc[i] = 1.0 / sqrt(gii);
-  }
+  int nv = NV;   // basis vectors whose pivots are usable (the same value in every lane)
+  for (int i = 0; i < NV; ++i)
+    if (nv == NV && !(G(i, i).re > 0.0)) nv = i;
+  if (lane < nv) dsc[lane] = 1.0 / sqrt(G(lane, lane).re);
+  __syncwarp();
   for (int j = 0; j < nv; ++j) {
     double s = 1.0;
     for (int i = 0; i < j; ++i) s -= cabs2(R[i][j]);
     if (!(s > 1e-12)) {   // v_j (numerically) in the span of v_0 .. v_{j-1}
-      R[j][j] = czero<double>();
+      if (lane == 0) R[j][j] = czero<double>();
       nv = j + 1;
       break;
     }
-    R[j][j] = mk<double>(sqrt(s), 0.0);
-    for (int k = j + 1; k < nv; ++k) {
+    const double rjj = sqrt(s);
+    const int k = lane;
+    if (k > j && k < nv) {
       cd t = (dsc[j] * dsc[k]) * G(j, k);
       for (int i = 0; i < j; ++i) t = t - cconj(R[i][j]) * R[i][k];
-      R[j][k] = (1.0 / R[j][j].re) * t;
+      R[j][k] = (1.0 / rjj) * t;
     }
+    if (lane == 0) R[j][j] = mk<double>(rjj, 0.0);
+    __syncwarp();
   }
-  for (int j = 0; j < nv; ++j)
-    for (int i = 0; i <= j; ++i) R[i][j] = (1.0 / dsc[j]) * R[i][j];
+  __syncwarp();
+  for (int t = lane; t < nv * nv; t += 32) {
+    const int jj = t / nv, ii = t - jj * nv;
+    if (ii <= jj) R[ii][jj] = (1.0 / dsc[jj]) * R[ii][jj];
+  }
+  __syncwarp();
   int kmax = nv - 1;   // usable steps: columns 1 .. kmax of R
   if (kmax > maxit - S.iterations) kmax = maxit - S.iterations;
+  __syncwarp();
+  if (kmax < 1) {   // no usable direction: stop this right-hand side
+    if (lane == 0) {
+      S.active = 0;
+      S.csteps += M;
+      S.gsum += NV;
+      S.done = 1;
+      S.converged = 0;
+      S.jend = 0;
+    }
+    return;
+  }
+  // Givens on the (kmax+1) x kmax upper-Hessenberg matrix H[i][c] = R[i][c+1], rhs g = R_00 e_0;
+  // lane c holds column c and applies each rotation as soon as it is known
+  const double thr = tol * S.tol_scale * S.bnorm;
+  cd col[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) col[i] = (lane < kmax && i <= lane + 1) ? R[i][lane + 1] : czero<double>();
+  cd g0 = R[0][0], g1 = czero<double>();   // g[c], g[c+1] of the current rotation (every lane)
+  cd gsv[NV];
+  int jend = kmax;
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    if (c < jend) {
+      // lane c forms rotation c from its rotated column; every lane receives it
+      double cc = 1.0;
+      cd sv = czero<double>();
+      if (lane == c) {
+        const cd aa = col[c], bb = col[c + 1];
+        if (bb.re == 0.0 && bb.im == 0.0) { cc = 1.0; sv = czero<double>(); }
+        else if (aa.re == 0.0 && aa.im == 0.0) { cc = 0.0; sv = mk<double>(1.0, 0.0); }
+        else {
+          const double na = sqrt(cabs2(aa)), rho = sqrt(cabs2(aa) + cabs2(bb));
+          cc = na / rho;
+          sv = (1.0 / (na * rho)) * (aa * cconj(bb));
+        }
+        col[c] = cc * col[c] + sv * col[c + 1];
+      }
+      cc = __shfl_sync(0xffffffffu, cc, c);
+      sv.re = __shfl_sync(0xffffffffu, sv.re, c);
+      sv.im = __shfl_sync(0xffffffffu, sv.im, c);
+      if (lane > c && lane < kmax) {
+        const cd t = cc * col[c] + sv * col[c + 1];
+        col[c + 1] = (-1.0 * cconj(sv)) * col[c] + cc * col[c + 1];
+        col[c] = t;
+      }
+      g1 = (-1.0 * cconj(sv)) * g0;
+      gsv[c] = cc * g0;
+      g0 = g1;
+      if (!(sqrt(cabs2(g1)) > thr)) jend = c + 1;   // the same decision in every lane
+    }
+  }
+  if (lane < jend) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i <= lane) Hs[i][lane] = col[i];
+  }
+  __syncwarp();
+  if (lane != 0) return;
   S.active = 0;
   S.csteps += M;
   S.gsum += NV;
-  if (kmax < 1) {   // no usable direction: stop this right-hand side
-    S.done = 1;
-    S.converged = 0;
-    S.jend = 0;
-    return;
-  }
-  // Givens on the (kmax+1) x kmax upper-Hessenberg matrix H[i][c] = R[i][c+1], rhs g = R_00 e_0
-  cd g[NV], H[NV][NV];
-  double cs[NV];
-  cd sn[NV];
-  g[0] = R[0][0];
-  for (int i = 1; i < NV; ++i) g[i] = czero<double>();
-  int jend = kmax;
-  for (int c = 0; c < kmax; ++c) {
-    cd col[NV];
-    for (int i = 0; i <= c + 1; ++i) col[i] = R[i][c + 1];
-    for (int i = 0; i < c; ++i) {
-      const cd t = cs[i] * col[i] + sn[i] * col[i + 1];
-      col[i + 1] = (-1.0 * cconj(sn[i])) * col[i] + cs[i] * col[i + 1];
-      col[i] = t;
-    }
-    const cd aa = col[c], bb = col[c + 1];
-    double cc;
-    cd sv;
-    if (bb.re == 0.0 && bb.im == 0.0) { cc = 1.0; sv = czero<double>(); }
-    else if (aa.re == 0.0 && aa.im == 0.0) { cc = 0.0; sv = mk<double>(1.0, 0.0); }
-    else {
-      const double na = sqrt(cabs2(aa)), rho = sqrt(cabs2(aa) + cabs2(bb));
-      cc = na / rho;
-      sv = (1.0 / (na * rho)) * (aa * cconj(bb));
-    }
-    col[c] = cc * col[c] + sv * col[c + 1];
-    cs[c] = cc;
-    sn[c] = sv;
-    g[c + 1] = (-1.0 * cconj(sv)) * g[c];
-    g[c] = cc * g[c];
-    for (int i = 0; i <= c; ++i) H[i][c] = col[i];
-    if (!(sqrt(cabs2(g[c + 1])) > tol * S.tol_scale * S.bnorm)) { jend = c + 1; break; }
-  }
   cd* yy = y + (size_t)rhs * a.m;
   for (int i = jend - 1; i >= 0; --i) {
-    cd t = g[i];
-    for (int k = i + 1; k < jend; ++k) t = t - H[i][k] * yy[k];
-    const cd d = H[i][i];
+    cd t = gsv[i];
+    for (int k = i + 1; k < jend; ++k) t = t - Hs[i][k] * yy[k];
+    const cd d = Hs[i][i];
     const double den = cabs2(d);
     yy[i] = den > 0.0 ? t * mk<double>(d.re / den, -d.im / den) : czero<double>();
   }
@@ -1365,7 +1399,7 @@ mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
   }
   {
     ProfScope ps(h, P_REDUCE);
-    k_ss_lsq<NV><<<B, 64, 0, h.stream>>>(a, h.partial, h.y, h.st, h.p.tol, h.p.maxit);
+    k_ss_lsq<NV><<<B, 32, 0, h.stream>>>(a, h.partial, h.y, h.st, h.p.tol, h.p.maxit);
     MGH_CHECK_LAUNCH(); h.launches++;
   }
   return df_xupdate(h, a, B);
