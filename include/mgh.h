@@ -336,6 +336,10 @@ typedef struct {
                                by level kernels); -1 = the automatic choice (the finest level whose
                                fields fit one block's shared memory); a level whose fields do not
                                fit returns MGH_INVALID_ARG */
+  int tail_cluster;         /* blocks per right-hand side of the coarse tail: 1 (one block), 2 or 4
+                               (a thread-block cluster over bands of rows, halo rows exchanged
+                               through distributed shared memory); 0 = 1; a count whose layout does
+                               not fit returns MGH_INVALID_ARG */
 } mgh_kernel_shape;
 
 /* Current launch shapes of a handle (tail_level reports the level in use, 0 if none). */

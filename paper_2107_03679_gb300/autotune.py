@@ -8,7 +8,7 @@ Two stages, both cached in a JSON file keyed by grid, batch, precision, level co
   spread-out sample of the illumination angles (CUDA events on the solver's stream); the pair with
   the least time per solve wins.
 * Launch shapes of the FP32 level kernels (mgh_set_kernel_shape): the wavefront segment length,
-  warps per block and ring depth, and the first level of the one-kernel coarse tail.  They do not
+  warps per block and ring depth, and the first level and cluster size of the one-kernel coarse tail.  They do not
   change results, only speed, so each candidate is timed on a fixed number of Arnoldi steps of the
   full batch (the launch configuration that will run), one axis at a time from the built-in choice,
   keeping a change only when it gains more than 2 %.
@@ -113,8 +113,8 @@ def _time_steps(solver: Solver, theta: torch.Tensor, reps: int = 3) -> float:
 def tune_shapes(w, f_d: torch.Tensor, theta: torch.Tensor, device: torch.device, precision: Optional[str] = None,
                 steps: int = 48, use_cache: bool = True, **solver_kw) -> Tuple[dict, list]:
     """Launch shapes of the level kernels for workload w's full batch theta, one axis at a time:
-    wavefront segment length (0 = the built-in model), warps per block, ring depth, first tail level.
-    Each candidate is timed on `steps` Arnoldi steps of forward solves (maxit = steps).  Returns
+    wavefront segment length (0 = the built-in model), warps per block, ring depth, first tail level,
+    blocks per right-hand side of the tail.  Each candidate is timed on `steps` Arnoldi steps of forward solves (maxit = steps).  Returns
     (shape, trials); shape also holds the time per step of the built-in choice and of the winner."""
     precision = precision or w.precision
     B = theta.numel()
@@ -141,7 +141,8 @@ def tune_shapes(w, f_d: torch.Tensor, theta: torch.Tensor, device: torch.device,
             for l in range(top)]
     axes += [("wave_warps", [(lambda sh, v=v: dict(sh, wave_warps=v)) for v in (2, 4)]),
              ("wave_ring", [(lambda sh, v=v: dict(sh, wave_ring=v)) for v in (1, 2)]),
-             ("tail_level", [(lambda sh, v=v: dict(sh, tail_level=v)) for v in (0, auto_tail, auto_tail + 1)])]
+             ("tail_level", [(lambda sh, v=v: dict(sh, tail_level=v)) for v in (0, auto_tail, auto_tail + 1)]),
+             ("tail_cluster", [(lambda sh, v=v: dict(sh, tail_cluster=v)) for v in (1, 2, 4)])]
     for _, moves in axes:
         for move in moves:
             cand = move(best)

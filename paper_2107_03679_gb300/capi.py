@@ -58,7 +58,7 @@ class mgh_profile(ctypes.Structure):
 
 class mgh_kernel_shape(ctypes.Structure):
     _fields_ = [("wave_seg", ctypes.c_int * MGH_MAX_LEVELS), ("wave_warps", ctypes.c_int), ("wave_ring", ctypes.c_int),
-                ("tail_level", ctypes.c_int)]
+                ("tail_level", ctypes.c_int), ("tail_cluster", ctypes.c_int)]
 
 
 class MGHError(RuntimeError):
@@ -313,14 +313,15 @@ def mgh_get_kernel_shape(h) -> dict:
     out = mgh_kernel_shape()
     _check("mgh_get_kernel_shape", _lib.mgh_get_kernel_shape(h, ctypes.byref(out)))
     return {"wave_seg": list(out.wave_seg), "wave_warps": out.wave_warps, "wave_ring": out.wave_ring,
-            "tail_level": out.tail_level}
+            "tail_level": out.tail_level, "tail_cluster": out.tail_cluster}
 
 
-def mgh_set_kernel_shape(h, wave_seg=0, wave_warps: int = 4, wave_ring: int = 1, tail_level: int = -1) -> None:
+def mgh_set_kernel_shape(h, wave_seg=0, wave_warps: int = 4, wave_ring: int = 1, tail_level: int = -1,
+                         tail_cluster: int = 1) -> None:
     """wave_seg: one length for every level, or a sequence of per-level lengths (0 = model)."""
     segs = [int(wave_seg)] * MGH_MAX_LEVELS if isinstance(wave_seg, int) else list(wave_seg)
     segs = (segs + [0] * MGH_MAX_LEVELS)[:MGH_MAX_LEVELS]
-    s = mgh_kernel_shape((ctypes.c_int * MGH_MAX_LEVELS)(*segs), wave_warps, wave_ring, tail_level)
+    s = mgh_kernel_shape((ctypes.c_int * MGH_MAX_LEVELS)(*segs), wave_warps, wave_ring, tail_level, tail_cluster)
     _check("mgh_set_kernel_shape", _lib.mgh_set_kernel_shape(h, ctypes.byref(s)))
 
 

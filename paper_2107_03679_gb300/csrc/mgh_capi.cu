@@ -356,6 +356,11 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   // MGH_TAIL=0 keeps every level on the level kernels
   h->tail_l0 = choose_tail_level(*h);
   if (const char* e = std::getenv("MGH_TAIL")) if (std::strcmp(e, "0") == 0) h->tail_l0 = 0;
+  // MGH_TAIL_CLUSTER=2|4 runs the tail over a cluster of that many blocks per right-hand side
+  if (const char* e = std::getenv("MGH_TAIL_CLUSTER")) {
+    const int c = std::atoi(e);
+    if (h->tail_l0 > 0 && tail_cluster_fits(*h, h->tail_l0, c)) h->tail_cluster = c;
+  }
   s = build_vcycle_tma(*h);
   if (s != MGH_OK) { free_handle(h); return s; }
   // start from f_d = 0 so that every later call finds a complete operator
@@ -548,6 +553,7 @@ mgh_status mgh_get_kernel_shape(const mgh_handle* h, mgh_kernel_shape* out) {
   out->wave_warps = h->wave_warps;
   out->wave_ring = h->wave_ring;
   out->tail_level = h->tail_l0;
+  out->tail_cluster = h->tail_cluster;
   return MGH_OK;
 }
 
@@ -559,12 +565,18 @@ mgh_status mgh_set_kernel_shape(mgh_handle* h, const mgh_kernel_shape* s) {
   if (s->wave_ring != 1 && s->wave_ring != 2) return MGH_INVALID_ARG;
   if (s->tail_level < -1 || s->tail_level > h->L - 2) return MGH_INVALID_ARG;
   if (s->tail_level > 0 && !tail_level_fits(*h, s->tail_level)) return MGH_INVALID_ARG;
+  if (s->tail_cluster != 0 && s->tail_cluster != 1 && s->tail_cluster != 2 && s->tail_cluster != 4)
+    return MGH_INVALID_ARG;
+  const int l0 = s->tail_level < 0 ? choose_tail_level(*h) : s->tail_level;
+  const int cl = s->tail_cluster == 0 ? 1 : s->tail_cluster;
+  if (cl > 1 && (l0 == 0 || !tail_cluster_fits(*h, l0, cl))) return MGH_INVALID_ARG;
   if (h->half && (s->wave_warps != 4 || s->wave_ring != 1)) return MGH_NOT_SUPPORTED;
   MGH_CUDA(cudaStreamSynchronize(h->stream));   // launches already queued keep their shapes
   for (int l = 0; l < kMaxLevels; ++l) h->wave_seg_level[l] = s->wave_seg[l];
   h->wave_warps = s->wave_warps;
   h->wave_ring = s->wave_ring;
-  h->tail_l0 = s->tail_level < 0 ? choose_tail_level(*h) : s->tail_level;
+  h->tail_l0 = l0;
+  h->tail_cluster = cl;
   return MGH_OK;
 }
 

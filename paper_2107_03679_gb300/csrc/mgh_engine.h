@@ -76,6 +76,7 @@ struct Handle {
   bool wave_lane_ring = true;  // rings filled per lane by cp.async (else by bulk copies)
   bool use_graphs = true;    // replay each restart cycle's launches from a captured CUDA graph
   int tail_l0 = 0;           // first level of the one-kernel coarse tail (0: every level by level kernels)
+  int tail_cluster = 1;      // blocks per right-hand side of the tail (1, 2 or 4: a thread-block cluster)
   cudaStream_t gstream = nullptr;  // non-blocking stream the cycle graphs are captured and replayed on
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;  // order gstream after / before `stream`
   size_t csize = 16;         // bytes per complex of the cycle precision
@@ -221,6 +222,7 @@ constexpr int kErrTimeout = 1;
 // (input lev[tail_l0].b, output lev[tail_l0].vfin; reps cycles of level tail_l0, the first from 0)
 int choose_tail_level(const Handle& h);
 bool tail_level_fits(const Handle& h, int l);   // level l's tail fields fit one block's shared memory
+bool tail_cluster_fits(const Handle& h, int l, int cl);   // the same for a tail over a cluster of cl blocks
 mgh_status launch_tail(Handle& h, int reps, int B, const RhsState* st, bool fp64);
 
 // mgh_inverse.cu: backward and momentum steps of the reconstruction loop (arguments checked by the caller)

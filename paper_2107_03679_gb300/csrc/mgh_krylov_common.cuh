@@ -64,7 +64,10 @@ __device__ __forceinline__ cd load_z(const Cx<TZ>* z, size_t q) { return ccast<d
 __device__ __forceinline__ void sum_partials(const KArgs& a, const cd* __restrict__ partial, int rhs, int nslots,
                                              cd* __restrict__ out_sh) {
   for (int s = threadIdx.x; s < nslots; s += blockDim.x) {
+    // the loads are independent: unrolled, they are in flight together while the adds keep
+    // the block order
     cd acc = czero<double>();
+#pragma unroll 8
     for (int b = 0; b < a.nblk; ++b) acc = acc + partial[((size_t)rhs * a.nblk + b) * a.pstride + s];
     out_sh[s] = acc;
   }

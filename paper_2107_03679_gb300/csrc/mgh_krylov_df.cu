@@ -1046,10 +1046,34 @@ __global__ void __launch_bounds__(32) k_ss_lsq(KArgs a, const cd* __restrict__ p
   const int rhs = blockIdx.x;
   if (!st[rhs].active) return;
   const int lane = threadIdx.x;
-  for (int t = lane; t < PR::NP; t += 32) {
-    cd acc = czero<double>();
-    for (int b = 0; b < a.nblk; ++b) acc = acc + partial[((size_t)rhs * a.nblk + b) * a.pstride + t];
-    Gs[t] = acc;
+  {
+    // the block sums of this right-hand side are contiguous rows of pstride entries: stage
+    // kLsqRows rows at a time with coalesced loads, then add each entry's rows in block order
+    constexpr int kLsqRows = 8;
+    __shared__ cd stage[kLsqRows * PR::NP];
+    constexpr int NT = (PR::NP + 31) / 32;
+    cd acc[NT];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) acc[u] = czero<double>();
+    const cd* base = partial + (size_t)rhs * a.nblk * a.pstride;
+    for (int b0 = 0; b0 < a.nblk; b0 += kLsqRows) {
+      const int nb = a.nblk - b0 < kLsqRows ? a.nblk - b0 : kLsqRows;
+      for (int e = lane; e < nb * PR::NP; e += 32) {
+        const int r = e / PR::NP, t = e - r * PR::NP;
+        stage[e] = base[(size_t)(b0 + r) * a.pstride + t];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < NT; ++u) {
+        const int t = lane + 32 * u;
+        if (t < PR::NP)
+          for (int r = 0; r < nb; ++r) acc[u] = acc[u] + stage[r * PR::NP + t];
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+      if (lane + 32 * u < PR::NP) Gs[lane + 32 * u] = acc[u];
   }
   __syncwarp();
   RhsState& S = st[rhs];

@@ -19,6 +19,8 @@
 // per visit of the level above it.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "mgh_engine.h"
 
 namespace mgh {
@@ -300,11 +302,364 @@ mgh_status launch_tail_t(Handle& h, int reps, int B, const RhsState* st) {
   return MGH_OK;
 }
 
+
+// ---------------------------------------------------------------- the tail over a cluster
+// The same cycle with each right-hand side split over a cluster of CL blocks by bands of rows:
+// block r of the cluster owns rows [r band_l, (r + 1) band_l) of level l, with band_l = 2 band_{l+1}
+// so that the rows a restriction or prolongation reads lie in the block's band or in the row just
+// above or below it.  Each field holds the band plus one halo row on each side (and the zero
+// column border); after every pass that writes a field whose vertical neighbours are read next,
+// the blocks meet at a cluster barrier and copy their halo rows from the neighbouring blocks'
+// shared memory.  The exact coarsest solve gathers the whole right-hand side from the cluster and
+// each block forms its own rows of v = K^{-1} b (each block reads 1/CL of the inverse).  Every
+// point and every row of the coarsest product is computed with the operations of k_tail, so the
+// results do not depend on CL.
+namespace cg = cooperative_groups;
+
+template <typename T>
+struct ClLevel {
+  const Cx<T>* D;      // diagonal of K_kappa on this level
+  const Cx<T>* wd;     // omega / D
+  int nx, ny, nu1, nu2;
+  int pitch;           // nx + 2
+  int band;            // rows per block (the last blocks may own fewer, or none)
+  int off_b, off_v, off_t;   // (band + 2) x pitch fields; off_t on the coarsest: the gathered b (nx * ny)
+  T inv_h2;
+};
+
+template <typename T>
+struct ClArgs {
+  ClLevel<T> lv[kMaxLevels];
+  int depth, gamma, reps, total, cl;
+  T om1;
+  const Cx<T>* b_in;
+  Cx<T>* v_out;
+  size_t stride;
+  const Cx<T>* kinv;
+  const RhsState* st;
+};
+
+// Rows [y0, y0 + rows) of a level owned by block `rank`.
+template <typename T>
+__device__ __forceinline__ void cl_rows(const ClLevel<T>& L, int rank, int& y0, int& rows) {
+  y0 = rank * L.band;
+  rows = L.ny - y0;
+  rows = rows < 0 ? 0 : (rows > L.band ? L.band : rows);
+}
+
+// The owned points of a level, TPB apart in row-major order: body(k, i, x, y) with k the plain
+// index of the level (coefficients), i the local bordered index, (x, y) the global point.
+template <int TPB, typename T, typename Body>
+__device__ __forceinline__ void cl_points(const ClLevel<T>& L, int y0, int rows, Body&& body) {
+  const int n = rows * L.nx;
+  const int dy = TPB / L.nx, dx = TPB - dy * L.nx;
+  int yl = threadIdx.x / L.nx, x = threadIdx.x - yl * L.nx;
+  for (int kl = threadIdx.x; kl < n; kl += TPB) {
+    body((y0 + yl) * L.nx + x, (yl + 1) * L.pitch + x + 1, x, y0 + yl);
+    x += dx;
+    yl += dy;
+    if (x >= L.nx) { x -= L.nx; ++yl; }
+  }
+}
+
+// Cluster barrier, then the halo rows of field `off` from the neighbouring blocks (rows outside
+// the grid stay 0), then a block barrier.
+template <typename T>
+__device__ void cl_halo(Cx<T>* sm, const ClLevel<T>& L, int off, int rank, int cl) {
+  cg::cluster_group cluster = cg::this_cluster();
+  cluster.sync();
+  int y0, rows;
+  cl_rows(L, rank, y0, rows);
+  if (rows > 0) {
+    if (rank > 0) {   // the block above owns a full band: its last row is local row band
+      const Cx<T>* src = cluster.map_shared_rank(sm + off, rank - 1) + (size_t)L.band * L.pitch;
+      for (int x = threadIdx.x; x < L.pitch; x += blockDim.x) sm[off + x] = src[x];
+    }
+    if (rank + 1 < cl && y0 + rows < L.ny) {   // first row of the block below: local row 1
+      const Cx<T>* src = cluster.map_shared_rank(sm + off, rank + 1) + L.pitch;
+      for (int x = threadIdx.x; x < L.pitch; x += blockDim.x) sm[off + (size_t)(rows + 1) * L.pitch + x] = src[x];
+    }
+  }
+  __syncthreads();
+}
+
+template <int TPB, typename T>
+__device__ int cl_smooth(Cx<T>* sm, const ClLevel<T>& L, int rank, int cl, int cur, int sweeps, bool zero, T om1) {
+  int y0, rows;
+  cl_rows(L, rank, y0, rows);
+  const Cx<T>* b = sm + L.off_b;
+  const Cx<T>* wd = L.wd;
+  const int P = L.pitch;
+  int s = 0;
+  if (zero) {
+    Cx<T>* v = sm + cur;
+    cl_points<TPB>(L, y0, rows, [&](int k, int i, int, int) { v[i] = sweeps > 0 ? wd[k] * b[i] : czero<T>(); });
+    cl_halo(sm, L, cur, rank, cl);
+    s = 1;
+  }
+  for (; s < sweeps; ++s) {
+    const Cx<T>* src = sm + cur;
+    const int nxt = cur == L.off_v ? L.off_t : L.off_v;
+    Cx<T>* dst = sm + nxt;
+    cl_points<TPB>(L, y0, rows, [&](int k, int i, int, int) {
+      const Cx<T> nb = src[i - 1] + src[i + 1] + src[i - P] + src[i + P];
+      const Cx<T> bk = b[i];
+      const Cx<T> t = mk<T>(bk.re + L.inv_h2 * nb.re, bk.im + L.inv_h2 * nb.im);
+      const Cx<T> c = src[i], w = wd[k];
+      dst[i] = mk<T>(om1 * c.re + w.re * t.re - w.im * t.im, om1 * c.im + w.re * t.im + w.im * t.re);
+    });
+    cl_halo(sm, L, nxt, rank, cl);
+    cur = nxt;
+  }
+  return cur;
+}
+
+template <int TPB, typename T>
+__device__ void cl_restrict(Cx<T>* sm, const ClLevel<T>& L, int rank, int cl, int cur, const ClLevel<T>& C) {
+  int y0, rows, cy0, crows;
+  cl_rows(L, rank, y0, rows);
+  cl_rows(C, rank, cy0, crows);
+  const Cx<T>* v = sm + cur;
+  const Cx<T>* b = sm + L.off_b;
+  const int roff = cur == L.off_v ? L.off_t : L.off_v;
+  Cx<T>* r = sm + roff;
+  const int P = L.pitch;
+  const Cx<T>* D = L.D;
+  cl_points<TPB>(L, y0, rows, [&](int k, int i, int, int) {
+    const Cx<T> s = v[i - 1] + v[i + 1] + v[i - P] + v[i + P];
+    const Cx<T> kv = D[k] * v[i] - L.inv_h2 * s;
+    r[i] = b[i] - kv;
+  });
+  cl_halo(sm, L, roff, rank, cl);
+  Cx<T>* bc = sm + C.off_b;
+  const T q16 = T(1) / T(16);
+  cl_points<TPB>(C, cy0, crows, [&](int, int ic, int ci, int cj) {
+    const int i = (2 * cj - y0 + 1) * P + 2 * ci + 1;   // fine point (2 ci, 2 cj), local row 2 cj - y0
+    const Cx<T> e = r[i - 1] + r[i + 1] + r[i - P] + r[i + P];
+    const Cx<T> c = r[i - P - 1] + r[i - P + 1] + r[i + P - 1] + r[i + P + 1];
+    const Cx<T> rc = r[i];
+    bc[ic] = mk<T>(q16 * (T(4) * rc.re + T(2) * e.re + c.re), q16 * (T(4) * rc.im + T(2) * e.im + c.im));
+  });
+  __syncthreads();
+}
+
+template <int TPB, typename T>
+__device__ void cl_prolong(Cx<T>* sm, const ClLevel<T>& L, int rank, int cl, int cur, const ClLevel<T>& C,
+                           int ccur) {
+  int y0, rows, cy0, crows;
+  cl_rows(L, rank, y0, rows);
+  cl_rows(C, rank, cy0, crows);
+  Cx<T>* v = sm + cur;
+  const Cx<T>* e = sm + ccur;
+  const int PC = C.pitch;
+  cl_points<TPB>(L, y0, rows, [&](int, int i, int x, int y) {
+    const int ic = ((y >> 1) - cy0 + 1) * PC + (x >> 1) + 1;
+    const bool ox = x & 1, oy = y & 1;
+    Cx<T> p;
+    if (!ox && !oy) {
+      p = e[ic];
+    } else if (ox && !oy) {
+      p = T(0.5) * (e[ic] + e[ic + 1]);
+    } else if (!ox && oy) {
+      p = T(0.5) * (e[ic] + e[ic + PC]);
+    } else {
+      p = T(0.25) * (e[ic] + e[ic + 1] + e[ic + PC] + e[ic + PC + 1]);
+    }
+    v[i] = v[i] + p;
+  });
+  cl_halo(sm, L, cur, rank, cl);
+}
+
+// Coarsest level: gather b from every block of the cluster into a plain copy, then this block's
+// rows of K^{-1} b, one warp per row (read from L2), lanes over columns, as in tail_coarsest.
+template <int TPB, typename T>
+__device__ void cl_coarsest(Cx<T>* sm, const ClLevel<T>& L, int rank, int cl, const Cx<T>* __restrict__ kinv) {
+  cg::cluster_group cluster = cg::this_cluster();
+  cluster.sync();
+  Cx<T>* bfull = sm + L.off_t;
+  const int n = L.nx * L.ny;
+  for (int k = threadIdx.x; k < n; k += TPB) {
+    const int y = k / L.nx, x = k - y * L.nx;
+    const int owner = y / L.band;
+    const Cx<T>* src = cluster.map_shared_rank(sm + L.off_b, owner);
+    bfull[k] = src[(y - owner * L.band + 1) * L.pitch + x + 1];
+  }
+  __syncthreads();
+  int y0, rows;
+  cl_rows(L, rank, y0, rows);
+  Cx<T>* v = sm + L.off_v;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = y0 * L.nx + warp; r < (y0 + rows) * L.nx; r += TPB / 32) {
+    const Cx<T>* row = kinv + (size_t)r * n;
+    T ar = 0, ai = 0;
+    for (int c = lane; c < n; c += 32) {
+      const Cx<T> k = row[c], x = bfull[c];
+      ar = fma(k.re, x.re, fma(-k.im, x.im, ar));
+      ai = fma(k.re, x.im, fma(k.im, x.re, ai));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) {
+      const int ry = r / L.nx, rx = r - ry * L.nx;
+      v[(ry - y0 + 1) * L.pitch + rx + 1] = mk<T>(ar, ai);
+    }
+  }
+  cl_halo(sm, L, L.off_v, rank, cl);
+}
+
+template <int TPB, typename T>
+__global__ void __launch_bounds__(TPB, 1) k_tail_cl(const ClArgs<T> a) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int rhs = blockIdx.x / a.cl;
+  // the state is read before any barrier: every block of a cluster takes the same branch
+  if (a.st && !a.st[rhs].active) return;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  Cx<T>* sm = reinterpret_cast<Cx<T>*>(tail_smem);
+  for (int k = threadIdx.x; k < a.total; k += TPB) sm[k] = czero<T>();
+  const ClLevel<T>& top = a.lv[0];
+  int ty0, trows;
+  cl_rows(top, rank, ty0, trows);
+  __syncthreads();
+  const int last = a.depth - 1;
+  {
+    const Cx<T>* bin = a.b_in + rhs * a.stride;
+    Cx<T>* b0 = sm + top.off_b;
+    cl_points<TPB>(top, ty0, trows, [&](int k, int i, int, int) { b0[i] = bin[k]; });
+  }
+  __syncthreads();
+  int cnt[kMaxLevels];
+  bool zero[kMaxLevels];
+  int cur[kMaxLevels];
+  for (int d = 0; d < a.depth; ++d) cur[d] = a.lv[d].off_v;
+  for (int rep = 0; rep < a.reps; ++rep) {
+    int d = 0;
+    bool down = true;
+    zero[0] = rep == 0;
+    while (true) {
+      if (down) {
+        if (d == last) {
+          cl_coarsest<TPB>(sm, a.lv[d], rank, a.cl, a.kinv);
+          cur[d] = a.lv[d].off_v;
+          --d;
+          down = false;
+          cnt[d] = a.gamma - 1;
+          continue;
+        }
+        cur[d] = cl_smooth<TPB>(sm, a.lv[d], rank, a.cl, cur[d], a.lv[d].nu1, zero[d], a.om1);
+        cl_restrict<TPB>(sm, a.lv[d], rank, a.cl, cur[d], a.lv[d + 1]);
+        cnt[d] = 0;
+        zero[d + 1] = true;
+        ++d;
+        continue;
+      }
+      if (++cnt[d] < a.gamma) {
+        zero[d + 1] = false;
+        ++d;
+        down = true;
+        continue;
+      }
+      cl_prolong<TPB>(sm, a.lv[d], rank, a.cl, cur[d], a.lv[d + 1], cur[d + 1]);
+      cur[d] = cl_smooth<TPB>(sm, a.lv[d], rank, a.cl, cur[d], a.lv[d].nu2, false, a.om1);
+      if (d == 0) break;
+      --d;
+    }
+  }
+  Cx<T>* vo = a.v_out + rhs * a.stride;
+  const Cx<T>* v0 = sm + cur[0];
+  cl_points<TPB>(top, ty0, trows, [&](int k, int i, int, int) { vo[k] = v0[i]; });
+  cluster.sync();   // no block leaves while another may still read its shared memory
+}
+
+// Shared-memory layout of one block of a CL-block tail from level l0 (element offsets; returns the
+// total), with band_l = 2^(L-1-l) ceil(ny_{L-1} / CL).
+template <typename T>
+int cl_layout(const Handle& h, int l0, int cl, ClLevel<T>* lv) {
+  const int last = h.L - 1;
+  const int bc = (h.lev[last].ny + cl - 1) / cl;
+  int off = 0;
+  for (int l = l0; l < h.L; ++l) {
+    const Level& L = h.lev[l];
+    ClLevel<T> t{};
+    t.nx = L.nx; t.ny = L.ny; t.pitch = L.nx + 2;
+    t.band = bc << (last - l);
+    const int ps = (t.band + 2) * t.pitch;
+    t.off_b = off; off += ps;
+    t.off_v = off; off += ps;
+    t.off_t = off; off += l + 1 < h.L ? ps : (int)L.n();
+    if (lv) lv[l - l0] = t;
+  }
+  return off;
+}
+
+template <typename T>
+size_t cl_smem_bytes(const Handle& h, int l0, int cl) {
+  return (size_t)cl_layout<T>(h, l0, cl, nullptr) * sizeof(Cx<T>);
+}
+
+template <typename T>
+mgh_status launch_tail_cl(Handle& h, int reps, int B, const RhsState* st) {
+  const int l0 = h.tail_l0, cl = h.tail_cluster;
+  ClArgs<T> a{};
+  a.total = cl_layout<T>(h, l0, cl, a.lv);
+  for (int l = l0; l < h.L; ++l) {
+    const Level& lv = h.lev[l];
+    ClLevel<T>& t = a.lv[l - l0];
+    t.D = (const Cx<T>*)lv.D;
+    t.wd = (const Cx<T>*)lv.wDinv;
+    t.nu1 = nu_pre(h, l); t.nu2 = nu_post(h, l);
+    t.inv_h2 = static_cast<T>(1.0 / (lv.h * lv.h));
+  }
+  a.depth = h.L - l0;
+  a.gamma = cycle_gamma(h);
+  a.reps = reps;
+  a.cl = cl;
+  a.om1 = static_cast<T>(1.0 - h.p.omega);
+  a.b_in = (const Cx<T>*)h.lev[l0].b;
+  a.v_out = (Cx<T>*)h.lev[l0].vfin;
+  a.stride = h.lev[l0].n();
+  a.kinv = sizeof(T) == 8 ? (const Cx<T>*)(const void*)h.kinv64r : (const Cx<T>*)(const void*)h.kinv32;
+  a.st = st;
+  const size_t smem = (size_t)a.total * sizeof(Cx<T>);
+  constexpr int kTpb2 = 1024, kTpb4 = 512;
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(k_tail_cl<kTpb2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTailSmemMax));
+           MGH_CUDA(cudaFuncSetAttribute(k_tail_cl<kTpb4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTailSmemMax)););
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(B * cl), 1, 1);
+  cfg.blockDim = dim3(cl == 2 ? kTpb2 : kTpb4, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ProfScope ps(h, P_COARSE);
+  if (cl == 2) MGH_CUDA(cudaLaunchKernelEx(&cfg, k_tail_cl<kTpb2, T>, a));
+  else MGH_CUDA(cudaLaunchKernelEx(&cfg, k_tail_cl<kTpb4, T>, a));
+  h.launches++;
+  return MGH_OK;
+}
+
 }  // namespace
 
 bool tail_level_fits(const Handle& h, int l) {
   if (l < 1 || l + 2 > h.L) return false;
   const size_t bytes = h.fp64 ? tail_smem_bytes<double>(h, l) : tail_smem_bytes<float>(h, l);
+  return bytes <= kTailSmemMax;
+}
+
+bool tail_cluster_fits(const Handle& h, int l, int cl) {
+  if (cl == 1) return tail_level_fits(h, l);
+  if ((cl != 2 && cl != 4) || l < 1 || l + 2 > h.L || h.lev[h.L - 1].ny < cl) return false;
+  const size_t bytes = h.fp64 ? cl_smem_bytes<double>(h, l, cl) : cl_smem_bytes<float>(h, l, cl);
   return bytes <= kTailSmemMax;
 }
 
@@ -317,6 +672,8 @@ int choose_tail_level(const Handle& h) {
 }
 
 mgh_status launch_tail(Handle& h, int reps, int B, const RhsState* st, bool fp64) {
+  if (h.tail_cluster > 1)
+    return fp64 ? launch_tail_cl<double>(h, reps, B, st) : launch_tail_cl<float>(h, reps, B, st);
   return fp64 ? launch_tail_t<double>(h, reps, B, st) : launch_tail_t<float>(h, reps, B, st);
 }
 

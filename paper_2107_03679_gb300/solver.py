@@ -293,7 +293,8 @@ class Solver:
         return capi.mgh_launch_count(self._h, reset)
 
     def kernel_shape(self) -> dict:
-        """Launch shapes of the FP32 level kernels (wave_seg, wave_warps, wave_ring, tail_level)."""
+        """Launch shapes of the FP32 level kernels (wave_seg, wave_warps, wave_ring, tail_level,
+        tail_cluster)."""
         return capi.mgh_get_kernel_shape(self._h)
 
     def set_kernel_shape(self, **shape) -> None:

@@ -2,7 +2,8 @@
 
 A shape changes the schedule, never the arithmetic of a point: the wavefront kernels recompute
 their halo rows with the same operations whatever the segment length, warps per block or ring
-depth, so the solve is bit-identical.  Moving the first level of the one-kernel coarse tail swaps
+depth, so the solve is bit-identical; so does splitting the coarse tail of a right-hand side over a
+cluster of blocks.  Moving the first level of the one-kernel coarse tail swaps
 level kernels for the tail kernel on some levels (same cycle, other rounding order), so the solve
 still meets the direct solution within the mixed tolerance."""
 import numpy as np
@@ -33,7 +34,8 @@ def test_kernel_shapes_leave_the_solve_unchanged():
     assert base["wave_seg"] == [0] * 12 and base["wave_warps"] == 4 and base["wave_ring"] == 1 and base["tail_level"] >= 1
     x0, inf0 = s.solve(torch.from_numpy(b).cuda())
     x0 = x0.cpu().numpy()
-    for shape in (dict(wave_seg=16), dict(wave_seg=[64, 24, 8], wave_warps=2), dict(wave_ring=2), dict(wave_seg=6)):
+    for shape in (dict(wave_seg=16), dict(wave_seg=[64, 24, 8], wave_warps=2), dict(wave_ring=2), dict(wave_seg=6),
+                  dict(tail_cluster=2), dict(tail_cluster=4)):
         s.set_kernel_shape(**dict(base, **shape))
         x, inf = s.solve(torch.from_numpy(b).cuda())
         np.testing.assert_array_equal(x.cpu().numpy(), x0)
@@ -44,7 +46,8 @@ def test_kernel_shapes_leave_the_solve_unchanged():
         x, inf = s.solve(torch.from_numpy(b).cuda())
         for q in range(3):
             assert inf[q]["converged"] and rel(x.cpu().numpy()[q], O.direct_solve(p, o.D, b[q])) < 1e-5
-    for bad in (dict(wave_warps=3), dict(wave_ring=3), dict(tail_level=3), dict(wave_seg=[0, -1])):
+    for bad in (dict(wave_warps=3), dict(wave_ring=3), dict(tail_level=3), dict(wave_seg=[0, -1]), dict(tail_cluster=3),
+                dict(tail_level=0, tail_cluster=2)):
         with pytest.raises(capi.MGHError):
             s.set_kernel_shape(**dict(base, **bad))
     s.close()

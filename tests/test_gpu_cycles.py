@@ -125,3 +125,28 @@ def test_one_kernel_coarse_tail_matches_level_kernels(precision, gamma, bound, m
     for q in range(3):
         assert rel(z["1"][q], z["0"][q]) < bound
         assert rel(z["1"][q], o.M(b[q])) < (1e-12 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed32"])
+@pytest.mark.parametrize("levels,gamma", [(4, 1), (4, 2), (5, 1)])
+def test_cluster_tail_equals_the_one_block_tail_bit_for_bit(precision, levels, gamma):
+    """The coarse tail split over a cluster of 2 or 4 blocks per right-hand side (bands of rows, halo
+    rows through distributed shared memory, each block forming its rows of the coarsest product)
+    computes every point with the one-block tail's operations.  On this grid the fourth block of a
+    4-block cluster owns no row of the tail's finest level, and with 4 levels none of the lower
+    levels either."""
+    torch = torch_cuda()
+    w = ragged(levels=levels, precision=precision)
+    p = O.Problem.from_workload(w)
+    f = W.phantom(w)
+    b = W.random_field((3, p.ny, p.nx), 16)
+    s = make_solver(w, B=3, cycle_type=gamma)
+    s.set_contrast(to_t(f, torch))
+    base = s.kernel_shape()
+    assert base["tail_level"] >= 1 and base["tail_cluster"] == 1
+    z1 = s.precondition(to_t(b, torch)).cpu().numpy()
+    for cl in (2, 4):
+        s.set_kernel_shape(**dict(base, tail_cluster=cl))
+        assert s.kernel_shape()["tail_cluster"] == cl
+        np.testing.assert_array_equal(s.precondition(to_t(b, torch)).cpu().numpy(), z1)
+    s.close()
