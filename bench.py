@@ -105,12 +105,16 @@ def make_inputs(w):
 # bytes read once per launch whatever the batch); see profiles/vcycle_post_l0_ellipses576.md and
 # profiles/gram_sstep_ellipses576.md.  Traffic grows with the right-hand sides (independent sweeps).
 NCU_TRAFFIC_24 = {"vcycle_post_l0": (215.5e6, 2.65e6), "gs_update": (577.4e6, 0.0)}
+POST_CAPTURE_FUSED = False   # whether the captured level-0 post kernel formed the s-step product itself
 
 
-def captured_traffic(cls: str, w, precision: str, B: int, shape=None):
-    """Scaled capture for this launch, or None when no capture matches (another workload, or launch
-    shapes other than the captured built-in ones: 4 warps per block, ring of one period)."""
+def captured_traffic(cls: str, w, precision: str, B: int, shape=None, fused=True):
+    """Scaled capture for this launch, or None when no capture matches (another workload, launch
+    shapes other than the captured built-in ones: 4 warps per block, ring of one period, or a
+    level-0 post kernel with or without the fused operator product unlike the captured one)."""
     if (w.nx, w.levels, w.nu1, w.nu2, w.restart, precision) != (576, 6, 2, 2, 8, "mixed32") or cls not in NCU_TRAFFIC_24:
+        return None
+    if cls == "vcycle_post_l0" and fused != POST_CAPTURE_FUSED:
         return None
     if shape and (shape.get("wave_warps", 4) != 4 or shape.get("wave_ring", 1) != 1 or any(shape.get("wave_seg", []))):
         return None
@@ -222,19 +226,24 @@ def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, 
     if engine == "sstep":
         # s-step cycles: every step of a cycle runs (cycle_steps), one Gram sweep per cycle
         run = prof["cycle_steps"]
-        return {
+        out = {
             # levels 1 .. L-2: pre reads b, writes v and the restricted residual; post reads b, v and
             # the coarse correction, writes the result
             "vcycle_coarse": run * N * cfrac * cs * (3.25 + 3.25),
             "vcycle_pre_l0": run * N * (8 + zs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
             "vcycle_post_l0": run * N * (8 + 2 * zs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
-            # v_{k+1} = A z_k in FP32: read z_k, write v_{k+1}; D_A (FP32) per launch
-            "matvec_dots": run * N * (zs + cs) + launches["matvec_dots"] * cs * N,
             # Gram sweep: read the m + 1 FP32 basis vectors
             "gs_update": prof["gram_reads"] * N * cs,
             "true_residual": prof["residuals"] * N * 3 * c16,
             "x_update": prof["updates"] * N * 2 * c16 + prof["update_reads"] * N * zs,
         }
+        if launches.get("matvec_dots", 0) > 0:
+            # v_{k+1} = A z_k in FP32: read z_k, write v_{k+1}; D_A (FP32) per launch
+            out["matvec_dots"] = run * N * (zs + cs) + launches["matvec_dots"] * cs * N
+        else:
+            # the product fused into the post kernel: it also writes v_{k+1}; D_A per launch
+            out["vcycle_post_l0"] += run * N * cs + launches["vcycle_post_l0"] * cs * N
+        return out
     if engine == "df":
         # double-float Arnoldi (mixed path): the V-cycle reads the 8-byte hi plane of u_j
         return {
@@ -719,7 +728,9 @@ def gpu_main(args, rank, world, local_rank):
         # launch) and the measured copy bandwidth
         achieved = alg[dom] / (ms_cls[dom] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": captured_traffic(dom, w, precision, B, (tuned or {}).get("shape")),
+                "frac": round(achieved / peak, 4),
+                "traffic": captured_traffic(dom, w, precision, B, (tuned or {}).get("shape"),
+                                            fused=prof["launches"].get("matvec_dots", 0) == 0),
                 "peak_kind": peak_kind, "bytes_per_launch": round(alg[dom] / n_l)}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,

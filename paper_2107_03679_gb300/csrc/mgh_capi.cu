@@ -79,6 +79,9 @@ size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Complex words of one right-hand side's deflated-restart data: C m x k, Hh (k+1) x k, R k x k,
 // the k Givens cosines (real parts) and sines.
+// Strips of at least 48 columns across a row: bounds the strips of every fused post launch.
+size_t npart_strips(int nx) { return (size_t)(nx + 47) / 48; }
+
 size_t dr_words(int m, int k) { return (size_t)m * k + (size_t)(k + 1) * k + (size_t)k * k + 2 * (size_t)k; }
 
 // Bytes of every device allocation of a handle, in allocation order.
@@ -107,6 +110,7 @@ size_t workspace_bytes(const mgh_params& p) {
   t += pad256(16 * Np) + pad256(16 * B * (m + 1)) + pad256(16 * B * 2 * m) + pad256(4);   // DAdf, hpend, coef, err
   t += pad256(56 * (size_t)p.nx_int * p.ny_int);                                          // tvbuf
   if (p.precision != MGH_PREC_FP64) t += 2 * pad256(16 * B * Np);                        // xdf, bdf
+  if (p.precision != MGH_PREC_FP64) t += pad256(4 * B * (size_t)nyl[0] * npart_strips(nxl[0]));   // npart
   if (p.deflate > 0)                                                                       // Hraw, drbuf, dr_mode
     t += pad256(16 * B * m * (m + 1)) + pad256(16 * B * dr_words(p.restart, p.deflate)) + pad256(4 * B) +
          pad256(16 * B * (m + 1));
@@ -139,7 +143,7 @@ void free_handle(mgh_handle* h) {
   cudaFree(h->hs_y); cudaFree(h->hs_r);
   cudaFree(h->dscratch); cudaFree(h->DAdf); cudaFree(h->hpend); cudaFree(h->coef);
   cudaFree(h->dev_err); cudaFree(h->xdf); cudaFree(h->bdf); cudaFree(h->tvbuf);
-  cudaFree(h->Hraw); cudaFree(h->drbuf); cudaFree(h->dr_mode); cudaFree(h->g0);
+  cudaFree(h->Hraw); cudaFree(h->drbuf); cudaFree(h->dr_mode); cudaFree(h->g0); cudaFree(h->npart);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->dr_hraw_host) cudaFreeHost(h->dr_hraw_host);
   if (h->dr_host) cudaFreeHost(h->dr_host);
@@ -307,6 +311,7 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   ALLOC(h->coef, 16 * B * 2 * m);
   ALLOC(h->dscratch, 8 * (B + 1));
   ALLOC(h->tvbuf, 56 * (size_t)p->nx_int * p->ny_int);
+  if (!h->fp64) ALLOC(h->npart, 4 * B * (size_t)h->ny * npart_strips(h->nx));
   if (p->deflate > 0) {
     ALLOC(h->Hraw, 16 * B * m * (m + 1));
     ALLOC(h->drbuf, 16 * B * dr_words(p->restart, p->deflate));
@@ -356,6 +361,8 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   // MGH_TAIL=0 keeps every level on the level kernels
   h->tail_l0 = choose_tail_level(*h);
   if (const char* e = std::getenv("MGH_TAIL")) if (std::strcmp(e, "0") == 0) h->tail_l0 = 0;
+  // MGH_FUSE_MATVEC=0 keeps the s-step operator product in its own kernel
+  if (const char* e = std::getenv("MGH_FUSE_MATVEC")) if (std::strcmp(e, "0") == 0) h->fuse_ok = false;
   // MGH_TAIL_CLUSTER=2|4 runs the tail over a cluster of that many blocks per right-hand side
   if (const char* e = std::getenv("MGH_TAIL_CLUSTER")) {
     const int c = std::atoi(e);

@@ -77,6 +77,13 @@ struct Handle {
   bool use_graphs = true;    // replay each restart cycle's launches from a captured CUDA graph
   int tail_l0 = 0;           // first level of the one-kernel coarse tail (0: every level by level kernels)
   int tail_cluster = 1;      // blocks per right-hand side of the tail (1, 2 or 4: a thread-block cluster)
+  // operator product of the s-step basis fused into the level-0 post kernel: the engine sets
+  // fuse_v around one cycle; the post kernel launcher fuses when it can and reports its strips
+  cf* fuse_v = nullptr;      // FP32 basis slot k+1 (hi plane) of right-hand side 0
+  size_t fuse_vstride = 0;   // elements between right-hand sides
+  int fuse_nstrips = 0;      // strips of the fused launch (0: not fused)
+  bool fuse_ok = true;       // fusion allowed (MGH_FUSE_MATVEC=0 turns it off)
+  float* npart = nullptr;    // [Bmax][ny][strips] norm partials of the fused product
   cudaStream_t gstream = nullptr;  // non-blocking stream the cycle graphs are captured and replayed on
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;  // order gstream after / before `stream`
   size_t csize = 16;         // bytes per complex of the cycle precision

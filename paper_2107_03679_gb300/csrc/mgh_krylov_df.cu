@@ -918,6 +918,27 @@ __global__ void k_ss_norm(KArgs a, int k, const cd* __restrict__ partial, double
   if (threadIdx.x == 0) vscale[(size_t)rhs * (a.m + 1) + k + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
 }
 
+// ||v_{k+1}||^2 from the per-(row pair, strip) partials of the level-0 post kernel that formed
+// v_{k+1} = A z_k itself: one block per right-hand side, FP64 sums in a fixed order.
+__global__ void __launch_bounds__(1024) k_ss_norm_rows(KArgs a, int k, const float* __restrict__ npart, int per_rhs,
+                                                      double* __restrict__ vscale, const RhsState* __restrict__ st) {
+  const int rhs = blockIdx.x;
+  if (!st[rhs].active) return;
+  const float* p = npart + (size_t)rhs * per_rhs;
+  double n2 = 0.0;
+#pragma unroll 4
+  for (int t = threadIdx.x; t < per_rhs; t += 1024) n2 += (double)p[t];
+  n2 = warp_sum(n2);
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = n2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 32; ++w) s += sh[w];
+    vscale[(size_t)rhs * (a.m + 1) + k + 1] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+  }
+}
+
 // The Gram sums of one tile's points for the pairs of thread group G, accumulated by FP32 FMAs
 // into the thread's running sums `run` (re, im per pair); k_ss_gram adds the running sums into
 // double-float totals every kGramRunTiles tiles.
@@ -1396,8 +1417,24 @@ mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
     // iterate unchanged, since v_{k+1} = A z_k is formed from the stored z_k
     __half2* zh = reinterpret_cast<__half2*>(h.Z) + (size_t)k * a.N;
     cf* zk = h.half ? reinterpret_cast<cf*>(zh) : (cf*)h.Z + (size_t)k * a.N;
-    MGH_TRY(vcycle_f32in(h, vhi, (size_t)(a.m + 1) * 2 * a.Np, h.vscale + k, (size_t)(a.m + 1), zk,
-                         (size_t)a.m * a.N, B, h.st, k));
+    // v_{k+1} = A z_k: fused into the level-0 post kernel when its launch path allows it
+    h.fuse_v = reinterpret_cast<cf*>(V + (size_t)(k + 1) * 2 * a.Np);
+    h.fuse_vstride = (size_t)(a.m + 1) * 2 * a.Np;
+    h.fuse_nstrips = 0;
+    const mgh_status vs = vcycle_f32in(h, vhi, (size_t)(a.m + 1) * 2 * a.Np, h.vscale + k, (size_t)(a.m + 1), zk,
+                                       (size_t)a.m * a.N, B, h.st, k);
+    const int fused = h.fuse_nstrips;
+    h.fuse_v = nullptr;
+    h.fuse_nstrips = 0;
+    MGH_TRY(vs);
+    if (fused > 0) {
+      if (k + 1 < a.m) {
+        ProfScope ps(h, P_REDUCE);
+        k_ss_norm_rows<<<B, 1024, 0, h.stream>>>(a, k, h.npart, ((a.ny + 1) / 2) * fused, h.vscale, h.st);
+        MGH_CHECK_LAUNCH(); h.launches++;
+      }
+      continue;
+    }
     {
       ProfScope ps(h, P_MATVEC_DOTS);
       if (h.half)

@@ -986,6 +986,30 @@ mgh_status post_lane_go(Handle& h, int l, const cf* bin, size_t b_stride, const 
   return MGH_OK;
 }
 
+// Level-0 post kernel with the s-step operator product fused (k_post_waf): v_{k+1} = A z_k into
+// h.fuse_v and per-(row, strip) norm partials into h.npart.
+template <int NU, int NW, int MS, typename VT = cf>
+mgh_status post_lane_fgo(Handle& h, int l, const cf* bin, size_t b_stride, const double* bscale,
+                         size_t scale_stride, cf* out, size_t out_stride, int B, const RhsState* st, int nstrips,
+                         int nwarps, int seg) {
+  const Level& lv = h.lev[l];
+  const Level& cl = h.lev[l + 1];
+  auto kern = wave::k_post_waf<NU, NW, MS, VT, VT>;
+  constexpr int S = wave::RingLen<wave::PostWF<NU, 1>::P, NU, MS>::S;
+  constexpr size_t smem = wave::LaneRingSmem<NW, S>::bytes();
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)););
+  const dim3 grid((nwarps + NW - 1) / NW, 1, B);
+  const float smul = std::is_same<VT, cf>::value ? 1.f : h.zmul;
+  const float ih = (float)(1.0 / (lv.h * lv.h));
+  kern<<<grid, 32 * NW, smem, h.stream>>>(bin, b_stride, bscale, scale_stride, (const cf*)lv.wDinv,
+                                          (const VT*)lv.vpre, lv.n(), (const cf*)cl.vfin, cl.n(), cl.nx, cl.ny,
+                                          reinterpret_cast<VT*>(out), out_stride, lv.nx, lv.ny, ih,
+                                          (float)(1.0 - h.p.omega), nstrips, nwarps, seg, st, smul,
+                                          reinterpret_cast<const cf*>(h.DAdf), ih, h.fuse_v, h.fuse_vstride,
+                                          h.npart);
+  return MGH_OK;
+}
+
 // Ring variants: ring length multiplier (1 or 2 unroll periods) and warps per block.
 #define MGH_RING_DISPATCH(GO, NU, MS, NW, ...)                                                   \
   ((MS) >= 2 ? ((NW) == 2 ? GO<NU, 2, 2>(__VA_ARGS__) : GO<NU, 4, 2>(__VA_ARGS__))            \
@@ -1068,6 +1092,31 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
                                          (int)smem1)););
   static std::atomic<long> resident_by_dev[64];
   const long resident = resident_cached(resident_by_dev, h, wave::k_post_wa<NU, 4, 1>, 128, smem1);
+  if (l == 0 && h.fuse_v && h.fuse_ok && ring && h.wave_lane_ring && a16(h.DAdf) && a16(h.fuse_v) &&
+      h.fuse_vstride % 2 == 0) {
+    // the s-step operator product fused in: one more halo column per side and row above and below
+    using GF = wave::PostWF<NU, 1>;
+    const int nstrips_f = (lv.nx + GF::XO - 1) / GF::XO;
+    constexpr int SF = wave::RingLen<GF::P, NU, 1>::S;
+    constexpr size_t smemf = wave::LaneRingSmem<4, SF>::bytes();
+    MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(wave::k_post_waf<NU, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smemf)););
+    static std::atomic<long> resident_f_by_dev[64];
+    const long resident_f = resident_cached(resident_f_by_dev, h, wave::k_post_waf<NU, 4, 1>, 128, smemf);
+    const int periodf = h.wave_ring >= 2 ? wave::RingLen<GF::P, NU, 2>::S : SF;
+    const int segf = wave_seg(h, l, lv.ny, nstrips_f, B, 2 * NU + 2, periodf, resident_f);
+    const int nwarps_f = nstrips_f * ((lv.ny + segf - 1) / segf);
+    ProfScope ps(h, P_POST0);
+    if (h.half)
+      MGH_TRY((post_lane_fgo<NU, 4, 1, __half2>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st,
+                                                nstrips_f, nwarps_f, segf)));
+    else
+      MGH_TRY(MGH_RING_DISPATCH(post_lane_fgo, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,
+                                scale_stride, out, out_stride, B, st, nstrips_f, nwarps_f, segf));
+    MGH_CHECK_LAUNCH(); h.launches++;
+    h.fuse_nstrips = nstrips_f;
+    return MGH_OK;
+  }
   const int seg = wave_seg(h, l, lv.ny, nstrips, B, 2 * NU, period, resident);
   const int nwarps = nstrips * ((lv.ny + seg - 1) / seg);
   ProfScope ps(h, l == 0 ? P_POST0 : P_COARSE);

@@ -1026,5 +1026,171 @@ k_post_wa(const cf* __restrict__ bin, size_t b_stride, const double* __restrict_
   cp_wait<0>();
 }
 
+
+// Geometry of the post kernel with the fused operator product (k_post_waf): the product A z is one
+// more stencil stage that reads across the strip edge, and it needs z one row above and below the
+// segment.
+template <int NU, int PF>
+struct PostWF {
+  static constexpr int H = NU + 1, HX = (NU + 2) & ~1, XO = 64 - 2 * HX;
+  static constexpr int R = NU + 1 > 3 ? NU + 1 : 3;
+  static constexpr int P = lcm_c(lcm_c(R, 2), PF);
+};
+
+// k_post_wa followed, one row behind its last sweep, by the operator product of the s-step basis:
+// w = A z on the stored z (FP32, or the FP16-rounded values under FP16 storage), written as the
+// FP32 basis vector v_{k+1} (vout), with the same operations as k_ss_matvec2, and the sum of
+// |w|^2 over the strip's owned points of each row pair (2i, 2i + 1) in
+// npart[(rhs * ceil(ny / 2) + i) * nstrips + strip] (FP32; a fixed warp butterfly, so the partials
+// do not depend on the segment length or warps per block).
+// DA32: the FP32 diagonal of A (complex, row-major like the level).
+template <int NU, int NW, int MS, typename VT = cf, typename OT = cf>
+__global__ void __launch_bounds__(32 * NW)
+k_post_waf(const cf* __restrict__ bin, size_t b_stride, const double* __restrict__ bscale, size_t scale_stride,
+           const cf* __restrict__ wD, const VT* __restrict__ vpre, size_t v_stride, const cf* __restrict__ ec,
+           size_t ec_stride, int nxc, int nyc, OT* __restrict__ out, size_t out_stride, int nx, int ny, float ih,
+           float om1, int nstrips, int nwarps, int seg, const RhsState* __restrict__ st, float smul,
+           const cf* __restrict__ DA32, float ih0, cf* __restrict__ vout, size_t vout_stride,
+           float* __restrict__ npart) {
+  static_assert(NU >= 1, "the wavefront post kernel ends with a sweep");
+  using G = PostWF<NU, 1>;
+  constexpr int HX = G::HX, XO = G::XO, R = G::R;
+  constexpr int S = RingLen<G::P, NU, MS>::S;
+  constexpr int PFD = S - NU - 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int rhs = blockIdx.z;
+  if (st && !st[rhs].active) return;
+  const int w = blockIdx.x * NW + (threadIdx.x >> 5);
+  if (w >= nwarps) return;
+  const int lane = threadIdx.x & 31;
+  const int strip = w % nstrips;
+  const int xs = strip * XO, ys = (w / nstrips) * seg;
+  const int g0 = xs - HX + 2 * lane;
+  const bool in0 = g0 >= 0 && g0 < nx, in1 = g0 + 1 >= 0 && g0 + 1 < nx;
+  const bool own = lane >= HX / 2 && lane < HX / 2 + XO / 2;
+  const int ci = g0 >> 1;
+  const bool okc0 = ci >= 0 && ci < nxc, okc1 = ci + 1 >= 0 && ci + 1 < nxc;
+  const float sc = smul * (bscale ? (float)bscale[rhs * scale_stride] : 1.f);
+  const cf* __restrict__ bb = bin + rhs * b_stride;
+  const VT* __restrict__ vp = vpre + rhs * v_stride;
+  const cf* __restrict__ eb = ec + rhs * ec_stride;
+  OT* __restrict__ o = out + rhs * out_stride;
+  cf* __restrict__ vo = vout + rhs * vout_stride;
+  float* __restrict__ np = npart + (size_t)rhs * ((ny + 1) >> 1) * nstrips + strip;
+  float nrm_even = 0.f;   // |w|^2 of the even row of the current row pair
+  const int i0 = ys - NU - 1;
+  const int rows = ny - ys < seg ? ny - ys : seg;
+  const int K = (rows + 2 * NU + 2 + S - 1) / S * S;
+  const LaneRing g = lane_ring_begin<NW, S>(smem_raw, nx, ny, i0, g0, in0, lane);
+  // slot arrays: 0 = v_pre, 1 = b, 2 = omega/D
+#pragma unroll
+  for (int r = 0; r < PFD; ++r) g.issue(r, r, vp, bb, wD);
+
+  const int e0 = clampi(ci, 0, nxc - 1), e1 = clampi(ci + 1, 0, nxc - 1);
+  auto load_e = [&](int c) {
+    E2 e;
+    if (c >= 0 && c < nyc) {
+      const cf* row = eb + (size_t)c * nxc;
+      e.c0 = sel(okc0, row[e0]);
+      e.c1 = sel(okc1, row[e1]);
+    } else {
+      e.c0 = e.c1 = czero<float>();
+    }
+    return e;
+  };
+  E2 ea = load_e(i0 >> 1), enext = ea;
+  if (i0 & 1) enext = load_e((i0 >> 1) + 1);
+  C2 v[NU][R];
+  C2 zr[R];   // the stored z of the last rows (0 outside the grid)
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+#pragma unroll
+    for (int s = 0; s < NU; ++s) v[s][i] = c2zero();
+    zr[i] = c2zero();
+  }
+  for (int kb = 0; kb < K; kb += S) {
+    unroll<S>([&](auto KC) {
+      constexpr int Kc = decltype(KC)::value;
+      constexpr bool odd = ((Kc + NU + 1) & 1) != 0;   // parity of y (ys and S are even)
+      const int k = kb + Kc;
+      g.issue(k + PFD, (Kc + PFD) % S, vp, bb, wD);
+      const int y = i0 + k;
+      // the diagonal of A on the product's row (read from L2 while the sweeps run)
+      const int ya = y - NU - 1;
+      const bool oka = ya >= 0 && ya < ny && in0;
+      const float4 da = __ldg(reinterpret_cast<const float4*>(DA32 + (oka ? (size_t)ya * nx + g0 : 0)));
+      C2 pe;
+      if constexpr (!odd) {
+        pe.a = ea.c0;
+        pe.b = 0.5f * (ea.c0 + ea.c1);
+        enext = load_e((y >> 1) + 1);
+      } else {
+        const cf m0 = 0.5f * (ea.c0 + enext.c0), m1 = 0.5f * (ea.c1 + enext.c1);
+        pe.a = m0;
+        pe.b = 0.5f * (m0 + m1);
+        ea = enext;
+      }
+      cp_wait<PFD>();
+      const bool oky = y >= 0 && y < ny;
+      constexpr int s0 = slot(Kc, 0, R);
+      {
+        const C2 vpk = g.template get0<VT>(Kc);
+        v[0][s0].a = sel(oky && in0, vpk.a + pe.a);
+        v[0][s0].b = sel(oky && in1, vpk.b + pe.b);
+      }
+      unroll<NU - 1>([&](auto SC) {
+        constexpr int s = decltype(SC)::value + 1;
+        constexpr int so = slot(Kc, s, R);
+        constexpr int gs = slot(Kc, s, S);
+        v[s][so] = jac_row(v[s - 1][slot(Kc, s + 1, R)], v[s - 1][so], v[s - 1][slot(Kc, s - 1, R)],
+                           scale2(sc, g.get(gs, 1)), g.get(gs, 2), ih, om1);
+      });
+      {
+        constexpr int so = slot(Kc, NU, R);
+        constexpr int gs = slot(Kc, NU, S);
+        const C2 vn = jac_row(v[NU - 1][slot(Kc, NU + 1, R)], v[NU - 1][so], v[NU - 1][slot(Kc, NU - 1, R)],
+                              scale2(sc, g.get(gs, 1)), g.get(gs, 2), ih, om1);
+        const int yv = y - NU;
+        if (yv >= ys && yv < ys + seg && yv < ny) st2v<OT>(o, (ptrdiff_t)yv * nx + g0, own && in0, own && in1, vn);
+        if constexpr (std::is_same<OT, __half2>::value) {   // the product reads what was stored
+          zr[so].a = from_h2(to_h2(vn.a));
+          zr[so].b = from_h2(to_h2(vn.b));
+        } else {
+          zr[so] = vn;
+        }
+      }
+      {
+        // w = A z on row ya = y - nu - 1: rows ya - 1, ya, ya + 1 of z
+        const C2& zu = zr[slot(Kc, NU + 2, R)];
+        const C2& zm = zr[slot(Kc, NU + 1, R)];
+        const C2& zd = zr[slot(Kc, NU, R)];
+        const cf zl = shfl_up1(zm.b), zrt = shfl_dn1(zm.a);
+        const float s0r = (zl.re + zm.b.re) + (zu.a.re + zd.a.re), s0i = (zl.im + zm.b.im) + (zu.a.im + zd.a.im);
+        const float s1r = (zm.a.re + zrt.re) + (zu.b.re + zd.b.re), s1i = (zm.a.im + zrt.im) + (zu.b.im + zd.b.im);
+        const float w0r = fmaf(da.x, zm.a.re, fmaf(-da.y, zm.a.im, -ih0 * s0r));
+        const float w0i = fmaf(da.x, zm.a.im, fmaf(da.y, zm.a.re, -ih0 * s0i));
+        const float w1r = fmaf(da.z, zm.b.re, fmaf(-da.w, zm.b.im, -ih0 * s1r));
+        const float w1i = fmaf(da.z, zm.b.im, fmaf(da.w, zm.b.re, -ih0 * s1i));
+        const bool rowok = ya >= ys && ya < ys + seg && ya < ny;
+        const bool put = rowok && own && in0;
+        if (put) *reinterpret_cast<float4*>(vo + (ptrdiff_t)ya * nx + g0) = make_float4(w0r, w0i, w1r, w1i);
+        const float nrm = put ? fmaf(w0r, w0r, fmaf(w0i, w0i, fmaf(w1r, w1r, w1i * w1i))) : 0.f;
+        // rows pair up as (2i, 2i + 1) (segments start on even rows and are of even length; ya has
+        // the parity of Kc): the pair's sum over the strip goes to npart[(rhs ny2 + i) nstrips + strip]
+        if constexpr (Kc % 2 == 0) {
+          nrm_even = nrm;
+        } else {
+          float t = nrm_even + nrm;
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(kFull, t, off);
+          const int y2 = ya - 1;
+          if (y2 >= ys && y2 < ys + seg && y2 < ny && lane == 0) np[(size_t)(y2 >> 1) * nstrips] = t;
+        }
+      }
+    });
+  }
+  cp_wait<0>();
+}
+
 }  // namespace wave
 }  // namespace mgh
