@@ -104,8 +104,8 @@ def make_inputs(w):
 # kernels on the 576^2 workload (6 levels, nu = 2, restart 8, FP32 cycle): (bytes of the capture,
 # bytes read once per launch whatever the batch); see profiles/vcycle_post_l0_ellipses576.md and
 # profiles/gram_sstep_ellipses576.md.  Traffic grows with the right-hand sides (independent sweeps).
-NCU_TRAFFIC_24 = {"vcycle_post_l0": (215.5e6, 2.65e6), "gs_update": (577.4e6, 0.0)}
-POST_CAPTURE_FUSED = False   # whether the captured level-0 post kernel formed the s-step product itself
+NCU_TRAFFIC_24 = {"vcycle_post_l0": (263.8e6, 5.3e6), "gs_update": (577.4e6, 0.0)}
+POST_CAPTURE_FUSED = True   # whether the captured level-0 post kernel formed the s-step product itself
 
 
 def captured_traffic(cls: str, w, precision: str, B: int, shape=None, fused=True):
