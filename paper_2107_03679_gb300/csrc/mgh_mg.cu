@@ -1092,9 +1092,11 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
                                          (int)smem1)););
   static std::atomic<long> resident_by_dev[64];
   const long resident = resident_cached(resident_by_dev, h, wave::k_post_wa<NU, 4, 1>, 128, smem1);
-  if (l == 0 && h.fuse_v && h.fuse_ok && ring && h.wave_lane_ring && a16(h.DAdf) && a16(h.fuse_v) &&
+  if (l == 0 && h.fuse_v && h.fuse_ok && !h.half && ring && h.wave_lane_ring && a16(h.DAdf) && a16(h.fuse_v) &&
       h.fuse_vstride % 2 == 0) {
     // the s-step operator product fused in: one more halo column per side and row above and below
+    // (FP32 storage only: with FP16 storage the fused kernel needs 111 registers and the product
+    // in its own kernel is faster)
     using GF = wave::PostWF<NU, 1>;
     const int nstrips_f = (lv.nx + GF::XO - 1) / GF::XO;
     constexpr int SF = wave::RingLen<GF::P, NU, 1>::S;
@@ -1107,12 +1109,8 @@ mgh_status launch_post_wave(Handle& h, int l, const cf* bin, size_t b_stride, co
     const int segf = wave_seg(h, l, lv.ny, nstrips_f, B, 2 * NU + 2, periodf, resident_f);
     const int nwarps_f = nstrips_f * ((lv.ny + segf - 1) / segf);
     ProfScope ps(h, P_POST0);
-    if (h.half)
-      MGH_TRY((post_lane_fgo<NU, 4, 1, __half2>(h, l, bin, b_stride, bscale, scale_stride, out, out_stride, B, st,
-                                                nstrips_f, nwarps_f, segf)));
-    else
-      MGH_TRY(MGH_RING_DISPATCH(post_lane_fgo, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,
-                                scale_stride, out, out_stride, B, st, nstrips_f, nwarps_f, segf));
+    MGH_TRY(MGH_RING_DISPATCH(post_lane_fgo, NU, h.wave_ring, h.wave_warps, h, l, bin, b_stride, bscale,
+                              scale_stride, out, out_stride, B, st, nstrips_f, nwarps_f, segf));
     MGH_CHECK_LAUNCH(); h.launches++;
     h.fuse_nstrips = nstrips_f;
     return MGH_OK;

@@ -1038,7 +1038,7 @@ struct PostWF {
 };
 
 // k_post_wa followed, one row behind its last sweep, by the operator product of the s-step basis:
-// w = A z on the stored z (FP32, or the FP16-rounded values under FP16 storage), written as the
+// w = A z on the stored z (FP32; the FP16-rounded values if OT is FP16 storage), written as the
 // FP32 basis vector v_{k+1} (vout), with the same operations as k_ss_matvec2, and the sum of
 // |w|^2 over the strip's owned points of each row pair (2i, 2i + 1) in
 // npart[(rhs * ceil(ny / 2) + i) * nstrips + strip] (FP32; a fixed warp butterfly, so the partials

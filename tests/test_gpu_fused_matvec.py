@@ -2,11 +2,12 @@
 (k_post_waf) against the separate product kernel (MGH_FUSE_MATVEC=0).
 
 The fused kernel forms every entry of v_{k+1} with the separate kernel's operations on the same
-stored z_k (FP32, or FP16 under FP16 storage); only the order in which ||v_{k+1}||^2 is summed
+stored z_k; only the order in which ||v_{k+1}||^2 is summed
 differs (per row pair and strip, then in FP64).  Both solves must meet the oracle's exact solution, with
 step counts within two of each other, and the fused path must launch fewer kernels.  Grids: two
 even widths, one with a ragged last strip; 1, 2 and 3 fine-level sweeps (each count has its own
-kernel) with one sweep on the coarser levels."""
+kernel) with one sweep on the coarser levels.  Under FP16 storage the product stays in its own
+kernel (faster there), so both runs must be the same."""
 import numpy as np
 import pytest
 
@@ -48,5 +49,10 @@ def test_fused_product_matches_the_separate_kernel(nu, precision, n, monkeypatch
         for q in range(3):
             assert rel(x[q], O.direct_solve(p, o.D, b[q])) < 1e-5
     assert all(abs(a - c) <= 2 for a, c in zip(res["1"][1], res["0"][1])), (res["1"][1], res["0"][1])
-    # one product kernel fewer per step
-    assert res["1"][2] <= res["0"][2] - min(res["1"][1]), (res["1"][2], res["0"][2])
+    if precision == "mixed16":
+        # FP16 storage keeps the product in its own kernel: the same launches and the same solve
+        assert res["1"][2] == res["0"][2]
+        np.testing.assert_array_equal(res["1"][0], res["0"][0])
+    else:
+        # one product kernel fewer per step
+        assert res["1"][2] <= res["0"][2] - min(res["1"][1]), (res["1"][2], res["0"][2])
