@@ -616,13 +616,10 @@ mgh_status fgmres_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) 
     k_zero_if_b_zero<<<grid, kKThreads, 0, h.stream>>>(a, x, h.st);
     MGH_CHECK_LAUNCH(); h.launches++;
   }
-  for (;;) {
-    MGH_CUDA(cudaMemcpyAsync(h.st_host, h.st, sizeof(RhsState) * B, cudaMemcpyDeviceToHost, h.stream));
-    MGH_CUDA(cudaStreamSynchronize(h.stream));
-    MGH_TRY(prof_flush(h));
-    bool any = false;
-    for (int i = 0; i < B; ++i) any |= (h.st_host[i].done == 0);
-    if (!any) break;
+  // a restart cycle: every launch is gated by the per-RHS state, so after the first cycle its
+  // launches are replayed from a captured graph
+  CycleGraph graph;
+  auto body = [&]() -> mgh_status {
     for (int j = 0; j < a.m; ++j) MGH_TRY(arnoldi_step<TZ>(h, a, j, B));
     {
       ProfScope ps(h, P_REDUCE);
@@ -640,6 +637,17 @@ mgh_status fgmres_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) 
       k_cycle_start<<<B, 32, 0, h.stream>>>(a, h.partial, h.vscale, h.g, h.st, h.p.tol, h.p.maxit, 0);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
+    return MGH_OK;
+  };
+  for (int ncycle = 0;; ++ncycle) {
+    MGH_CUDA(cudaMemcpyAsync(h.st_host, h.st, sizeof(RhsState) * B, cudaMemcpyDeviceToHost, h.stream));
+    MGH_CUDA(cudaStreamSynchronize(h.stream));
+    MGH_TRY(prof_flush(h));
+    bool any = false;
+    for (int i = 0; i < B; ++i) any |= (h.st_host[i].done == 0);
+    if (!any) break;
+    if (!h.use_graphs || h.prof || ncycle == 0) MGH_TRY(body());
+    else MGH_TRY(graph.run(h, body));
   }
   return finish_solve(h, B, info);
 }
