@@ -338,8 +338,10 @@ typedef struct {
                                fit returns MGH_INVALID_ARG */
   int tail_cluster;         /* blocks per right-hand side of the coarse tail: 1 (one block), 2 or 4
                                (a thread-block cluster over bands of rows, halo rows exchanged
-                               through distributed shared memory); 0 = 1; a count whose layout does
-                               not fit returns MGH_INVALID_ARG */
+                               through distributed shared memory); 0 = automatic (the default): per
+                               launch of B right-hand sides, 4 or else 2 when B such clusters fit on
+                               the GPU at once, else 1; a count whose layout does not fit returns
+                               MGH_INVALID_ARG */
 } mgh_kernel_shape;
 
 /* Current launch shapes of a handle (tail_level reports the level in use, 0 if none). */

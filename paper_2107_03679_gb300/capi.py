@@ -317,7 +317,7 @@ def mgh_get_kernel_shape(h) -> dict:
 
 
 def mgh_set_kernel_shape(h, wave_seg=0, wave_warps: int = 4, wave_ring: int = 1, tail_level: int = -1,
-                         tail_cluster: int = 1) -> None:
+                         tail_cluster: int = 0) -> None:
     """wave_seg: one length for every level, or a sequence of per-level lengths (0 = model)."""
     segs = [int(wave_seg)] * MGH_MAX_LEVELS if isinstance(wave_seg, int) else list(wave_seg)
     segs = (segs + [0] * MGH_MAX_LEVELS)[:MGH_MAX_LEVELS]

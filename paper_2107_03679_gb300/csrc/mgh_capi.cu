@@ -575,7 +575,7 @@ mgh_status mgh_set_kernel_shape(mgh_handle* h, const mgh_kernel_shape* s) {
   if (s->tail_cluster != 0 && s->tail_cluster != 1 && s->tail_cluster != 2 && s->tail_cluster != 4)
     return MGH_INVALID_ARG;
   const int l0 = s->tail_level < 0 ? choose_tail_level(*h) : s->tail_level;
-  const int cl = s->tail_cluster == 0 ? 1 : s->tail_cluster;
+  const int cl = s->tail_cluster;
   if (cl > 1 && (l0 == 0 || !tail_cluster_fits(*h, l0, cl))) return MGH_INVALID_ARG;
   if (h->half && (s->wave_warps != 4 || s->wave_ring != 1)) return MGH_NOT_SUPPORTED;
   MGH_CUDA(cudaStreamSynchronize(h->stream));   // launches already queued keep their shapes

@@ -76,7 +76,10 @@ struct Handle {
   bool wave_lane_ring = true;  // rings filled per lane by cp.async (else by bulk copies)
   bool use_graphs = true;    // replay each restart cycle's launches from a captured CUDA graph
   int tail_l0 = 0;           // first level of the one-kernel coarse tail (0: every level by level kernels)
-  int tail_cluster = 1;      // blocks per right-hand side of the tail (1, 2 or 4: a thread-block cluster)
+  int tail_cluster = 0;      // blocks per right-hand side of the tail (1, 2 or 4: a thread-block cluster;
+                             // 0: per launch, the largest cluster whose launch fits the GPU at once)
+  int tail_cap_l0 = -1;      // tail level tail_cap was queried for
+  int tail_cap[5] = {};      // [2], [4]: clusters of that size the GPU holds at once
   // operator product of the s-step basis fused into the level-0 post kernel: the engine sets
   // fuse_v around one cycle; the post kernel launcher fuses when it can and reports its strips
   cf* fuse_v = nullptr;      // FP32 basis slot k+1 (hi plane) of right-hand side 0

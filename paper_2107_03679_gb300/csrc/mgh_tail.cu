@@ -600,9 +600,42 @@ size_t cl_smem_bytes(const Handle& h, int l0, int cl) {
   return (size_t)cl_layout<T>(h, l0, cl, nullptr) * sizeof(Cx<T>);
 }
 
+constexpr int kTpb2 = 1024, kTpb4 = 512;   // threads per block of the 2- and 4-block clusters
+
 template <typename T>
-mgh_status launch_tail_cl(Handle& h, int reps, int B, const RhsState* st) {
-  const int l0 = h.tail_l0, cl = h.tail_cluster;
+mgh_status set_tail_cl_attrs() {
+  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(k_tail_cl<kTpb2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTailSmemMax));
+           MGH_CUDA(cudaFuncSetAttribute(k_tail_cl<kTpb4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTailSmemMax)););
+  return MGH_OK;
+}
+
+// Clusters of cl blocks of the tail from level tail_l0 that the GPU holds at once (0 if none).
+template <typename T>
+int tail_cl_capacity(Handle& h, int cl) {
+  if (set_tail_cl_attrs<T>() != MGH_OK) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cl, 1, 1);
+  cfg.blockDim = dim3(cl == 2 ? kTpb2 : kTpb4, 1, 1);
+  cfg.dynamicSmemBytes = cl_smem_bytes<T>(h, h.tail_l0, cl);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  const cudaError_t e = cl == 2 ? cudaOccupancyMaxActiveClusters(&n, k_tail_cl<kTpb2, T>, &cfg)
+                                : cudaOccupancyMaxActiveClusters(&n, k_tail_cl<kTpb4, T>, &cfg);
+  if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+  return n;
+}
+
+template <typename T>
+mgh_status launch_tail_cl(Handle& h, int reps, int B, const RhsState* st, int cl) {
+  const int l0 = h.tail_l0;
   ClArgs<T> a{};
   a.total = cl_layout<T>(h, l0, cl, a.lv);
   for (int l = l0; l < h.L; ++l) {
@@ -624,11 +657,7 @@ mgh_status launch_tail_cl(Handle& h, int reps, int B, const RhsState* st) {
   a.kinv = sizeof(T) == 8 ? (const Cx<T>*)(const void*)h.kinv64r : (const Cx<T>*)(const void*)h.kinv32;
   a.st = st;
   const size_t smem = (size_t)a.total * sizeof(Cx<T>);
-  constexpr int kTpb2 = 1024, kTpb4 = 512;
-  MGH_ONCE(MGH_CUDA(cudaFuncSetAttribute(k_tail_cl<kTpb2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kTailSmemMax));
-           MGH_CUDA(cudaFuncSetAttribute(k_tail_cl<kTpb4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kTailSmemMax)););
+  MGH_TRY(set_tail_cl_attrs<T>());
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(B * cl), 1, 1);
   cfg.blockDim = dim3(cl == 2 ? kTpb2 : kTpb4, 1, 1);
@@ -671,9 +700,26 @@ int choose_tail_level(const Handle& h) {
   return 0;
 }
 
+// Blocks per right-hand side of a tail launch of B right-hand sides: the handle's setting, or with
+// the automatic setting (0) the largest cluster (4, then 2) whose B clusters the GPU holds at once,
+// else one block.  The cluster size changes no result.
+int tail_cluster_for(Handle& h, int B) {
+  if (h.tail_cluster > 0) return h.tail_cluster;
+  if (h.tail_cap_l0 != h.tail_l0) {   // capacities of this tail level, queried once
+    for (int c : {2, 4})
+      h.tail_cap[c] = tail_cluster_fits(h, h.tail_l0, c)
+                          ? (h.fp64 ? tail_cl_capacity<double>(h, c) : tail_cl_capacity<float>(h, c)) : 0;
+    h.tail_cap_l0 = h.tail_l0;
+  }
+  if (B <= h.tail_cap[4]) return 4;
+  if (B <= h.tail_cap[2]) return 2;
+  return 1;
+}
+
 mgh_status launch_tail(Handle& h, int reps, int B, const RhsState* st, bool fp64) {
-  if (h.tail_cluster > 1)
-    return fp64 ? launch_tail_cl<double>(h, reps, B, st) : launch_tail_cl<float>(h, reps, B, st);
+  const int cl = tail_cluster_for(h, B);
+  if (cl > 1)
+    return fp64 ? launch_tail_cl<double>(h, reps, B, st, cl) : launch_tail_cl<float>(h, reps, B, st, cl);
   return fp64 ? launch_tail_t<double>(h, reps, B, st) : launch_tail_t<float>(h, reps, B, st);
 }
 

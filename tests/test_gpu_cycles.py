@@ -143,9 +143,10 @@ def test_cluster_tail_equals_the_one_block_tail_bit_for_bit(precision, levels, g
     s = make_solver(w, B=3, cycle_type=gamma)
     s.set_contrast(to_t(f, torch))
     base = s.kernel_shape()
-    assert base["tail_level"] >= 1 and base["tail_cluster"] == 1
+    assert base["tail_level"] >= 1 and base["tail_cluster"] == 0   # automatic
+    s.set_kernel_shape(**dict(base, tail_cluster=1))
     z1 = s.precondition(to_t(b, torch)).cpu().numpy()
-    for cl in (2, 4):
+    for cl in (2, 4, 0):
         s.set_kernel_shape(**dict(base, tail_cluster=cl))
         assert s.kernel_shape()["tail_cluster"] == cl
         np.testing.assert_array_equal(s.precondition(to_t(b, torch)).cpu().numpy(), z1)
