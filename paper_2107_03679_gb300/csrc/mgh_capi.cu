@@ -361,6 +361,9 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   // MGH_TAIL=0 keeps every level on the level kernels
   h->tail_l0 = choose_tail_level(*h);
   if (const char* e = std::getenv("MGH_TAIL")) if (std::strcmp(e, "0") == 0) h->tail_l0 = 0;
+  // MGH_GRAM8=0 sums the s-step Gram matrix with four groups of 64 threads (two blocks per SM)
+  // instead of eight one-warp groups (three blocks per SM)
+  if (const char* e = std::getenv("MGH_GRAM8")) if (std::strcmp(e, "0") == 0) h->gram8 = false;
   // MGH_FUSE_MATVEC=0 keeps the s-step operator product in its own kernel
   if (const char* e = std::getenv("MGH_FUSE_MATVEC")) if (std::strcmp(e, "0") == 0) h->fuse_ok = false;
   // MGH_TAIL_CLUSTER=2|4 runs the tail over a cluster of that many blocks per right-hand side

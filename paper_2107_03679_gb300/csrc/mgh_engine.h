@@ -86,6 +86,7 @@ struct Handle {
   size_t fuse_vstride = 0;   // elements between right-hand sides
   int fuse_nstrips = 0;      // strips of the fused launch (0: not fused)
   bool fuse_ok = true;       // fusion allowed (MGH_FUSE_MATVEC=0 turns it off)
+  bool gram8 = true;         // s-step Gram sweep by eight one-warp groups (MGH_GRAM8=0: four groups of 64)
   float* npart = nullptr;    // [Bmax][ny][strips] norm partials of the fused product
   cudaStream_t gstream = nullptr;  // non-blocking stream the cycle graphs are captured and replayed on
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;  // order gstream after / before `stream`

@@ -1048,6 +1048,112 @@ k_ss_gram(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial
   }
 }
 
+// ---- eight thread groups of one warp each: half the pairs per thread of k_ss_gram, so that the
+// kernel holds half the accumulators and three blocks fit on an SM
+template <int NV>
+struct GramPairs8 {
+  static constexpr int NP = NV * (NV + 1) / 2;
+  static constexpr int PG = (NP + 7) / 8;   // most pairs of one group
+  __host__ __device__ static constexpr int first(int g) { return (g * NP + 4) / 8; }
+};
+
+// Tiles between promotions of the running sums in k_ss_gram8: a thread sums 8 points of a tile,
+// so a running sum again holds 32 products.
+constexpr int kGramRunTiles8 = 4;
+
+template <int NV, int G>
+__device__ __forceinline__ void gram_tile8(const Pipe& pp, int slot, size_t q0, size_t p1, int lane, float2* run) {
+  using PR = GramPairs<NV>;
+  using P8 = GramPairs8<NV>;
+  constexpr int P0 = P8::first(G);
+  constexpr int P1 = P8::first(G + 1);
+  static_assert(P1 - P0 <= P8::PG, "group share above its accumulators");
+  if constexpr (P1 > P0) {
+    constexpr int IMIN = PR::row(P0);
+#pragma unroll 1
+    for (int r = 0; r < kTile / 32; ++r) {
+      const int t = lane + 32 * r;
+      if (q0 + t >= p1) break;
+      float2 v[NV];
+#pragma unroll
+      for (int i = IMIN; i < NV; ++i) v[i] = pp.plane(slot, i)[t];
+      unroll<P1 - P0>([&](auto PC) {
+        constexpr int p = P0 + decltype(PC)::value;
+        constexpr int i = PR::row(p), j = PR::col(p);
+        float2& c = run[p - P0];
+        if constexpr (i == j) {
+          c.x = __fmaf_rn(v[i].x, v[i].x, __fmaf_rn(v[i].y, v[i].y, c.x));
+        } else {   // conj(v_i) v_j
+          c.x = __fmaf_rn(v[i].x, v[j].x, __fmaf_rn(v[i].y, v[j].y, c.x));
+          c.y = __fmaf_rn(v[i].x, v[j].y, __fmaf_rn(-v[i].y, v[j].x, c.y));
+        }
+      });
+    }
+  }
+}
+
+// k_ss_gram with warp w summing the pairs of group w (eight groups) over all 256 points of a tile.
+template <int NV>
+__global__ void __launch_bounds__(kDfThreads, 3)
+k_ss_gram8(KArgs a, int S, const float2* __restrict__ V, cd* __restrict__ partial, const RhsState* __restrict__ st,
+           int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using P8 = GramPairs8<NV>;
+  static_assert(kDfThreads == 256, "eight warps, one group each");
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (!st[rhs].active) return;
+  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
+  Pipe pp = pipe_begin(smem, S, NV, p0, p1);   // the FP32 (hi) planes of the basis
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NV; ++i) pp.src[i] = vplane(V, a, rhs, i, 0);
+  int* fail = reinterpret_cast<int*>(smem + kSmemHeader - 16);
+  pipe_start(pp, fail);
+  const int grp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cdf acc[P8::PG];
+  float2 run[P8::PG];
+#pragma unroll
+  for (int c = 0; c < P8::PG; ++c) {
+    acc[c] = cdf_zero();
+    run[c] = make_float2(0.f, 0.f);
+  }
+  for (int k = 0; k < pp.ntiles; k += 2) {
+    const bool two = k + 1 < pp.ntiles;
+    const bool ready = pipe_wait(pp, k, fail) && (!two || pipe_wait(pp, k + 1, fail));
+    if (ready) {
+      for (int u = 0; u < (two ? 2 : 1); ++u) {
+        const int slot = (k + u) % S;
+        const size_t q0 = p0 + (size_t)(k + u) * kTile;
+        switch (grp) {
+          case 0: gram_tile8<NV, 0>(pp, slot, q0, p1, lane, run); break;
+          case 1: gram_tile8<NV, 1>(pp, slot, q0, p1, lane, run); break;
+          case 2: gram_tile8<NV, 2>(pp, slot, q0, p1, lane, run); break;
+          case 3: gram_tile8<NV, 3>(pp, slot, q0, p1, lane, run); break;
+          case 4: gram_tile8<NV, 4>(pp, slot, q0, p1, lane, run); break;
+          case 5: gram_tile8<NV, 5>(pp, slot, q0, p1, lane, run); break;
+          case 6: gram_tile8<NV, 6>(pp, slot, q0, p1, lane, run); break;
+          default: gram_tile8<NV, 7>(pp, slot, q0, p1, lane, run); break;
+        }
+      }
+    }
+    if (!pipe_release2(pp, k, fail, err)) return;
+    if ((k + 2) % kGramRunTiles8 == 0 || k + 2 >= pp.ntiles) {
+#pragma unroll
+      for (int c = 0; c < P8::PG; ++c) {
+        df_add1(acc[c].re, run[c].x);
+        df_add1(acc[c].im, run[c].y);
+        run[c] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  cd* out = partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
+  const int f0 = P8::first(grp), f1 = P8::first(grp + 1);
+#pragma unroll
+  for (int c = 0; c < P8::PG; ++c) {
+    const df re = warp_sum_df(acc[c].re), im = warp_sum_df(acc[c].im);
+    if (lane == 0 && f0 + c < f1) out[f0 + c] = mk<double>(df_to_double(re), df_to_double(im));
+  }
+}
+
 // Per right-hand side: the Gram matrix from the block sums, its equilibrated Cholesky factor,
 // the cycle's least-squares problem by Givens rotations, the prefix to keep and its y.  One warp
 // per right-hand side (launched with 32 threads): the Gram entries are summed by lanes, row j of
@@ -1406,7 +1512,7 @@ namespace {
 
 template <int NV>
 mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
-  MGH_ONCE(MGH_TRY(set_smem(k_ss_gram<NV>)););
+  MGH_ONCE(MGH_TRY(set_smem(k_ss_gram<NV>)); MGH_TRY(set_smem(k_ss_gram8<NV>)););
   const dim3 grid(a.nblk, B);
   float2* V = reinterpret_cast<float2*>(h.V);
   for (int k = 0; k < a.m; ++k) {
@@ -1453,9 +1559,14 @@ mgh_status ss_cycle(Handle& h, const KArgs& a, int B) {
     }
   }
   {
-    const int P = NV, S = stages_for(P);
     ProfScope ps(h, P_UPDATE);
-    k_ss_gram<NV><<<grid, kDfThreads, smem_for(P, S), h.stream>>>(a, S, V, h.partial, h.st, h.dev_err);
+    if (h.gram8) {   // three blocks per SM: a ring of at most 3 stages
+      const int S = std::min(3, stages_for(NV));
+      k_ss_gram8<NV><<<grid, kDfThreads, smem_for(NV, S), h.stream>>>(a, S, V, h.partial, h.st, h.dev_err);
+    } else {
+      const int S = stages_for(NV);
+      k_ss_gram<NV><<<grid, kDfThreads, smem_for(NV, S), h.stream>>>(a, S, V, h.partial, h.st, h.dev_err);
+    }
     MGH_CHECK_LAUNCH(); h.launches++;
   }
   {
