@@ -111,26 +111,28 @@ def test_reconstruction_entry_points_validate_on_the_host(lib):
     assert L.mgh_debug_inject_timeout(None) == capi.MGH_INVALID_ARG
 
 
-def test_params_layout_matches_the_c_header(tmp_path):
-    """The ctypes mirror of mgh_params has the C struct's size and field offsets (compiled from
-    include/mgh.h with the host C compiler)."""
+@pytest.mark.parametrize("struct", ["mgh_params", "mgh_solve_info", "mgh_profile", "mgh_kernel_shape"])
+def test_struct_layouts_match_the_c_header(tmp_path, struct):
+    """Each ctypes mirror of a C-ABI struct has the C struct's size and field offsets (compiled
+    from include/mgh.h with the host C compiler)."""
     import shutil
     import subprocess
     import paper_2107_03679_gb300.capi as capi
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    fields = [f for f, _ in capi.mgh_params._fields_]
+    cls = getattr(capi, struct)
+    fields = [f for f, _ in cls._fields_]
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mgh.h"\nint main(void) {\n'
-                   '  printf("%zu\\n", sizeof(mgh_params));\n'
-                   + "".join(f'  printf("%zu\\n", offsetof(mgh_params, {f}));\n' for f in fields)
+                   f'  printf("%zu\\n", sizeof({struct}));\n'
+                   + "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
                    + "  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    assert out[0] == ctypes.sizeof(capi.mgh_params)
-    assert out[1:] == [getattr(capi.mgh_params, f).offset for f in fields]
+    assert out[0] == ctypes.sizeof(cls)
+    assert out[1:] == [getattr(cls, f).offset for f in fields]
 
 
 def test_cycle_type_and_per_level_sweeps_validate_on_the_host(lib):

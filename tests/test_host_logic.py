@@ -201,3 +201,36 @@ def test_split_batch_equals_one_handle_over_all_angles():
     np.testing.assert_allclose(u.numpy(), u_ref, rtol=0, atol=1e-12 * np.abs(u_ref).max())
     np.testing.assert_array_equal(uc.numpy(), O.crop(p, u.numpy()))
     assert len(inf_f) == 5 and len(inf_a) == 5
+
+
+def test_bench_byte_model_with_and_without_the_fused_product():
+    """The bench's algorithmic bytes for the s-step engine: with the basis product in its own kernel
+    it reads z and writes v_{k+1} (16 B per point and step plus D_A per launch); fused into the
+    level-0 post kernel, the post class carries the v_{k+1} write and D_A instead and there is no
+    product class.  The captured ncu traffic is reported only for the kernel that was captured."""
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    N, cs = 1000, 8
+    prof = {"arnoldi_steps": 40, "cycle_steps": 48, "gram_reads": 54, "residuals": 7, "updates": 6,
+            "update_reads": 40}
+    sep = {"vcycle_pre_l0": 48, "vcycle_post_l0": 48, "matvec_dots": 48}
+    fus = {"vcycle_pre_l0": 48, "vcycle_post_l0": 48, "matvec_dots": 0}
+    a = bench.algorithmic_bytes(prof, N, cs, sep, "sstep")
+    b = bench.algorithmic_bytes(prof, N, cs, fus, "sstep")
+    assert a["matvec_dots"] == 48 * N * (cs + cs) + 48 * cs * N
+    assert "matvec_dots" not in b
+    # fused: the post class gains the v_{k+1} write and D_A, not the z re-read
+    assert b["vcycle_post_l0"] - a["vcycle_post_l0"] == 48 * N * cs + 48 * cs * N
+    assert sum(a.values()) - sum(b.values()) == 48 * N * cs   # the z re-read saved
+    w = W.WORKLOADS["ellipses576"]
+    fused_cap = bench.captured_traffic("vcycle_post_l0", w, "mixed32", 60, fused=True)
+    assert (fused_cap is not None) == bench.POST_CAPTURE_FUSED
+    assert (bench.captured_traffic("vcycle_post_l0", w, "mixed32", 60, fused=False) is None) == bench.POST_CAPTURE_FUSED
+    if fused_cap is not None:
+        cap, once = bench.NCU_TRAFFIC_24["vcycle_post_l0"]
+        assert fused_cap == round((cap - once) * 60 / 24 + once)
+    assert bench.captured_traffic("vcycle_post_l0", w, "mixed32", 60, shape={"wave_warps": 2}) is None
