@@ -574,6 +574,71 @@ k_df_residual(KArgs a, const float2* __restrict__ bdf, const float2* __restrict_
   block_reduce_store<1>(acc, 1, df_to_double(bn), 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
 }
 
+// The same for rows of even width: two adjacent points per thread and step (the pair never
+// straddles a row), 16-byte loads of the x, b and D_A pairs and of the rows above and below, one
+// 16-byte store per plane; each point is computed with k_df_residual's operations.
+__device__ __forceinline__ void load_df2(const float2* __restrict__ h, size_t Np, size_t q, cdf& u0, cdf& u1) {
+  const float4 a = *reinterpret_cast<const float4*>(h + q), b = *reinterpret_cast<const float4*>(h + q + Np);
+  u0.re.hi = a.x; u0.im.hi = a.y; u0.re.lo = b.x; u0.im.lo = b.y;
+  u1.re.hi = a.z; u1.im.hi = a.w; u1.re.lo = b.z; u1.im.lo = b.w;
+}
+
+__device__ __forceinline__ cdf df_residual_pt(cdf r, const cdf& D, const cdf& xc, const cdf& vw, const cdf& ve,
+                                              const cdf& vs, const cdf& vn, const df& ih) {
+  cdf sum;
+  sum.re = df_add(df_add(vw.re, ve.re), df_add(vs.re, vn.re));
+  sum.im = df_add(df_add(vw.im, ve.im), df_add(vs.im, vn.im));
+  cdf_sub_mul(r, D, xc);
+  df_fma(r.re, ih.hi, ih.lo, sum.re.hi, sum.re.lo);
+  df_fma(r.im, ih.hi, ih.lo, sum.im.hi, sum.im.lo);
+  r.re = df_norm(r.re);
+  r.im = df_norm(r.im);
+  return r;
+}
+
+__global__ void __launch_bounds__(kKThreads)
+k_df_residual2(KArgs a, const float2* __restrict__ bdf, const float2* __restrict__ xdf, const float2* __restrict__ DAdf,
+               float2* __restrict__ V, cd* __restrict__ partial, const RhsState* __restrict__ st, int first,
+               int write_lo) {
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  if (st[rhs].done) return;
+  const float2* xb = xdf + (size_t)rhs * 2 * a.Np;
+  const float2* bb = bdf + (size_t)rhs * 2 * a.Np;
+  float2* rh = V + ((size_t)rhs * (a.m + 1) * 2) * a.Np;
+  float2* rl = rh + a.Np;
+  const df ih = df_from_double(a.inv_h2);
+  float rn = 0.f;
+  df bn = {0.f, 0.f};
+  const size_t p0 = blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;   // both even
+  size_t q = p0 + 2 * threadIdx.x;
+  int n = (int)((unsigned)q / (unsigned)a.nx);
+  int m = (int)((unsigned)q - (unsigned)n * (unsigned)a.nx);
+  for (; q < p1; q += 2 * kKThreads, m += 2 * kKThreads) {
+    while (m >= a.nx) { m -= a.nx; ++n; }
+    const cdf z = cdf_zero();
+    cdf x0, x1, b0, b1, d0, d1, s0 = z, s1 = z, n0 = z, n1 = z;
+    load_df2(xb, a.Np, q, x0, x1);
+    load_df2(bb, a.Np, q, b0, b1);
+    load_df2(DAdf, a.Np, q, d0, d1);
+    if (n > 0) load_df2(xb, a.Np, q - a.nx, s0, s1);
+    if (n < a.ny - 1) load_df2(xb, a.Np, q + a.nx, n0, n1);
+    const cdf wl = m > 0 ? load_df(xb, a.Np, q - 1) : z;
+    const cdf er = m + 2 < a.nx ? load_df(xb, a.Np, q + 2) : z;
+    if (first) {
+      cdf_abs2_acc(bn, b0);
+      cdf_abs2_acc(bn, b1);
+    }
+    const cdf r0 = df_residual_pt(b0, d0, x0, wl, x1, s0, n0, ih);
+    const cdf r1 = df_residual_pt(b1, d1, x1, x0, er, s1, n1, ih);
+    *reinterpret_cast<float4*>(rh + q) = make_float4(r0.re.hi, r0.im.hi, r1.re.hi, r1.im.hi);
+    if (write_lo) *reinterpret_cast<float4*>(rl + q) = make_float4(r0.re.lo, r0.im.lo, r1.re.lo, r1.im.lo);
+    rn = fmaf(r0.re.hi, r0.re.hi, fmaf(r0.im.hi, r0.im.hi, rn));
+    rn = fmaf(r1.re.hi, r1.re.hi, fmaf(r1.im.hi, r1.im.hi, rn));
+  }
+  cd acc[1] = {mk<double>((double)rn, 0.0)};
+  block_reduce_store<1>(acc, 1, df_to_double(bn), 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
+}
+
 // Cycle start from the double-float residual: a right-hand side whose residual meets its target
 // waits for the FP64 verification instead of starting a cycle.
 __global__ void k_df_cycle_start(KArgs a, const cd* __restrict__ partial, double* __restrict__ vscale,
@@ -1426,8 +1491,12 @@ mgh_status df_driver(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info,
   auto residual_and_start = [&](int first) -> mgh_status {
     {
       ProfScope ps(h, P_RESIDUAL);
-      k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, h.bdf, h.xdf, h.DAdf, V, h.partial, h.st, first,
-                                                      write_lo ? 1 : 0);
+      if (a.nx % 2 == 0)
+        k_df_residual2<<<grid, kKThreads, 0, h.stream>>>(a, h.bdf, h.xdf, h.DAdf, V, h.partial, h.st, first,
+                                                         write_lo ? 1 : 0);
+      else
+        k_df_residual<<<grid, kKThreads, 0, h.stream>>>(a, h.bdf, h.xdf, h.DAdf, V, h.partial, h.st, first,
+                                                        write_lo ? 1 : 0);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
     {
