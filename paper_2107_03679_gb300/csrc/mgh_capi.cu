@@ -361,6 +361,8 @@ mgh_status mgh_create(const mgh_params* p, void* cuda_stream, mgh_handle** out) 
   // MGH_TAIL=0 keeps every level on the level kernels
   h->tail_l0 = choose_tail_level(*h);
   if (const char* e = std::getenv("MGH_TAIL")) if (std::strcmp(e, "0") == 0) h->tail_l0 = 0;
+  // MGH_DEFLATE_FORCE_PLAIN=1 sends every deflated restart down its plain-restart fallback (tests)
+  if (const char* e = std::getenv("MGH_DEFLATE_FORCE_PLAIN")) if (std::strcmp(e, "1") == 0) h->dr_force_plain = true;
   // MGH_GRAM8=0 sums the s-step Gram matrix with four groups of 64 threads (two blocks per SM)
   // instead of eight one-warp groups (three blocks per SM)
   if (const char* e = std::getenv("MGH_GRAM8")) if (std::strcmp(e, "0") == 0) h->gram8 = false;

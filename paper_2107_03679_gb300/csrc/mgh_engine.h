@@ -152,6 +152,8 @@ struct Handle {
   cd* dr_y_host = nullptr;
   cd* dr_host = nullptr;
   int* dr_mode_host = nullptr;
+  bool dr_force_plain = false;  // test hook (MGH_DEFLATE_FORCE_PLAIN=1): every deflated restart takes the
+                                // plain-restart fallback, as when the host routine gives up
   double* tvbuf = nullptr;      // [7][ny_int][nx_int] TV proximal operator: w, the dual momentum
                                 // point (p twice, q twice: ping-pong) and the last dual iterate (p, q)
   int* dev_err = nullptr;       // device error word written by kernels with bounded waits

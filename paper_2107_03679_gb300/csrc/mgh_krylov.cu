@@ -727,7 +727,7 @@ mgh_status dr_restart(Handle& h, const KArgs& a, int B, int* j0, bool* any_defl)
       cplx* R = Hh + (size_t)(k + 1) * k;
       cplx* cs = R + (size_t)k * k;
       cplx* sn = cs + k;
-      const bool ok = deflate_restart(m, k, Hb.data(), c.data(), C, Hh, R, rc.data(), sn);
+      const bool ok = !h.dr_force_plain && deflate_restart(m, k, Hb.data(), c.data(), C, Hh, R, rc.data(), sn);
       for (int i = 0; i < k; ++i) cs[i] = cplx(rc[i], 0.0);
       h.dr_mode_host[rhs] = ok ? 1 : 2;
     }

@@ -95,3 +95,24 @@ def test_deflation_beats_plain_restarts_on_the_strong_scattering_recipe(precisio
             assert rel(x.cpu().numpy()[0], ref) < (1e-6 if precision == "fp64" else 1e-5)
         s.close()
     assert steps[4] < 0.8 * steps[0], steps
+
+
+@pytest.mark.parametrize("precision,arnoldi", [("fp64", "auto"), ("mixed32", "fp64")])
+def test_fallback_restart_equals_plain_restarts(precision, arnoldi, monkeypatch):
+    """When the host routine gives up, a right-hand side restarts plainly from its true residual
+    (copied from W into basis slot 0).  With every deflated restart sent down that path
+    (MGH_DEFLATE_FORCE_PLAIN=1) the solve is the plain-restart engine's, bit for bit."""
+    torch = torch_cuda()
+    w = _w(precision=precision)
+    p, f, o = oracle_solver(w, tol=1e-10)
+    b = np.stack([O.rhs(p, f, t) for t in W.angles(w)[:2]])
+    res = {}
+    for k, force in ((0, "0"), (4, "1")):
+        monkeypatch.setenv("MGH_DEFLATE_FORCE_PLAIN", force)
+        s = make_solver(w, B=2, maxit=3000, arnoldi=arnoldi, deflate=k)
+        s.set_contrast(torch.from_numpy(f).cuda())
+        x, infos = s.solve(torch.from_numpy(b).cuda())
+        res[k] = (x.cpu().numpy(), [i["iterations"] for i in infos], [i["converged"] for i in infos])
+        s.close()
+    assert all(res[4][2]) and res[4][1] == res[0][1], (res[4][1], res[0][1])
+    np.testing.assert_array_equal(res[4][0], res[0][0])
