@@ -283,3 +283,89 @@ def fgmres_dr(apply_A: Callable, apply_M: Callable, b: np.ndarray, tol: float, m
         H[:k + 1, :k] = H_new
         g[:k + 1] = g_new
         j0 = k
+
+def idrs(apply_A: Callable, apply_M: Callable, b: np.ndarray, tol: float, s: int, maxit: int,
+         x0: np.ndarray = None, shadow: np.ndarray = None, kappa: float = 0.7, seed: int = 0):
+    """Right-preconditioned IDR(s) with biorthogonalisation (induced dimension reduction:
+    Sonneveld & van Gijzen 2008; the biorthogonal variant of van Gijzen & Sonneveld 2011).
+
+    Residuals are driven into a sequence of shrinking spaces G_j orthogonal to an s-dimensional
+    shadow space P (random orthonormal unless `shadow` is given, n x s).  Each outer step makes s
+    intermediate residuals with update directions U (preconditioned) and G = A U kept biorthogonal
+    to P, then one dimension-reduction step r <- r - omega A M^{-1} r with omega the local
+    minimal-residual choice, increased to keep |cos(t, r)| >= kappa ("maintaining the
+    convergence"; kappa = 0 keeps the plain minimal residual).  Recurrences are short: storage is
+    2s + 2 vectors, and each step costs one preconditioner application and one operator product.
+    The iterate is accepted on the true residual ||b - A x|| <= tol ||b||; iterations count
+    preconditioner applications; history holds the relative recursive residual after every
+    dimension-reduction step.  With s = 1 and the shadow vector r_0 it is Bi-CGSTAB."""
+    info = SolveInfo()
+    x = np.zeros_like(b) if x0 is None else x0.astype(np.complex128).copy()
+    bnorm = _norm(b)
+    if bnorm == 0.0:
+        info.converged, info.rel_residual = True, 0.0
+        return np.zeros_like(b), info
+    shape, n = b.shape, b.size
+    xr = x.ravel().astype(np.complex128)
+    r = (b - apply_A(x)).ravel()
+    if shadow is None:
+        rng = np.random.default_rng(seed)
+        P = rng.standard_normal((n, s)) + 1j * rng.standard_normal((n, s))
+        P, _ = np.linalg.qr(P)
+    else:
+        P = np.asarray(shadow, dtype=np.complex128).reshape(n, s)
+    G = np.zeros((n, s), dtype=np.complex128)
+    U = np.zeros((n, s), dtype=np.complex128)
+    Ms = np.eye(s, dtype=np.complex128)     # M_s = P^H G, lower triangular after biorthogonalisation
+    omega = 1.0 + 0.0j
+
+    def accept():
+        true_rel = _norm(b - apply_A(xr.reshape(shape))) / bnorm
+        info.rel_residual = true_rel
+        return true_rel <= tol
+
+    while info.iterations < maxit:
+        f = P.conj().T @ r
+        for k in range(s):
+            # v = r - G[:, k:] c with M_s[k:, k:] c = f[k:] (lower triangular)
+            c = np.linalg.solve(np.tril(Ms[k:, k:]), f[k:])
+            v = r - G[:, k:] @ c
+            v = apply_M(v.reshape(shape)).ravel()
+            U[:, k] = U[:, k:] @ c + omega * v
+            G[:, k] = apply_A(U[:, k].reshape(shape)).ravel()
+            info.iterations += 1
+            for i in range(k):                  # G[:, k] perpendicular to P[:, :k]
+                alpha = (P[:, i].conj() @ G[:, k]) / Ms[i, i]
+                G[:, k] -= alpha * G[:, i]
+                U[:, k] -= alpha * U[:, i]
+            Ms[k:, k] = P[:, k:].conj().T @ G[:, k]
+            if Ms[k, k] == 0:
+                return xr.reshape(shape), info
+            beta = f[k] / Ms[k, k]
+            r = r - beta * G[:, k]
+            xr = xr + beta * U[:, k]
+            if _norm(r) <= tol * bnorm and accept():
+                info.converged = True
+                return xr.reshape(shape), info
+            f[k + 1:] -= beta * Ms[k + 1:, k]
+            if info.iterations >= maxit:
+                break
+        if info.iterations >= maxit:
+            break
+        # dimension reduction: r <- (I - omega A M^{-1}) r
+        v = apply_M(r.reshape(shape)).ravel()
+        t = apply_A(v.reshape(shape)).ravel()
+        info.iterations += 1
+        nt, nr, tr = _norm(t), _norm(r), complex(t.conj() @ r)
+        omega = tr / nt ** 2
+        rho = abs(tr) / (nt * nr) if nt > 0 and nr > 0 else 1.0
+        if kappa > 0 and rho < kappa:
+            omega = omega * kappa / rho
+        xr = xr + omega * v
+        r = r - omega * t
+        info.history.append(_norm(r) / bnorm)
+        if _norm(r) <= tol * bnorm and accept():
+            info.converged = True
+            return xr.reshape(shape), info
+    info.rel_residual = _norm(b - apply_A(xr.reshape(shape))) / bnorm
+    return xr.reshape(shape), info
