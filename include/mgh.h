@@ -87,11 +87,23 @@ typedef enum {
 
 typedef enum {
   MGH_KRYLOV_FGMRES = 0,    /* right-preconditioned flexible GMRES(restart) (the target's method) */
-  MGH_KRYLOV_BICGSTAB = 1   /* right-preconditioned Bi-CGSTAB of Alg. 3 (the paper's method): two
+  MGH_KRYLOV_BICGSTAB = 1,  /* right-preconditioned Bi-CGSTAB of Alg. 3 (the paper's method): two
                                multigrid cycles per iteration, FP64 vectors and inner products, the
                                cycle in the handle's precision; uses the GMRES workspace, so it needs
                                restart >= 5; `arnoldi` is ignored; iterations count cycles (2 per
                                Bi-CGSTAB iteration) */
+  MGH_KRYLOV_IDRS = 2       /* right-preconditioned IDR(s) with biorthogonalisation (Sonneveld & van
+                               Gijzen 2008; van Gijzen & Sonneveld 2011), s = idr_s: a short-
+                               recurrence alternative to Bi-CGSTAB (s = 1 with the shadow vector r_0
+                               is Bi-CGSTAB) whose step count grows less with the grid and does not
+                               grow with an FP32 cycle on strongly scattering media.  One cycle and
+                               one operator product per step; FP64 vectors and inner products, the
+                               cycle in the handle's precision (FP64 or MIXED32; MIXED16 is
+                               MGH_NOT_SUPPORTED); shadow space of random signs +-1 +-j from
+                               MurmurHash3's 32-bit finaliser of the point index; omega raised to
+                               keep |cos(A M^{-1} r, r)| >= 0.7.  Uses the GMRES workspace, so it
+                               needs restart >= 2 idr_s + 2; `arnoldi` is ignored; iterations count
+                               cycles, restarts count outer steps (s + 1 cycles each) */
 } mgh_krylov;
 
 #define MGH_MAX_LEVELS 12
@@ -134,6 +146,8 @@ typedef struct {
                                orthogonalised against them.  Needs krylov MGH_KRYLOV_FGMRES with the
                                native-FP64 Arnoldi: precision MGH_PREC_FP64, or MGH_PREC_MIXED32 with
                                arnoldi MGH_ARNOLDI_FP64 (MGH_NOT_SUPPORTED otherwise) */
+  int idr_s;                /* shadow-space dimension s of MGH_KRYLOV_IDRS, 1..8 (default 4; read only
+                               with that krylov) */
 } mgh_params;
 
 typedef struct {

@@ -17,8 +17,8 @@ MGH_PREC_FP64, MGH_PREC_MIXED32, MGH_PREC_MIXED16 = 0, 1, 2
 PRECISIONS = {"fp64": MGH_PREC_FP64, "mixed32": MGH_PREC_MIXED32, "mixed16": MGH_PREC_MIXED16}
 MGH_ARNOLDI_DF, MGH_ARNOLDI_FP64, MGH_ARNOLDI_SSTEP = 0, 1, 2
 ARNOLDI = {"df": MGH_ARNOLDI_DF, "fp64": MGH_ARNOLDI_FP64, "sstep": MGH_ARNOLDI_SSTEP}
-MGH_KRYLOV_FGMRES, MGH_KRYLOV_BICGSTAB = 0, 1
-KRYLOV = {"fgmres": MGH_KRYLOV_FGMRES, "bicgstab": MGH_KRYLOV_BICGSTAB}
+MGH_KRYLOV_FGMRES, MGH_KRYLOV_BICGSTAB, MGH_KRYLOV_IDRS = 0, 1, 2
+KRYLOV = {"fgmres": MGH_KRYLOV_FGMRES, "bicgstab": MGH_KRYLOV_BICGSTAB, "idrs": MGH_KRYLOV_IDRS}
 MGH_MAX_LEVELS = 12
 CYCLES = {"v": 1, "w": 2}
 
@@ -34,7 +34,7 @@ class mgh_params(ctypes.Structure):
         ("precision", ctypes.c_int), ("batch_max", ctypes.c_int), ("arnoldi", ctypes.c_int),
         ("krylov", ctypes.c_int), ("cycle_type", ctypes.c_int), ("nu_per_level", ctypes.c_int),
         ("nu1_level", ctypes.c_int * MGH_MAX_LEVELS), ("nu2_level", ctypes.c_int * MGH_MAX_LEVELS),
-        ("deflate", ctypes.c_int),
+        ("deflate", ctypes.c_int), ("idr_s", ctypes.c_int),
     ]
 
 

@@ -41,7 +41,8 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
   if (p->precision != MGH_PREC_FP64 && p->arnoldi == MGH_ARNOLDI_SSTEP && p->restart > kMaxRestartSs &&
       p->krylov == MGH_KRYLOV_FGMRES)
     return MGH_INVALID_ARG;
-  if (p->krylov != MGH_KRYLOV_FGMRES && p->krylov != MGH_KRYLOV_BICGSTAB) return MGH_INVALID_ARG;
+  if (p->krylov != MGH_KRYLOV_FGMRES && p->krylov != MGH_KRYLOV_BICGSTAB && p->krylov != MGH_KRYLOV_IDRS)
+    return MGH_INVALID_ARG;
   if (p->cycle_type < 0 || p->cycle_type > kMaxCycleType) return MGH_INVALID_ARG;
   if (p->nu_per_level != 0 && p->nu_per_level != 1) return MGH_INVALID_ARG;
   if (p->nu_per_level)
@@ -49,6 +50,10 @@ mgh_status validate(const mgh_params* p, int* nx_l = nullptr, int* ny_l = nullpt
       if (p->nu1_level[l] < 0 || p->nu1_level[l] > kMaxSweeps || p->nu2_level[l] < 0 || p->nu2_level[l] > kMaxSweeps)
         return MGH_INVALID_ARG;
   if (p->krylov == MGH_KRYLOV_BICGSTAB && p->restart < 5) return MGH_INVALID_ARG;
+  // IDR(s) keeps r, G_0..G_{s-1}, U_0..U_{s-1}, v and t in the restart + 1 basis slots and its
+  // scalars (M_s, f, c, alpha, omega, beta, ||r||^2) in the m (m + 1) Hessenberg words
+  if (p->krylov == MGH_KRYLOV_IDRS && (p->idr_s < 1 || p->idr_s > kMaxIdrS || p->restart < 2 * p->idr_s + 2))
+    return MGH_INVALID_ARG;
   if (!std::isfinite(p->shift_re) || !std::isfinite(p->shift_im)) return MGH_INVALID_ARG;
   const long long nx = p->nx_int + 2LL * p->abl, ny = p->ny_int + 2LL * p->abl;
   if (p->precision == MGH_PREC_MIXED16) {
@@ -223,6 +228,7 @@ void mgh_default_params(mgh_params* p) {
   p->levels = 4; p->nu1 = 2; p->nu2 = 2; p->omega = 0.8;
   p->restart = 20; p->maxit = 5000; p->tol = 1e-8;
   p->precision = MGH_PREC_FP64; p->batch_max = 1;
+  p->idr_s = 4;
 }
 
 mgh_status mgh_workspace_bytes(const mgh_params* p, size_t* bytes) {

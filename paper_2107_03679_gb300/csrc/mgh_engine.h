@@ -18,6 +18,7 @@ constexpr int kMaxRestart = 32;
 constexpr int kMaxRestartDf = 20;  // restart limit of the double-float Arnoldi (register budget)
 constexpr int kMaxRestartSs = 8;   // restart limit of the s-step engine (Gram sums held in registers)
 constexpr int kMaxDeflate = 16;    // harmonic Ritz vectors kept by a deflated restart
+constexpr int kMaxIdrS = 8;        // shadow-space dimension limit of the IDR(s) engine
 
 // Complex slots per block in the partial-sum buffer: two Gram-Schmidt regions of m + 2, or the
 // (m + 1)(m + 2) / 2 entries of an s-step Gram matrix.
@@ -253,5 +254,7 @@ bool deflate_restart(int m, int k, const std::complex<double>* Hbar, const std::
 // mgh_krylov.cu
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
 mgh_status bicgstab_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
+// mgh_idrs.cu: batched IDR(s) with biorthogonalisation (krylov MGH_KRYLOV_IDRS)
+mgh_status idrs_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info);
 
 }  // namespace mgh

@@ -832,6 +832,7 @@ mgh_status fgmres_dr_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* inf
 
 mgh_status fgmres_solve(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
   if (h.p.krylov == MGH_KRYLOV_BICGSTAB) return bicgstab_solve(h, b, B, x, info);
+  if (h.p.krylov == MGH_KRYLOV_IDRS) return idrs_solve(h, b, B, x, info);
   if (h.fp64) return h.p.deflate > 0 ? fgmres_dr_t<double>(h, b, B, x, info) : fgmres_t<double>(h, b, B, x, info);
   if (h.p.arnoldi == MGH_ARNOLDI_FP64)
     return h.p.deflate > 0 ? fgmres_dr_t<float>(h, b, B, x, info) : fgmres_t<float>(h, b, B, x, info);

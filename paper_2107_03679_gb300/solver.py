@@ -33,10 +33,11 @@ def resolve_arnoldi(arnoldi: str, precision: str, restart: int, deflate: int = 0
 def make_params(nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: float = 0.15, shift=(1.0, 0.5),
                 levels: int = 4, nu1=1, nu2=1, omega: float = 0.8, restart: int = 20, maxit: int = 5000,
                 tol: float = 1e-6, precision: str = "mixed32", batch_max: int = 1, arnoldi: str = "auto",
-                krylov: str = "fgmres", cycle_type=1, deflate: int = 0):
+                krylov: str = "fgmres", cycle_type=1, deflate: int = 0, idr_s: int = 4):
     """The mgh_params of a solver (host only) and the resolved Arnoldi engine.  nu1 / nu2: one
     count for every level, or one per level above the coarsest (per-level fields of mgh_params);
-    deflate: harmonic Ritz vectors kept across FGMRES restarts (0 = plain restarts)."""
+    deflate: harmonic Ritz vectors kept across FGMRES restarts (0 = plain restarts); idr_s: shadow
+    dimension of krylov="idrs" (its workspace needs restart >= 2 idr_s + 2)."""
     p = capi.mgh_params()
     p.nx_int, p.ny_int, p.abl = nx_int, ny_int, abl
     p.h, p.k, p.beta = h, k, beta
@@ -63,6 +64,7 @@ def make_params(nx_int: int, ny_int: int, abl: int, h: float, k: float, beta: fl
     p.arnoldi = capi.ARNOLDI[resolved]
     p.krylov = capi.KRYLOV[krylov]
     p.deflate = int(deflate)
+    p.idr_s = int(idr_s)
     return p, resolved
 
 
@@ -73,14 +75,15 @@ class Solver:
                  shift=(1.0, 0.5), levels: int = 4, nu1: int = 1, nu2: int = 1, omega: float = 0.8,
                  restart: int = 20, maxit: int = 5000, tol: float = 1e-6, precision: str = "mixed32",
                  batch_max: int = 1, arnoldi: str = "auto", krylov: str = "fgmres", cycle_type: int = 1,
-                 device: Optional[torch.device] = None, stream=None, deflate: int = 0):
+                 device: Optional[torch.device] = None, stream=None, deflate: int = 0, idr_s: int = 4):
         """nu1 / nu2: sweeps on every level, or a sequence with one count per level (the coarsest's
         is ignored); cycle_type: CycleType of Alg. 2 (1 = V, 2 = W, 3; or "v" / "w"); deflate:
-        harmonic Ritz vectors kept across FGMRES restarts (GMRES-DR; 0 = plain restarts)."""
+        harmonic Ritz vectors kept across FGMRES restarts (GMRES-DR; 0 = plain restarts); idr_s:
+        shadow dimension of krylov="idrs" (IDR(s); restart >= 2 idr_s + 2 sizes its workspace)."""
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         p, self.arnoldi = make_params(nx_int, ny_int, abl, h, k, beta, shift, levels, nu1, nu2, omega, restart, maxit,
-                                      tol, precision, batch_max, arnoldi, krylov, cycle_type, deflate)
+                                      tol, precision, batch_max, arnoldi, krylov, cycle_type, deflate, idr_s)
         # (pre, post) sweeps of every level above the coarsest
         self.nu_levels = [(p.nu1_level[l], p.nu2_level[l]) if p.nu_per_level else (p.nu1, p.nu2)
                           for l in range(levels - 1)]
@@ -102,7 +105,7 @@ class Solver:
                     shift=(w.shift_re, w.shift_im), levels=w.levels, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
                     restart=w.restart, tol=w.tol, precision=precision or w.precision,
                     batch_max=batch_max or w.n_angles, krylov=getattr(w, "krylov", "fgmres"),
-                    deflate=getattr(w, "deflate", 0))
+                    deflate=getattr(w, "deflate", 0), idr_s=getattr(w, "idr_s", 4))
         args.update(kw)
         return cls(**args)
 

@@ -50,7 +50,7 @@ class Workload:
     tol: float = 1e-6
     precision: str = "mixed32"  # "fp64" | "mixed32" | "mixed16"
     h: float = 1.0
-    krylov: str = "fgmres"      # outer method: "fgmres" | "bicgstab" (Alg. 3)
+    krylov: str = "fgmres"      # outer method: "fgmres" | "bicgstab" (Alg. 3) | "idrs"
     extra: dict = field(default_factory=dict)
 
     @property
@@ -246,3 +246,31 @@ def angle_subsets(n_angles: int, subset: int, iters: int, seed: int = 0):
         return [np.arange(n_angles) for _ in range(iters)]
     rng = np.random.default_rng(seed)
     return [np.sort(rng.choice(n_angles, subset, replace=False)) for _ in range(iters)]
+
+
+def fmix32(h: np.ndarray) -> np.ndarray:
+    """MurmurHash3's 32-bit finaliser (Appleby): h ^= h >> 16; h *= 0x85EBCA6B; h ^= h >> 13;
+    h *= 0xC2B2AE35; h ^= h >> 16, all modulo 2^32."""
+    h = np.asarray(h).astype(np.uint32)
+    h = h ^ (h >> np.uint32(16))
+    h = h * np.uint32(0x85EBCA6B)
+    h = h ^ (h >> np.uint32(13))
+    h = h * np.uint32(0xC2B2AE35)
+    return h ^ (h >> np.uint32(16))
+
+
+def idr_shadow(n_points: int, s: int) -> np.ndarray:
+    """The shadow space of IDR(s) (random numbers the method draws), n_points x s: entry (q, i) is
+    (1 - 2 b_{2i}) + j (1 - 2 b_{2i+1}) with b the bits of fmix32(q + 0x9E3779B9 mod 2^32), q the
+    point index idx = n*nx + m.  The CUDA engine generates the same entries from the same
+    published finaliser; a test hands this matrix to the oracle as its shadow space."""
+    if not 1 <= s <= 16:
+        raise ValueError("idr_shadow: 1 <= s <= 16")
+    q = np.arange(n_points, dtype=np.uint64)
+    bits = fmix32(((q + np.uint64(0x9E3779B9)) & np.uint64(0xFFFFFFFF)).astype(np.uint32))
+    P = np.empty((n_points, s), dtype=np.complex128)
+    for i in range(s):
+        a = (bits >> np.uint32(2 * i)) & np.uint32(1)
+        b = (bits >> np.uint32(2 * i + 1)) & np.uint32(1)
+        P[:, i] = (1.0 - 2.0 * a) + 1j * (1.0 - 2.0 * b)
+    return P
