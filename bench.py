@@ -61,9 +61,12 @@ def parse_args(argv=None):
                          "native-FP64 Arnoldi; auto = s-step when the restart length is at most 8")
     ap.add_argument("--cycle", choices=["v", "w"], default="v",
                     help="multigrid cycle of the preconditioner (CycleType of Alg. 2)")
-    ap.add_argument("--krylov", choices=["fgmres", "bicgstab"], default=None,
-                    help="outer Krylov method: flexible GMRES or the paper's Bi-CGSTAB (Alg. 3); default: the "
-                         "workload's")
+    ap.add_argument("--krylov", choices=["fgmres", "bicgstab", "idrs"], default=None,
+                    help="outer Krylov method: flexible GMRES, the paper's Bi-CGSTAB (Alg. 3) or IDR(s) with "
+                         "biorthogonalisation; default: the workload's")
+    ap.add_argument("--idr-s", type=int, default=4,
+                    help="shadow-space dimension s of --krylov idrs (1..8; the restart length is raised to 2 s + 2 "
+                         "to hold its vectors)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (nu, restart length and level-kernel launch shapes, chosen by timing "
                          "before the timed region and cached)")
@@ -202,7 +205,7 @@ def coarse_fraction(nx: int, ny: int, levels: int, gamma: int = 1) -> float:
 
 
 def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, cfrac: float = 0.0,
-                      zs: int = None) -> dict:
+                      zs: int = None, idr_s: int = 4) -> dict:
     """Minimal bytes of each kernel class from the engine counters (fields read once, per-grid
     coefficient arrays counted once per launch).  N = fine points, cs = bytes of one complex
     number of the multigrid precision, zs = bytes of one stored level-0 iterate / preconditioned
@@ -221,6 +224,24 @@ def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, 
             "vcycle_coarse": steps * N * cfrac * cs * (3.25 + 3.25),
             "matvec_dots": steps * N * (cs + 2 * c16) + launches["matvec_dots"] * c16 * N,
             "gs_update": steps / 2 * N * (72 + 96 + 104),
+            "true_residual": prof["residuals"] * N * 3 * c16,
+        }
+    if engine == "idrs":
+        # IDR(s), per outer step of s + 1 cycles (counters count cycles).  Intermediate step k: v reads
+        # r and G_k..G_{s-1}, writes the cycle input (cs); U_k reads U_k..U_{s-1} and the cycle output
+        # (cs), writes U_k; G_k = A U_k reads U_k, writes G_k; the projection update reads G_k, U_k,
+        # G_0..G_{k-1}, U_0..U_{k-1}, r, x and writes G_k, U_k, r, x.  Dimension reduction: t = A y reads
+        # y (cs) and r, writes t; the update reads y (cs), x, r, t and writes x, r.
+        s = idr_s
+        outer = steps / (s + 1)
+        upd = sum((16 + 16 * (s - k) + cs) + (16 * (s - k) + cs + 16) + (8 + 2 * k) * c16 for k in range(s))
+        upd += cs + 80
+        return {
+            "vcycle_pre_l0": steps * N * (8 + cs + cs / 4) + launches["vcycle_pre_l0"] * 2 * cs * N,
+            "vcycle_post_l0": steps * N * (8 + 2 * cs + cs / 4) + launches["vcycle_post_l0"] * cs * N,
+            "vcycle_coarse": steps * N * cfrac * cs * (3.25 + 3.25),
+            "matvec_dots": outer * N * (2 * c16 * s + cs + 2 * c16) + launches["matvec_dots"] * c16 * N,
+            "gs_update": outer * N * upd,
             "true_residual": prof["residuals"] * N * 3 * c16,
         }
     if engine == "sstep":
@@ -427,6 +448,8 @@ def gpu_main(args, rank, world, local_rank):
         w.shift_im = args.shift_im
     if args.krylov is None:
         args.krylov = getattr(w, "krylov", "fgmres")
+    if args.krylov == "idrs":       # r, G, U, v and t live in the restart + 1 basis slots
+        w.restart = max(w.restart, 2 * args.idr_s + 2)
     precision = args.precision or w.precision
     f_gt, f_step, th, rec = make_inputs(w)
     if args.angles:
@@ -441,7 +464,7 @@ def gpu_main(args, rank, world, local_rank):
         w.nu1 = w.nu2 = tuned["nu"]
         w.restart = tuned["restart"]
     solver = Solver.from_workload(w, batch_max=B, precision=precision, device=dev, maxit=args.maxit, arnoldi=args.arnoldi,
-                                  krylov=args.krylov, cycle_type=args.cycle)
+                                  krylov=args.krylov, cycle_type=args.cycle, idr_s=args.idr_s)
     stream = solver.stream
     d_th = torch.from_numpy(th).to(dev)
     d_rec = torch.from_numpy(rec).to(dev)
@@ -464,7 +487,7 @@ def gpu_main(args, rank, world, local_rank):
         solver.close()
         runner = SplitBatch.from_workload(w, batch_max=B, parts=args.split, precision=precision, device=dev,
                                           maxit=args.maxit, arnoldi=args.arnoldi, krylov=args.krylov,
-                                          cycle_type=args.cycle)
+                                          cycle_type=args.cycle, idr_s=args.idr_s)
         solver = runner.solvers[0]
         stream = torch.cuda.current_stream(dev)
         u_crop = torch.empty((B, w.ny_int, w.nx_int), dtype=torch.complex128, device=dev)
@@ -701,10 +724,10 @@ def gpu_main(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel class (CUDA events over the timed region)
     cs = 16 if precision == "fp64" else 8
     N = solver.N
-    engine = "bicgstab" if args.krylov == "bicgstab" else (solver.arnoldi if precision != "fp64" else "fp64")
+    engine = args.krylov if args.krylov in ("bicgstab", "idrs") else (solver.arnoldi if precision != "fp64" else "fp64")
     alg = algorithmic_bytes(prof, N, cs, prof["launches"], engine,
                             coarse_fraction(w.nx, w.ny, w.levels, 2 if args.cycle == "w" else 1),
-                            zs=4 if precision == "mixed16" else cs)
+                            zs=4 if precision == "mixed16" else cs, idr_s=args.idr_s)
     ms_cls = prof["ms"]
     # the dominant kernel: the class with the most time among those that are one kernel each (the
     # coarser multigrid levels and the per-RHS reductions are many small kernels)
@@ -764,7 +787,7 @@ def gpu_main(args, rank, world, local_rank):
         "dtype": {"mixed32": "f32+f64", "mixed16": "f16-stored f32+f64"}.get(precision, "f64"), "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny} ({w.nx_int}^2 + {w.abl}-cell layer)",
                    "angles_per_gpu": B, "angles_total": B * world, "precision": precision, "levels": w.levels, "nu": [w.nu1, w.nu2],
-                   "restart": w.restart, "tol": w.tol, "krylov": args.krylov, "cycle": args.cycle.upper(), "arnoldi": solver.arnoldi if precision != "fp64" else "fp64", "shift": [w.shift_re, w.shift_im],
+                   "restart": w.restart, "tol": w.tol, "krylov": args.krylov if args.krylov != "idrs" else f"idrs(s={args.idr_s})", "cycle": args.cycle.upper(), "arnoldi": solver.arnoldi if precision != "fp64" else "fp64", "shift": [w.shift_re, w.shift_im],
                    "step": (f"set_contrast + {B} forward solves + crop" if forward_only else
                             f"set_contrast + {B} forward + crop/sample/misfit + {B} adjoint solves + gradient"),
                    "solves_per_step": (1 if forward_only else 2) * B, "l2": "inputs larger than L2 (Krylov basis "
