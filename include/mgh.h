@@ -151,10 +151,11 @@ typedef struct {
 } mgh_params;
 
 typedef struct {
-  int iterations;           /* Arnoldi steps (preconditioner applications) */
-  int restarts;             /* completed GMRES cycles */
+  int iterations;           /* preconditioner applications: Arnoldi steps (FGMRES), cycles (Bi-CGSTAB, IDR(s)) */
+  int restarts;             /* completed GMRES cycles; IDR(s): completed outer steps of s + 1 cycles */
   int converged;            /* 1 if the true relative residual reached tol */
-  double rel_residual;      /* final true ||b - A x|| / ||b|| (0 when b = 0) */
+  double rel_residual;      /* final true ||b - A x|| / ||b|| (0 when b = 0); a Bi-CGSTAB or IDR(s) solve stopped
+                               by maxit between two true-residual checks reports its recursive residual */
 } mgh_solve_info;
 
 typedef struct mgh_handle mgh_handle;

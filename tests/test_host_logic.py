@@ -234,3 +234,30 @@ def test_bench_byte_model_with_and_without_the_fused_product():
         cap, once = bench.NCU_TRAFFIC_24["vcycle_post_l0"]
         assert fused_cap == round((cap - once) * 60 / 24 + once)
     assert bench.captured_traffic("vcycle_post_l0", w, "mixed32", 60, shape={"wave_warps": 2}) is None
+
+
+def test_bench_byte_model_of_idrs():
+    """The bench's algorithmic bytes for IDR(s), counted by hand for one outer step of s = 1 (two
+    cycles, FP32 cycle input and output, cs = 8): the intermediate step reads r and G_0 and writes
+    v (40 B), reads U_0 and y and writes U_0 (40 B), then updates G_0, U_0, r, x (read 4 x 16, write
+    4 x 16: 128 B); the dimension reduction reads y, x, r, t and writes x, r (88 B).  The products
+    G_0 = A U_0 (32 B) and t = A y (cs + 32 B) carry D_A per launch."""
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    N, cs = 1000, 8
+    prof = {"arnoldi_steps": 20, "residuals": 3}
+    launches = {"vcycle_pre_l0": 20, "vcycle_post_l0": 20, "matvec_dots": 20}
+    a = bench.algorithmic_bytes(prof, N, cs, launches, "idrs", idr_s=1)
+    outer = 20 / 2
+    assert a["gs_update"] == outer * N * (40 + 40 + 128 + 88)
+    assert a["matvec_dots"] == outer * N * (32 + cs + 32) + 20 * 16 * N
+    b = bench.algorithmic_bytes(prof, N, cs, launches, "bicgstab")
+    for k in ("vcycle_pre_l0", "vcycle_post_l0", "true_residual"):      # the same cycle and check
+        assert a[k] == b[k]
+    # larger s: more vector bytes per cycle (the U and G combinations grow with s)
+    per_cycle = [bench.algorithmic_bytes(prof, N, cs, launches, "idrs", idr_s=s)["gs_update"] for s in (1, 2, 4, 8)]
+    assert all(x < y for x, y in zip(per_cycle, per_cycle[1:]))
