@@ -209,9 +209,9 @@ def algorithmic_bytes(prof: dict, N: int, cs: int, launches: dict, engine: str, 
     """Minimal bytes of each kernel class from the engine counters (fields read once, per-grid
     coefficient arrays counted once per launch).  N = fine points, cs = bytes of one complex
     number of the multigrid precision, zs = bytes of one stored level-0 iterate / preconditioned
-    vector entry (cs, or 4 with FP16 storage); engine = "df", "sstep" or "fp64"; cfrac = points of
-    the coarser smoothing levels per fine point (their fields fit in L2, so this class is not
-    bound by DRAM alone)."""
+    vector entry (cs, or 4 with FP16 storage); engine = "df", "sstep", "fp64", "bicgstab" or
+    "idrs" (with idr_s its s); cfrac = points of the coarser smoothing levels per fine point (their
+    fields fit in L2, so this class is not bound by DRAM alone)."""
     zs = cs if zs is None else zs
     steps = prof["arnoldi_steps"]
     c16 = 16
