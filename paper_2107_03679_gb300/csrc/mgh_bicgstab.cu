@@ -16,7 +16,7 @@
 // first six basis slots (so restart >= 5) and p32, y, s32, z in the first four preconditioned
 // slots.  The host reads the state once per iteration; the iteration's launches are replayed from
 // a captured CUDA graph after the first one.
-#include "mgh_krylov_common.cuh"
+#include "mgh_short_rec.cuh"
 
 namespace mgh {
 
@@ -32,29 +32,6 @@ struct Vec {
   __device__ __forceinline__ cd* at(int rhs) const { return base + rhs * stride; }
 };
 
-__device__ __forceinline__ cd cdiv(cd a, cd b) {
-  const double d = cabs2(b);
-  return mk<double>((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
-}
-
-// A x at point q of one field (FP64 operator diagonal, neighbours 0 outside the grid).
-template <typename T>
-__device__ __forceinline__ cd apply_at(const Cx<T>* __restrict__ x, const cd* __restrict__ DA, size_t q, int m, int n,
-                                       const KArgs& a) {
-  cd s = czero<double>();
-  if (m > 0) s = s + ccast<double>(x[q - 1]);
-  if (m < a.nx - 1) s = s + ccast<double>(x[q + 1]);
-  if (n > 0) s = s + ccast<double>(x[q - a.nx]);
-  if (n < a.ny - 1) s = s + ccast<double>(x[q + a.nx]);
-  return DA[q] * ccast<double>(x[q]) - a.inv_h2 * s;
-}
-
-#define BC_POINT_LOOP                                                                       \
-  const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;  \
-  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);                            \
-  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);              \
-  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads)
-
 // r = b - A x, r^ = r, p = v = 0; partial ||b||^2 (slot 0) and ||r||^2 (slot 1).
 __global__ void __launch_bounds__(kKThreads)
 k_bc_init(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const cd* __restrict__ DA, Vec r, Vec rh,
@@ -67,7 +44,7 @@ k_bc_init(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const cd*
   cd* pp = p.at(rhs);
   cd* vv = v.at(rhs);
   cd acc[2] = {czero<double>(), czero<double>()};
-  BC_POINT_LOOP {
+  SR_POINT_LOOP {
     while (m >= a.nx) { m -= a.nx; ++n; }
     const cd bq = bb[q];
     const cd rq = bq - apply_at(xb, DA, q, m, n, a);
@@ -133,7 +110,7 @@ k_bc_apply_dots(KArgs a, const Cx<TZ>* __restrict__ y, size_t y_stride, const cd
   cd* ob = out.at(rhs);
   const cd* wb = w.at(rhs);
   cd acc[2] = {czero<double>(), czero<double>()};
-  BC_POINT_LOOP {
+  SR_POINT_LOOP {
     while (m >= a.nx) { m -= a.nx; ++n; }
     const cd oq = apply_at(yb, DA, q, m, n, a);
     ob[q] = oq;
@@ -236,38 +213,6 @@ __global__ void k_bc_end(KArgs a, const cd* __restrict__ partial, cd* __restrict
   if (!S.verify && (S.iterations >= maxit || !(S.rnorm == S.rnorm))) { S.done = 1; S.converged = 0; S.active = 0; }
 }
 
-// ||b - A x||^2 of the right-hand sides awaiting the check (slot 0).
-__global__ void __launch_bounds__(kKThreads)
-k_bc_true_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const cd* __restrict__ DA,
-                   cd* __restrict__ partial, const RhsState* __restrict__ st) {
-  const int rhs = blockIdx.y, blk = blockIdx.x;
-  if (!st[rhs].active || !st[rhs].verify) return;
-  const cd* bb = b + rhs * a.N;
-  const cd* xb = x + rhs * a.N;
-  cd acc[1] = {czero<double>()};
-  BC_POINT_LOOP {
-    while (m >= a.nx) { m -= a.nx; ++n; }
-    acc[0].re += cabs2(bb[q] - apply_at(xb, DA, q, m, n, a));
-  }
-  block_reduce_store<1>(acc, 1, 0.0, 1, partial + ((size_t)rhs * a.nblk + blk) * a.pstride);
-}
-
-// Accept on the true residual, else go on from the recursive one (as Alg. 3 does).
-__global__ void k_bc_decide(KArgs a, const cd* __restrict__ partial, RhsState* __restrict__ st, double tol,
-                            int maxit) {
-  __shared__ cd sh[1];
-  const int rhs = blockIdx.x;
-  if (!st[rhs].active || !st[rhs].verify) return;
-  sum_partials(a, partial, rhs, 1, sh);
-  if (threadIdx.x != 0) return;
-  RhsState& S = st[rhs];
-  S.verify = 0;
-  S.nres += 1;
-  const double r64 = sqrt(sh[0].re);
-  if (r64 <= tol * S.bnorm) { S.done = 1; S.converged = 1; S.active = 0; S.rnorm = r64; return; }
-  if (S.iterations >= maxit) { S.done = 1; S.converged = 0; S.active = 0; S.rnorm = r64; }
-}
-
 template <typename TZ>
 mgh_status bicgstab_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
   KArgs a = make_kargs(h, B);
@@ -352,12 +297,12 @@ mgh_status bicgstab_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info
     }
     {
       ProfScope ps(h, P_RESIDUAL);
-      k_bc_true_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.partial, h.st);
+      k_sr_true_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.partial, h.st);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
     {
       ProfScope ps(h, P_REDUCE);
-      k_bc_decide<<<B, 32, 0, h.stream>>>(a, h.partial, h.st, tol, maxit);
+      k_sr_decide<<<B, 32, 0, h.stream>>>(a, h.partial, h.st, tol, maxit);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
     return MGH_OK;

@@ -30,7 +30,7 @@
 // restart >= 2s + 2), the FP32 cycle input and the cycle output in preconditioned slots 0 and 1.
 // The host reads the state once per outer step; the outer step's launches are replayed from a
 // captured CUDA graph after the first one.
-#include "mgh_krylov_common.cuh"
+#include "mgh_short_rec.cuh"
 
 namespace mgh {
 
@@ -63,11 +63,6 @@ __host__ __device__ __forceinline__ int slot_v(int s) { return 2 * s + 1; }
 __host__ __device__ __forceinline__ int slot_t(int s) { return 2 * s + 2; }
 enum { zIn32 = 0, zY = 1 };                       // preconditioned slots
 
-__device__ __forceinline__ cd idr_cdiv(cd a, cd b) {
-  const double d = cabs2(b);
-  return mk<double>((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
-}
-
 // Sign bits of the shadow space at point q.
 __device__ __forceinline__ uint32_t shadow_bits(size_t q) {
   uint32_t h = (uint32_t)q + 0x9E3779B9u;
@@ -95,25 +90,8 @@ __device__ __forceinline__ void shadow_dots(cd* acc, int s, uint32_t bits, cd x)
   }
 }
 
-// A x at point q of one field (FP64 operator diagonal, neighbours 0 outside the grid).
-template <typename T>
-__device__ __forceinline__ cd idr_apply_at(const Cx<T>* __restrict__ x, const cd* __restrict__ DA, size_t q, int m,
-                                           int n, const KArgs& a) {
-  cd s = czero<double>();
-  if (m > 0) s = s + ccast<double>(x[q - 1]);
-  if (m < a.nx - 1) s = s + ccast<double>(x[q + 1]);
-  if (n > 0) s = s + ccast<double>(x[q - a.nx]);
-  if (n < a.ny - 1) s = s + ccast<double>(x[q + a.nx]);
-  return DA[q] * ccast<double>(x[q]) - a.inv_h2 * s;
-}
-
 #define IDR_POINTS                                                                         \
   const size_t p0 = (size_t)blk * a.chunk, p1 = (p0 + a.chunk < a.N) ? p0 + a.chunk : a.N;
-#define IDR_GRID_POINTS                                                                    \
-  IDR_POINTS                                                                               \
-  int n = (int)((unsigned)(p0 + threadIdx.x) / (unsigned)a.nx);                            \
-  int m = (int)((unsigned)(p0 + threadIdx.x) - (unsigned)n * (unsigned)a.nx);              \
-  for (size_t q = p0 + threadIdx.x; q < p1; q += kKThreads, m += kKThreads)
 
 __device__ __forceinline__ cd* partial_of(const KArgs& a, cd* partial, int rhs, int blk) {
   return partial + ((size_t)rhs * a.nblk + blk) * a.pstride;
@@ -130,10 +108,10 @@ k_idr_init(KArgs a, IArgs ia, const cd* __restrict__ b, const cd* __restrict__ x
   cd acc[kIdrNV];
 #pragma unroll
   for (int i = 0; i < kIdrNV; ++i) acc[i] = czero<double>();
-  IDR_GRID_POINTS {
+  SR_POINT_LOOP {
     while (m >= a.nx) { m -= a.nx; ++n; }
     const cd bq = bb[q];
-    const cd rq = bq - idr_apply_at(xb, DA, q, m, n, a);
+    const cd rq = bq - apply_at(xb, DA, q, m, n, a);
     rr[q] = rq;
     for (int j = 0; j < s; ++j) {
       ia.slot(rhs, slot_g(j), a.Np)[q] = czero<double>();
@@ -183,7 +161,7 @@ __global__ void k_idr_coef(IArgs ia, const RhsState* __restrict__ st, int B, int
   for (int i = k; i < s; ++i) {
     cd t = f[i];
     for (int j = k; j < i; ++j) t = t - M[i * s + j] * c[j];
-    c[i] = idr_cdiv(t, M[i * s + i]);
+    c[i] = cdiv(t, M[i * s + i]);
   }
 }
 
@@ -254,9 +232,9 @@ k_idr_g(KArgs a, IArgs ia, const cd* __restrict__ DA, cd* __restrict__ partial, 
   cd acc[kIdrNV];
 #pragma unroll
   for (int i = 0; i < kIdrNV; ++i) acc[i] = czero<double>();
-  IDR_GRID_POINTS {
+  SR_POINT_LOOP {
     while (m >= a.nx) { m -= a.nx; ++n; }
-    const cd g = idr_apply_at(uk, DA, q, m, n, a);
+    const cd g = apply_at(uk, DA, q, m, n, a);
     gk[q] = g;
     shadow_dots(acc, s, shadow_bits(q), g);
   }
@@ -277,7 +255,7 @@ __global__ void k_idr_col(KArgs a, IArgs ia, const cd* __restrict__ partial, Rhs
   for (int i = 0; i < k; ++i) {
     cd t = sh[i];
     for (int j = 0; j < i; ++j) t = t - M[i * s + j] * al[j];
-    al[i] = idr_cdiv(t, M[i * s + i]);
+    al[i] = cdiv(t, M[i * s + i]);
   }
   for (int i = k; i < s; ++i) {
     cd t = sh[i];
@@ -286,7 +264,7 @@ __global__ void k_idr_col(KArgs a, IArgs ia, const cd* __restrict__ partial, Rhs
   }
   const cd mkk = M[k * s + k];
   if (!(cabs2(mkk) > 0.0)) { st[rhs].done = 1; st[rhs].converged = 0; st[rhs].active = 0; return; }
-  const cd beta = idr_cdiv(f[k], mkk);
+  const cd beta = cdiv(f[k], mkk);
   ia.misc(rhs)[1] = beta;
   for (int i = k + 1; i < s; ++i) f[i] = f[i] - beta * M[i * s + k];
 }
@@ -364,9 +342,9 @@ k_idr_t(KArgs a, IArgs ia, const Cx<TZ>* __restrict__ y, size_t y_stride, const 
   const cd* rr = ia.slot(rhs, sR, a.Np);
   cd* tt = ia.slot(rhs, slot_t(s), a.Np);
   cd acc[2] = {czero<double>(), czero<double>()};
-  IDR_GRID_POINTS {
+  SR_POINT_LOOP {
     while (m >= a.nx) { m -= a.nx; ++n; }
-    const cd t = idr_apply_at(yb, DA, q, m, n, a);
+    const cd t = apply_at(yb, DA, q, m, n, a);
     tt[q] = t;
     cdot_acc(acc[0], rr[q], t);
     acc[1].re += cabs2(t);
@@ -439,38 +417,6 @@ __global__ void k_idr_dr_end(KArgs a, IArgs ia, const cd* __restrict__ partial, 
   if (!S.verify && (S.iterations >= maxit || !(S.rnorm == S.rnorm))) { S.done = 1; S.converged = 0; S.active = 0; }
 }
 
-// ||b - A x||^2 of the right-hand sides awaiting the check (slot 0).
-__global__ void __launch_bounds__(kKThreads)
-k_idr_true_residual(KArgs a, const cd* __restrict__ b, const cd* __restrict__ x, const cd* __restrict__ DA,
-                    cd* __restrict__ partial, const RhsState* __restrict__ st) {
-  const int rhs = blockIdx.y, blk = blockIdx.x;
-  if (!st[rhs].active || !st[rhs].verify) return;
-  const cd* bb = b + rhs * a.N;
-  const cd* xb = x + rhs * a.N;
-  cd acc[1] = {czero<double>()};
-  IDR_GRID_POINTS {
-    while (m >= a.nx) { m -= a.nx; ++n; }
-    acc[0].re += cabs2(bb[q] - idr_apply_at(xb, DA, q, m, n, a));
-  }
-  block_reduce_store<1>(acc, 1, 0.0, 1, partial_of(a, partial, rhs, blk));
-}
-
-// Accept on the true residual, else go on from the recursive one; maxit stops.
-__global__ void k_idr_decide(KArgs a, const cd* __restrict__ partial, RhsState* __restrict__ st, int maxit,
-                             double tol) {
-  __shared__ cd sh[1];
-  const int rhs = blockIdx.x;
-  if (!st[rhs].active || !st[rhs].verify) return;
-  sum_partials(a, partial, rhs, 1, sh);
-  if (threadIdx.x != 0) return;
-  RhsState& S = st[rhs];
-  S.verify = 0;
-  S.nres += 1;
-  const double r64 = sqrt(sh[0].re);
-  if (r64 <= tol * S.bnorm) { S.done = 1; S.converged = 1; S.active = 0; S.rnorm = r64; return; }
-  if (S.iterations >= maxit) { S.done = 1; S.converged = 0; S.active = 0; S.rnorm = r64; }
-}
-
 template <typename TZ>
 mgh_status idrs_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
   KArgs a = make_kargs(h, B);
@@ -510,12 +456,12 @@ mgh_status idrs_t(Handle& h, const cd* b, int B, cd* x, mgh_solve_info* info) {
   auto check = [&]() -> mgh_status {
     {
       ProfScope ps(h, P_RESIDUAL);
-      k_idr_true_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.partial, h.st);
+      k_sr_true_residual<<<grid, kKThreads, 0, h.stream>>>(a, b, x, h.DA, h.partial, h.st);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
     {
       ProfScope ps(h, P_REDUCE);
-      k_idr_decide<<<B, 32, 0, h.stream>>>(a, h.partial, h.st, maxit, tol);
+      k_sr_decide<<<B, 32, 0, h.stream>>>(a, h.partial, h.st, tol, maxit);
       MGH_CHECK_LAUNCH(); h.launches++;
     }
     return MGH_OK;
