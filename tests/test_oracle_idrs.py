@@ -8,7 +8,10 @@ strong-scattering workload (CPU):
   or a missed biorthogonalisation step anywhere in the s = 1 path shows;
 * for s = 2, 4, 8 (random orthonormal shadow space, kappa = 0.7) the iterate reaches the sparse
   direct solution of the same system;
-* the reported residual is the true one, and a zero right-hand side returns zero at once.
+* the reported residual is the true one, and a zero right-hand side returns zero at once;
+* finite termination (the IDR theorem): on an n-dimensional system without preconditioning the
+  residual vanishes after at most n + ceil(n / s) operator products, and not three products
+  earlier, on small dense random systems.
 """
 import numpy as np
 import pytest
@@ -60,3 +63,19 @@ def test_idrs_zero_rhs_and_iteration_cap():
     assert info.converged and info.iterations == 0 and not np.any(x)
     _, info = idrs(s.apply_A, s.M, b, 1e-30, 4, 7)
     assert not info.converged and info.iterations == 7
+
+
+@pytest.mark.parametrize("n,s", [(12, 4), (12, 3), (10, 2), (9, 1)])
+def test_idrs_terminates_within_n_plus_n_over_s_products(n, s):
+    rng = np.random.default_rng(10 * n + s)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 4 * np.eye(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    bound = n + -(-n // s)
+
+    def run(maxit):
+        x, info = idrs(lambda v: A @ v, lambda v: v, b, 1e-30, s, maxit, kappa=0.0, seed=3)
+        assert info.iterations == maxit
+        return np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+
+    assert run(bound) < 1e-8          # rounding level (cond(A) up to ~40)
+    assert run(bound - 3) > 1e-5
