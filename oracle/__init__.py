@@ -9,8 +9,9 @@ to check against the paper by eye:
                  (Sec. IV-A), shifted-Laplacian operator K_kappa (Sec. IV-B)
   multigrid.py   damped Jacobi (Sec. III, eq. dampedJ), full weighting and bilinear
                  prolongation (Sec. IV-C), coarse re-discretisation, the MG cycle (Alg. 2)
-  krylov.py      right-preconditioned flexible GMRES(m) (Saad & Schultz; Saad 1993) and
-                 the paper's preconditioned Bi-CGSTAB (Alg. 3)
+  krylov.py      right-preconditioned flexible GMRES(m) (Saad & Schultz; Saad 1993), the
+                 paper's preconditioned Bi-CGSTAB (Alg. 3), its s-step, deflated-restart and
+                 IDR(s) relatives
   tomography.py  plane-wave incident field and right-hand side (Sec. II-A), truncation to
                  Omega, receiver sampling, the quadratic data term (Sec. V) and its
                  gradient through one adjoint solve per illumination (Prop. 1)

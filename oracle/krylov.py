@@ -14,6 +14,9 @@
 * fgmres_dr: flexible GMRES with deflated restarting (Morgan 2002; Giraud et al. 2010), which
   keeps k harmonic Ritz vectors across restarts: the method for problems on which ordinary
   restarts stagnate (the strong-scattering workload).
+* idrs: IDR(s) with biorthogonalisation (Sonneveld & van Gijzen 2008; van Gijzen & Sonneveld
+  2011), the short-recurrence family Alg. 3 belongs to (s = 1 with the shadow vector r_0 is
+  Bi-CGSTAB).
 
 Iterations are counted as preconditioner applications (Arnoldi steps for GMRES).
 """
